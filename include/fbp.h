@@ -1,0 +1,220 @@
+/*
+ * fbp.h -- C ABI of libfbp.so: parallel-beam filtered backprojection (FBP)
+ * on one NVIDIA GB300 GPU (sm_103a), with its matched forward projector.
+ *
+ * The operation.  FBP reconstructs each slice of a parallel-beam scan in two
+ * steps (paper Sec. IV-B; Sec. V-A(c), stage 2 "FBP Computation"): every
+ * projection row is filtered, then the filtered rows are backprojected onto
+ * the image and summed over all angles, at cost O(N_p * N_x * N_y) per slice.
+ * Each detector row maps to one independent slice (Sec. V-A(a), "Scan-rows
+ * Partition"), so a call takes a stack of per-row sinograms
+ * [n_angles, n_det] and returns one N x N slice per row.  The paper cites
+ * Kak & Slaney ch. 3 for the filter; the discrete sums implemented here are:
+ *
+ *   filter      q_k[j] = tau * sum_{m=0}^{D-1} h[j-m] p_k[m]    (linear, zero-padded)
+ *               h = band-limited Ram-Lak or Shepp-Logan kernel, tau = det_spacing
+ *   backproject f[r][c] = scale * sum_k Q_k(u_k(r,c))           (scale = dtheta for FBP)
+ *               u_k = (pixel_size/det_spacing) (X cos th_k + Y sin th_k) + det_center
+ *               X = c - (N-1)/2, Y = r - (N-1)/2, th_k = angle_start + k*angle_step
+ *               Q_k = linear interpolation of q_k, zero outside [0, D)
+ *   forward     (A f)_k[j] = sum_{r,c} f[r][c] max(0, 1 - |u_k(r,c) - j|)
+ *               (exactly the transpose of backproject with scale 1)
+ *
+ * Conventions for every call.
+ *   * Pointers to arrays are DEVICE pointers owned by the caller, unless a
+ *     parameter says "host".  The library never frees caller memory.
+ *   * Arrays are dense and row-major: sino/filt [n_slices][n_angles][n_det],
+ *     row_scale [n_slices][n_angles], slice [n_slices][n][n].
+ *   * Work is enqueued asynchronously on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream).  Argument validation is synchronous: a call that
+ *     returns an error other than FBP_ERR_CUDA has enqueued nothing.
+ *   * No C++ exception crosses this boundary.  fbp_last_error_message()
+ *     gives a human-readable reason for the calling thread's last error.
+ *   * Constant tables (the FP64 angle table, the filter spectrum and the FFT
+ *     twiddles) are built on the device in double precision the first time a
+ *     geometry is seen on a device, and cached by the library until
+ *     fbp_release_tables() or process exit.  That first call allocates device
+ *     memory and must not happen inside CUDA stream capture (it returns
+ *     FBP_ERR_UNSUPPORTED there); later calls with the same geometry allocate
+ *     nothing and may be captured.
+ *   * Limits: 1 <= n_det <= 8192 for filtering; n_angles >= 1; n >= 1;
+ *     pixel_size/det_spacing in [1/8, 2.5] for backprojection and projection.
+ */
+#ifndef FBP_H
+#define FBP_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+struct CUstream_st;
+/* Same type as cudaStream_t. */
+typedef struct CUstream_st *fbp_stream_t;
+
+typedef enum {
+    FBP_OK = 0,
+    FBP_ERR_INVALID_ARG = -1,   /* NULL pointer, bad size, bad enum, bad geometry */
+    FBP_ERR_UNSUPPORTED = -2,   /* valid but outside the limits above, or table
+                                   creation requested during stream capture */
+    FBP_ERR_WORKSPACE = -3,     /* workspace NULL, too small or misaligned */
+    FBP_ERR_CUDA = -4,          /* a CUDA runtime call or launch failed */
+    FBP_ERR_DEVICE_STATUS = -5  /* a kernel reported a fault through the
+                                   device status word (see below) */
+} fbp_status;
+
+typedef enum {
+    FBP_FILTER_RAMLAK = 0,      /* h(0)=1/(4 tau^2), h(odd n)=-1/(pi^2 n^2 tau^2), 0 else */
+    FBP_FILTER_SHEPP_LOGAN = 1  /* h(n) = -2 / (pi^2 tau^2 (4 n^2 - 1))                    */
+} fbp_filter_kind;
+
+typedef enum {
+    FBP_F32 = 0,                /* filtered rows stored as float                      */
+    FBP_F16 = 1,                /* as IEEE half, q / s_k rounded to nearest even       */
+    FBP_BF16 = 2                /* as bfloat16, q / s_k rounded to nearest even        */
+} fbp_dtype;
+
+/* Geometry of one slice (paper Table I: N_p = n_angles, N_c = n_det,
+ * N_x = N_y = n).  Angles and det_center are doubles: at n = 8192 the
+ * detector coordinate needs more than float precision. */
+typedef struct {
+    int n_angles;        /* K >= 1                                          */
+    int n_det;           /* D >= 1                                          */
+    int n;               /* output slice is n x n, n >= 1                   */
+    double angle_start;  /* theta_0, radians                                */
+    double angle_step;   /* dtheta, radians (pi/K for a half turn)          */
+    double det_center;   /* bin coordinate of the rotation axis ((D-1)/2)   */
+    double det_spacing;  /* tau: bin width, > 0 (1)                          */
+    double pixel_size;   /* pixel width, same unit as det_spacing, > 0 (1)  */
+} fbp_geometry;
+
+/* One slice of a ragged batch: its own sinogram [n_angles][n_det] (device,
+ * float), its own output [n][n] (device, float) and its own geometry. */
+typedef struct {
+    const float *sino;
+    float *slice;
+    fbp_geometry g;
+} fbp_batch_item;
+
+/* Tile shape of one compiled backprojection variant. */
+typedef struct {
+    int angle_tile;      /* angles staged in shared memory per pass         */
+    int tile_x, tile_y;  /* output pixels per thread block                  */
+    int px, py;          /* output pixels per thread (x, y)                 */
+    int threads;         /* threads per block                               */
+} fbp_bp_shape;
+
+/* Library version (major*10000 + minor*100 + patch). */
+int fbp_version(void);
+
+/* Geometry with the defaults: angles k*pi/K on [0, pi), det_center (D-1)/2,
+ * det_spacing 1, pixel_size 1. */
+fbp_geometry fbp_geometry_default(int n_angles, int n_det, int n);
+
+/* Short name of a status code (static string, never NULL). */
+const char *fbp_status_string(fbp_status s);
+
+/* Reason for the calling thread's most recent non-OK status ("" if none). */
+const char *fbp_last_error_message(void);
+
+/*
+ * fbp_filter -- the filtering step (Sec. V-A(c) stage 2, "filtering").
+ *   sino       device, float [n_slices][K][D]: line integrals p_k[m].
+ *   filt       device, [n_slices][K][D] of `dtype`: receives q_k[j]
+ *              (F32), or RNE(q_k[j] / s_k) (F16/BF16).  May not alias sino.
+ *   row_scale  device, float [n_slices][K]: receives s_k = max_j |q_k[j]|
+ *              (1 where the row is all zero).  Required for F16/BF16,
+ *              ignored (may be NULL) for F32.
+ *   kind       filter kernel; g->det_spacing is tau.
+ *   n_slices   >= 0 slices sharing geometry g (0 enqueues nothing).
+ * The convolution is computed in FP32 as a length-L FFT, L the smallest
+ * power of two >= max(512, 2D-1), with the spectrum of the truncated FP64
+ * kernel; it equals the linear convolution over the D detector samples.
+ */
+fbp_status fbp_filter(const float *sino, void *filt, float *row_scale,
+                      fbp_dtype dtype, fbp_filter_kind kind,
+                      const fbp_geometry *g, int n_slices, fbp_stream_t stream);
+
+/*
+ * fbp_backproject -- the backprojection step (Sec. V-A(c) stage 2,
+ * "back-projection computation O(N_p N_x N_y N_z)").
+ *   filt       device, [n_slices][K][D] of `dtype` (as written by fbp_filter).
+ *   row_scale  device, float [n_slices][K] for F16/BF16 (NULL for F32):
+ *              each row is multiplied by s_k before interpolation.
+ *   slice      device, float [n_slices][n][n]: receives scale * sum_k Q_k,
+ *              or has it added when `accumulate` is nonzero.
+ *   scale      angle_step for FBP; 1 for the transpose of radon_forward.
+ * Every pixel of the n x n square is computed.  Accumulation is FP32; the
+ * per-(tile, angle) base coordinate is formed in FP64.
+ */
+fbp_status fbp_backproject(const void *filt, const float *row_scale,
+                           fbp_dtype dtype, float *slice, const fbp_geometry *g,
+                           int n_slices, float scale, int accumulate,
+                           fbp_stream_t stream);
+
+/* fbp_backproject with an explicit compiled tile variant
+ * (0 <= variant < fbp_bp_variant_count(); -1 = the library's default). */
+fbp_status fbp_backproject_variant(const void *filt, const float *row_scale,
+                                   fbp_dtype dtype, float *slice,
+                                   const fbp_geometry *g, int n_slices,
+                                   float scale, int accumulate, int variant,
+                                   fbp_stream_t stream);
+
+/*
+ * radon_forward -- the matched forward projector A (the adjoint of
+ * fbp_backproject with scale 1; the paper's data generation uses a forward
+ * model, Sec. V-B(a)).
+ *   slice  device, float [n_slices][n][n].
+ *   sino   device, float [n_slices][K][D]: receives A f (overwritten).
+ * Gather form (one output bin per thread), deterministic, no atomics.
+ */
+fbp_status radon_forward(const float *slice, float *sino, const fbp_geometry *g,
+                         int n_slices, fbp_stream_t stream);
+
+/* Number of compiled backprojection tile variants, and the shape of one. */
+int fbp_bp_variant_count(void);
+fbp_status fbp_bp_variant_info(int variant, fbp_bp_shape *out);
+
+/*
+ * Ragged batches (Sec. V-A(b): specimens with various N_p and N_c
+ * reconstructed together).  One persistent filter launch and one persistent
+ * backprojection launch cover every item; items may differ in K, D, n and
+ * geometry.
+ *   items      HOST array of `count` items (1 <= count <= 256); each item's
+ *              sino/slice are device pointers as above.  n_det <= 8192.
+ *   workspace  device, >= fbp_batched_workspace_bytes(items, count, dtype)
+ *              bytes, 256-byte aligned, owned by the caller.  It holds the
+ *              filtered rows of every item and the work-queue counter.
+ *   bp_variant tile variant for backprojection, -1 = default.
+ * The call captures into a CUDA graph once each item's geometry has been
+ * seen by the library (tables exist).
+ */
+size_t fbp_batched_workspace_bytes(const fbp_batch_item *items, int count,
+                                   fbp_dtype dtype);
+fbp_status fbp_batched(const fbp_batch_item *items, int count,
+                       fbp_filter_kind kind, fbp_dtype dtype, int bp_variant,
+                       void *workspace, size_t ws_bytes, fbp_stream_t stream);
+
+/*
+ * Device status word.  Kernels never trap: a kernel that detects a fault
+ * (a work-queue loop past its iteration cap, or -- in the checked build --
+ * an out-of-range table index) records a nonzero code in a device word and
+ * returns.  This call synchronises `stream`, reads and clears the word, and
+ * returns FBP_OK or FBP_ERR_DEVICE_STATUS (code in *code if non-NULL).
+ */
+fbp_status fbp_last_device_status(fbp_stream_t stream, int *code);
+
+/* Build the constant tables for geometry g on the current device (the same
+ * work the first fbp_* call for g does), so that later calls can be captured
+ * in a CUDA graph.  kind < 0 skips the filter tables. */
+fbp_status fbp_prepare(const fbp_geometry *g, int kind, fbp_stream_t stream);
+
+/* Free every cached table on every device (synchronises those devices). */
+void fbp_release_tables(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* FBP_H */

@@ -1,0 +1,114 @@
+"""ctypes declarations for libfbp.so (the C ABI in include/fbp.h).
+
+Argument marshalling only.  If the library has not been built this module
+raises on first use: there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_NAMES = {"default": "libfbp.so", "checked": "libfbp_checked.so"}
+
+FBP_OK = 0
+FBP_ERR_INVALID_ARG = -1
+FBP_ERR_UNSUPPORTED = -2
+FBP_ERR_WORKSPACE = -3
+FBP_ERR_CUDA = -4
+FBP_ERR_DEVICE_STATUS = -5
+
+FBP_FILTER_RAMLAK = 0
+FBP_FILTER_SHEPP_LOGAN = 1
+
+FBP_F32 = 0
+FBP_F16 = 1
+FBP_BF16 = 2
+
+# Every function include/fbp.h declares, with (restype, argtypes).
+_vp = ctypes.c_void_p
+
+
+class CGeometry(ctypes.Structure):
+    _fields_ = [
+        ("n_angles", ctypes.c_int),
+        ("n_det", ctypes.c_int),
+        ("n", ctypes.c_int),
+        ("angle_start", ctypes.c_double),
+        ("angle_step", ctypes.c_double),
+        ("det_center", ctypes.c_double),
+        ("det_spacing", ctypes.c_double),
+        ("pixel_size", ctypes.c_double),
+    ]
+
+
+class CBatchItem(ctypes.Structure):
+    _fields_ = [("sino", _vp), ("slice", _vp), ("g", CGeometry)]
+
+
+class CBpShape(ctypes.Structure):
+    _fields_ = [("angle_tile", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
+                ("px", ctypes.c_int), ("py", ctypes.c_int), ("threads", ctypes.c_int)]
+
+
+_G = ctypes.POINTER(CGeometry)
+SIGNATURES = {
+    "fbp_version": (ctypes.c_int, []),
+    "fbp_geometry_default": (CGeometry, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "fbp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "fbp_last_error_message": (ctypes.c_char_p, []),
+    "fbp_filter": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _G, ctypes.c_int, _vp]),
+    "fbp_backproject": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int, ctypes.c_float,
+                                       ctypes.c_int, _vp]),
+    "fbp_backproject_variant": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int,
+                                               ctypes.c_float, ctypes.c_int, ctypes.c_int, _vp]),
+    "radon_forward": (ctypes.c_int, [_vp, _vp, _G, ctypes.c_int, _vp]),
+    "fbp_bp_variant_count": (ctypes.c_int, []),
+    "fbp_bp_variant_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(CBpShape)]),
+    "fbp_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(CBatchItem), ctypes.c_int,
+                                                      ctypes.c_int]),
+    "fbp_batched": (ctypes.c_int, [ctypes.POINTER(CBatchItem), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                   ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "fbp_last_device_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
+    "fbp_prepare": (ctypes.c_int, [_G, ctypes.c_int, _vp]),
+    "fbp_release_tables": (None, []),
+}
+
+_libs: dict[str, ctypes.CDLL] = {}
+
+
+class FbpError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        self.status = status
+        super().__init__(message)
+
+
+def lib_path(which: str = "default") -> str:
+    return os.path.join(HERE, LIB_NAMES[which])
+
+
+def load(which: str = "default") -> ctypes.CDLL:
+    """Load libfbp.so (or the bounds-checked build); raises if it is missing."""
+    L = _libs.get(which)
+    if L is not None:
+        return L
+    path = lib_path(which)
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"{os.path.basename(path)} is not built; build it with "
+            "`python -c \"import __graft_entry__ as g; g.build()\"` "
+            "(there is no CPU fallback)")
+    L = ctypes.CDLL(path)
+    for name, (res, args) in SIGNATURES.items():
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _libs[which] = L
+    return L
+
+
+def check(status: int, lib: ctypes.CDLL, what: str) -> None:
+    if status != FBP_OK:
+        name = lib.fbp_status_string(status).decode()
+        msg = lib.fbp_last_error_message().decode()
+        raise FbpError(status, f"{what}: {name}: {msg}")

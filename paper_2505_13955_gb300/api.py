@@ -1,0 +1,306 @@
+"""Python binding of libfbp.so: same names as the C ABI, torch tensors in/out.
+
+PyTorch provides device memory and streams; every step of the computation
+runs in the library's CUDA kernels.  Tensors must be contiguous CUDA tensors
+of the stated dtypes; results are enqueued on the current torch stream.
+
+  filter(sino, g)            -> fbp_filter       (K1, FFT ramp filter)
+  backproject(filt, g)       -> fbp_backproject  (K2, pixel-driven, linear interp.)
+  radon_forward(img, g)      -> radon_forward    (K3, matched forward projector)
+  fbp(sino, g)               -> fbp_filter + fbp_backproject
+  fbp_batched(sinos, gs)     -> fbp_batched      (ragged batch, persistent launch)
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass
+
+import torch
+
+from . import _lib
+
+_DTYPES = {torch.float32: _lib.FBP_F32, torch.float16: _lib.FBP_F16, torch.bfloat16: _lib.FBP_BF16}
+_KINDS = {"ramlak": _lib.FBP_FILTER_RAMLAK, "ram-lak": _lib.FBP_FILTER_RAMLAK,
+          "shepp_logan": _lib.FBP_FILTER_SHEPP_LOGAN, "shepp-logan": _lib.FBP_FILTER_SHEPP_LOGAN}
+
+FbpError = _lib.FbpError
+
+
+@dataclass
+class Geometry:
+    """Parallel-beam geometry of a slice (mirrors ``fbp_geometry``).
+
+    Angles th_k = angle_start + k * angle_step (default k*pi/K on [0, pi)),
+    detector centre det_center (default (D-1)/2), bin width det_spacing,
+    pixel width pixel_size.  Pixel [r][c] sits at X = c-(n-1)/2, Y = r-(n-1)/2.
+    """
+    n_angles: int
+    n_det: int
+    n: int
+    angle_start: float = 0.0
+    angle_step: float | None = None
+    det_center: float | None = None
+    det_spacing: float = 1.0
+    pixel_size: float = 1.0
+
+    def __post_init__(self):
+        if self.angle_step is None:
+            self.angle_step = math.pi / self.n_angles if self.n_angles > 0 else 0.0
+        if self.det_center is None:
+            self.det_center = 0.5 * (self.n_det - 1)
+
+    def c(self) -> _lib.CGeometry:
+        return _lib.CGeometry(int(self.n_angles), int(self.n_det), int(self.n),
+                              float(self.angle_start), float(self.angle_step),
+                              float(self.det_center), float(self.det_spacing),
+                              float(self.pixel_size))
+
+
+def lib(which: str = "default"):
+    return _lib.load(which)
+
+
+def _stream(device) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _ptr(t: torch.Tensor | None) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr() if t is not None else None)
+
+
+def _need(t: torch.Tensor, name: str, dtype=None):
+    if not isinstance(t, torch.Tensor):
+        raise TypeError(f"{name} must be a torch.Tensor")
+    if not t.is_cuda:
+        raise ValueError(f"{name} must be a CUDA tensor (there is no CPU path)")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"{name} must have dtype {dtype}, got {t.dtype}")
+
+
+def _slices(t: torch.Tensor, tail: tuple[int, ...], name: str) -> int:
+    if t.dim() == len(tail):
+        if tuple(t.shape) != tail:
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tail}")
+        return 1
+    if t.dim() == len(tail) + 1 and tuple(t.shape[1:]) == tail:
+        return int(t.shape[0])
+    raise ValueError(f"{name} has shape {tuple(t.shape)}, expected [S, {', '.join(map(str, tail))}]")
+
+
+def kind_id(kind) -> int:
+    if isinstance(kind, int):
+        return kind
+    return _KINDS[kind.lower()]
+
+
+def filter(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
+           out: torch.Tensor | None = None, row_scale: torch.Tensor | None = None,
+           which: str = "default"):
+    """fbp_filter: ramp-filter every row.  Returns (filt, row_scale or None)."""
+    _need(sino, "sino", torch.float32)
+    S = _slices(sino, (g.n_angles, g.n_det), "sino")
+    if out is None:
+        out = torch.empty(sino.shape, dtype=dtype, device=sino.device)
+    _need(out, "out", dtype)
+    if dtype != torch.float32 and row_scale is None:
+        row_scale = torch.empty(sino.shape[:-1], dtype=torch.float32, device=sino.device)
+    L = lib(which)
+    gc = g.c()
+    st = L.fbp_filter(_ptr(sino), _ptr(out), _ptr(row_scale), _DTYPES[dtype], kind_id(kind),
+                      ctypes.byref(gc), S, _stream(sino.device))
+    _lib.check(st, L, "fbp_filter")
+    return out, (row_scale if dtype != torch.float32 else None)
+
+
+def backproject(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None = None,
+                scale: float | None = None, out: torch.Tensor | None = None,
+                accumulate: bool = False, variant: int = -1, which: str = "default"):
+    """fbp_backproject: f = scale * sum_k Q_k(u_k) (scale defaults to angle_step)."""
+    _need(filt, "filt")
+    if filt.dtype not in _DTYPES:
+        raise ValueError(f"unsupported filt dtype {filt.dtype}")
+    S = _slices(filt, (g.n_angles, g.n_det), "filt")
+    shape = (g.n, g.n) if filt.dim() == 2 else (S, g.n, g.n)
+    if out is None:
+        out = (torch.zeros if accumulate else torch.empty)(shape, dtype=torch.float32,
+                                                           device=filt.device)
+    _need(out, "out", torch.float32)
+    if tuple(out.shape) != shape:
+        raise ValueError(f"out has shape {tuple(out.shape)}, expected {shape}")
+    if row_scale is not None:
+        _need(row_scale, "row_scale", torch.float32)
+    if scale is None:
+        scale = g.angle_step
+    L = lib(which)
+    gc = g.c()
+    st = L.fbp_backproject_variant(_ptr(filt), _ptr(row_scale), _DTYPES[filt.dtype], _ptr(out),
+                                   ctypes.byref(gc), S, float(scale), int(bool(accumulate)),
+                                   int(variant), _stream(filt.device))
+    _lib.check(st, L, "fbp_backproject")
+    return out
+
+
+def radon_forward(img: torch.Tensor, g: Geometry, out: torch.Tensor | None = None,
+                  which: str = "default"):
+    """radon_forward: the matched projector A (transpose of backproject, scale 1)."""
+    _need(img, "slice", torch.float32)
+    S = _slices(img, (g.n, g.n), "slice")
+    shape = (g.n_angles, g.n_det) if img.dim() == 2 else (S, g.n_angles, g.n_det)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=img.device)
+    _need(out, "out", torch.float32)
+    L = lib(which)
+    gc = g.c()
+    st = L.radon_forward(_ptr(img), _ptr(out), ctypes.byref(gc), S, _stream(img.device))
+    _lib.check(st, L, "radon_forward")
+    return out
+
+
+def fbp(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
+        out: torch.Tensor | None = None, variant: int = -1):
+    """Filtered backprojection: fbp_filter then fbp_backproject (scale = angle_step)."""
+    filt, rs = filter(sino, g, kind=kind, dtype=dtype)
+    return backproject(filt, g, row_scale=rs, out=out, variant=variant)
+
+
+def bp_variants() -> list[dict]:
+    L = lib()
+    out = []
+    for v in range(L.fbp_bp_variant_count()):
+        s = _lib.CBpShape()
+        _lib.check(L.fbp_bp_variant_info(v, ctypes.byref(s)), L, "fbp_bp_variant_info")
+        out.append({"variant": v, "angle_tile": s.angle_tile, "tile_x": s.tile_x,
+                    "tile_y": s.tile_y, "px": s.px, "py": s.py, "threads": s.threads})
+    return out
+
+
+def _items(sinos, outs, geoms):
+    arr = (_lib.CBatchItem * len(sinos))()
+    for i, (s, o, g) in enumerate(zip(sinos, outs, geoms)):
+        arr[i].sino = s.data_ptr()
+        arr[i].slice = o.data_ptr()
+        arr[i].g = g.c()
+    return arr
+
+
+def batched_workspace_bytes(sinos, outs, geoms, dtype=torch.float32) -> int:
+    L = lib()
+    n = L.fbp_batched_workspace_bytes(_items(sinos, outs, geoms), len(sinos), _DTYPES[dtype])
+    if n == 0:
+        raise FbpError(_lib.FBP_ERR_INVALID_ARG,
+                       "fbp_batched_workspace_bytes: " + L.fbp_last_error_message().decode())
+    return int(n)
+
+
+def fbp_batched(sinos: list, geoms: list, kind="ramlak", dtype=torch.float32, variant: int = -1,
+                outs: list | None = None, workspace: torch.Tensor | None = None):
+    """fbp_batched: ragged batch of slices in one filter launch and one
+    persistent backprojection launch.  Returns the list of output slices."""
+    if len(sinos) != len(geoms):
+        raise ValueError("sinos and geoms differ in length")
+    for i, (s, g) in enumerate(zip(sinos, geoms)):
+        _need(s, f"sinos[{i}]", torch.float32)
+        _slices(s, (g.n_angles, g.n_det), f"sinos[{i}]")
+    dev = sinos[0].device
+    if outs is None:
+        outs = [torch.empty((g.n, g.n), dtype=torch.float32, device=dev) for g in geoms]
+    items = _items(sinos, outs, geoms)
+    L = lib()
+    need = L.fbp_batched_workspace_bytes(items, len(sinos), _DTYPES[dtype])
+    if need == 0:
+        raise FbpError(_lib.FBP_ERR_INVALID_ARG, "fbp_batched: " + L.fbp_last_error_message().decode())
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    st = L.fbp_batched(items, len(sinos), kind_id(kind), _DTYPES[dtype], int(variant),
+                       _ptr(workspace), workspace.numel(), _stream(dev))
+    _lib.check(st, L, "fbp_batched")
+    return outs
+
+
+def prepare(g: Geometry, kind="ramlak", device=None):
+    """Build the geometry's constant tables now (before CUDA graph capture)."""
+    L = lib()
+    gc = g.c()
+    k = -1 if kind is None else kind_id(kind)
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    _lib.check(L.fbp_prepare(ctypes.byref(gc), k, _stream(dev)), L, "fbp_prepare")
+
+
+def device_status(which: str = "default", device=None) -> int:
+    """Synchronise, read and clear the device status word (0 = no fault)."""
+    L = lib(which)
+    code = ctypes.c_int(0)
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    st = L.fbp_last_device_status(_stream(dev), ctypes.byref(code))
+    if st not in (_lib.FBP_OK, _lib.FBP_ERR_DEVICE_STATUS):
+        _lib.check(st, L, "fbp_last_device_status")
+    return int(code.value)
+
+
+def release_tables():
+    lib().fbp_release_tables()
+
+
+# ---------------------------------------------------------------------------
+# Differentiation: A and A^T as a torch.autograd.Function pair.
+# ---------------------------------------------------------------------------
+class RadonForward(torch.autograd.Function):
+    """y = A x (radon_forward); the gradient is A^T (fbp_backproject, scale 1)."""
+
+    @staticmethod
+    def forward(ctx, x: torch.Tensor, g: Geometry):
+        ctx.g = g
+        return radon_forward(x.contiguous(), g)
+
+    @staticmethod
+    def backward(ctx, gy: torch.Tensor):
+        return backproject(gy.contiguous(), ctx.g, scale=1.0), None
+
+
+class RadonBackproject(torch.autograd.Function):
+    """x = A^T y (fbp_backproject, scale 1); the gradient is A (radon_forward)."""
+
+    @staticmethod
+    def forward(ctx, y: torch.Tensor, g: Geometry):
+        ctx.g = g
+        return backproject(y.contiguous(), g, scale=1.0)
+
+    @staticmethod
+    def backward(ctx, gx: torch.Tensor):
+        return radon_forward(gx.contiguous(), ctx.g), None
+
+
+def radon(x: torch.Tensor, g: Geometry) -> torch.Tensor:
+    """Differentiable A x."""
+    return RadonForward.apply(x, g)
+
+
+def radon_t(y: torch.Tensor, g: Geometry) -> torch.Tensor:
+    """Differentiable A^T y."""
+    return RadonBackproject.apply(y, g)
+
+
+def lsq_refine(x0: torch.Tensor, b: torch.Tensor, g: Geometry, eta: float, iters: int,
+               return_losses: bool = True):
+    """Gradient-descent least-squares refinement min 0.5 ||A x - b||^2 on the
+    device: x <- x - eta * grad, the gradient taken by autograd through
+    RadonForward (so it is A^T (A x - b), computed by the library's kernels).
+    Returns (x, losses); the loss before each step is kept on the device and
+    copied once at the end."""
+    x = x0.detach().clone().requires_grad_(True)
+    losses = []
+    for _ in range(iters):
+        r = radon(x, g) - b
+        loss = 0.5 * (r.double() * r.double()).sum()
+        (gx,) = torch.autograd.grad(loss, x)
+        losses.append(loss.detach())
+        with torch.no_grad():
+            x -= eta * gx.float()
+    with torch.no_grad():
+        r = radon_forward(x.detach(), g) - b
+        losses.append(0.5 * (r.double() * r.double()).sum())
+    out = [float(v) for v in torch.stack(losses).cpu()] if return_losses else None
+    return x.detach(), out

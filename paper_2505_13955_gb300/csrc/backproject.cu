@@ -1,0 +1,276 @@
+// backproject.cu -- launches of the backprojection tile routine (bp_tile.cuh):
+// a uniform grid over (tile, slice) for fbp_backproject, and a persistent
+// work-queue kernel for ragged batches.
+#include <algorithm>
+#include <climits>
+#include <map>
+#include <mutex>
+
+#include "bp_tile.cuh"
+#include "bp_batch.cuh"
+
+namespace fbp {
+namespace {
+
+// Compiled tile shapes: threads TXT x TYT, pixels per thread PX x PY,
+// angles per staged tile KT.
+struct ShapeDesc {
+    int txt, tyt, px, py, kt;
+};
+constexpr ShapeDesc kShapes[] = {
+    {16, 16, 4, 4, 32},   // 0: 64 x 64 tile
+    {16, 16, 4, 4, 16},   // 1
+    {16, 16, 4, 2, 32},   // 2: 64 x 32
+    {16, 16, 2, 4, 32},   // 3: 32 x 64
+    {16, 16, 4, 4, 64},   // 4
+    {32, 8, 2, 8, 32},    // 5: 64 x 64, warps 4 x 2
+};
+constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
+
+struct BpArgs {
+    const void *filt;
+    const float *row_scale;
+    float *slice;
+    const double2 *cs;
+    int K, D, N;
+    double alpha, det_center;
+    float scale;
+    int accumulate;
+    int H, W;
+    int tiles_x;
+    int slice_base;
+    unsigned *status;
+};
+
+template <int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED>
+__global__ void __launch_bounds__(TXT *TYT) bp_kernel(BpArgs a)
+{
+    extern __shared__ __align__(16) unsigned char bp_smem[];
+    constexpr int TW = TXT * PX, TH = TYT * PY;
+    const int tile = blockIdx.x;
+    const int sl = a.slice_base + blockIdx.y;
+    BpTileJob j;
+    const size_t kd = (size_t)a.K * a.D;
+    j.filt = static_cast<const char *>(a.filt) + (size_t)sl * kd * sizeof(T);
+    j.row_scale = a.row_scale ? a.row_scale + (size_t)sl * a.K : nullptr;
+    j.out = a.slice + (size_t)sl * a.N * a.N;
+    j.cs = a.cs;
+    j.K = a.K;
+    j.D = a.D;
+    j.N = a.N;
+    j.alpha = a.alpha;
+    j.det_center = a.det_center;
+    j.scale = a.scale;
+    j.accumulate = a.accumulate;
+    j.H = a.H;
+    j.W = a.W;
+    j.x0 = (tile % a.tiles_x) * TW;
+    j.y0 = (tile / a.tiles_x) * TH;
+    j.status = a.status;
+    bp_tile<TXT, TYT, PX, PY, KT, T, CHECKED>(j, bp_smem);
+}
+
+template <int V, typename T>
+fbp_status launch_shape(const BpLaunch &L, cudaStream_t s, unsigned *status)
+{
+    constexpr ShapeDesc sd = kShapes[V];
+    constexpr int TW = sd.txt * sd.px, TH = sd.tyt * sd.py;
+#ifdef FBP_CHECKED
+    constexpr bool kChecked = true;
+#else
+    constexpr bool kChecked = false;
+#endif
+    auto kern = bp_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, T, kChecked>;
+    BpArgs a;
+    a.filt = L.filt;
+    a.row_scale = L.row_scale;
+    a.slice = L.slice;
+    a.cs = L.cs;
+    a.K = L.K;
+    a.D = L.D;
+    a.N = L.N;
+    a.alpha = L.alpha;
+    a.det_center = L.det_center;
+    a.scale = L.scale;
+    a.accumulate = L.accumulate;
+    a.H = bp_window_half(L.alpha, TW, TH);
+    a.W = 2 * a.H + 1;
+    a.status = status;
+    const size_t smem = bp_smem_size<sd.kt>(a.W);
+    if (smem > 200 * 1024) return fail(FBP_ERR_UNSUPPORTED, "backprojection window too wide");
+    fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
+    if (st != FBP_OK) return st;
+    a.tiles_x = (L.N + TW - 1) / TW;
+    const long long tiles = (long long)a.tiles_x * ((L.N + TH - 1) / TH);
+    if (tiles > INT_MAX) return fail(FBP_ERR_UNSUPPORTED, "too many tiles");
+    for (int base = 0; base < L.S; base += 65535) {
+        a.slice_base = base;
+        dim3 grid((unsigned)tiles, (unsigned)std::min(65535, L.S - base));
+        kern<<<grid, sd.txt * sd.tyt, smem, s>>>(a);
+        FBP_CUDA_TRY(cudaGetLastError());
+    }
+    return FBP_OK;
+}
+
+template <typename T>
+fbp_status launch_variant(const BpLaunch &L, int v, cudaStream_t s, unsigned *status)
+{
+    switch (v) {
+        case 0: return launch_shape<0, T>(L, s, status);
+        case 1: return launch_shape<1, T>(L, s, status);
+        case 2: return launch_shape<2, T>(L, s, status);
+        case 3: return launch_shape<3, T>(L, s, status);
+        case 4: return launch_shape<4, T>(L, s, status);
+        case 5: return launch_shape<5, T>(L, s, status);
+    }
+    return fail(FBP_ERR_INVALID_ARG, "backprojection variant %d", v);
+}
+
+// ---------------------------------------------------------------------------
+// Persistent ragged-batch kernel: blocks pull (item, tile) units from a
+// global counter until the queue is empty.  Items arrive sorted by angle
+// count, largest first, so the heaviest tiles are handed out first.  The
+// loop is capped at total+1 iterations per block; past the cap it records
+// FAULT_QUEUE_CAP and exits (it cannot wait on anything).
+// ---------------------------------------------------------------------------
+template <int TXT, int TYT, int PX, int PY, int KT, typename T>
+__global__ void __launch_bounds__(TXT *TYT) bp_persistent_kernel(BpBatchArgs a)
+{
+    extern __shared__ __align__(16) unsigned char bp_smem[];
+    __shared__ int s_unit;
+    constexpr int TW = TXT * PX, TH = TYT * PY;
+    for (int iter = 0;; ++iter) {
+        if (threadIdx.x == 0) s_unit = atomicAdd(a.counter, 1);
+        __syncthreads();
+        const int u = s_unit;
+        __syncthreads();
+        if (u >= a.total_units) break;
+        if (iter > a.total_units) {
+            if (threadIdx.x == 0) atomicCAS(a.status, 0u, (unsigned)FAULT_QUEUE_CAP);
+            break;
+        }
+        // item owning unit u (unit_begin is ascending)
+        int lo = 0, hi = a.count - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (a.items[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+        }
+        const BpBatchItem &it = a.items[lo];
+        const int t = u - it.unit_begin;
+        BpTileJob j;
+        j.filt = it.filt;
+        j.row_scale = it.row_scale;
+        j.out = it.slice;
+        j.cs = it.cs;
+        j.K = it.K;
+        j.D = it.D;
+        j.N = it.N;
+        j.alpha = it.alpha;
+        j.det_center = it.det_center;
+        j.scale = it.scale;
+        j.accumulate = 0;
+        j.H = it.H;
+        j.W = 2 * it.H + 1;
+        j.x0 = (t % it.tiles_x) * TW;
+        j.y0 = (t / it.tiles_x) * TH;
+        j.status = a.status;
+        bp_tile<TXT, TYT, PX, PY, KT, T, false>(j, bp_smem);
+    }
+}
+
+template <int V, typename T>
+fbp_status launch_persistent_shape(BpBatchArgs &a, int sms, cudaStream_t s)
+{
+    constexpr ShapeDesc sd = kShapes[V];
+    auto kern = bp_persistent_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, T>;
+    const size_t smem = bp_smem_size<sd.kt>(2 * a.max_H + 1);
+    if (smem > 200 * 1024) return fail(FBP_ERR_UNSUPPORTED, "backprojection window too wide");
+    fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
+    if (st != FBP_OK) return st;
+    int per_sm = 0;
+    st = blocks_per_sm(reinterpret_cast<const void *>(kern), sd.txt * sd.tyt, smem, &per_sm);
+    if (st != FBP_OK) return st;
+    if (per_sm < 1) return fail(FBP_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
+    const int grid = std::max(1, std::min(sms * per_sm, a.total_units));
+    kern<<<grid, sd.txt * sd.tyt, smem, s>>>(a);
+    FBP_CUDA_TRY(cudaGetLastError());
+    return FBP_OK;
+}
+
+template <typename T>
+fbp_status launch_persistent_t(BpBatchArgs &a, int v, int sms, cudaStream_t s)
+{
+    switch (v) {
+        case 0: return launch_persistent_shape<0, T>(a, sms, s);
+        case 1: return launch_persistent_shape<1, T>(a, sms, s);
+        case 2: return launch_persistent_shape<2, T>(a, sms, s);
+        case 3: return launch_persistent_shape<3, T>(a, sms, s);
+        case 4: return launch_persistent_shape<4, T>(a, sms, s);
+        case 5: return launch_persistent_shape<5, T>(a, sms, s);
+    }
+    return fail(FBP_ERR_INVALID_ARG, "backprojection variant %d", v);
+}
+
+}  // namespace
+
+int bp_variant_count() { return kNumShapes; }
+
+bool bp_variant_shape(int v, fbp_bp_shape *out)
+{
+    if (v < 0 || v >= kNumShapes || !out) return false;
+    const ShapeDesc &d = kShapes[v];
+    out->angle_tile = d.kt;
+    out->tile_x = d.txt * d.px;
+    out->tile_y = d.tyt * d.py;
+    out->px = d.px;
+    out->py = d.py;
+    out->threads = d.txt * d.tyt;
+    return true;
+}
+
+int bp_tile_w(int v) { return kShapes[v].txt * kShapes[v].px; }
+int bp_tile_h(int v) { return kShapes[v].tyt * kShapes[v].py; }
+
+int bp_default_variant(const BpLaunch &) { return 0; }
+
+fbp_status launch_backproject(const BpLaunch &L, int variant, cudaStream_t s)
+{
+    if (L.S <= 0) return FBP_OK;
+    if (variant < 0) variant = bp_default_variant(L);
+    unsigned *status = nullptr;
+    fbp_status st = device_status_word(&status);
+    if (st != FBP_OK) return st;
+    switch (L.dtype) {
+        case FBP_F32: return launch_variant<float>(L, variant, s, status);
+        case FBP_F16: return launch_variant<__half>(L, variant, s, status);
+        case FBP_BF16: return launch_variant<__nv_bfloat16>(L, variant, s, status);
+    }
+    return fail(FBP_ERR_INVALID_ARG, "dtype");
+}
+
+fbp_status launch_bp_persistent(BpBatchArgs &a, int variant, fbp_dtype dtype, cudaStream_t s)
+{
+    if (variant < 0) variant = 0;
+    int dev = 0;
+    FBP_CUDA_TRY(cudaGetDevice(&dev));
+    static std::mutex mu;
+    static std::map<int, int> sm_count;
+    int sms = 0;
+    {
+        std::lock_guard<std::mutex> lock(mu);
+        auto it = sm_count.find(dev);
+        if (it == sm_count.end()) {
+            FBP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+            it = sm_count.emplace(dev, sms).first;
+        }
+        sms = it->second;
+    }
+    switch (dtype) {
+        case FBP_F32: return launch_persistent_t<float>(a, variant, sms, s);
+        case FBP_F16: return launch_persistent_t<__half>(a, variant, sms, s);
+        case FBP_BF16: return launch_persistent_t<__nv_bfloat16>(a, variant, sms, s);
+    }
+    return fail(FBP_ERR_INVALID_ARG, "dtype");
+}
+
+}  // namespace fbp

@@ -1,0 +1,399 @@
+// fbp_api.cu -- the exported C ABI of libfbp.so (declared in include/fbp.h).
+// Validation happens here, synchronously, before anything is enqueued.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <string>
+#include <new>
+#include <numeric>
+#include <vector>
+
+#include "bp_batch.cuh"
+#include "fbp_internal.cuh"
+
+namespace fbp {
+void clear_error();
+void release_tables();
+}  // namespace fbp
+
+using namespace fbp;
+
+namespace {
+
+size_t dtype_size(fbp_dtype d) { return d == FBP_F32 ? 4 : 2; }
+bool dtype_ok(int d) { return d == FBP_F32 || d == FBP_F16 || d == FBP_BF16; }
+bool kind_ok(int k) { return k == FBP_FILTER_RAMLAK || k == FBP_FILTER_SHEPP_LOGAN; }
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+bool overlap(const void *a, size_t na, const void *b, size_t nb)
+{
+    const char *pa = static_cast<const char *>(a), *pb = static_cast<const char *>(b);
+    return pa < pb + nb && pb < pa + na;
+}
+
+template <typename F>
+fbp_status guarded(F &&f)
+{
+    clear_error();
+    try {
+        return f();
+    } catch (const std::bad_alloc &) {
+        return fail(FBP_ERR_CUDA, "host allocation failed");
+    } catch (...) {
+        return fail(FBP_ERR_CUDA, "unexpected host exception");
+    }
+}
+
+}  // namespace
+
+extern "C" {
+
+int fbp_version(void) { return 100; }
+
+fbp_geometry fbp_geometry_default(int n_angles, int n_det, int n)
+{
+    fbp_geometry g;
+    g.n_angles = n_angles;
+    g.n_det = n_det;
+    g.n = n;
+    g.angle_start = 0.0;
+    g.angle_step = n_angles > 0 ? 3.14159265358979323846 / (double)n_angles : 0.0;
+    g.det_center = 0.5 * (double)(n_det - 1);
+    g.det_spacing = 1.0;
+    g.pixel_size = 1.0;
+    return g;
+}
+
+const char *fbp_status_string(fbp_status s)
+{
+    switch (s) {
+        case FBP_OK: return "FBP_OK";
+        case FBP_ERR_INVALID_ARG: return "FBP_ERR_INVALID_ARG";
+        case FBP_ERR_UNSUPPORTED: return "FBP_ERR_UNSUPPORTED";
+        case FBP_ERR_WORKSPACE: return "FBP_ERR_WORKSPACE";
+        case FBP_ERR_CUDA: return "FBP_ERR_CUDA";
+        case FBP_ERR_DEVICE_STATUS: return "FBP_ERR_DEVICE_STATUS";
+    }
+    return "FBP_UNKNOWN_STATUS";
+}
+
+const char *fbp_last_error_message(void);
+
+fbp_status fbp_filter(const float *sino, void *filt, float *row_scale, fbp_dtype dtype,
+                      fbp_filter_kind kind, const fbp_geometry *g, int n_slices,
+                      fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        fbp_status st = check_geometry(g, true, false);
+        if (st != FBP_OK) return st;
+        if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
+        if (!kind_ok(kind)) return fail(FBP_ERR_INVALID_ARG, "filter kind %d", (int)kind);
+        if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
+        if (n_slices == 0) return FBP_OK;
+        if (!sino || !filt) return fail(FBP_ERR_INVALID_ARG, "sino or filt is NULL");
+        if (dtype != FBP_F32 && !row_scale)
+            return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit output");
+        const long long rows = (long long)n_slices * g->n_angles;
+        const size_t nin = (size_t)rows * g->n_det * 4, nout = (size_t)rows * g->n_det * dtype_size(dtype);
+        if (overlap(sino, nin, filt, nout)) return fail(FBP_ERR_INVALID_ARG, "filt overlaps sino");
+        const float *H = nullptr;
+        const float2 *tw = nullptr;
+        int L = 0;
+        st = filter_tables(g->n_det, kind, g->det_spacing, stream, &H, &tw, &L);
+        if (st != FBP_OK) return st;
+        FilterLaunch a;
+        a.sino = sino;
+        a.filt = filt;
+        a.row_scale = dtype == FBP_F32 ? nullptr : row_scale;
+        a.rows = rows;
+        a.D = g->n_det;
+        a.L = L;
+        a.H = H;
+        a.tw = tw;
+        a.dtype = dtype;
+        return launch_filter(a, stream);
+    });
+}
+
+fbp_status fbp_backproject_variant(const void *filt, const float *row_scale, fbp_dtype dtype,
+                                   float *slice, const fbp_geometry *g, int n_slices, float scale,
+                                   int accumulate, int variant, fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        fbp_status st = check_geometry(g, false, true);
+        if (st != FBP_OK) return st;
+        if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
+        if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
+        if (variant < -1 || variant >= bp_variant_count())
+            return fail(FBP_ERR_INVALID_ARG, "variant %d", variant);
+        if (!std::isfinite(scale)) return fail(FBP_ERR_INVALID_ARG, "scale is not finite");
+        if (n_slices == 0) return FBP_OK;
+        if (!filt || !slice) return fail(FBP_ERR_INVALID_ARG, "filt or slice is NULL");
+        if (dtype != FBP_F32 && !row_scale)
+            return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit input");
+        const size_t nin = (size_t)n_slices * g->n_angles * g->n_det * dtype_size(dtype);
+        const size_t nout = (size_t)n_slices * g->n * g->n * 4;
+        if (overlap(filt, nin, slice, nout)) return fail(FBP_ERR_INVALID_ARG, "slice overlaps filt");
+        const double2 *cs = nullptr;
+        st = angle_table(*g, stream, &cs);
+        if (st != FBP_OK) return st;
+        BpLaunch a;
+        a.filt = filt;
+        a.row_scale = dtype == FBP_F32 ? nullptr : row_scale;
+        a.slice = slice;
+        a.cs = cs;
+        a.K = g->n_angles;
+        a.D = g->n_det;
+        a.N = g->n;
+        a.S = n_slices;
+        a.alpha = g->pixel_size / g->det_spacing;
+        a.det_center = g->det_center;
+        a.scale = scale;
+        a.accumulate = accumulate ? 1 : 0;
+        a.dtype = dtype;
+        return launch_backproject(a, variant, stream);
+    });
+}
+
+fbp_status fbp_backproject(const void *filt, const float *row_scale, fbp_dtype dtype, float *slice,
+                           const fbp_geometry *g, int n_slices, float scale, int accumulate,
+                           fbp_stream_t stream)
+{
+    return fbp_backproject_variant(filt, row_scale, dtype, slice, g, n_slices, scale, accumulate,
+                                   -1, stream);
+}
+
+fbp_status radon_forward(const float *slice, float *sino, const fbp_geometry *g, int n_slices,
+                         fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        fbp_status st = check_geometry(g, false, true);
+        if (st != FBP_OK) return st;
+        if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
+        if (n_slices == 0) return FBP_OK;
+        if (!slice || !sino) return fail(FBP_ERR_INVALID_ARG, "slice or sino is NULL");
+        const size_t nin = (size_t)n_slices * g->n * g->n * 4;
+        const size_t nout = (size_t)n_slices * g->n_angles * g->n_det * 4;
+        if (overlap(slice, nin, sino, nout)) return fail(FBP_ERR_INVALID_ARG, "sino overlaps slice");
+        const double2 *cs = nullptr;
+        st = angle_table(*g, stream, &cs);
+        if (st != FBP_OK) return st;
+        FwdLaunch a;
+        a.slice = slice;
+        a.sino = sino;
+        a.cs = cs;
+        a.K = g->n_angles;
+        a.D = g->n_det;
+        a.N = g->n;
+        a.S = n_slices;
+        a.alpha = g->pixel_size / g->det_spacing;
+        a.det_center = g->det_center;
+        return launch_forward(a, stream);
+    });
+}
+
+int fbp_bp_variant_count(void) { return bp_variant_count(); }
+
+fbp_status fbp_bp_variant_info(int variant, fbp_bp_shape *out)
+{
+    return guarded([&]() -> fbp_status {
+        if (!out) return fail(FBP_ERR_INVALID_ARG, "out is NULL");
+        if (!bp_variant_shape(variant, out)) return fail(FBP_ERR_INVALID_ARG, "variant %d", variant);
+        return FBP_OK;
+    });
+}
+
+// ---------------------------------------------------------------------------
+// Ragged batches
+// ---------------------------------------------------------------------------
+static fbp_status check_items(const fbp_batch_item *items, int count)
+{
+    if (!items) return fail(FBP_ERR_INVALID_ARG, "items is NULL");
+    if (count < 1 || count > kMaxBatch)
+        return fail(FBP_ERR_INVALID_ARG, "count %d outside [1, %d]", count, kMaxBatch);
+    for (int i = 0; i < count; ++i) {
+        fbp_status st = check_geometry(&items[i].g, true, true);
+        if (st != FBP_OK) {
+            const std::string why = fbp_last_error_message();
+            return fail(st, "item %d: %s", i, why.c_str());
+        }
+        if (!items[i].sino || !items[i].slice)
+            return fail(FBP_ERR_INVALID_ARG, "item %d: sino or slice is NULL", i);
+    }
+    return FBP_OK;
+}
+
+// Workspace: [256 B: queue counter] then, per item, its filtered rows and
+// (16-bit dtypes) its row scales, each 256-byte aligned.
+static size_t workspace_layout(const fbp_batch_item *items, int count, fbp_dtype dtype,
+                               std::vector<size_t> *filt_off, std::vector<size_t> *scale_off)
+{
+    size_t off = 256;
+    for (int i = 0; i < count; ++i) {
+        const size_t rows = (size_t)items[i].g.n_angles;
+        if (filt_off) filt_off->push_back(off);
+        off += align256(rows * items[i].g.n_det * dtype_size(dtype));
+        if (scale_off) scale_off->push_back(dtype == FBP_F32 ? 0 : off);
+        if (dtype != FBP_F32) off += align256(rows * 4);
+    }
+    return off;
+}
+
+size_t fbp_batched_workspace_bytes(const fbp_batch_item *items, int count, fbp_dtype dtype)
+{
+    clear_error();
+    if (!dtype_ok(dtype) || check_items(items, count) != FBP_OK) return 0;
+    return workspace_layout(items, count, dtype, nullptr, nullptr);
+}
+
+fbp_status fbp_batched(const fbp_batch_item *items, int count, fbp_filter_kind kind,
+                       fbp_dtype dtype, int bp_variant, void *workspace, size_t ws_bytes,
+                       fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        fbp_status st = check_items(items, count);
+        if (st != FBP_OK) return st;
+        if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
+        if (!kind_ok(kind)) return fail(FBP_ERR_INVALID_ARG, "filter kind %d", (int)kind);
+        if (bp_variant < -1 || bp_variant >= bp_variant_count())
+            return fail(FBP_ERR_INVALID_ARG, "variant %d", bp_variant);
+        const int variant = bp_variant < 0 ? 0 : bp_variant;
+        std::vector<size_t> foff, soff;
+        const size_t need = workspace_layout(items, count, dtype, &foff, &soff);
+        if (!workspace) return fail(FBP_ERR_WORKSPACE, "workspace is NULL");
+        if (reinterpret_cast<uintptr_t>(workspace) & 255)
+            return fail(FBP_ERR_WORKSPACE, "workspace is not 256-byte aligned");
+        if (ws_bytes < need)
+            return fail(FBP_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+        char *ws = static_cast<char *>(workspace);
+        unsigned *status = nullptr;
+        st = device_status_word(&status);
+        if (st != FBP_OK) return st;
+
+        // tables (all before any launch, so a failure enqueues nothing)
+        std::vector<const double2 *> cs(count);
+        std::vector<const float *> Hs(count);
+        std::vector<const float2 *> tws(count);
+        std::vector<int> Ls(count);
+        for (int i = 0; i < count; ++i) {
+            st = angle_table(items[i].g, stream, &cs[i]);
+            if (st != FBP_OK) return st;
+            st = filter_tables(items[i].g.n_det, kind, items[i].g.det_spacing, stream, &Hs[i],
+                               &tws[i], &Ls[i]);
+            if (st != FBP_OK) return st;
+        }
+
+        // filter descriptors, in item order
+        auto *fa = new FilterBatchArgs();
+        std::unique_ptr<FilterBatchArgs> fa_owner(fa);
+        int groups = 0;
+        for (int i = 0; i < count; ++i) {
+            FilterBatchItem &f = fa->items[i];
+            f.sino = items[i].sino;
+            f.filt = ws + foff[i];
+            f.row_scale = dtype == FBP_F32 ? nullptr : reinterpret_cast<float *>(ws + soff[i]);
+            f.H = Hs[i];
+            f.tw = tws[i];
+            f.K = items[i].g.n_angles;
+            f.D = items[i].g.n_det;
+            f.L = Ls[i];
+            f.group_begin = groups;
+            const int G = 32 / (Ls[i] / 512);
+            const long long pairs = ((long long)f.K + 1) / 2;
+            const long long gi = (pairs + G - 1) / G;
+            if ((long long)groups + gi > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "batch too large");
+            groups += (int)gi;
+        }
+        fa->count = count;
+
+        // backprojection descriptors: items by angle count, largest first
+        std::vector<int> order(count);
+        std::iota(order.begin(), order.end(), 0);
+        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+            return (long long)items[x].g.n_angles * items[x].g.n * items[x].g.n >
+                   (long long)items[y].g.n_angles * items[y].g.n * items[y].g.n;
+        });
+        auto *ba = new BpBatchArgs();
+        std::unique_ptr<BpBatchArgs> ba_owner(ba);
+        const int TW = bp_tile_w(variant), TH = bp_tile_h(variant);
+        long long units = 0;
+        int max_H = 0;
+        for (int r = 0; r < count; ++r) {
+            const int i = order[r];
+            const fbp_geometry &g = items[i].g;
+            BpBatchItem &b = ba->items[r];
+            b.filt = ws + foff[i];
+            b.row_scale = dtype == FBP_F32 ? nullptr : reinterpret_cast<const float *>(ws + soff[i]);
+            b.slice = items[i].slice;
+            b.cs = cs[i];
+            b.alpha = g.pixel_size / g.det_spacing;
+            b.det_center = g.det_center;
+            b.K = g.n_angles;
+            b.D = g.n_det;
+            b.N = g.n;
+            b.scale = (float)g.angle_step;
+            b.tiles_x = (g.n + TW - 1) / TW;
+            b.H = bp_window_half(b.alpha, TW, TH);
+            b.unit_begin = (int)units;
+            b.pad_ = 0;
+            max_H = std::max(max_H, b.H);
+            units += (long long)b.tiles_x * ((g.n + TH - 1) / TH);
+            if (units > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "batch too large");
+        }
+        ba->count = count;
+        ba->total_units = (int)units;
+        ba->max_H = max_H;
+        ba->counter = reinterpret_cast<int *>(ws);
+        ba->status = status;
+
+        FBP_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), stream));
+        st = launch_filter_batched(*fa, groups, dtype, stream);
+        if (st != FBP_OK) return st;
+        return launch_bp_persistent(*ba, variant, dtype, stream);
+    });
+}
+
+fbp_status fbp_last_device_status(fbp_stream_t stream, int *code)
+{
+    return guarded([&]() -> fbp_status {
+        unsigned *p = nullptr;
+        fbp_status st = device_status_word(&p);
+        if (st != FBP_OK) return st;
+        FBP_CUDA_TRY(cudaStreamSynchronize(stream));
+        unsigned v = 0;
+        FBP_CUDA_TRY(cudaMemcpy(&v, p, sizeof(v), cudaMemcpyDeviceToHost));
+        if (v) {
+            const unsigned zero = 0;
+            FBP_CUDA_TRY(cudaMemcpy(p, &zero, sizeof(zero), cudaMemcpyHostToDevice));
+        }
+        if (code) *code = (int)v;
+        if (v) return fail(FBP_ERR_DEVICE_STATUS, "device status word = %u", v);
+        return FBP_OK;
+    });
+}
+
+fbp_status fbp_prepare(const fbp_geometry *g, int kind, fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        fbp_status st = check_geometry(g, kind >= 0, false);
+        if (st != FBP_OK) return st;
+        const double2 *cs = nullptr;
+        st = angle_table(*g, stream, &cs);
+        if (st != FBP_OK) return st;
+        if (kind >= 0) {
+            if (!kind_ok(kind)) return fail(FBP_ERR_INVALID_ARG, "filter kind %d", kind);
+            const float *H;
+            const float2 *tw;
+            int L;
+            st = filter_tables(g->n_det, kind, g->det_spacing, stream, &H, &tw, &L);
+            if (st != FBP_OK) return st;
+        }
+        unsigned *p = nullptr;
+        return device_status_word(&p);
+    });
+}
+
+void fbp_release_tables(void) { release_tables(); }
+
+}  // extern "C"

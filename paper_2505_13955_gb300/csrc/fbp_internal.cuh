@@ -1,0 +1,109 @@
+// fbp_internal.cuh -- declarations shared by the translation units of
+// libfbp.so (never by the oracle, which is a separate program).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "fbp.h"
+
+namespace fbp {
+
+// ---------------------------------------------------------------------------
+// Error reporting (thread-local message; see fbp_last_error_message()).
+// ---------------------------------------------------------------------------
+fbp_status fail(fbp_status st, const char *fmt, ...);
+fbp_status cuda_fail(cudaError_t e, const char *what);
+#define FBP_CUDA_TRY(call)                                              \
+    do {                                                                \
+        cudaError_t e_ = (call);                                        \
+        if (e_ != cudaSuccess) return ::fbp::cuda_fail(e_, #call);      \
+    } while (0)
+
+// Device status word: kernels record fault codes here instead of trapping.
+enum DeviceFault : unsigned {
+    FAULT_NONE = 0,
+    FAULT_QUEUE_CAP = 1,      // persistent work loop ran past its iteration cap
+    FAULT_TABLE_INDEX = 2,    // checked build: interpolation index outside the staged window
+    FAULT_FILTER_SHAPE = 3,   // filter kernel got an unsupported transform length
+};
+fbp_status device_status_word(unsigned **out);   // current device
+
+// ---------------------------------------------------------------------------
+// Constant tables, built on the device in FP64 and cached per device.
+// ---------------------------------------------------------------------------
+struct AngleKey {
+    int K;
+    double start, step;
+};
+// cos/sin of theta_k = start + k*step, k in [0, K), in double precision.
+fbp_status angle_table(const fbp_geometry &g, cudaStream_t s, const double2 **out);
+
+// Filter tables for detector width D:
+//   L   = transform length (power of two >= max(512, 2D-1), <= 16384)
+//   H   = real spectrum of tau * h_tau, divided by L (length L, float)
+//   tw  = twiddles exp(-2 pi i m / L), m in [0, L) (float2)
+fbp_status filter_tables(int D, int kind, double tau, cudaStream_t s,
+                         const float **H, const float2 **tw, int *L);
+int filter_length(int D);   // 0 if D is outside [1, 8192]
+
+bool stream_is_capturing(cudaStream_t s);
+
+// Per-device, per-kernel caches of launch attributes, so that a call repeated
+// inside stream capture only enqueues work.
+fbp_status ensure_dynamic_smem(const void *func, size_t bytes);
+fbp_status blocks_per_sm(const void *func, int threads, size_t smem, int *out);
+
+// ---------------------------------------------------------------------------
+// Geometry validation shared by the entry points.
+// ---------------------------------------------------------------------------
+fbp_status check_geometry(const fbp_geometry *g, bool for_filter, bool for_projection);
+
+// Half-width H of the detector window one backprojection tile needs:
+// every tile pixel's interpolation index lies in [-H, H] around the tile
+// centre's bin.  Returns -1 if the window would exceed max_w entries.
+int bp_window_half(double alpha, int tile_w, int tile_h);
+
+// ---------------------------------------------------------------------------
+// Kernel launchers (defined next to their kernels).
+// ---------------------------------------------------------------------------
+struct FilterLaunch {
+    const float *sino;     // [rows][D]
+    void *filt;            // [rows][D] of dtype
+    float *row_scale;      // [rows] (16-bit dtypes)
+    long long rows;        // n_slices * K
+    int D, L;
+    const float *H;
+    const float2 *tw;
+    fbp_dtype dtype;
+};
+fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s);
+
+struct BpLaunch {
+    const void *filt;        // [S][K][D]
+    const float *row_scale;  // [S][K] or null
+    float *slice;            // [S][N][N]
+    const double2 *cs;       // [K]
+    int K, D, N, S;
+    double alpha, det_center;
+    float scale;
+    int accumulate;
+    fbp_dtype dtype;
+};
+fbp_status launch_backproject(const BpLaunch &a, int variant, cudaStream_t s);
+int bp_default_variant(const BpLaunch &a);
+int bp_variant_count();
+bool bp_variant_shape(int v, fbp_bp_shape *out);
+size_t bp_smem_bytes(int v, int W);
+
+struct FwdLaunch {
+    const float *slice;   // [S][N][N]
+    float *sino;          // [S][K][D]
+    const double2 *cs;
+    int K, D, N, S;
+    double alpha, det_center;
+};
+fbp_status launch_forward(const FwdLaunch &a, cudaStream_t s);
+
+}  // namespace fbp

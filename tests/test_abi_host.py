@@ -1,0 +1,138 @@
+"""The C-ABI library on a CPU-only host: it loads, exports every function that
+include/fbp.h declares, and its validation paths reject bad arguments before
+any CUDA call.  (No compute call is made here.)"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2505_13955_gb300 import _lib
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2505_13955_gb300 import build
+    build.build_cuda("libfbp.so")
+    return _lib.load()
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "fbp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    names = re.findall(r"^[A-Za-z_][\w \*]*?\b(\w+)\s*\(", src, flags=re.M)
+    return sorted(set(n for n in names if n not in ("if", "sizeof")))
+
+
+def test_header_declares_the_boundary():
+    names = declared_functions()
+    for n in ("fbp_filter", "fbp_backproject", "radon_forward", "fbp_batched",
+              "fbp_batched_workspace_bytes", "fbp_last_device_status", "fbp_status_string"):
+        assert n in names
+
+
+def test_every_declared_symbol_is_exported_and_bound(L):
+    for n in declared_functions():
+        assert hasattr(L, n), n
+        assert n in _lib.SIGNATURES, f"{n} has no ctypes signature"
+
+
+def test_status_strings(L):
+    for code, name in [(0, "FBP_OK"), (-1, "FBP_ERR_INVALID_ARG"), (-2, "FBP_ERR_UNSUPPORTED"),
+                       (-3, "FBP_ERR_WORKSPACE"), (-4, "FBP_ERR_CUDA"), (-5, "FBP_ERR_DEVICE_STATUS")]:
+        assert L.fbp_status_string(code).decode() == name
+    assert L.fbp_version() >= 100
+
+
+def test_default_geometry(L):
+    g = L.fbp_geometry_default(360, 256, 256)
+    assert (g.n_angles, g.n_det, g.n) == (360, 256, 256)
+    assert g.angle_step == pytest.approx(3.141592653589793 / 360)
+    assert g.det_center == 127.5 and g.det_spacing == 1.0 and g.pixel_size == 1.0
+
+
+def test_variant_table(L):
+    n = L.fbp_bp_variant_count()
+    assert n >= 4
+    for v in range(n):
+        s = _lib.CBpShape()
+        assert L.fbp_bp_variant_info(v, ctypes.byref(s)) == 0
+        assert s.tile_x == s.px * (s.threads // (s.tile_y // s.py))
+        assert s.threads % 32 == 0
+    s = _lib.CBpShape()
+    assert L.fbp_bp_variant_info(n, ctypes.byref(s)) == _lib.FBP_ERR_INVALID_ARG
+
+
+def dummy_ptr():
+    return ctypes.c_void_p(0x1000)
+
+
+def test_invalid_arguments_are_rejected_without_cuda(L):
+    g = L.fbp_geometry_default(10, 16, 16)
+    p = dummy_ptr()
+    # NULL geometry
+    assert L.fbp_filter(p, p, None, 0, 0, None, 1, None) == _lib.FBP_ERR_INVALID_ARG
+    assert "NULL" in L.fbp_last_error_message().decode()
+    # bad dtype / kind
+    assert L.fbp_filter(p, dummy_ptr(), None, 7, 0, ctypes.byref(g), 1, None) == _lib.FBP_ERR_INVALID_ARG
+    assert L.fbp_filter(p, dummy_ptr(), None, 0, 9, ctypes.byref(g), 1, None) == _lib.FBP_ERR_INVALID_ARG
+    # 16-bit without row_scale
+    assert L.fbp_filter(p, ctypes.c_void_p(0x9000000), None, 1, 0, ctypes.byref(g), 1, None) == _lib.FBP_ERR_INVALID_ARG
+    # NULL data
+    assert L.fbp_backproject(None, None, 0, p, ctypes.byref(g), 1, 1.0, 0, None) == _lib.FBP_ERR_INVALID_ARG
+    assert L.radon_forward(p, None, ctypes.byref(g), 1, None) == _lib.FBP_ERR_INVALID_ARG
+    # aliasing
+    assert L.fbp_filter(p, p, None, 0, 0, ctypes.byref(g), 1, None) == _lib.FBP_ERR_INVALID_ARG
+    # negative slice count; zero slices is a no-op
+    assert L.fbp_backproject(p, None, 0, p, ctypes.byref(g), -1, 1.0, 0, None) == _lib.FBP_ERR_INVALID_ARG
+    assert L.radon_forward(p, dummy_ptr(), ctypes.byref(g), 0, None) == 0
+    # geometry limits
+    bad = L.fbp_geometry_default(10, 16, 16)
+    bad.det_spacing = 0.0
+    assert L.fbp_backproject(p, None, 0, ctypes.c_void_p(0x9000000), ctypes.byref(bad), 1, 1.0, 0, None) == _lib.FBP_ERR_INVALID_ARG
+    wide = L.fbp_geometry_default(10, 9000, 16)
+    assert L.fbp_filter(p, ctypes.c_void_p(0x90000000), None, 0, 0, ctypes.byref(wide), 1, None) == _lib.FBP_ERR_UNSUPPORTED
+    fine = L.fbp_geometry_default(10, 16, 16)
+    fine.pixel_size = 3.0
+    assert L.radon_forward(p, ctypes.c_void_p(0x9000000), ctypes.byref(fine), 1, None) == _lib.FBP_ERR_UNSUPPORTED
+    nan = L.fbp_geometry_default(10, 16, 16)
+    nan.det_center = float("nan")
+    assert L.radon_forward(p, ctypes.c_void_p(0x9000000), ctypes.byref(nan), 1, None) == _lib.FBP_ERR_INVALID_ARG
+    # bad variant
+    assert L.fbp_backproject_variant(p, None, 0, ctypes.c_void_p(0x9000000), ctypes.byref(g), 1, 1.0, 0, 99, None) == _lib.FBP_ERR_INVALID_ARG
+
+
+def test_batched_workspace_query_and_validation(L):
+    items = (_lib.CBatchItem * 3)()
+    dims = [(720, 512, 512), (1800, 1024, 1024), (3600, 2048, 2048)]
+    for i, (K, D, N) in enumerate(dims):
+        items[i].sino = 0x1000 * (i + 1)
+        items[i].slice = 0x100000 * (i + 1)
+        items[i].g = L.fbp_geometry_default(K, D, N)
+    n32 = L.fbp_batched_workspace_bytes(items, 3, 0)
+    n16 = L.fbp_batched_workspace_bytes(items, 3, 1)
+    raw32 = sum(K * D * 4 for K, D, _ in dims)
+    raw16 = sum(K * D * 2 + K * 4 for K, D, _ in dims)
+    assert raw32 + 256 <= n32 <= raw32 + 256 + 3 * 255
+    assert raw16 + 256 <= n16 <= raw16 + 256 + 6 * 255
+    assert n32 % 256 == 0
+    # count limits and NULL pointers
+    assert L.fbp_batched_workspace_bytes(items, 0, 0) == 0
+    assert L.fbp_batched_workspace_bytes(items, 257, 0) == 0
+    items[1].sino = None
+    assert L.fbp_batched_workspace_bytes(items, 3, 0) == 0
+    items[1].sino = 0x2000
+    # workspace checks happen before any launch
+    assert L.fbp_batched(items, 3, 0, 0, -1, None, 0, None) == _lib.FBP_ERR_WORKSPACE
+    assert L.fbp_batched(items, 3, 0, 0, -1, ctypes.c_void_p(0x10010), n32, None) == _lib.FBP_ERR_WORKSPACE
+    assert L.fbp_batched(items, 3, 0, 0, -1, ctypes.c_void_p(0x10000), n32 - 256, None) == _lib.FBP_ERR_WORKSPACE
+    assert L.fbp_batched(items, 3, 5, 0, -1, ctypes.c_void_p(0x10000), n32, None) == _lib.FBP_ERR_INVALID_ARG
+
+
+def test_missing_library_fails_loudly(monkeypatch, tmp_path):
+    monkeypatch.setattr(_lib, "HERE", str(tmp_path))
+    monkeypatch.setattr(_lib, "_libs", {})
+    with pytest.raises(RuntimeError, match="not built"):
+        _lib.load()

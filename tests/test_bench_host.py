@@ -1,0 +1,60 @@
+"""Host logic of bench.py's multi-GPU path, run as two gloo ranks on CPU:
+slices shard with no overlap, per-rank times gather to every rank, and the
+job rate is total units over the slowest rank's time."""
+import os
+import socket
+
+import pytest
+import torch.distributed as dist
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    s = socket.socket()
+    s.bind(("127.0.0.1", 0))
+    port = s.getsockname()[1]
+    s.close()
+    return port
+
+
+def _worker(rank, ws, port, q):
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank),
+                      WORLD_SIZE=str(ws), LOCAL_RANK=str(rank))
+    dist.init_process_group("gloo", rank=rank, world_size=ws)
+    try:
+        env = bench.dist_env()
+        mine = bench.shard_slices(16, rank)
+        elapsed = 100.0 + 50.0 * rank          # rank 1 is the slow one
+        units = 16 * 8192 * 8192 * 4096
+        gathered = bench.allgather_floats([elapsed, float(units)])
+        bench.barrier()
+        rate, t = bench.aggregate([g[0] for g in gathered], [int(g[1]) for g in gathered])
+        q.put((rank, env, mine, gathered, rate, t))
+    finally:
+        dist.destroy_process_group()
+
+
+def test_two_rank_sharding_and_aggregation():
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    port = _free_port()
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, env0, s0, g0, rate0, t0), (r1, env1, s1, g1, rate1, t1) = res
+    assert env0 == (2, 0, 0) and env1 == (2, 1, 1)
+    assert set(s0).isdisjoint(s1) and len(s0) == len(s1) == 16
+    assert g0 == g1 == [[100.0, float(16 * 8192 * 8192 * 4096)], [150.0, float(16 * 8192 * 8192 * 4096)]]
+    assert t0 == t1 == 150.0
+    assert rate0 == pytest.approx(2 * 16 * 8192 * 8192 * 4096 / 0.150)
+
+
+def test_aggregate_single_rank():
+    rate, t = bench.aggregate([80.0], [1000])
+    assert t == 80.0 and rate == pytest.approx(1000 / 0.08)

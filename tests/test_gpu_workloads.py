@@ -1,0 +1,85 @@
+"""GPU parity at the workloads' full sizes, in the launch configuration the
+benchmark times, on outputs the oracle can compute one by one (sampled
+pixels, all angles):
+
+* FBP stack, N = 2048, 1800 angles, Shepp-Logan filter, Poisson 1e4 (2 slices);
+* precision, N = 8192, 4096 angles: FP32, FP16 and BF16 staged rows
+  (2 slices), the 16-bit forms also against the FP32 GPU image.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from gpu_util import fbp_api, needs_gpu, to_gpu, to_np, torch
+from paper_2505_13955_gb300 import phantoms
+
+pytestmark = [pytest.mark.gpu, needs_gpu]
+
+
+def sample_pixels(N, n, seed):
+    rng = np.random.default_rng(seed)
+    rows = rng.integers(0, N, n)
+    cols = rng.integers(0, N, n)
+    edge = np.array([0, N - 1, N // 2, N // 2 - 1, 1, N - 2])
+    rr, cc = np.meshgrid(edge, edge)
+    return np.concatenate([rows, rr.ravel()]), np.concatenate([cols, cc.ravel()])
+
+
+def test_stack_n2048_sampled():
+    api = fbp_api()
+    w = phantoms.WORKLOADS["fbp_stack_n2048"]
+    N, K = 2048, 1800
+    sinos = np.stack([phantoms.slice_sinogram(w, i) for i in range(2)])
+    g = api.Geometry(K, N, N)
+    f = to_np(api.fbp(to_gpu(sinos), g, kind="shepp_logan"))
+    go = oracle.Geometry(K, N, N)
+    for s in range(2):
+        q = oracle.filter(sinos[s].astype(np.float64), oracle.SHEPP_LOGAN)
+        rows, cols = sample_pixels(N, 2000, s)
+        ref = oracle.backproject_pixels(q, go, rows, cols)
+        dr = ref.max() - ref.min()
+        assert np.max(np.abs(f[s][rows, cols] - ref)) <= 1e-4 * dr
+
+
+@pytest.fixture(scope="module")
+def n8192():
+    api = fbp_api()
+    w = phantoms.WORKLOADS["fbp_precision_n8192"]
+    N, K = 8192, 4096
+    sinos = np.stack([phantoms.slice_sinogram(w, i) for i in range(2)])
+    go = oracle.Geometry(K, N, N)
+    refs = []
+    for s in range(2):
+        q = oracle.filter(sinos[s].astype(np.float64))
+        rows, cols = sample_pixels(N, 1500, 10 + s)
+        refs.append((rows, cols, oracle.backproject_pixels(q, go, rows, cols)))
+    return api, sinos, refs
+
+
+def test_precision_n8192_f32_sampled(n8192):
+    api, sinos, refs = n8192
+    g = api.Geometry(4096, 8192, 8192)
+    f = api.fbp(to_gpu(sinos), g)
+    for s, (rows, cols, ref) in enumerate(refs):
+        got = to_np(f[s][torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()])
+        dr = ref.max() - ref.min()
+        assert np.max(np.abs(got - ref)) <= 1e-4 * dr
+
+
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+def test_precision_n8192_16bit_sampled(n8192, dtype):
+    api, sinos, refs = n8192
+    g = api.Geometry(4096, 8192, 8192)
+    x = to_gpu(sinos)
+    f16 = api.fbp(x, g, dtype=dtype)
+    f32 = api.fbp(x, g)
+    for s, (rows, cols, ref) in enumerate(refs):
+        r, c = torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()
+        got = to_np(f16[s][r, c])
+        dr = ref.max() - ref.min()
+        err = np.max(np.abs(got - ref)) / dr
+        assert err <= 2e-3, f"{dtype}: {err:.2e} of DR vs the FP64 oracle"
+        full32 = f32[s]
+        dr32 = (full32.max() - full32.min()).item()
+        e32 = ((f16[s] - full32).abs().max().item()) / dr32
+        assert e32 <= 2e-3, f"{dtype}: {e32:.2e} of DR vs the FP32 GPU image"
