@@ -162,6 +162,31 @@ fbp_status fbp_backproject_variant(const void *filt, const float *row_scale,
                                    fbp_stream_t stream);
 
 /*
+ * fbp_backproject_noalloc -- fbp_backproject for callers that cannot
+ * allocate device memory.  The paper has no counterpart: this is a library
+ * service, not a step of the method.
+ *
+ * fbp_backproject caches its FP64 angle table in device memory it allocates
+ * with cudaMalloc the first time it sees a geometry.  Callers whose device
+ * memory is owned by a framework's pool, fixed up front, or who enqueue work
+ * inside CUDA stream capture cannot allow that allocation.  This variant
+ * computes the angle table on `stream` into a static device array of at most
+ * 16384 angles (256 KB, held on every device that runs it until the library
+ * is unloaded) and calls no allocating routine; inputs and outputs are as for
+ * fbp_backproject, and the result equals fbp_backproject's.
+ *   * n_angles > 16384 returns FBP_ERR_UNSUPPORTED.
+ *   * The first call on a device looks up the array's device address; make
+ *     that first call before any stream capture.
+ *   * All calls share the array and overwrite it completely.  Calls whose
+ *     work overlaps on the GPU (unordered streams) race on it: order them.
+ */
+fbp_status fbp_backproject_noalloc(const void *filt, const float *row_scale,
+                                   fbp_dtype dtype, float *slice,
+                                   const fbp_geometry *g, int n_slices,
+                                   float scale, int accumulate,
+                                   fbp_stream_t stream);
+
+/*
  * radon_forward -- the matched forward projector A (the adjoint of
  * fbp_backproject with scale 1; the paper's data generation uses a forward
  * model, Sec. V-B(a)).

@@ -24,7 +24,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 
-CU_SOURCES = ["runtime.cu", "filter.cu", "backproject.cu", "forward.cu", "fbp_api.cu"]
+CU_SOURCES = ["runtime.cu", "filter.cu", "backproject.cu", "forward.cu", "fbp_api.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
