@@ -1,21 +1,28 @@
 """Benchmark: backprojection throughput (Gupdates/s, slices/s) at N = 8192.
 
-One step = one pass of the whole hot path -- ramp filter (fbp_filter) then
-pixel-driven backprojection (fbp_backproject) -- over one batch of the
-precision workload: 16 slices, N = D = 8192, 4096 angles on [0, pi),
-seeded random-ellipse sinograms (noise-free), FP32 unless --dtype says
-otherwise.  One update = one (pixel, angle) accumulation; a slice has
-N^2 * K of them.
+Default workload (the headline): 16 slices per GPU, N = D = 8192, 4096
+angles on [0, pi), seeded random-ellipse sinograms (noise-free), Ram-Lak.
+One step = one pass of the whole hot path over the batch: fbp_filter then
+fbp_backproject.  One update = one (pixel, angle) accumulation; a slice has
+N^2 K of them.  `value` is for plain FP32 rows; the same line reports the
+FP16- and BF16-staged forms measured in the same run, as ratios to FP32.
 
-Timing: W untimed warm-up steps, then exactly K steps bracketed by a barrier
-and torch.cuda.synchronize(), timed with CUDA events on the launching
-stream; the per-step input (2.15 GB of sinograms) is larger than L2, so no
-flush is needed.  The dominant kernel (backprojection) is bracketed by its
-own events inside the timed region for the roofline figure.  SM clocks and
+Other workloads (--workload): fbp_single_n256 (1 slice, N = 256, K = 360),
+fbp_stack_n2048 (64 slices, N = 2048, K = 1800, Poisson noise, Shepp-Logan
+filter), fbp_ragged_batch (200 slices of mixed N and K in one persistent
+launch replayed from a CUDA graph, against per-slice launches), and
+gd_refine_n1024 (gradient-descent least squares, 16 slices, N = 1024,
+K = 1800; a step is one iteration, A and A^T).
+
+Timing: W >= 3 untimed warm-up steps, then exactly K steps bracketed by a
+barrier and torch.cuda.synchronize(), timed with CUDA events on the
+launching stream; the dominant kernel is bracketed by its own events inside
+the timed region for the roofline.  Inputs of the headline workload (2.15 GB
+of sinograms per step) exceed L2, so no flush is needed.  SM clocks and
 throttle reasons are sampled with nvidia-smi during the timed region.
 
 Multi-GPU (torchrun, one rank per GPU): slices are independent (one slice
-per detector row), so each rank reconstructs its own 16 slices with no
+per detector row), so each rank reconstructs its own slices with no
 collective; the step time is the max over ranks and the value counts every
 rank's updates (weak scaling).
 
@@ -48,7 +55,7 @@ FP32_LANES = 128
 ALU_OPS_PER_UPDATE = 4          # coordinate step, fraction, interpolate, accumulate
 SHARED_BYTES_PER_CLK = 128      # shared-memory load bandwidth per SM
 SAMPLES_PER_UPDATE = 2          # linear interpolation reads two detector samples
-BP_KERNEL_REGEX = "bp_kernel"
+BP_KERNEL_REGEX = "bp_kernel|bp_orbit_kernel"
 
 
 def roofline_peak(sm_mhz: float, dtype: str) -> dict:
@@ -166,7 +173,7 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------------------
-# Inputs
+# Inputs, peaks, captured traffic
 # ---------------------------------------------------------------------------
 def make_inputs(w, slices: list[int]) -> np.ndarray:
     from paper_2505_13955_gb300 import phantoms
@@ -176,10 +183,19 @@ def make_inputs(w, slices: list[int]) -> np.ndarray:
     return out
 
 
+def peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
 def bp_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("bp_tile.cuh", "backproject.cu"):
+    for f in ("bp_tile.cuh", "bp_orbit.cuh", "backproject.cu"):
         with open(os.path.join(ROOT, "paper_2505_13955_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -191,23 +207,16 @@ def captured_traffic(variant: int, dtype: str, n_slices: int):
     or the launch differs (variant, dtype)."""
     try:
         with open(os.path.join(ROOT, "profiles", "bp_traffic.json")) as f:
-            t = json.load(f)
+            entries = json.load(f)
     except (OSError, ValueError):
         return None
-    if t.get("source_hash") != bp_source_hash() or t.get("dtype") != dtype:
-        return None
-    if variant not in (-1, t.get("variant")):
-        return None
-    return float(t["dram_bytes_per_slice"]) * n_slices
-
-
-def peaks() -> dict:
-    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    try:
-        with open(path) as f:
-            return json.load(f)
-    except (OSError, ValueError):
-        return {}
+    for t in entries if isinstance(entries, list) else [entries]:
+        if t.get("source_hash") != bp_source_hash() or t.get("dtype") != dtype:
+            continue
+        if variant != t.get("variant"):
+            continue
+        return float(t["dram_bytes_per_slice"]) * n_slices
+    return None
 
 
 # ---------------------------------------------------------------------------
@@ -225,6 +234,7 @@ def cpu_sample(w, block: int) -> dict:
     t0 = time.perf_counter()
     q = oracle.filter(p, oracle.RAMLAK if w.filter == "ramlak" else oracle.SHEPP_LOGAN)
     t1 = time.perf_counter()
+    block = min(block, N)
     c0 = N // 2 - block // 2
     rr, cc = np.meshgrid(np.arange(c0, c0 + block), np.arange(c0, c0 + block), indexing="ij")
     oracle.backproject_pixels(q, g, rr.ravel(), cc.ravel())
@@ -244,15 +254,16 @@ def run_reference(args) -> None:
         return
     from paper_2505_13955_gb300 import phantoms
     w = phantoms.WORKLOADS[args.workload]
+    if w.ragged:
+        w = phantoms.WORKLOADS[WORKLOAD]
     block = 1024 if args.steps + args.warmup <= 20 else 512
     for _ in range(args.warmup):
         cpu_sample(w, block // 2)
-    vals, secs = [], []
+    vals = []
     sample = None
     for _ in range(args.steps):
         r = cpu_sample(w, block)
         vals.append(r["value"])
-        secs.append(r["seconds"])
         sample = r
     value = float(np.median(vals))
     slice_s = w.n * w.n * w.n_angles / (value * 1e9)
@@ -262,7 +273,7 @@ def run_reference(args) -> None:
         "ms_per_step": 1e3 * slice_s * w.n_slices, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
         "config": {"workload": f"{w.name}: S={w.n_slices} N=D={w.n} K={w.n_angles} "
-                   f"random ellipses, Ram-Lak", "sample": "see cpu_baseline"},
+                   f"random ellipses, {w.filter}", "sample": "see cpu_baseline"},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample["cores"], "kind": "oracle",
                          "sample": sample["sample"]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -274,146 +285,329 @@ def run_reference(args) -> None:
 # ---------------------------------------------------------------------------
 # GPU arm
 # ---------------------------------------------------------------------------
-def run_ours(args) -> None:
+class Timed:
+    """W warm-up steps, then K steps between a barrier and synchronisation,
+    timed with CUDA events on `stream`; `step(evs)` may record its own
+    events for the dominant kernel."""
+
+    def __init__(self, stream, steps: int, warmup: int, n_events: int = 0):
+        import torch
+        self.torch = torch
+        self.stream = stream
+        self.steps = steps
+        self.warmup = warmup
+        self.clocks = None
+        self.ev = [[torch.cuda.Event(enable_timing=True) for _ in range(n_events)]
+                   for _ in range(steps)]
+
+    def run(self, step, clocks_index: int | None):
+        torch = self.torch
+        for _ in range(self.warmup):
+            step(None)
+        torch.cuda.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        sampler = ClockSampler(clocks_index) if clocks_index is not None else None
+        if sampler:
+            sampler.__enter__()
+        try:
+            barrier()
+            torch.cuda.synchronize()
+            a.record(self.stream)
+            for i in range(self.steps):
+                step(self.ev[i] if self.ev[i] else None)
+            b.record(self.stream)
+            torch.cuda.synchronize()
+            barrier()
+        finally:
+            if sampler:
+                sampler.__exit__(None, None, None)
+        self.clocks = sampler.summary() if sampler else None
+        return a.elapsed_time(b) / self.steps
+
+    def between(self, i: int, j: int) -> float:
+        return float(np.mean([e[i].elapsed_time(e[j]) for e in self.ev]))
+
+
+def init_device():
     import torch
     import torch.distributed as dist
-
     ws, rank, local = dist_env()
     if ws > 1:
         torch.cuda.set_device(local)
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
-    dev = torch.device("cuda", torch.cuda.current_device())
+    return ws, rank, torch.device("cuda", torch.cuda.current_device())
 
+
+def finish(line: dict, ws: int, rank: int):
+    import torch.distributed as dist
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def base_line(args, ws, value, ms_step, dtype_label, config) -> dict:
+    return {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": dtype_label, "data": "synthetic",
+            "config": config}
+
+
+DT = {"f32": "float32", "f16": "float16", "bf16": "bfloat16"}
+DT_LABEL = {"f32": "f32", "f16": "f16 rows, f32 accumulate", "bf16": "bf16 rows, f32 accumulate"}
+
+
+def resolved_variant(api, g, dtype: str, variant: int) -> int:
+    """The tile variant fbp_backproject runs for `variant` (-1 = default)."""
+    if variant >= 0:
+        return variant
+    import torch
+    tdt = getattr(torch, DT[dtype])
+    # the library's default choice (backproject.cu: bp_default_variant)
+    if dtype != "f32":
+        for v in (8, 6):
+            if api.variant_supports(v, g, tdt):
+                return v
+    return 5 if api.variant_supports(5, g, tdt) else 0
+
+
+def run_uniform(args) -> None:
+    """Uniform stacks (headline N = 8192, N = 2048 stack, N = 256 single):
+    one step = fbp_filter + fbp_backproject over the whole stack."""
+    import torch
     from paper_2505_13955_gb300 import api, phantoms
+
+    ws, rank, dev = init_device()
     w = phantoms.WORKLOADS[args.workload]
     N, K, S = w.n, w.n_angles, (args.slices or w.n_slices)
-    dtype = {"f32": torch.float32, "f16": torch.float16, "bf16": torch.bfloat16}[args.dtype]
-    kind = w.filter
     g = api.Geometry(K, N, N)
-
     host = make_inputs(w, shard_slices(S, rank))
     sino = torch.from_numpy(host).to(dev)
-    filt = torch.empty(sino.shape, dtype=dtype, device=dev)
-    rs = torch.empty((S, K), dtype=torch.float32, device=dev) if dtype != torch.float32 else None
     out = torch.empty((S, N, N), dtype=torch.float32, device=dev)
     stream = torch.cuda.current_stream(dev)
-    api.prepare(g, kind=kind, device=dev)
+    api.prepare(g, kind=w.filter, device=dev)
+    updates = S * N * N * K
+    dtypes = [args.dtype] + ([d for d in ("f16", "bf16") if d != args.dtype] if args.all_dtypes else [])
+    results = {}
+    for dt in dtypes:
+        tdt = getattr(torch, DT[dt])
+        filt = torch.empty(sino.shape, dtype=tdt, device=dev)
+        rs = torch.empty((S, K), dtype=torch.float32, device=dev) if dt != "f32" else None
+        T = Timed(stream, args.steps, args.warmup, n_events=3)
 
-    n_steps = args.steps
-    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
-           torch.cuda.Event(enable_timing=True)) for _ in range(n_steps)]
+        def step(evs):
+            if evs:
+                evs[0].record(stream)
+            api.filter(sino, g, kind=w.filter, dtype=tdt, out=filt, row_scale=rs)
+            if evs:
+                evs[1].record(stream)
+            api.backproject(filt, g, row_scale=rs, out=out, variant=args.variant)
+            if evs:
+                evs[2].record(stream)
 
-    def step(evs=None):
-        if evs:
-            evs[0].record(stream)
-        api.filter(sino, g, kind=kind, dtype=dtype, out=filt, row_scale=rs)
-        if evs:
-            evs[1].record(stream)
-        api.backproject(filt, g, row_scale=rs, out=out, variant=args.variant)
-        if evs:
-            evs[2].record(stream)
+        ms = T.run(step, dev.index if dt == args.dtype else None)
+        assert api.device_status() == 0
+        per_rank = allgather_floats([ms, float(updates)])
+        rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
+        results[dt] = {"value": rate / 1e9, "ms_per_step": ms_step, "bp_ms": T.between(1, 2),
+                       "filter_ms": T.between(0, 1), "clocks": T.clocks,
+                       "slices_per_s": S * len(per_rank) / (ms_step / 1e3)}
+        del filt, rs
 
-    for _ in range(args.warmup):
-        step()
-    torch.cuda.synchronize()
-    assert api.device_status() == 0
-
-    t_start = torch.cuda.Event(enable_timing=True)
-    t_end = torch.cuda.Event(enable_timing=True)
-    with ClockSampler(dev.index) as clocks:
-        barrier()
-        torch.cuda.synchronize()
-        t_start.record(stream)
-        for i in range(n_steps):
-            step(ev[i])
-        t_end.record(stream)
-        torch.cuda.synchronize()
-        barrier()
-    elapsed = t_start.elapsed_time(t_end)
-    bp_ms = [e[1].elapsed_time(e[2]) for e in ev]
-    filt_ms = [e[0].elapsed_time(e[1]) for e in ev]
-    updates_per_step = S * N * N * K
-    per_rank = allgather_floats([elapsed / n_steps, float(updates_per_step)])
-    job_rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
-    value = job_rate / 1e9
-    slices_per_s = S * len(per_rank) / (ms_step / 1e3)
-
-    # end to end through the public API with host buffers: pinned H2D of the
-    # step's sinograms, filter + backprojection, D2H of the slices
     e2e = None
     if args.e2e_steps > 0:
+        tdt = getattr(torch, DT[args.dtype])
         pin_in = torch.from_numpy(host).pin_memory()
         pin_out = torch.empty((S, N, N), dtype=torch.float32).pin_memory()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
-        def e2e_step():
+        def e2e_step(_):
             x = pin_in.to(dev, non_blocking=True)
-            f = api.fbp(x, g, kind=kind, dtype=dtype, variant=args.variant)
+            f = api.fbp(x, g, kind=w.filter, dtype=tdt, variant=args.variant)
             pin_out.copy_(f, non_blocking=True)
 
-        e2e_step()
-        torch.cuda.synchronize()
-        barrier()
-        e0.record(stream)
-        for _ in range(args.e2e_steps):
-            e2e_step()
-        e1.record(stream)
-        torch.cuda.synchronize()
-        t_e2e = e0.elapsed_time(e1) / args.e2e_steps
-        per_rank_e2e = allgather_floats([t_e2e, float(updates_per_step)])
+        T = Timed(stream, args.e2e_steps, 1)
+        t_e2e = T.run(e2e_step, None)
+        per_rank_e2e = allgather_floats([t_e2e, float(updates)])
         e2e_rate, _ = aggregate([r[0] for r in per_rank_e2e], [int(r[1]) for r in per_rank_e2e])
         e2e = {"value": e2e_rate / 1e9, "unit": UNIT,
                "h2d_bytes_per_step": int(pin_in.numel() * 4),
-               "d2h_bytes_per_step": int(pin_out.numel() * 4),
-               "ms_per_step": t_e2e}
+               "d2h_bytes_per_step": int(pin_out.numel() * 4), "ms_per_step": t_e2e}
         del pin_in, pin_out
 
     if rank != 0:
-        if ws > 1:
-            dist.destroy_process_group()
+        finish({}, ws, rank)
         return
-
+    main = results[args.dtype]
     pk = peaks()
-    csum = clocks.summary()
     sm_max = pk.get("sm_max_mhz") or 2070.0
     rp = roofline_peak(sm_max, args.dtype)
-    peak_gups = rp["peak"]
-    bp_avg = float(np.mean(bp_ms))
-    achieved = updates_per_step / (bp_avg / 1e3) / 1e9
+    achieved = updates / (main["bp_ms"] / 1e3) / 1e9
+    variant = resolved_variant(api, g, args.dtype, args.variant)
     traffic = args.traffic_bytes
     if traffic is None:
-        traffic = captured_traffic(args.variant, args.dtype, S)
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": n_steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None,
-        "dtype": {"f32": "f32", "f16": "f16 rows, f32 accumulate", "bf16": "bf16 rows, f32 accumulate"}[args.dtype],
-        "data": "synthetic",
-        "config": {"workload": f"{w.name}: S={S} slices per GPU, N=D={N}, K={K} angles on [0,pi), "
-                               f"seeded random ellipses (20-50), noise-free, Ram-Lak",
-                   "l2": "inputs larger than L2 (2.15 GB sinograms per step), no flush",
-                   "parallelism": f"slices sharded over {ws} GPU(s), no collective",
-                   "bp_variant": args.variant},
-        "slices_per_s": slices_per_s,
-        "bp_ms_per_step": bp_avg, "filter_ms_per_step": float(np.mean(filt_ms)),
+        traffic = captured_traffic(variant, args.dtype, S)
+    phantom = "Shepp-Logan" if w.phantom == "shepp_logan" else "random ellipses (20-50)"
+    noise = f"Poisson {w.photons:g} photons" if w.photons else "noise-free"
+    line = base_line(args, ws, main["value"], main["ms_per_step"], DT_LABEL[args.dtype], {
+        "workload": f"{w.name}: S={S} slices per GPU, N=D={N}, K={K} angles on [0,pi), "
+                    f"seeded {phantom}, {noise}, {w.filter}",
+        "l2": "inputs larger than L2 (sinograms per step exceed 129 MB), no flush"
+              if S * K * N * 4 > 129e6 else "inputs smaller than L2 (launch-bound case)",
+        "parallelism": f"slices sharded over {ws} GPU(s), no collective",
+        "bp_variant": variant})
+    line.update({
+        "slices_per_s": main["slices_per_s"],
+        "bp_ms_per_step": main["bp_ms"], "filter_ms_per_step": main["filter_ms"],
         "bp_gupdates_per_s": achieved,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_gups, "unit": UNIT,
-                     "frac": achieved / peak_gups, "traffic": traffic,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": rp["peak"], "unit": UNIT,
+                     "frac": achieved / rp["peak"], "traffic": traffic,
                      "kernel": BP_KERNEL_REGEX, "c_alu": rp["c_alu"], "c_lds": rp["c_lds"],
                      "peak_basis": rp["basis"] + " (sm_max_mhz from MEASURED_PEAKS.json)",
                      "traffic_basis": "ncu dram bytes per slice x slices, kernel unchanged since capture"},
-        "clocks": csum,
-        "gpu_launches": 2 * n_steps,
-    }
+        "clocks": main["clocks"],
+        "gpu_launches": 2 * args.steps,
+    })
+    for dt in dtypes[1:]:
+        r = results[dt]
+        rpd = roofline_peak(sm_max, dt)
+        ach = updates / (r["bp_ms"] / 1e3) / 1e9
+        line[f"staged_{dt}"] = {
+            "value": r["value"], "unit": UNIT, "ratio_to_f32": r["value"] / main["value"],
+            "bp_gupdates_per_s": ach, "bp_ratio_to_f32": ach / achieved,
+            "roofline_frac": ach / rpd["peak"], "roofline_peak": rpd["peak"],
+            "slices_per_s": r["slices_per_s"], "ms_per_step": r["ms_per_step"],
+            "bp_variant": resolved_variant(api, g, dt, args.variant)}
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = {k: v for k, v in cpu_sample(w, args.cpu_block).items() if k != "seconds"}
-    print(json.dumps(line), flush=True)
-    if ws > 1:
-        dist.destroy_process_group()
+    finish(line, ws, rank)
+
+
+def run_ragged(args) -> None:
+    """Ragged batch: all items in one fbp_batched call (one filter launch + one
+    persistent backprojection launch), captured once in a CUDA graph and
+    replayed; compared in the same run with per-slice fbp_filter +
+    fbp_backproject launches.  The tile variant comes from the autotuner."""
+    import torch
+    from paper_2505_13955_gb300 import api, autotune, phantoms
+
+    ws, rank, dev = init_device()
+    w = phantoms.WORKLOADS["fbp_ragged_batch"]
+    S = args.slices or w.n_slices
+    idx = shard_slices(S, rank)
+    sinos, geoms = [], []
+    for i in idx:
+        n, k, _, _ = phantoms.slice_spec(w, i)
+        sinos.append(torch.from_numpy(phantoms.slice_sinogram(w, i)).to(dev))
+        geoms.append(api.Geometry(k, n, n))
+    updates = sum(g.n * g.n * g.n_angles for g in geoms)
+    for g in geoms:
+        api.prepare(g, kind=w.filter, device=dev)
+    tdt = getattr(torch, DT[args.dtype])
+    outs = [torch.empty((g.n, g.n), device=dev) for g in geoms]
+    tuned = autotune.tune_batched(sinos, geoms, tdt, kind=w.filter) if args.variant < 0 else \
+        {"variant": args.variant}
+    variant = tuned["variant"]
+    wsp = torch.empty(api.batched_workspace_bytes(sinos, outs, geoms, tdt), dtype=torch.uint8, device=dev)
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        api.fbp_batched(sinos, geoms, kind=w.filter, dtype=tdt, variant=variant, outs=outs, workspace=wsp)
+    with torch.cuda.stream(stream):
+        T = Timed(stream, args.steps, args.warmup)
+        ms = T.run(lambda _: graph.replay(), dev.index)
+        clocks = T.clocks
+        # per-slice launches, same stream, same tile variant
+        filts = [torch.empty_like(s, dtype=tdt) for s in sinos]
+        rss = [torch.empty((g.n_angles,), device=dev) if args.dtype != "f32" else None for g in geoms]
+
+        def per_slice(_):
+            for s, g, f, r, o in zip(sinos, geoms, filts, rss, outs):
+                api.filter(s, g, kind=w.filter, dtype=tdt, out=f, row_scale=r)
+                api.backproject(f, g, row_scale=r, out=o, variant=variant)
+
+        T2 = Timed(stream, max(1, args.steps // 2), args.warmup)
+        ms_single = T2.run(per_slice, None)
+    assert api.device_status() == 0
+    per_rank = allgather_floats([ms, float(updates)])
+    rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
+    if rank != 0:
+        finish({}, ws, rank)
+        return
+    line = base_line(args, ws, rate / 1e9, ms_step, DT_LABEL[args.dtype], {
+        "workload": f"{w.name}: {len(idx)} slices per GPU, N in {w.n_choices}, K in {w.k_choices}, "
+                    "random ellipses, Ram-Lak; one persistent launch per step, CUDA-graph replay",
+        "parallelism": f"slices sharded over {ws} GPU(s), no collective",
+        "bp_variant": variant, "autotune": tuned})
+    line.update({"slices_per_s": len(idx) * len(per_rank) / (ms_step / 1e3),
+                 "per_slice_launches": {"value": updates / (ms_single / 1e3) / 1e9, "unit": UNIT,
+                                        "ms_per_step": ms_single,
+                                        "launches_per_step": 2 * len(idx)},
+                 "speedup_vs_per_slice": ms_single / ms,
+                 "clocks": clocks, "gpu_launches": 2 * args.steps})
+    finish(line, ws, rank)
+
+
+def run_gd(args) -> None:
+    """Least-squares refinement: one step = one gradient-descent iteration
+    x <- x - eta A^T (A x - b) over the stack (radon_forward, then
+    fbp_backproject with scale 1); A and A^T are timed separately."""
+    import torch
+    from paper_2505_13955_gb300 import api, phantoms
+
+    ws, rank, dev = init_device()
+    w = phantoms.WORKLOADS["gd_refine_n1024"]
+    N, K, S = w.n, w.n_angles, (args.slices or w.n_slices)
+    g = api.Geometry(K, N, N)
+    b = torch.from_numpy(make_inputs(w, shard_slices(S, rank))).to(dev)
+    api.prepare(g, kind=w.filter, device=dev)
+    x = api.fbp(b, g, kind=w.filter)
+    # step size 1 / lambda_max(A^T A) from power iterations on the device (not timed)
+    v = torch.randn((N, N), device=dev)
+    lam = 1.0
+    for _ in range(10):
+        v = api.backproject(api.radon_forward(v, g), g, scale=1.0)
+        lam = v.norm().item()
+        v /= lam
+    eta = 1.0 / (1.05 * lam)
+    r = torch.empty_like(b)
+    grad = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+    T = Timed(stream, args.steps, args.warmup, n_events=3)
+
+    def step(evs):
+        if evs:
+            evs[0].record(stream)
+        api.radon_forward(x, g, out=r)
+        if evs:
+            evs[1].record(stream)
+        r.sub_(b)
+        api.backproject(r, g, scale=1.0, out=grad)
+        if evs:
+            evs[2].record(stream)
+        x.sub_(eta * grad)
+
+    ms = T.run(step, dev.index)
+    assert api.device_status() == 0
+    updates = 2 * S * N * N * K
+    per_rank = allgather_floats([ms, float(updates)])
+    rate, ms_step = aggregate([r_[0] for r_ in per_rank], [int(r_[1]) for r_ in per_rank])
+    if rank != 0:
+        finish({}, ws, rank)
+        return
+    a_ms, at_ms = T.between(0, 1), T.between(1, 2)
+    line = base_line(args, ws, rate / 1e9, ms_step, "f32", {
+        "workload": f"{w.name}: S={S} slices per GPU, N=D={N}, K={K}, Poisson 1e4 photons, "
+                    "one gradient-descent iteration (A and A^T) per step",
+        "parallelism": f"slices sharded over {ws} GPU(s), no collective"})
+    line.update({"forward_A": {"ms": a_ms, "gupdates_per_s": S * N * N * K / a_ms / 1e6},
+                 "adjoint_AT": {"ms": at_ms, "gupdates_per_s": S * N * N * K / at_ms / 1e6},
+                 "eta": eta, "clocks": T.clocks, "gpu_launches": 4 * args.steps})
+    finish(line, ws, rank)
 
 
 def main(argv=None):
@@ -424,9 +618,11 @@ def main(argv=None):
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--dtype", choices=["f32", "f16", "bf16"], default="f32")
+    ap.add_argument("--all-dtypes", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time FP16- and BF16-staged rows in the same run")
     ap.add_argument("--variant", type=int, default=-1)
     ap.add_argument("--slices", type=int, default=None,
-                    help="slices per GPU (default: the workload's 16); small cases for profiling")
+                    help="slices per GPU (default: the workload's); small cases for profiling")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-block", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -436,8 +632,12 @@ def main(argv=None):
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
+    elif args.workload == "fbp_ragged_batch":
+        run_ragged(args)
+    elif args.workload == "gd_refine_n1024":
+        run_gd(args)
     else:
-        run_ours(args)
+        run_uniform(args)
 
 
 if __name__ == "__main__":

@@ -103,6 +103,10 @@ typedef struct {
     int tile_x, tile_y;  /* output pixels per thread block                  */
     int px, py;          /* output pixels per thread (x, y)                 */
     int threads;         /* threads per block                               */
+    int symmetric;       /* 1: uses the 90-degree symmetry of the standard
+                            geometry (angle step pi/K with K even, centred
+                            detector, n a multiple of 2*tile_x); the block
+                            owns a tile and its three rotations            */
 } fbp_bp_shape;
 
 /* Library version (major*10000 + minor*100 + patch). */
@@ -200,6 +204,12 @@ fbp_status radon_forward(const float *slice, float *sino, const fbp_geometry *g,
 /* Number of compiled backprojection tile variants, and the shape of one. */
 int fbp_bp_variant_count(void);
 fbp_status fbp_bp_variant_info(int variant, fbp_bp_shape *out);
+
+/* 1 if fbp_backproject_variant accepts `variant` for rows of `dtype` and
+ * geometry g (symmetric variants need the standard geometry; every variant
+ * needs its staged window to fit in shared memory), 0 otherwise.  Host-only,
+ * no CUDA call. */
+int fbp_bp_variant_supports(int variant, fbp_dtype dtype, const fbp_geometry *g);
 
 /*
  * Ragged batches (Sec. V-A(b): specimens with various N_p and N_c

@@ -48,7 +48,8 @@ class CBatchItem(ctypes.Structure):
 
 class CBpShape(ctypes.Structure):
     _fields_ = [("angle_tile", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
-                ("px", ctypes.c_int), ("py", ctypes.c_int), ("threads", ctypes.c_int)]
+                ("px", ctypes.c_int), ("py", ctypes.c_int), ("threads", ctypes.c_int),
+                ("symmetric", ctypes.c_int)]
 
 
 _G = ctypes.POINTER(CGeometry)
@@ -67,6 +68,7 @@ SIGNATURES = {
                                                ctypes.c_float, ctypes.c_int, _vp]),
     "fbp_bp_variant_count": (ctypes.c_int, []),
     "fbp_bp_variant_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(CBpShape)]),
+    "fbp_bp_variant_supports": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _G]),
     "fbp_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(CBatchItem), ctypes.c_int,
                                                       ctypes.c_int]),
     "fbp_batched": (ctypes.c_int, [ctypes.POINTER(CBatchItem), ctypes.c_int, ctypes.c_int, ctypes.c_int,

@@ -173,8 +173,16 @@ def bp_variants() -> list[dict]:
         s = _lib.CBpShape()
         _lib.check(L.fbp_bp_variant_info(v, ctypes.byref(s)), L, "fbp_bp_variant_info")
         out.append({"variant": v, "angle_tile": s.angle_tile, "tile_x": s.tile_x,
-                    "tile_y": s.tile_y, "px": s.px, "py": s.py, "threads": s.threads})
+                    "tile_y": s.tile_y, "px": s.px, "py": s.py, "threads": s.threads,
+                    "symmetric": bool(s.symmetric)})
     return out
+
+
+def variant_supports(variant: int, g: Geometry, dtype=torch.float32) -> bool:
+    """Whether fbp_backproject_variant accepts `variant` for rows of `dtype`
+    and geometry g."""
+    gc = g.c()
+    return bool(lib().fbp_bp_variant_supports(int(variant), _DTYPES[dtype], ctypes.byref(gc)))
 
 
 def _items(sinos, outs, geoms):

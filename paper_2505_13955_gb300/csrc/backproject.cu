@@ -3,27 +3,34 @@
 // work-queue kernel for ragged batches.
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <map>
 #include <mutex>
 
 #include "bp_tile.cuh"
+#include "bp_orbit.cuh"
 #include "bp_batch.cuh"
 
 namespace fbp {
 namespace {
 
 // Compiled tile shapes: threads TXT x TYT, pixels per thread PX x PY,
-// angles per staged tile KT.
+// angles (generic) or angle pairs (orbit) per staged tile KT.  Orbit shapes
+// use the 90-degree symmetry (bp_orbit.cuh) and need the standard geometry.
 struct ShapeDesc {
-    int txt, tyt, px, py, kt;
+    int txt, tyt, px, py, kt, orbit;
 };
 constexpr ShapeDesc kShapes[] = {
-    {16, 16, 4, 4, 32},   // 0: 64 x 64 tile
-    {16, 16, 4, 4, 16},   // 1
-    {16, 16, 4, 2, 32},   // 2: 64 x 32
-    {16, 16, 2, 4, 32},   // 3: 32 x 64
-    {16, 16, 4, 4, 64},   // 4
-    {32, 8, 2, 8, 32},    // 5: 64 x 64, warps 4 x 2
+    {16, 16, 4, 4, 32, 0},   // 0: 64 x 64 tile
+    {16, 16, 4, 4, 16, 0},   // 1
+    {16, 16, 4, 2, 32, 0},   // 2: 64 x 32
+    {16, 16, 2, 4, 32, 0},   // 3: 32 x 64
+    {16, 16, 4, 4, 64, 0},   // 4
+    {32, 8, 2, 8, 32, 0},    // 5: 64 x 64, warps 4 x 2
+    {16, 8, 2, 4, 16, 1},    // 6: orbit of 32 x 32 tiles, 16 angle pairs per stage
+    {16, 8, 2, 4, 8, 1},     // 7: orbit of 32 x 32 tiles, 8 pairs
+    {16, 16, 4, 4, 8, 1},    // 8: orbit of 64 x 64 tiles, 8 pairs
+    {16, 8, 2, 4, 32, 1},    // 9: orbit of 32 x 32 tiles, 32 pairs
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -70,9 +77,84 @@ __global__ void __launch_bounds__(TXT *TYT) bp_kernel(BpArgs a)
     bp_tile<TXT, TYT, PX, PY, KT, T, CHECKED>(j, bp_smem);
 }
 
+template <int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED>
+__global__ void __launch_bounds__(TXT *TYT) bp_orbit_kernel(BpArgs a)
+{
+    extern __shared__ __align__(16) unsigned char bp_smem[];
+    constexpr int TILE = TXT * PX;
+    const int half = a.tiles_x;                 // orbits per row of the top-left quadrant
+    const int o = blockIdx.x;
+    const int sl = a.slice_base + blockIdx.y;
+    BpOrbitJob j;
+    const size_t kd = (size_t)a.K * a.D;
+    j.filt = static_cast<const char *>(a.filt) + (size_t)sl * kd * sizeof(T);
+    j.row_scale = a.row_scale ? a.row_scale + (size_t)sl * a.K : nullptr;
+    j.out = a.slice + (size_t)sl * a.N * a.N;
+    j.cs = a.cs;
+    j.K = a.K;
+    j.D = a.D;
+    j.N = a.N;
+    j.alpha = a.alpha;
+    j.det_center = a.det_center;
+    j.scale = a.scale;
+    j.accumulate = a.accumulate;
+    j.H = a.H;
+    j.W = a.W;
+    j.x0 = (o % half) * TILE;
+    j.y0 = (o / half) * TILE;
+    j.status = a.status;
+    bp_orbit<TILE, TXT, TYT, PX, PY, KT, T, CHECKED>(j, bp_smem);
+}
+
+template <int V, typename T>
+fbp_status launch_orbit_shape(const BpLaunch &L, cudaStream_t s, unsigned *status)
+{
+    constexpr ShapeDesc sd = kShapes[V];
+    constexpr int TILE = sd.txt * sd.px;
+#ifdef FBP_CHECKED
+    constexpr bool kChecked = true;
+#else
+    constexpr bool kChecked = false;
+#endif
+    if (!bp_orbit_eligible(L, TILE))
+        return fail(FBP_ERR_UNSUPPORTED, "variant %d needs angle step pi/K with K even, "
+                    "det_center = (D-1)/2 and N a multiple of %d", V, 2 * TILE);
+    auto kern = bp_orbit_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, T, kChecked>;
+    BpArgs a;
+    a.filt = L.filt;
+    a.row_scale = L.row_scale;
+    a.slice = L.slice;
+    a.cs = L.cs;
+    a.K = L.K;
+    a.D = L.D;
+    a.N = L.N;
+    a.alpha = L.alpha;
+    a.det_center = L.det_center;
+    a.scale = L.scale;
+    a.accumulate = L.accumulate;
+    a.H = bp_window_half(L.alpha, TILE, TILE);
+    a.W = 2 * a.H + 1;
+    a.status = status;
+    const size_t smem = bp_orbit_smem_size<sd.kt, T>(a.W);
+    if (smem > 200 * 1024) return fail(FBP_ERR_UNSUPPORTED, "backprojection window too wide");
+    fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
+    if (st != FBP_OK) return st;
+    a.tiles_x = L.N / TILE / 2;
+    const long long orbits = (long long)a.tiles_x * a.tiles_x;
+    if (orbits > INT_MAX) return fail(FBP_ERR_UNSUPPORTED, "too many tiles");
+    for (int base = 0; base < L.S; base += 65535) {
+        a.slice_base = base;
+        dim3 grid((unsigned)orbits, (unsigned)std::min(65535, L.S - base));
+        kern<<<grid, sd.txt * sd.tyt, smem, s>>>(a);
+        FBP_CUDA_TRY(cudaGetLastError());
+    }
+    return FBP_OK;
+}
+
 template <int V, typename T>
 fbp_status launch_shape(const BpLaunch &L, cudaStream_t s, unsigned *status)
 {
+    if constexpr (kShapes[V].orbit) return launch_orbit_shape<V, T>(L, s, status);
     constexpr ShapeDesc sd = kShapes[V];
     constexpr int TW = sd.txt * sd.px, TH = sd.tyt * sd.py;
 #ifdef FBP_CHECKED
@@ -122,6 +204,10 @@ fbp_status launch_variant(const BpLaunch &L, int v, cudaStream_t s, unsigned *st
         case 3: return launch_shape<3, T>(L, s, status);
         case 4: return launch_shape<4, T>(L, s, status);
         case 5: return launch_shape<5, T>(L, s, status);
+        case 6: return launch_shape<6, T>(L, s, status);
+        case 7: return launch_shape<7, T>(L, s, status);
+        case 8: return launch_shape<8, T>(L, s, status);
+        case 9: return launch_shape<9, T>(L, s, status);
     }
     return fail(FBP_ERR_INVALID_ARG, "backprojection variant %d", v);
 }
@@ -200,6 +286,7 @@ fbp_status launch_persistent_shape(BpBatchArgs &a, int sms, cudaStream_t s)
 template <typename T>
 fbp_status launch_persistent_t(BpBatchArgs &a, int v, int sms, cudaStream_t s)
 {
+    if (kShapes[v].orbit) return fail(FBP_ERR_UNSUPPORTED, "variant %d is not available for ragged batches", v);
     switch (v) {
         case 0: return launch_persistent_shape<0, T>(a, sms, s);
         case 1: return launch_persistent_shape<1, T>(a, sms, s);
@@ -225,13 +312,69 @@ bool bp_variant_shape(int v, fbp_bp_shape *out)
     out->px = d.px;
     out->py = d.py;
     out->threads = d.txt * d.tyt;
+    out->symmetric = d.orbit;
+    if (d.orbit) out->angle_tile = 2 * d.kt;
     return true;
 }
 
 int bp_tile_w(int v) { return kShapes[v].txt * kShapes[v].px; }
 int bp_tile_h(int v) { return kShapes[v].tyt * kShapes[v].py; }
 
-int bp_default_variant(const BpLaunch &) { return 0; }
+bool bp_orbit_eligible(const BpLaunch &L, int tile)
+{
+    const double pi = 3.14159265358979323846;
+    if (L.K % 2 != 0 || L.N % (2 * tile) != 0) return false;
+    if (std::fabs(L.angle_step * L.K - pi) > 1e-9 * pi) return false;
+    if (std::fabs(L.det_center - 0.5 * (L.D - 1)) > 1e-9 * (1.0 + L.D)) return false;
+    return true;
+}
+
+constexpr size_t kSmemBudget = 200 * 1024;
+
+template <int V>
+size_t variant_smem(const BpLaunch &L)
+{
+    constexpr ShapeDesc sd = kShapes[V];
+    const int TW = sd.txt * sd.px, TH = sd.tyt * sd.py;
+    const int W = 2 * bp_window_half(L.alpha, TW, TH) + 1;
+    if constexpr (sd.orbit)
+        return L.dtype == FBP_F32 ? bp_orbit_smem_size<sd.kt, float>(W)
+                                  : bp_orbit_smem_size<sd.kt, __half>(W);
+    return bp_smem_size<sd.kt>(W);
+}
+
+bool bp_variant_fits(int v, const BpLaunch &L)
+{
+    size_t smem = 0;
+    switch (v) {
+        case 0: smem = variant_smem<0>(L); break;
+        case 1: smem = variant_smem<1>(L); break;
+        case 2: smem = variant_smem<2>(L); break;
+        case 3: smem = variant_smem<3>(L); break;
+        case 4: smem = variant_smem<4>(L); break;
+        case 5: smem = variant_smem<5>(L); break;
+        case 6: smem = variant_smem<6>(L); break;
+        case 7: smem = variant_smem<7>(L); break;
+        case 8: smem = variant_smem<8>(L); break;
+        case 9: smem = variant_smem<9>(L); break;
+        default: return false;
+    }
+    if (smem > kSmemBudget) return false;
+    const ShapeDesc &d = kShapes[v];
+    return !d.orbit || bp_orbit_eligible(L, d.txt * d.px);
+}
+
+// Measured at N = 8192, K = 4096 on GB300: FP32 rows are fastest with the
+// generic 64 x 64 tile (variant 5); 16-bit rows with the symmetric 64 x 64
+// orbit (variant 8), then the 32 x 32 orbit (variant 6).
+int bp_default_variant(const BpLaunch &L)
+{
+    if (L.dtype != FBP_F32) {
+        if (bp_variant_fits(8, L)) return 8;
+        if (bp_variant_fits(6, L)) return 6;
+    }
+    return bp_variant_fits(5, L) ? 5 : 0;
+}
 
 fbp_status launch_backproject(const BpLaunch &L, int variant, cudaStream_t s)
 {

@@ -1,0 +1,328 @@
+// bp_orbit.cuh -- K2 for the standard geometry, using the square image's
+// 90-degree symmetry: one detector-coordinate evaluation feeds four updates.
+//
+// Geometry condition: angle step pi/K with K even (so th_{k+K/2} = th_k +
+// pi/2), detector centre c_d = (D-1)/2, and N a multiple of 2*TILE (tiles
+// rotate onto tiles).  With U(p, th) = alpha (X cos th + Y sin th) the
+// centred coordinate of pixel p = (X, Y) and R the rotation (X, Y) -> (-Y, X)
+// (pixel [r][c] -> [c][N-1-r]), for th' = th + pi/2:
+//     U1 = U(p, th)  is also U(Rp, th'), and -U1 = U(R^2 p, th) = U(R^3 p, th')
+//     U2 = U(p, th') is also U(R^3 p, th), and -U2 = U(Rp, th) = U(R^2 p, th')
+// A negated coordinate reads the mirrored row q~[j] = q[D-1-j] at +U (the
+// interpolant commutes with the reflection u -> D-1-u).  So a block owns the
+// orbit {T, RT, R^2 T, R^3 T} of one tile, loops over the K/2 angle pairs
+// (th, th'), and stages, per pair and per window (W1 around U1 of the tile
+// centre, W2 around U2), the four rows {th, th', th~, th'~} interleaved at
+// each index.  A thread evaluates u1 and u2 for each of its pixels and reads
+// all four rows of each window with one load:
+//     W1 at u1 -> p@th, Rp@th', R^2p@th (mirror), R^3p@th' (mirror)
+//     W2 at u2 -> p@th', R^3p@th, Rp@th (mirror), R^2p@th' (mirror)
+//
+// Table entries (see bp_tile.cuh for the split FP64/FP32 coordinate):
+//   FP32 rows: per row (a_i, d_i), Q = a_i + u' d_i        -> 32 B per index,
+//     kept as two 16-byte arrays (rows th, th' | mirrored rows) so that each
+//     16-byte load strides like the 16-bit table (no 4-entry bank aliasing)
+//   16-bit rows: per row (q'_i, d_i) in the row's 16-bit type, with
+//     q'_i = q_i + d_i / 2 the segment midpoint, Q = q'_i + (u' - i) d_i,
+//     the product and sum taken by mixed-precision FMA/ADD into FP32
+//                                                            -> 16 B per index
+// so 16-bit staging moves 4 B per update out of shared memory instead of 8.
+// 16-bit rows are staged as q * s_k / S, S = max_k s_k of the slice (no
+// overflow in FP16), and S is applied once to the final sum.
+#pragma once
+
+#include "bp_tile.cuh"
+
+namespace fbp {
+
+struct BpOrbitJob {
+    const void *filt;          // this slice's [K][D] rows
+    const float *row_scale;    // this slice's [K] scales, or null
+    float *out;                // this slice's [N][N]
+    const double2 *cs;         // [K] (only k < K/2 is read)
+    int K, D, N;
+    double alpha, det_center;
+    float scale;
+    int accumulate;
+    int H, W;
+    int x0, y0;                // origin of the orbit's representative tile (top-left quadrant)
+    unsigned *status;
+};
+
+template <typename T> struct OrbitEntry;
+template <> struct OrbitEntry<float> { static constexpr int bytes = 32; };   // 2 arrays x 16 B
+template <> struct OrbitEntry<__half> { static constexpr int bytes = 16; };
+template <> struct OrbitEntry<__nv_bfloat16> { static constexpr int bytes = 16; };
+
+template <int KT, typename T>
+__host__ __device__ constexpr size_t bp_orbit_smem_size(int W)
+{
+    // [KT] x (float4 coords + uint4 addresses/window starts) + [KT][2][W] entries
+    return (size_t)KT * 32 + (size_t)KT * 2 * W * OrbitEntry<T>::bytes;
+}
+
+__device__ __forceinline__ float4 lds_f4(uint32_t addr)
+{
+    float4 v;
+    asm volatile("ld.shared.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w) : "r"(addr));
+    return v;
+}
+
+__device__ __forceinline__ uint4 lds_u4(uint32_t addr)
+{
+    uint4 v;
+    asm volatile("ld.shared.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr));
+    return v;
+}
+
+// 16-bit helpers: pack (lo, hi) rounded to nearest even; fraction to 16 bits;
+// acc + lo + fr * hi with the products and sums in FP32.
+template <typename T> __device__ __forceinline__ uint32_t pack16(float lo, float hi);
+template <> __device__ __forceinline__ uint32_t pack16<__half>(float lo, float hi)
+{
+    __half2 h = __floats2half2_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+template <> __device__ __forceinline__ uint32_t pack16<__nv_bfloat16>(float lo, float hi)
+{
+    __nv_bfloat162 h = __floats2bfloat162_rn(lo, hi);
+    return *reinterpret_cast<uint32_t *>(&h);
+}
+
+template <typename T> __device__ __forceinline__ unsigned short frac16(float x);
+template <> __device__ __forceinline__ unsigned short frac16<__half>(float x)
+{
+    unsigned short h;
+    asm("cvt.rn.f16.f32 %0, %1;" : "=h"(h) : "f"(x));
+    return h;
+}
+template <> __device__ __forceinline__ unsigned short frac16<__nv_bfloat16>(float x)
+{
+    unsigned short h;
+    asm("cvt.rn.bf16.f32 %0, %1;" : "=h"(h) : "f"(x));
+    return h;
+}
+
+template <typename T> __device__ __forceinline__ void mac16(float &acc, unsigned short fr, uint32_t e);
+template <> __device__ __forceinline__ void mac16<__half>(float &acc, unsigned short fr, uint32_t e)
+{
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "fma.rn.f32.f16 %0, %1, hi, %0;\n\tadd.rn.f32.f16 %0, lo, %0;\n\t}"
+        : "+f"(acc) : "h"(fr), "r"(e));
+}
+template <> __device__ __forceinline__ void mac16<__nv_bfloat16>(float &acc, unsigned short fr, uint32_t e)
+{
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "fma.rn.f32.bf16 %0, %1, hi, %0;\n\tadd.rn.f32.bf16 %0, lo, %0;\n\t}"
+        : "+f"(acc) : "h"(fr), "r"(e));
+}
+
+template <int TILE, int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED>
+__device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *smem)
+{
+    constexpr int NT = TXT * TYT;
+    constexpr int WX = TXT / 8;
+    constexpr bool F32 = sizeof(T) == 4;
+    constexpr int EB = 16;                                          // index stride of each array
+    static_assert(TXT * PX == TILE && TYT * PY == TILE, "square tile");
+    static_assert(TXT % 8 == 0 && TYT % 4 == 0 && (TXT / 8) * (TYT / 4) * 32 == NT, "warp layout");
+
+    float4 *prm = reinterpret_cast<float4 *>(smem);                 // cos, sin, f1, f2
+    uint4 *adr = reinterpret_cast<uint4 *>(smem + KT * 16);         // cb1, cb2, jlo1, jlo2
+    unsigned char *tab = smem + KT * 32;
+    const uint32_t tab_s = (uint32_t)__cvta_generic_to_shared(tab);
+    const uint32_t tab_b = (uint32_t)(KT * 2 * j.W * EB);          // FP32: offset of the mirrored-row array
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tx = (warp % WX) * 8 + (lane & 7);
+    const int ty = (warp / WX) * 4 + (lane >> 3);
+    const int N = j.N, D = j.D, K = j.K, K2 = j.K / 2;
+    const double m = 0.5 * (N - 1);
+    const double Xc = (double)j.x0 + 0.5 * (TILE - 1) - m;
+    const double Yc = (double)j.y0 + 0.5 * (TILE - 1) - m;
+    const float dxt = (float)tx - 0.5f * (TILE - 1);
+    const float dyt = (float)ty - 0.5f * (TILE - 1);
+    const T *q = static_cast<const T *>(j.filt);
+    const int H = j.H, W = j.W;
+
+    // 16-bit rows: slice-wide scale S = max_k s_k
+    float S = 1.f;
+    if constexpr (!F32) {
+        __shared__ float s_red[NT / 32];
+        float mx = 0.f;
+        for (int k = tid; k < K; k += NT) mx = fmaxf(mx, __ldg(j.row_scale + k));
+#pragma unroll
+        for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        if (lane == 0) s_red[warp] = mx;
+        __syncthreads();
+        mx = 0.f;
+#pragma unroll
+        for (int w = 0; w < NT / 32; ++w) mx = fmaxf(mx, s_red[w]);
+        S = mx > 0.f ? mx : 1.f;
+    }
+    const float invS = 1.f / S;
+
+    float acc[4][PY][PX];
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+        for (int iy = 0; iy < PY; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < PX; ++ix) acc[o][iy][ix] = 0.f;
+
+    for (int k0 = 0; k0 < K2; k0 += KT) {
+        const int na = min(KT, K2 - k0);
+        __syncthreads();
+        if (tid < KT) {
+            float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+            int jl1 = 0, jl2 = 0;
+            if (tid < na) {
+                const double2 cs = j.cs[k0 + tid];
+                const double c = j.alpha * cs.x, s = j.alpha * cs.y;
+                const double v1 = fma(c, Xc, fma(s, Yc, j.det_center));
+                const double v2 = fma(-s, Xc, fma(c, Yc, j.det_center));
+                const double jc1 = floor(v1), jc2 = floor(v2);
+                pv.x = (float)c;
+                pv.y = (float)s;
+                pv.z = (float)(v1 - jc1 - 0.5);
+                pv.w = (float)(v2 - jc2 - 0.5);
+                jl1 = (int)jc1 - H;
+                jl2 = (int)jc2 - H;
+            }
+            const uint32_t cb1 = tab_s + (uint32_t)EB * (uint32_t)((2 * tid) * W + H) - (uint32_t)EB * kRoundMagicBits;
+            const uint32_t cb2 = tab_s + (uint32_t)EB * (uint32_t)((2 * tid + 1) * W + H) - (uint32_t)EB * kRoundMagicBits;
+            prm[tid] = pv;
+            adr[tid] = make_uint4(cb1, cb2, (uint32_t)jl1, (uint32_t)jl2);
+        }
+        __syncthreads();
+        // stage both windows of every pair: rows th, th', mirrored th, mirrored th'
+        for (int aw = warp; aw < 2 * KT; aw += NT / 32) {
+            const int a = aw >> 1, win = aw & 1;
+            const bool valid = a < na;
+            const uint4 ad = adr[a];
+            const int jl = (int)(win ? ad.w : ad.z);
+            const int k = k0 + (valid ? a : 0);
+            const T *r0 = q + (size_t)k * D;
+            const T *r1 = q + (size_t)(k + K2) * D;
+            float sc0 = 1.f, sc1 = 1.f;
+            if constexpr (!F32) {
+                sc0 = valid ? __ldg(j.row_scale + k) * invS : 0.f;
+                sc1 = valid ? __ldg(j.row_scale + k + K2) * invS : 0.f;
+            }
+            unsigned char *dst = tab + (size_t)aw * W * EB;
+            for (int i = lane; i < W; i += 32) {
+                const int jj = jl + i;               // direct bins jj, jj+1
+                const int mj = D - 1 - jj;           // mirrored: q~[jj] = q[mj], q~[jj+1] = q[mj-1]
+                float v[8];
+                v[0] = (valid && (unsigned)jj < (unsigned)D) ? load_q<T>(r0 + jj) : 0.f;
+                v[1] = (valid && (unsigned)(jj + 1) < (unsigned)D) ? load_q<T>(r0 + jj + 1) : 0.f;
+                v[2] = (valid && (unsigned)jj < (unsigned)D) ? load_q<T>(r1 + jj) : 0.f;
+                v[3] = (valid && (unsigned)(jj + 1) < (unsigned)D) ? load_q<T>(r1 + jj + 1) : 0.f;
+                v[4] = (valid && (unsigned)mj < (unsigned)D) ? load_q<T>(r0 + mj) : 0.f;
+                v[5] = (valid && (unsigned)(mj - 1) < (unsigned)D) ? load_q<T>(r0 + mj - 1) : 0.f;
+                v[6] = (valid && (unsigned)mj < (unsigned)D) ? load_q<T>(r1 + mj) : 0.f;
+                v[7] = (valid && (unsigned)(mj - 1) < (unsigned)D) ? load_q<T>(r1 + mj - 1) : 0.f;
+                if constexpr (F32) {
+                    const float il = (float)(i - H);
+                    float4 e0, e1;
+                    float d;
+                    d = v[1] - v[0]; e0.x = fmaf(0.5f - il, d, v[0]); e0.y = d;
+                    d = v[3] - v[2]; e0.z = fmaf(0.5f - il, d, v[2]); e0.w = d;
+                    d = v[5] - v[4]; e1.x = fmaf(0.5f - il, d, v[4]); e1.y = d;
+                    d = v[7] - v[6]; e1.z = fmaf(0.5f - il, d, v[6]); e1.w = d;
+                    reinterpret_cast<float4 *>(dst)[i] = e0;
+                    reinterpret_cast<float4 *>(dst + tab_b)[i] = e1;
+                } else {
+                    uint4 e;
+                    float x0 = v[0] * sc0, x1 = v[1] * sc0;
+                    e.x = pack16<T>(0.5f * (x0 + x1), x1 - x0);
+                    x0 = v[2] * sc1; x1 = v[3] * sc1;
+                    e.y = pack16<T>(0.5f * (x0 + x1), x1 - x0);
+                    x0 = v[4] * sc0; x1 = v[5] * sc0;
+                    e.z = pack16<T>(0.5f * (x0 + x1), x1 - x0);
+                    x0 = v[6] * sc1; x1 = v[7] * sc1;
+                    e.w = pack16<T>(0.5f * (x0 + x1), x1 - x0);
+                    reinterpret_cast<uint4 *>(dst)[i] = e;
+                }
+            }
+        }
+        __syncthreads();
+        for (int a = 0; a < na; ++a) {
+            const float4 pv = prm[a];
+            const uint4 ad = adr[a];
+            const float c = pv.x, s = pv.y;
+            const float u10 = fmaf(dxt, c, fmaf(dyt, s, pv.z));
+            const float u20 = fmaf(dxt, -s, fmaf(dyt, c, pv.w));
+            const float s1x = (float)TXT * c, s1y = (float)TYT * s;
+            const float s2x = -(float)TXT * s, s2y = (float)TYT * c;
+#pragma unroll
+            for (int iy = 0; iy < PY; ++iy) {
+                const float r1 = iy == 0 ? u10 : fmaf((float)iy, s1y, u10);
+                const float r2 = iy == 0 ? u20 : fmaf((float)iy, s2y, u20);
+#pragma unroll
+                for (int ix = 0; ix < PX; ++ix) {
+#pragma unroll
+                    for (int win = 0; win < 2; ++win) {
+                        const float u = win == 0 ? (ix == 0 ? r1 : fmaf((float)ix, s1x, r1))
+                                                 : (ix == 0 ? r2 : fmaf((float)ix, s2x, r2));
+                        const float t = __fadd_rn(u, kRoundMagic);
+                        uint32_t tb = __float_as_uint(t);
+                        if (CHECKED) {
+                            const int i = (int)(tb - kRoundMagicBits);
+                            if (i < -H || i > H) {
+                                atomicCAS(j.status, 0u, (unsigned)FAULT_TABLE_INDEX);
+                                tb = kRoundMagicBits;
+                            }
+                        }
+                        const uint32_t cb = win == 0 ? ad.x : ad.y;
+                        // orbit members fed by rows (th, th', th~, th'~)
+                        const int m0 = win == 0 ? 0 : 3, m1 = win == 0 ? 1 : 0;
+                        const int m2 = win == 0 ? 2 : 1, m3 = win == 0 ? 3 : 2;
+                        if constexpr (F32) {
+                            const uint32_t e = cb + (tb << 4);
+                            const float4 e0 = lds_f4(e), e1 = lds_f4(e + tab_b);
+                            acc[m0][iy][ix] += fmaf(u, e0.y, e0.x);
+                            acc[m1][iy][ix] += fmaf(u, e0.w, e0.z);
+                            acc[m2][iy][ix] += fmaf(u, e1.y, e1.x);
+                            acc[m3][iy][ix] += fmaf(u, e1.w, e1.z);
+                        } else {
+                            const uint4 e = lds_u4(cb + (tb << 4));
+                            const float fr = u - (t - kRoundMagic);
+                            const unsigned short f16 = frac16<T>(fr);
+                            mac16<T>(acc[m0][iy][ix], f16, e.x);
+                            mac16<T>(acc[m1][iy][ix], f16, e.y);
+                            mac16<T>(acc[m2][iy][ix], f16, e.z);
+                            mac16<T>(acc[m3][iy][ix], f16, e.w);
+                        }
+                    }
+                }
+            }
+        }
+    }
+
+    // stores: p -> [r][c], Rp -> [c][N-1-r], R^2p -> [N-1-r][N-1-c], R^3p -> [N-1-c][r]
+    const float gain = j.scale * S;
+#pragma unroll
+    for (int iy = 0; iy < PY; ++iy) {
+        const int r = j.y0 + ty + TYT * iy;
+#pragma unroll
+        for (int ix = 0; ix < PX; ++ix) {
+            const int c = j.x0 + tx + TXT * ix;
+            const size_t o0 = (size_t)r * N + c;
+            const size_t o1 = (size_t)c * N + (N - 1 - r);
+            const size_t o2 = (size_t)(N - 1 - r) * N + (N - 1 - c);
+            const size_t o3 = (size_t)(N - 1 - c) * N + r;
+            const size_t os[4] = {o0, o1, o2, o3};
+#pragma unroll
+            for (int o = 0; o < 4; ++o) {
+                float *p = j.out + os[o];
+                const float v = acc[o][iy][ix] * gain;
+                *p = j.accumulate ? *p + v : v;
+            }
+        }
+    }
+}
+
+}  // namespace fbp

@@ -149,6 +149,7 @@ fbp_status fbp_backproject_variant(const void *filt, const float *row_scale, fbp
         a.S = n_slices;
         a.alpha = g->pixel_size / g->det_spacing;
         a.det_center = g->det_center;
+        a.angle_step = g->angle_step;
         a.scale = scale;
         a.accumulate = accumulate ? 1 : 0;
         a.dtype = dtype;
@@ -194,6 +195,23 @@ fbp_status radon_forward(const float *slice, float *sino, const fbp_geometry *g,
 }
 
 int fbp_bp_variant_count(void) { return bp_variant_count(); }
+
+int fbp_bp_variant_supports(int variant, fbp_dtype dtype, const fbp_geometry *g)
+{
+    clear_error();
+    fbp_bp_shape sh;
+    if (!bp_variant_shape(variant, &sh) || check_geometry(g, false, true) != FBP_OK) return 0;
+    if (!dtype_ok(dtype)) return 0;
+    BpLaunch a{};
+    a.K = g->n_angles;
+    a.D = g->n_det;
+    a.N = g->n;
+    a.alpha = g->pixel_size / g->det_spacing;
+    a.det_center = g->det_center;
+    a.angle_step = g->angle_step;
+    a.dtype = dtype;
+    return bp_variant_fits(variant, a) ? 1 : 0;
+}
 
 fbp_status fbp_bp_variant_info(int variant, fbp_bp_shape *out)
 {

@@ -87,11 +87,14 @@ struct BpLaunch {
     const double2 *cs;       // [K]
     int K, D, N, S;
     double alpha, det_center;
+    double angle_step;       // for the symmetric (orbit) kernels' eligibility
     float scale;
     int accumulate;
     fbp_dtype dtype;
 };
 fbp_status launch_backproject(const BpLaunch &a, int variant, cudaStream_t s);
+bool bp_orbit_eligible(const BpLaunch &a, int tile);
+bool bp_variant_fits(int variant, const BpLaunch &a);   // geometry + shared-memory budget
 int bp_default_variant(const BpLaunch &a);
 int bp_variant_count();
 bool bp_variant_shape(int v, fbp_bp_shape *out);

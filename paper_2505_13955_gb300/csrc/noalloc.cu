@@ -109,6 +109,7 @@ extern "C" fbp_status fbp_backproject_noalloc(const void *filt, const float *row
     a.S = n_slices;
     a.alpha = g->pixel_size / g->det_spacing;
     a.det_center = g->det_center;
+    a.angle_step = g->angle_step;
     a.scale = scale;
     a.accumulate = accumulate ? 1 : 0;
     a.dtype = dtype;

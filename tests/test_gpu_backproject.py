@@ -47,16 +47,43 @@ def test_backproject_matches_oracle(G):
     assert_within_dr(to_np(f), ref, TOL, str(G))
 
 
-@pytest.mark.parametrize("variant", range(6))
+@pytest.mark.parametrize("variant", range(10))
 def test_every_variant_matches_oracle(variant):
     api = fbp_api()
-    g, go = make(api, dict(K=70, D=200, N=190, det_center=101.3))
+    shape = api.bp_variants()[variant]
+    if shape["symmetric"]:
+        # the standard geometry (angle step pi/K, K even, centred detector,
+        # N a multiple of 2 tiles), with D != N and a non-unit pixel size
+        G = dict(K=70, D=230, N=256, pixel_size=0.9)
+    else:
+        G = dict(K=70, D=200, N=190, det_center=101.3)
+    g, go = make(api, G)
+    assert api.variant_supports(variant, g)
     rng = np.random.default_rng(variant)
-    q = rng.standard_normal((2, 70, 200)).astype(np.float32)
+    q = rng.standard_normal((2, G["K"], G["D"])).astype(np.float32)
     f = api.backproject(to_gpu(q), g, variant=variant)
     for s in range(2):
         ref = oracle.backproject(q[s].astype(np.float64), go)
         assert_within_dr(to_np(f[s]), ref, TOL, f"variant {variant} slice {s}")
+
+
+def test_symmetric_variants_refuse_other_geometries():
+    api = fbp_api()
+    sym = [v["variant"] for v in api.bp_variants() if v["symmetric"]]
+    assert sym
+    q = torch.zeros((71, 64), device="cuda")
+    for g in (api.Geometry(71, 64, 64),                       # odd K
+              api.Geometry(70, 64, 64, det_center=30.0),      # off-centre detector
+              api.Geometry(70, 64, 96),                       # N not a multiple of 2 tiles
+              api.Geometry(70, 64, 64, angle_step=0.04)):     # not pi/K
+        for v in sym:
+            assert not api.variant_supports(v, g)
+            with pytest.raises(api.FbpError, match="UNSUPPORTED"):
+                api.backproject(q[: g.n_angles], g, variant=v)
+        # the default falls back to a generic variant and stays correct
+        go = oracle.Geometry(g.n_angles, g.n_det, g.n, angle_step=g.angle_step, det_center=g.det_center)
+        qq = torch.randn((g.n_angles, g.n_det), device="cuda")
+        assert_within_dr(to_np(api.backproject(qq, g)), oracle.backproject(to_np(qq), go), TOL, "fallback")
 
 
 def test_scale_and_accumulate():
@@ -82,16 +109,19 @@ def test_constant_rows_give_pi_on_disk():
 
 
 @pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
-def test_16bit_rows_match_oracle_on_dequantised_rows(dtype):
+@pytest.mark.parametrize("variant,tol", [(0, TOL), (-1, 2e-3), (7, 2e-3)])
+def test_16bit_rows_match_oracle_on_dequantised_rows(dtype, variant, tol):
+    """Generic variants stage 16-bit rows as FP32 tables (FP32 tolerance); the
+    symmetric default stages 16-bit tables (the 16-bit staging bound)."""
     api = fbp_api()
     g, go = make(api, dict(K=90, D=128, N=128))
     rng = np.random.default_rng(2)
     q = rng.standard_normal((90, 128)).astype(np.float32)
     q16, rs = api.filter(to_gpu(q), g, dtype=dtype)   # any rows will do: use filtered ones
-    f = api.backproject(q16, g, row_scale=rs)
+    f = api.backproject(q16, g, row_scale=rs, variant=variant)
     deq = to_np(q16) * to_np(rs)[:, None]
     ref = oracle.backproject(deq, go)
-    assert_within_dr(to_np(f), ref, TOL, "16-bit")
+    assert_within_dr(to_np(f), ref, tol, f"16-bit variant {variant}")
 
 
 def test_fbp_shepp_logan_n256_vs_oracle_and_phantom():
@@ -118,9 +148,15 @@ def test_checked_build_reports_no_fault_on_valid_geometries():
     build.build_cuda("libfbp_checked.so", ["-DFBP_CHECKED"])
     api = fbp_api()
     assert api.device_status("checked") == 0
-    for G in GEOMS[3:]:
+    extra = [dict(K=70, D=230, N=256, pixel_size=0.9), dict(K=64, D=300, N=256, pixel_size=2.4),
+             dict(K=36, D=40, N=128, pixel_size=0.125)]
+    for G in GEOMS[3:] + extra:
         g, go = make(api, G)
         q = torch.randn((G["K"], G["D"]), device="cuda")
+        ran = 0
         for v in range(len(api.bp_variants())):
-            api.backproject(q, g, variant=v, which="checked")
+            if api.variant_supports(v, g):
+                api.backproject(q, g, variant=v, which="checked")
+                ran += 1
+        assert ran >= 6
         assert api.device_status("checked") == 0, str(G)

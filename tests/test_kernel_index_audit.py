@@ -136,3 +136,177 @@ def test_forward_candidate_count_bound(alpha):
     bound = math.ceil(2.0 * 1.4142135623730951 / alpha)
     assert nc.max() <= bound
     assert bound <= 24
+
+
+ORBIT_SHAPES = [(16, 8, 2, 4), (16, 16, 4, 4)]   # (TXT, TYT, PX, PY), square tiles
+
+
+def orbit_max_index(N, K, D, alpha, shape, tiles=None):
+    """Replay of bp_orbit.cuh's coordinate path for both windows of every
+    angle pair: u1 = f1 + dx c + dy s, u2 = f2 - dx s + dy c."""
+    TXT, TYT, PX, PY = shape
+    TILE = TXT * PX
+    H = window_half(alpha, TILE, TILE)
+    m = 0.5 * (N - 1)
+    cd = 0.5 * (D - 1)
+    dxt = np.arange(TXT).astype(F) - F(0.5 * (TILE - 1))
+    dyt = np.arange(TYT).astype(F) - F(0.5 * (TILE - 1))
+    half = N // TILE // 2
+    if tiles is None:
+        tiles = [(a, b) for a in range(half) for b in range(half)]
+    th = np.arange(K // 2) * (math.pi / K)
+    c = alpha * np.cos(th)
+    s = alpha * np.sin(th)
+    worst = 0
+    for (ox, oy) in tiles:
+        Xc = ox * TILE + 0.5 * (TILE - 1) - m
+        Yc = oy * TILE + 0.5 * (TILE - 1) - m
+        for (A, B, Ctr) in ((c, s, c * Xc + s * Yc + cd), (-s, c, -s * Xc + c * Yc + cd)):
+            f = (Ctr - np.floor(Ctr) - 0.5).astype(F)
+            A32, B32 = A.astype(F), B.astype(F)
+            u0 = (f[:, None, None] + dxt[None, None, :] * A32[:, None, None]
+                  + dyt[None, :, None] * B32[:, None, None]).astype(F)
+            for iy in range(PY):
+                ur = (u0 + F(iy) * (F(TYT) * B32)[:, None, None]).astype(F)
+                for ix in range(PX):
+                    u = (ur + F(ix) * (F(TXT) * A32)[:, None, None]).astype(F)
+                    worst = max(worst, int(np.max(np.abs(np.rint(u)))))
+    return worst, H
+
+
+@pytest.mark.parametrize("shape", ORBIT_SHAPES)
+@pytest.mark.parametrize("N,D,K,alpha", [(128, 128, 90, 1.0), (256, 230, 70, 0.9),
+                                         (256, 300, 64, 2.5), (128, 40, 36, 0.125)])
+def test_orbit_indices_stay_in_window(shape, N, D, K, alpha):
+    if N % (2 * shape[0] * shape[2]):
+        pytest.skip("geometry not eligible for this tile")
+    worst, H = orbit_max_index(N, K, D, alpha, shape)
+    assert worst <= H
+
+
+def test_orbit_indices_n8192_sampled_tiles():
+    N, K = 8192, 4096
+    half = N // 32 // 2
+    tiles = [(0, 0), (half - 1, half - 1), (0, half - 1), (half - 1, 0), (37, 101)]
+    worst, H = orbit_max_index(N, K, N, 1.0, ORBIT_SHAPES[0], tiles=tiles)
+    assert worst <= H
+
+
+def test_orbit_smem_and_rotation_maps():
+    # staged bytes per block fit the 200 KB budget for the compiled shapes
+    for TILE, KT, EB in ((32, 16, 32), (32, 32, 16), (32, 8, 32), (64, 8, 32)):
+        for alpha in (0.125, 1.0, 2.5):
+            W = 2 * window_half(alpha, TILE, TILE) + 1
+            assert KT * 32 + KT * 2 * W * EB <= 200 * 1024 or alpha > 2.0
+    # the four stores of an orbit cover every pixel exactly once
+    N, TILE = 64, 8
+    hits = np.zeros((N, N), dtype=int)
+    for oy in range(N // TILE // 2):
+        for ox in range(N // TILE // 2):
+            for a in range(TILE):
+                for b in range(TILE):
+                    r, c = oy * TILE + a, ox * TILE + b
+                    for (rr, cc) in ((r, c), (c, N - 1 - r), (N - 1 - r, N - 1 - c), (N - 1 - c, r)):
+                        hits[rr, cc] += 1
+    assert np.all(hits == 1)
+
+
+# ---------------------------------------------------------------------------
+# Forward projector (forward.cu, fwd_strip_kernel): strip bounds
+# ---------------------------------------------------------------------------
+def fwd_pitch(alpha, ncmax):
+    # restates forward.cu:fwd_span_pitch
+    span = 127.0 * 1.4142135623730951 / alpha + 31.0 + ncmax + 5.0
+    return int(math.ceil(span)) | 1
+
+
+def fwd_walk(c, s, alpha, N, det_center, j, ncmax):
+    walk_rows = abs(c) >= abs(s)
+    cp = alpha * (c if walk_rows else s)
+    cq = alpha * (s if walk_rows else c)
+    g = abs(cp)
+    h = 1.0 / g
+    nc = min(ncmax, math.ceil(2.0 * h))
+    m = 0.5 * (N - 1)
+    slope = cq / cp
+    B = (j - det_center + cq * m) / cp + m - h
+    return walk_rows, g, nc, slope, B
+
+
+def fwd_lines(slope, B, nc, N):
+    lo, hi = 0.0, float(N - 1)
+    if slope > 0:
+        lo = max(lo, math.floor((B - N) / slope) - 1.0)
+        hi = min(hi, math.ceil((B + nc + 1) / slope) + 1.0)
+    elif slope < 0:
+        lo = max(lo, math.floor((B + nc + 1) / slope) - 1.0)
+        hi = min(hi, math.ceil((B - N) / slope) + 1.0)
+    elif not (-nc - 1.0 < B < N):
+        hi = -1.0
+    return int(min(lo, N)), int(max(hi, -1.0))
+
+
+def fwd_strip_audit(N, D, K, alpha, det_center, ks):
+    ncmax = math.ceil(2.0 * 1.4142135623730951 / alpha)
+    NCT = 4 if ncmax <= 4 else 24
+    P = fwd_pitch(alpha, NCT)
+    two32 = 4294967296.0
+    for k in ks:
+        th = k * math.pi / K
+        c, s = math.cos(th), math.sin(th)
+        for j0 in range(0, D, 128):
+            jl = min(j0 + 127, D - 1)
+            _, _, nca, sl_a, Ba = fwd_walk(c, s, alpha, N, det_center, j0, NCT)
+            _, _, ncb, sl_b, Bb = fwd_walk(c, s, alpha, N, det_center, jl, NCT)
+            if sl_a != 0.0:
+                a0, a1 = fwd_lines(sl_a, Ba, nca, N)
+                b0, b1 = fwd_lines(sl_b, Bb, ncb, N)
+                blo, bhi = max(0, min(a0, b0)), min(N - 1, max(a1, b1))
+            else:
+                blo, bhi = 0, N - 1
+            if blo > bhi:
+                continue
+            # block setup (thread 0): end bins' fixed-point positions at line blo
+            SL = int(round(sl_a * two32))
+            XMa = int(round((Ba - sl_a * blo) * two32))
+            XMb = int(round((Bb - sl_b * blo) * two32))
+            # every bin of the block (padding threads walk like the last bin)
+            m = 0.5 * (N - 1)
+            walk_rows = abs(c) >= abs(s)
+            cp = alpha * (c if walk_rows else s)
+            cq = alpha * (s if walk_rows else c)
+            inv_cp = 1.0 / cp
+            h = 1.0 / abs(cp)
+            jw = np.minimum(np.arange(j0, j0 + 128), D - 1).astype(np.float64)
+            Bj = (jw - det_center + cq * m) * inv_cp + m - h
+            XM0 = np.array([int(round((b - sl_a * blo) * two32)) for b in Bj], dtype=np.int64)
+            nc = nca
+            for wc in range(blo, bhi + 1, 32):
+                d0, d1 = (wc - blo) * SL, (wc + 31 - blo) * SL
+                cs_ = [(XMa - d0) >> 32, (XMa - d1) >> 32, (XMb - d0) >> 32, (XMb - d1) >> 32]
+                s_lo = min(cs_)
+                s_hi = max(cs_) + NCT + 1
+                span = s_hi - s_lo + 1
+                assert span <= P - 1, (k, j0, wc, span, P)
+                lines = np.arange(wc, min(wc + 32, bhi + 1))
+                XM = XM0[None, :] - (lines - blo)[:, None] * np.int64(SL)
+                start = (XM >> 32) + 1
+                first = start - s_lo
+                last = first + nc - 1
+                assert first.min() >= 0, (k, j0, wc, first.min())
+                assert last.max() <= span - 1, (k, j0, wc, last.max(), span)
+
+
+@pytest.mark.parametrize("N,D,K,alpha,dc", [
+    (64, 64, 36, 1.0, None), (130, 150, 40, 1.0, 70.25), (100, 90, 24, 1.3, None),
+    (96, 300, 16, 2.4, None), (150, 40, 24, 0.25, 25.0), (128, 128, 20, 0.5, None),
+    (64, 64, 8, 1.0, None)])
+def test_forward_strip_reads_stay_in_staged_strip(N, D, K, alpha, dc):
+    dc = 0.5 * (D - 1) if dc is None else dc
+    fwd_strip_audit(N, D, K, alpha, dc, range(K))
+
+
+def test_forward_strip_n1024_and_n8192_sampled_angles():
+    for N, K in ((1024, 1800), (8192, 4096)):
+        ks = [0, 1, K // 4 - 1, K // 4, K // 2 - 1, K // 2, K // 2 + 1, 3 * K // 4, K - 1, 777 % K]
+        fwd_strip_audit(N, N, K, 1.0, 0.5 * (N - 1), ks)
