@@ -366,11 +366,10 @@ def resolved_variant(api, g, dtype: str, variant: int) -> int:
     import torch
     tdt = getattr(torch, DT[dtype])
     # the library's default choice (backproject.cu: bp_default_variant)
-    if dtype != "f32":
-        for v in (8, 6):
-            if api.variant_supports(v, g, tdt):
-                return v
-    return 5 if api.variant_supports(5, g, tdt) else 0
+    for v in ((10, 8, 11, 6) if dtype != "f32" else (7, 5)):
+        if api.variant_supports(v, g, tdt):
+            return v
+    return 0
 
 
 def run_uniform(args) -> None:

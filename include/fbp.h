@@ -107,6 +107,9 @@ typedef struct {
                             geometry (angle step pi/K with K even, centred
                             detector, n a multiple of 2*tile_x); the block
                             owns a tile and its three rotations            */
+    int packed16;        /* 1: 16-bit rows only; interpolates two rows with
+                            one packed 16-bit FMA (the interpolated value is
+                            rounded to the 16-bit type, then summed in FP32) */
 } fbp_bp_shape;
 
 /* Library version (major*10000 + minor*100 + patch). */

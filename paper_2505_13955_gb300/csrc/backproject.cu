@@ -18,19 +18,21 @@ namespace {
 // angles (generic) or angle pairs (orbit) per staged tile KT.  Orbit shapes
 // use the 90-degree symmetry (bp_orbit.cuh) and need the standard geometry.
 struct ShapeDesc {
-    int txt, tyt, px, py, kt, orbit;
+    int txt, tyt, px, py, kt, orbit, packed;
 };
 constexpr ShapeDesc kShapes[] = {
-    {16, 16, 4, 4, 32, 0},   // 0: 64 x 64 tile
-    {16, 16, 4, 4, 16, 0},   // 1
-    {16, 16, 4, 2, 32, 0},   // 2: 64 x 32
-    {16, 16, 2, 4, 32, 0},   // 3: 32 x 64
-    {16, 16, 4, 4, 64, 0},   // 4
-    {32, 8, 2, 8, 32, 0},    // 5: 64 x 64, warps 4 x 2
-    {16, 8, 2, 4, 16, 1},    // 6: orbit of 32 x 32 tiles, 16 angle pairs per stage
-    {16, 8, 2, 4, 8, 1},     // 7: orbit of 32 x 32 tiles, 8 pairs
-    {16, 16, 4, 4, 8, 1},    // 8: orbit of 64 x 64 tiles, 8 pairs
-    {16, 8, 2, 4, 32, 1},    // 9: orbit of 32 x 32 tiles, 32 pairs
+    {16, 16, 4, 4, 32, 0, 0},   // 0: 64 x 64 tile
+    {16, 16, 4, 4, 16, 0, 0},   // 1
+    {16, 16, 4, 2, 32, 0, 0},   // 2: 64 x 32
+    {16, 16, 2, 4, 32, 0, 0},   // 3: 32 x 64
+    {16, 16, 4, 4, 64, 0, 0},   // 4
+    {32, 8, 2, 8, 32, 0, 0},    // 5: 64 x 64, warps 4 x 2
+    {16, 8, 2, 4, 16, 1, 0},    // 6: orbit of 32 x 32 tiles, 16 angle pairs per stage
+    {16, 8, 2, 4, 8, 1, 0},     // 7: orbit of 32 x 32 tiles, 8 pairs
+    {16, 16, 4, 4, 8, 1, 0},    // 8: orbit of 64 x 64 tiles, 8 pairs
+    {16, 8, 2, 4, 32, 1, 0},    // 9: orbit of 32 x 32 tiles, 32 pairs
+    {16, 16, 4, 4, 8, 1, 1},    // 10: as 8, packed pair arithmetic (16-bit rows only)
+    {16, 8, 2, 4, 16, 1, 1},    // 11: as 6, packed pair arithmetic (16-bit rows only)
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -77,8 +79,8 @@ __global__ void __launch_bounds__(TXT *TYT) bp_kernel(BpArgs a)
     bp_tile<TXT, TYT, PX, PY, KT, T, CHECKED>(j, bp_smem);
 }
 
-template <int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED>
-__global__ void __launch_bounds__(TXT *TYT) bp_orbit_kernel(BpArgs a)
+template <int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED, bool PACKED>
+__global__ void __launch_bounds__(TXT *TYT, (TXT * TYT >= 256) ? 2 : 4) bp_orbit_kernel(BpArgs a)
 {
     extern __shared__ __align__(16) unsigned char bp_smem[];
     constexpr int TILE = TXT * PX;
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(TXT *TYT) bp_orbit_kernel(BpArgs a)
     j.x0 = (o % half) * TILE;
     j.y0 = (o / half) * TILE;
     j.status = a.status;
-    bp_orbit<TILE, TXT, TYT, PX, PY, KT, T, CHECKED>(j, bp_smem);
+    bp_orbit<TILE, TXT, TYT, PX, PY, KT, T, CHECKED, PACKED>(j, bp_smem);
 }
 
 template <int V, typename T>
@@ -119,7 +121,10 @@ fbp_status launch_orbit_shape(const BpLaunch &L, cudaStream_t s, unsigned *statu
     if (!bp_orbit_eligible(L, TILE))
         return fail(FBP_ERR_UNSUPPORTED, "variant %d needs angle step pi/K with K even, "
                     "det_center = (D-1)/2 and N a multiple of %d", V, 2 * TILE);
-    auto kern = bp_orbit_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, T, kChecked>;
+    constexpr bool kPacked = sd.packed && sizeof(T) == 2;
+    if (sd.packed && sizeof(T) != 2)
+        return fail(FBP_ERR_UNSUPPORTED, "variant %d is for 16-bit rows", V);
+    auto kern = bp_orbit_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, T, kChecked, kPacked>;
     BpArgs a;
     a.filt = L.filt;
     a.row_scale = L.row_scale;
@@ -208,6 +213,8 @@ fbp_status launch_variant(const BpLaunch &L, int v, cudaStream_t s, unsigned *st
         case 7: return launch_shape<7, T>(L, s, status);
         case 8: return launch_shape<8, T>(L, s, status);
         case 9: return launch_shape<9, T>(L, s, status);
+        case 10: return launch_shape<10, T>(L, s, status);
+        case 11: return launch_shape<11, T>(L, s, status);
     }
     return fail(FBP_ERR_INVALID_ARG, "backprojection variant %d", v);
 }
@@ -313,6 +320,7 @@ bool bp_variant_shape(int v, fbp_bp_shape *out)
     out->py = d.py;
     out->threads = d.txt * d.tyt;
     out->symmetric = d.orbit;
+    out->packed16 = d.packed;
     if (d.orbit) out->angle_tile = 2 * d.kt;
     return true;
 }
@@ -357,23 +365,29 @@ bool bp_variant_fits(int v, const BpLaunch &L)
         case 7: smem = variant_smem<7>(L); break;
         case 8: smem = variant_smem<8>(L); break;
         case 9: smem = variant_smem<9>(L); break;
+        case 10: smem = variant_smem<10>(L); break;
+        case 11: smem = variant_smem<11>(L); break;
         default: return false;
     }
     if (smem > kSmemBudget) return false;
     const ShapeDesc &d = kShapes[v];
+    if (d.packed && L.dtype == FBP_F32) return false;
     return !d.orbit || bp_orbit_eligible(L, d.txt * d.px);
 }
 
-// Measured at N = 8192, K = 4096 on GB300: FP32 rows are fastest with the
-// generic 64 x 64 tile (variant 5); 16-bit rows with the symmetric 64 x 64
-// orbit (variant 8), then the 32 x 32 orbit (variant 6).
+// Measured at N = 8192, K = 4096 on GB300 (Gupdates/s): FP32 rows --
+// generic 64 x 64 tile (variant 5) 4290, symmetric 32 x 32 orbit (7) 4330;
+// 16-bit rows -- packed 64 x 64 orbit (10) 7170-7210, unpacked (8) 6340-6370.
 int bp_default_variant(const BpLaunch &L)
 {
     if (L.dtype != FBP_F32) {
-        if (bp_variant_fits(8, L)) return 8;
-        if (bp_variant_fits(6, L)) return 6;
+        for (int v : {10, 8, 11, 6})
+            if (bp_variant_fits(v, L)) return v;
+    } else {
+        for (int v : {7, 5})
+            if (bp_variant_fits(v, L)) return v;
     }
-    return bp_variant_fits(5, L) ? 5 : 0;
+    return 0;
 }
 
 fbp_status launch_backproject(const BpLaunch &L, int variant, cudaStream_t s)

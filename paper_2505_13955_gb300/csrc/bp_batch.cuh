@@ -33,7 +33,7 @@ struct FilterBatchItem {        // 56 bytes
     const float *sino;          // [K][D]
     void *filt;                 // [K][D] in the workspace
     float *row_scale;           // [K] or null
-    const float *H;             // spectrum for (D, kind, tau), length L
+    const float2 *G;            // difference-form spectrum for (D, kind, tau), length L
     const float2 *tw;           // twiddles for L
     int K, D, L, group_begin;   // group = up to 32/N1 row pairs
 };

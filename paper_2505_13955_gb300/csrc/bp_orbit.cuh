@@ -119,12 +119,94 @@ template <> __device__ __forceinline__ void mac16<__nv_bfloat16>(float &acc, uns
         : "+f"(acc) : "h"(fr), "r"(e));
 }
 
-template <int TILE, int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED>
+// Packed FP32 pairs (two windows' coordinates at once) and packed 16-bit
+// interpolation (two rows at once), for the PACKED 16-bit variant.
+__device__ __forceinline__ unsigned long long pk2(float lo, float hi)
+{
+    unsigned long long r;
+    asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(lo), "f"(hi));
+    return r;
+}
+__device__ __forceinline__ void upk2(unsigned long long p, float &lo, float &hi)
+{
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(p));
+}
+__device__ __forceinline__ unsigned long long ffma2(unsigned long long a, unsigned long long b,
+                                                    unsigned long long c)
+{
+    unsigned long long d;
+    asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fadd2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("add.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+__device__ __forceinline__ unsigned long long fsub2(unsigned long long a, unsigned long long b)
+{
+    unsigned long long d;
+    asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+    return d;
+}
+
+// (x, x) rounded to the 16-bit type and packed
+template <typename T> __device__ __forceinline__ uint32_t splat16(float x);
+template <> __device__ __forceinline__ uint32_t splat16<__half>(float x)
+{
+    uint32_t r;
+    asm("cvt.rn.f16x2.f32 %0, %1, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+template <> __device__ __forceinline__ uint32_t splat16<__nv_bfloat16>(float x)
+{
+    uint32_t r;
+    asm("cvt.rn.bf16x2.f32 %0, %1, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+// a * b + c on packed pairs of the 16-bit type
+template <typename T> __device__ __forceinline__ uint32_t hfma2(uint32_t a, uint32_t b, uint32_t c);
+template <> __device__ __forceinline__ uint32_t hfma2<__half>(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("fma.rn.f16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+template <> __device__ __forceinline__ uint32_t hfma2<__nv_bfloat16>(uint32_t a, uint32_t b, uint32_t c)
+{
+    uint32_t d;
+    asm("fma.rn.bf16x2 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+// lo_acc += low half of v, hi_acc += high half, in FP32
+template <typename T> __device__ __forceinline__ void add2to32(float &lo_acc, float &hi_acc, uint32_t v);
+template <> __device__ __forceinline__ void add2to32<__half>(float &lo_acc, float &hi_acc, uint32_t v)
+{
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "add.rn.f32.f16 %0, lo, %0;\n\tadd.rn.f32.f16 %1, hi, %1;\n\t}"
+        : "+f"(lo_acc), "+f"(hi_acc) : "r"(v));
+}
+template <> __device__ __forceinline__ void add2to32<__nv_bfloat16>(float &lo_acc, float &hi_acc, uint32_t v)
+{
+    asm("{\n\t.reg .b16 lo, hi;\n\tmov.b32 {lo, hi}, %2;\n\t"
+        "add.rn.f32.bf16 %0, lo, %0;\n\tadd.rn.f32.bf16 %1, hi, %1;\n\t}"
+        : "+f"(lo_acc), "+f"(hi_acc) : "r"(v));
+}
+
+// PACKED (16-bit rows only): entries hold (q'_th, q'_th'), (d_th, d_th'),
+// and the same for the mirrored rows, so one packed FMA interpolates two
+// rows (the interpolated value is rounded once to the 16-bit type before the
+// FP32 accumulation), and both windows' coordinates are formed with packed
+// FP32 pair instructions.
+template <int TILE, int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED,
+          bool PACKED = false>
 __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *smem)
 {
     constexpr int NT = TXT * TYT;
     constexpr int WX = TXT / 8;
     constexpr bool F32 = sizeof(T) == 4;
+    static_assert(!(PACKED && F32), "packed interpolation is for 16-bit rows");
     constexpr int EB = 16;                                          // index stride of each array
     static_assert(TXT * PX == TILE && TYT * PY == TILE, "square tile");
     static_assert(TXT % 8 == 0 && TYT % 4 == 0 && (TXT / 8) * (TYT / 4) * 32 == NT, "warp layout");
@@ -235,66 +317,123 @@ __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *sme
                     reinterpret_cast<float4 *>(dst)[i] = e0;
                     reinterpret_cast<float4 *>(dst + tab_b)[i] = e1;
                 } else {
+                    // midpoints and slopes of the four rows (scaled by s_k / S)
+                    float mid[4], slp[4];
+#pragma unroll
+                    for (int r = 0; r < 4; ++r) {
+                        const float sc = (r & 1) ? sc1 : sc0;
+                        const float x0 = v[2 * r] * sc, x1 = v[2 * r + 1] * sc;
+                        mid[r] = 0.5f * (x0 + x1);
+                        slp[r] = x1 - x0;
+                    }
                     uint4 e;
-                    float x0 = v[0] * sc0, x1 = v[1] * sc0;
-                    e.x = pack16<T>(0.5f * (x0 + x1), x1 - x0);
-                    x0 = v[2] * sc1; x1 = v[3] * sc1;
-                    e.y = pack16<T>(0.5f * (x0 + x1), x1 - x0);
-                    x0 = v[4] * sc0; x1 = v[5] * sc0;
-                    e.z = pack16<T>(0.5f * (x0 + x1), x1 - x0);
-                    x0 = v[6] * sc1; x1 = v[7] * sc1;
-                    e.w = pack16<T>(0.5f * (x0 + x1), x1 - x0);
+                    if constexpr (PACKED) {
+                        e.x = pack16<T>(mid[0], mid[1]);
+                        e.y = pack16<T>(slp[0], slp[1]);
+                        e.z = pack16<T>(mid[2], mid[3]);
+                        e.w = pack16<T>(slp[2], slp[3]);
+                    } else {
+                        e.x = pack16<T>(mid[0], slp[0]);
+                        e.y = pack16<T>(mid[1], slp[1]);
+                        e.z = pack16<T>(mid[2], slp[2]);
+                        e.w = pack16<T>(mid[3], slp[3]);
+                    }
                     reinterpret_cast<uint4 *>(dst)[i] = e;
                 }
             }
         }
         __syncthreads();
-        for (int a = 0; a < na; ++a) {
-            const float4 pv = prm[a];
-            const uint4 ad = adr[a];
-            const float c = pv.x, s = pv.y;
-            const float u10 = fmaf(dxt, c, fmaf(dyt, s, pv.z));
-            const float u20 = fmaf(dxt, -s, fmaf(dyt, c, pv.w));
-            const float s1x = (float)TXT * c, s1y = (float)TYT * s;
-            const float s2x = -(float)TXT * s, s2y = (float)TYT * c;
+        if constexpr (PACKED) {
+            const unsigned long long Mp = pk2(kRoundMagic, kRoundMagic);
+            const unsigned long long nMp = pk2(-kRoundMagic, -kRoundMagic);
+            for (int a = 0; a < na; ++a) {
+                const float4 pv = prm[a];
+                const uint4 ad = adr[a];
+                const float c = pv.x, s = pv.y;
+                // (u1, u2) of the thread's first pixel, and per-row / per-column steps
+                const unsigned long long u0 = pk2(fmaf(dxt, c, fmaf(dyt, s, pv.z)),
+                                                  fmaf(dxt, -s, fmaf(dyt, c, pv.w)));
+                const unsigned long long sx = pk2((float)TXT * c, -(float)TXT * s);
+                const unsigned long long sy = pk2((float)TYT * s, (float)TYT * c);
 #pragma unroll
-            for (int iy = 0; iy < PY; ++iy) {
-                const float r1 = iy == 0 ? u10 : fmaf((float)iy, s1y, u10);
-                const float r2 = iy == 0 ? u20 : fmaf((float)iy, s2y, u20);
+                for (int iy = 0; iy < PY; ++iy) {
+                    const unsigned long long r = iy == 0 ? u0 : ffma2(pk2((float)iy, (float)iy), sy, u0);
 #pragma unroll
-                for (int ix = 0; ix < PX; ++ix) {
-#pragma unroll
-                    for (int win = 0; win < 2; ++win) {
-                        const float u = win == 0 ? (ix == 0 ? r1 : fmaf((float)ix, s1x, r1))
-                                                 : (ix == 0 ? r2 : fmaf((float)ix, s2x, r2));
-                        const float t = __fadd_rn(u, kRoundMagic);
-                        uint32_t tb = __float_as_uint(t);
+                    for (int ix = 0; ix < PX; ++ix) {
+                        const unsigned long long u = ix == 0 ? r : ffma2(pk2((float)ix, (float)ix), sx, r);
+                        const unsigned long long t = fadd2(u, Mp);
+                        const unsigned long long fr = fsub2(u, fadd2(t, nMp));
+                        float t1, t2, f1, f2;
+                        upk2(t, t1, t2);
+                        upk2(fr, f1, f2);
+                        uint32_t tb1 = __float_as_uint(t1), tb2 = __float_as_uint(t2);
                         if (CHECKED) {
-                            const int i = (int)(tb - kRoundMagicBits);
-                            if (i < -H || i > H) {
+                            const int i1 = (int)(tb1 - kRoundMagicBits), i2 = (int)(tb2 - kRoundMagicBits);
+                            if (i1 < -H || i1 > H || i2 < -H || i2 > H) {
                                 atomicCAS(j.status, 0u, (unsigned)FAULT_TABLE_INDEX);
-                                tb = kRoundMagicBits;
+                                tb1 = tb2 = kRoundMagicBits;
                             }
                         }
-                        const uint32_t cb = win == 0 ? ad.x : ad.y;
-                        // orbit members fed by rows (th, th', th~, th'~)
-                        const int m0 = win == 0 ? 0 : 3, m1 = win == 0 ? 1 : 0;
-                        const int m2 = win == 0 ? 2 : 1, m3 = win == 0 ? 3 : 2;
-                        if constexpr (F32) {
-                            const uint32_t e = cb + (tb << 4);
-                            const float4 e0 = lds_f4(e), e1 = lds_f4(e + tab_b);
-                            acc[m0][iy][ix] += fmaf(u, e0.y, e0.x);
-                            acc[m1][iy][ix] += fmaf(u, e0.w, e0.z);
-                            acc[m2][iy][ix] += fmaf(u, e1.y, e1.x);
-                            acc[m3][iy][ix] += fmaf(u, e1.w, e1.z);
-                        } else {
-                            const uint4 e = lds_u4(cb + (tb << 4));
-                            const float fr = u - (t - kRoundMagic);
-                            const unsigned short f16 = frac16<T>(fr);
-                            mac16<T>(acc[m0][iy][ix], f16, e.x);
-                            mac16<T>(acc[m1][iy][ix], f16, e.y);
-                            mac16<T>(acc[m2][iy][ix], f16, e.z);
-                            mac16<T>(acc[m3][iy][ix], f16, e.w);
+                        const uint4 e1 = lds_u4(ad.x + (tb1 << 4));
+                        const uint4 e2 = lds_u4(ad.y + (tb2 << 4));
+                        const uint32_t h1 = splat16<T>(f1), h2 = splat16<T>(f2);
+                        // W1: th -> p, th' -> Rp, th~ -> R^2 p, th'~ -> R^3 p
+                        add2to32<T>(acc[0][iy][ix], acc[1][iy][ix], hfma2<T>(h1, e1.y, e1.x));
+                        add2to32<T>(acc[2][iy][ix], acc[3][iy][ix], hfma2<T>(h1, e1.w, e1.z));
+                        // W2: th -> R^3 p, th' -> p, th~ -> Rp, th'~ -> R^2 p
+                        add2to32<T>(acc[3][iy][ix], acc[0][iy][ix], hfma2<T>(h2, e2.y, e2.x));
+                        add2to32<T>(acc[1][iy][ix], acc[2][iy][ix], hfma2<T>(h2, e2.w, e2.z));
+                    }
+                }
+            }
+        } else {
+            for (int a = 0; a < na; ++a) {
+                const float4 pv = prm[a];
+                const uint4 ad = adr[a];
+                const float c = pv.x, s = pv.y;
+                const float u10 = fmaf(dxt, c, fmaf(dyt, s, pv.z));
+                const float u20 = fmaf(dxt, -s, fmaf(dyt, c, pv.w));
+                const float s1x = (float)TXT * c, s1y = (float)TYT * s;
+                const float s2x = -(float)TXT * s, s2y = (float)TYT * c;
+#pragma unroll
+                for (int iy = 0; iy < PY; ++iy) {
+                    const float r1 = iy == 0 ? u10 : fmaf((float)iy, s1y, u10);
+                    const float r2 = iy == 0 ? u20 : fmaf((float)iy, s2y, u20);
+#pragma unroll
+                    for (int ix = 0; ix < PX; ++ix) {
+#pragma unroll
+                        for (int win = 0; win < 2; ++win) {
+                            const float u = win == 0 ? (ix == 0 ? r1 : fmaf((float)ix, s1x, r1))
+                                                     : (ix == 0 ? r2 : fmaf((float)ix, s2x, r2));
+                            const float t = __fadd_rn(u, kRoundMagic);
+                            uint32_t tb = __float_as_uint(t);
+                            if (CHECKED) {
+                                const int i = (int)(tb - kRoundMagicBits);
+                                if (i < -H || i > H) {
+                                    atomicCAS(j.status, 0u, (unsigned)FAULT_TABLE_INDEX);
+                                    tb = kRoundMagicBits;
+                                }
+                            }
+                            const uint32_t cb = win == 0 ? ad.x : ad.y;
+                            // orbit members fed by rows (th, th', th~, th'~)
+                            const int m0 = win == 0 ? 0 : 3, m1 = win == 0 ? 1 : 0;
+                            const int m2 = win == 0 ? 2 : 1, m3 = win == 0 ? 3 : 2;
+                            if constexpr (F32) {
+                                const uint32_t e = cb + (tb << 4);
+                                const float4 e0 = lds_f4(e), e1 = lds_f4(e + tab_b);
+                                acc[m0][iy][ix] += fmaf(u, e0.y, e0.x);
+                                acc[m1][iy][ix] += fmaf(u, e0.w, e0.z);
+                                acc[m2][iy][ix] += fmaf(u, e1.y, e1.x);
+                                acc[m3][iy][ix] += fmaf(u, e1.w, e1.z);
+                            } else {
+                                const uint4 e = lds_u4(cb + (tb << 4));
+                                const float fr = u - (t - kRoundMagic);
+                                const unsigned short f16 = frac16<T>(fr);
+                                mac16<T>(acc[m0][iy][ix], f16, e.x);
+                                mac16<T>(acc[m1][iy][ix], f16, e.y);
+                                mac16<T>(acc[m2][iy][ix], f16, e.z);
+                                mac16<T>(acc[m3][iy][ix], f16, e.w);
+                            }
                         }
                     }
                 }

@@ -97,10 +97,10 @@ fbp_status fbp_filter(const float *sino, void *filt, float *row_scale, fbp_dtype
         const long long rows = (long long)n_slices * g->n_angles;
         const size_t nin = (size_t)rows * g->n_det * 4, nout = (size_t)rows * g->n_det * dtype_size(dtype);
         if (overlap(sino, nin, filt, nout)) return fail(FBP_ERR_INVALID_ARG, "filt overlaps sino");
-        const float *H = nullptr;
+        const float2 *G = nullptr;
         const float2 *tw = nullptr;
         int L = 0;
-        st = filter_tables(g->n_det, kind, g->det_spacing, stream, &H, &tw, &L);
+        st = filter_tables(g->n_det, kind, g->det_spacing, stream, &G, &tw, &L);
         if (st != FBP_OK) return st;
         FilterLaunch a;
         a.sino = sino;
@@ -109,7 +109,7 @@ fbp_status fbp_filter(const float *sino, void *filt, float *row_scale, fbp_dtype
         a.rows = rows;
         a.D = g->n_det;
         a.L = L;
-        a.H = H;
+        a.G = G;
         a.tw = tw;
         a.dtype = dtype;
         return launch_filter(a, stream);
@@ -291,13 +291,13 @@ fbp_status fbp_batched(const fbp_batch_item *items, int count, fbp_filter_kind k
 
         // tables (all before any launch, so a failure enqueues nothing)
         std::vector<const double2 *> cs(count);
-        std::vector<const float *> Hs(count);
+        std::vector<const float2 *> Gs(count);
         std::vector<const float2 *> tws(count);
         std::vector<int> Ls(count);
         for (int i = 0; i < count; ++i) {
             st = angle_table(items[i].g, stream, &cs[i]);
             if (st != FBP_OK) return st;
-            st = filter_tables(items[i].g.n_det, kind, items[i].g.det_spacing, stream, &Hs[i],
+            st = filter_tables(items[i].g.n_det, kind, items[i].g.det_spacing, stream, &Gs[i],
                                &tws[i], &Ls[i]);
             if (st != FBP_OK) return st;
         }
@@ -311,7 +311,7 @@ fbp_status fbp_batched(const fbp_batch_item *items, int count, fbp_filter_kind k
             f.sino = items[i].sino;
             f.filt = ws + foff[i];
             f.row_scale = dtype == FBP_F32 ? nullptr : reinterpret_cast<float *>(ws + soff[i]);
-            f.H = Hs[i];
+            f.G = Gs[i];
             f.tw = tws[i];
             f.K = items[i].g.n_angles;
             f.D = items[i].g.n_det;
@@ -401,10 +401,10 @@ fbp_status fbp_prepare(const fbp_geometry *g, int kind, fbp_stream_t stream)
         if (st != FBP_OK) return st;
         if (kind >= 0) {
             if (!kind_ok(kind)) return fail(FBP_ERR_INVALID_ARG, "filter kind %d", kind);
-            const float *H;
+            const float2 *G;
             const float2 *tw;
             int L;
-            st = filter_tables(g->n_det, kind, g->det_spacing, stream, &H, &tw, &L);
+            st = filter_tables(g->n_det, kind, g->det_spacing, stream, &G, &tw, &L);
             if (st != FBP_OK) return st;
         }
         unsigned *p = nullptr;

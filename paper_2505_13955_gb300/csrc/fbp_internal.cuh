@@ -41,11 +41,12 @@ struct AngleKey {
 fbp_status angle_table(const fbp_geometry &g, cudaStream_t s, const double2 **out);
 
 // Filter tables for detector width D:
-//   L   = transform length (power of two >= max(512, 2D-1), <= 16384)
-//   H   = real spectrum of tau * h_tau, divided by L (length L, float)
+//   L   = transform length (power of two >= max(512, 2D-1), so L >= 2D; <= 16384)
+//   G   = spectrum of the cumulative (difference-form) kernel, times tau / L
+//         (length L, complex); applied to the row's first differences
 //   tw  = twiddles exp(-2 pi i m / L), m in [0, L) (float2)
 fbp_status filter_tables(int D, int kind, double tau, cudaStream_t s,
-                         const float **H, const float2 **tw, int *L);
+                         const float2 **G, const float2 **tw, int *L);
 int filter_length(int D);   // 0 if D is outside [1, 8192]
 
 bool stream_is_capturing(cudaStream_t s);
@@ -74,7 +75,7 @@ struct FilterLaunch {
     float *row_scale;      // [rows] (16-bit dtypes)
     long long rows;        // n_slices * K
     int D, L;
-    const float *H;
+    const float2 *G;
     const float2 *tw;
     fbp_dtype dtype;
 };

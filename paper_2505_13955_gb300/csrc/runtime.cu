@@ -190,10 +190,10 @@ __global__ void cos_table_kernel(double *c, int L)
     c[m] = cospi(2.0 * (double)m / (double)L);
 }
 
-// H[k] = (tau / L) * (h(0) + 2 sum_{n=1}^{D-1} h(n) cos(2 pi k n / L)), the
-// (real, even) L-point DFT of the truncated kernel laid out circularly.
-__global__ void spectrum_kernel(float *H, const double *h, const double *ctab,
-                                int D, int L, int kind, double tau)
+// Hr[k] = h(0) + 2 sum_{n=1}^{D-1} h(n) cos(2 pi k n / L): the (real, even)
+// L-point DFT of the truncated kernel laid out circularly, in double.
+__global__ void spectrum_kernel(double *Hr, const double *h, const double *ctab, int D, int L,
+                                int kind)
 {
     int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k > L / 2) return;
@@ -204,9 +204,41 @@ __global__ void spectrum_kernel(float *H, const double *h, const double *ctab,
         int m = (int)(((long long)k * n) & mask);
         acc = fma(h[n], ctab[m], acc);
     }
-    double v = (h[0] + 2.0 * acc) * tau / (double)L;
-    H[k] = (float)v;
-    if (k > 0 && k < L / 2) H[L - k] = (float)v;
+    const double v = h[0] + 2.0 * acc;
+    Hr[k] = v;
+    if (k > 0 && k < L / 2) Hr[L - k] = v;
+}
+
+// Spectrum of the difference-form kernel.  The filter is applied to the
+// first differences d[m] = p[m] - p[m-1] (m in [0, D], p = 0 outside) with
+// the cumulative kernel g[n] = sum_{k <= n} h(k), n in [-D, D-1]; summation by
+// parts gives the same linear convolution, but the FP32 transform's rounding
+// then scales with |d| instead of |p| (line integrals are large and the ramp
+// filter removes most of their magnitude).  On the circle of length L >= 2D,
+// G (1 - W^k) = H - DC W^{kD} with W = exp(-2 pi i / L), DC = sum h = H(0),
+// so G[k] = (H[k] - DC W^{kD}) / (1 - W^k) for k > 0, and G[0] = D * DC
+// (h is even).  Stored as (tau / L) G in float2.
+__global__ void diff_spectrum_kernel(float2 *G, const double *Hr, int D, int L, double tau)
+{
+    int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= L) return;
+    const double dc = Hr[0];
+    double gr, gi;
+    if (k == 0) {
+        gr = (double)D * dc;
+        gi = 0.0;
+    } else {
+        double s1, c1, sD, cD;
+        sincospi(2.0 * (double)k / (double)L, &s1, &c1);                            // W^k = c1 - i s1
+        sincospi(2.0 * (double)(((long long)k * D) % L) / (double)L, &sD, &cD);     // W^{kD}
+        const double nr = Hr[k] - dc * cD, ni = dc * sD;                            // H - DC W^{kD}
+        const double dr = 1.0 - c1, di = s1;                                        // 1 - W^k
+        const double den = dr * dr + di * di;
+        gr = (nr * dr + ni * di) / den;
+        gi = (ni * dr - nr * di) / den;
+    }
+    const double sc = tau / (double)L;
+    G[k] = make_float2((float)(gr * sc), (float)(gi * sc));
 }
 
 // ---------------------------------------------------------------------------
@@ -215,7 +247,7 @@ __global__ void spectrum_kernel(float *H, const double *h, const double *ctab,
 namespace {
 
 struct FilterEntry {
-    float *H = nullptr;       // L floats
+    float2 *G = nullptr;      // L complex
     double *scratch = nullptr;
     int L = 0;
 };
@@ -273,7 +305,7 @@ fbp_status angle_table(const fbp_geometry &g, cudaStream_t s, const double2 **ou
 }
 
 fbp_status filter_tables(int D, int kind, double tau, cudaStream_t s,
-                         const float **H, const float2 **tw, int *Lout)
+                         const float2 **G, const float2 **tw, int *Lout)
 {
     int L = filter_length(D);
     if (!L) return fail(FBP_ERR_UNSUPPORTED, "n_det = %d outside [1, 8192]", D);
@@ -285,7 +317,7 @@ fbp_status filter_tables(int D, int kind, double tau, cudaStream_t s,
     auto fit = g_filters.find(fkey);
     auto tit = g_twiddles.find(tkey);
     if (fit != g_filters.end() && tit != g_twiddles.end()) {
-        *H = fit->second.H;
+        *G = fit->second.G;
         *tw = tit->second;
         *Lout = L;
         return FBP_OK;
@@ -309,27 +341,28 @@ fbp_status filter_tables(int D, int kind, double tau, cudaStream_t s,
     if (fit == g_filters.end()) {
         FilterEntry fe;
         fe.L = L;
-        FBP_CUDA_TRY(cudaMalloc(&fe.H, sizeof(float) * (size_t)L));
-        cudaError_t e = cudaMalloc(&fe.scratch, sizeof(double) * ((size_t)D + (size_t)L));
+        FBP_CUDA_TRY(cudaMalloc(&fe.G, sizeof(float2) * (size_t)L));
+        cudaError_t e = cudaMalloc(&fe.scratch, sizeof(double) * ((size_t)D + 2 * (size_t)L));
         if (e != cudaSuccess) {
-            cudaFree(fe.H);
+            cudaFree(fe.G);
             return cuda_fail(e, "cudaMalloc(filter scratch)");
         }
-        double *h = fe.scratch, *ctab = fe.scratch + D;
+        double *h = fe.scratch, *ctab = fe.scratch + D, *Hr = fe.scratch + D + L;
         taps_kernel<<<(D + 255) / 256, 256, 0, s>>>(h, D, kind, tau);
         cos_table_kernel<<<(L + 255) / 256, 256, 0, s>>>(ctab, L);
-        spectrum_kernel<<<(L / 2 + 1 + 127) / 128, 128, 0, s>>>(fe.H, h, ctab, D, L, kind, tau);
+        spectrum_kernel<<<(L / 2 + 1 + 127) / 128, 128, 0, s>>>(Hr, h, ctab, D, L, kind);
+        diff_spectrum_kernel<<<(L + 255) / 256, 256, 0, s>>>(fe.G, Hr, D, L, tau);
         e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         cudaFree(fe.scratch);
         fe.scratch = nullptr;
         if (e != cudaSuccess) {
-            cudaFree(fe.H);
+            cudaFree(fe.G);
             return cuda_fail(e, "spectrum_kernel");
         }
         fit = g_filters.emplace(fkey, fe).first;
     }
-    *H = fit->second.H;
+    *G = fit->second.G;
     *tw = tit->second;
     *Lout = L;
     return FBP_OK;
@@ -342,7 +375,7 @@ void release_tables()
     cudaGetDevice(&cur);
     auto on = [&](int dev) { cudaSetDevice(dev); cudaDeviceSynchronize(); };
     for (auto &kv : g_angles) { on(std::get<0>(kv.first)); cudaFree(kv.second); }
-    for (auto &kv : g_filters) { on(std::get<0>(kv.first)); cudaFree(kv.second.H); }
+    for (auto &kv : g_filters) { on(std::get<0>(kv.first)); cudaFree(kv.second.G); }
     for (auto &kv : g_twiddles) { on(kv.first.first); cudaFree(kv.second); }
     g_angles.clear();
     g_filters.clear();
