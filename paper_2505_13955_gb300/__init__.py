@@ -11,7 +11,7 @@ binding (``api``) is loaded on first attribute access.
 from __future__ import annotations
 
 _API_NAMES = {
-    "Geometry", "filter", "backproject", "radon_forward", "fbp", "fbp_batched",
+    "Geometry", "filter", "backproject", "radon_forward", "fbp", "fbp_host", "fbp_batched",
     "bp_variants", "variant_supports", "batched_workspace_bytes", "prepare", "device_status", "release_tables",
     "RadonForward", "RadonBackproject", "radon", "radon_t", "lsq_refine", "FbpError", "lib",
 }

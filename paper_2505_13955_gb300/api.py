@@ -166,6 +166,60 @@ def fbp(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
     return backproject(filt, g, row_scale=rs, out=out, variant=variant)
 
 
+def fbp_host(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
+             out: torch.Tensor | None = None, variant: int = -1, chunk: int = 2,
+             n_streams: int = 3, device=None) -> torch.Tensor:
+    """FBP of a stack held in host memory: returns (or fills) a host tensor.
+
+    The stack is processed in chunks of `chunk` slices on `n_streams` CUDA
+    streams; each stream copies its chunk in, runs fbp_filter and
+    fbp_backproject, and copies the slices out, so host<->device copies of one
+    chunk overlap the kernels of another.  Use pinned host tensors
+    (``tensor.pin_memory()``) for asynchronous copies.  Blocks until the
+    result is in `out`.
+    """
+    if sino.is_cuda:
+        raise ValueError("fbp_host takes a host (CPU) tensor; use fbp for device tensors")
+    if sino.dtype != torch.float32 or not sino.is_contiguous():
+        raise ValueError("sino must be a contiguous float32 tensor")
+    S = _slices(sino, (g.n_angles, g.n_det), "sino")
+    squeeze = sino.dim() == 2
+    if squeeze:
+        sino = sino.unsqueeze(0)
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if out is None:
+        out = torch.empty((S, g.n, g.n), dtype=torch.float32, pin_memory=True)
+    o3 = out.view(S, g.n, g.n)
+    chunk = max(1, min(chunk, S))
+    n_streams = max(1, min(n_streams, -(-S // chunk)))
+    caller = torch.cuda.current_stream(dev)
+    streams = [torch.cuda.Stream(dev) for _ in range(n_streams)]
+    bufs = []
+    for _ in range(n_streams):
+        bufs.append((torch.empty((chunk, g.n_angles, g.n_det), dtype=torch.float32, device=dev),
+                     torch.empty((chunk, g.n_angles, g.n_det), dtype=dtype, device=dev),
+                     torch.empty((chunk, g.n_angles), dtype=torch.float32, device=dev)
+                     if dtype != torch.float32 else None,
+                     torch.empty((chunk, g.n, g.n), dtype=torch.float32, device=dev)))
+    for st in streams:
+        st.wait_stream(caller)
+    for i, i0 in enumerate(range(0, S, chunk)):
+        i1 = min(S, i0 + chunk)
+        n = i1 - i0
+        st = streams[i % n_streams]
+        d_in, d_filt, d_rs, d_out = bufs[i % n_streams]
+        with torch.cuda.stream(st):
+            d_in[:n].copy_(sino[i0:i1], non_blocking=True)
+            filter(d_in[:n], g, kind=kind, dtype=dtype, out=d_filt[:n],
+                   row_scale=None if d_rs is None else d_rs[:n])
+            backproject(d_filt[:n], g, row_scale=None if d_rs is None else d_rs[:n],
+                        out=d_out[:n], variant=variant)
+            o3[i0:i1].copy_(d_out[:n], non_blocking=True)
+    for st in streams:
+        st.synchronize()
+    return out[0] if squeeze and out.dim() == 3 else out
+
+
 def bp_variants() -> list[dict]:
     L = lib()
     out = []
