@@ -580,7 +580,7 @@ def run_gd(args) -> None:
     def step(evs):
         if evs:
             evs[0].record(stream)
-        api.radon_forward(x, g, out=r)
+        api.radon_forward(x, g, out=r, variant=args.fwd_variant)
         if evs:
             evs[1].record(stream)
         r.sub_(b)
@@ -598,13 +598,25 @@ def run_gd(args) -> None:
         finish({}, ws, rank)
         return
     a_ms, at_ms = T.between(0, 1), T.between(1, 2)
+    fwd_variant = args.fwd_variant if args.fwd_variant >= 0 else 2
+    sm_max = peaks().get("sm_max_mhz") or 2070.0
+    rp = roofline_peak(sm_max, "f32")
+    a_rate = S * N * N * K / a_ms / 1e6
     line = base_line(args, ws, rate / 1e9, ms_step, "f32", {
         "workload": f"{w.name}: S={S} slices per GPU, N=D={N}, K={K}, Poisson 1e4 photons, "
                     "one gradient-descent iteration (A and A^T) per step",
         "parallelism": f"slices sharded over {ws} GPU(s), no collective"})
-    line.update({"forward_A": {"ms": a_ms, "gupdates_per_s": S * N * N * K / a_ms / 1e6},
+    line["config"]["forward_variant"] = fwd_variant
+    line.update({"forward_A": {"ms": a_ms, "gupdates_per_s": a_rate},
                  "adjoint_AT": {"ms": at_ms, "gupdates_per_s": S * N * N * K / at_ms / 1e6},
-                 "eta": eta, "clocks": T.clocks, "gpu_launches": 4 * args.steps})
+                 # the forward projector dominates the step; it has the
+                 # backprojection's per-update accounting (one pixel-angle pair)
+                 "roofline": {"bound": "alu", "achieved": a_rate, "peak": rp["peak"], "unit": UNIT,
+                              "frac": a_rate / rp["peak"], "traffic": None,
+                              "kernel": "fwd_tile_kernel" if fwd_variant else "fwd_strip_kernel",
+                              "c_alu": rp["c_alu"], "c_lds": rp["c_lds"],
+                              "peak_basis": rp["basis"] + " (sm_max_mhz from MEASURED_PEAKS.json)"},
+                 "eta": eta, "clocks": T.clocks, "gpu_launches": 2 * args.steps})
     finish(line, ws, rank)
 
 
@@ -619,6 +631,8 @@ def main(argv=None):
     ap.add_argument("--all-dtypes", action=argparse.BooleanOptionalAction, default=True,
                     help="also time FP16- and BF16-staged rows in the same run")
     ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--fwd-variant", type=int, default=-1,
+                    help="radon_forward kernel for the refinement workload (-1 = default)")
     ap.add_argument("--slices", type=int, default=None,
                     help="slices per GPU (default: the workload's); small cases for profiling")
     ap.add_argument("--e2e-steps", type=int, default=2)

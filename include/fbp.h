@@ -196,13 +196,32 @@ fbp_status fbp_backproject_noalloc(const void *filt, const float *row_scale,
 /*
  * radon_forward -- the matched forward projector A (the adjoint of
  * fbp_backproject with scale 1; the paper's data generation uses a forward
- * model, Sec. V-B(a)).
+ * model, Sec. V-B(a)):  (A f)_k[j] = sum_{r,c} f[r][c] max(0, 1 - |u_k(r,c) - j|).
  *   slice  device, float [n_slices][n][n].
  *   sino   device, float [n_slices][K][D]: receives A f (overwritten).
- * Gather form (one output bin per thread), deterministic, no atomics.
+ * Uses the library's default variant (see radon_forward_variant).
  */
 fbp_status radon_forward(const float *slice, float *sino, const fbp_geometry *g,
                          int n_slices, fbp_stream_t stream);
+
+/*
+ * radon_forward with an explicit kernel:
+ *   0   gather form: one thread per output bin walks the image; deterministic,
+ *       any pixel_size / det_spacing in [1/8, 2.5].
+ *   1-3 tile-owned form: one block per 64 x 64 pixel tile visits every angle
+ *       and adds per-tile partial bins with floating-point atomics (8, 16 or
+ *       32 bins per warp).  The sum over tiles is not in a fixed order, so
+ *       results may differ between runs in the last bits.  Needs
+ *       pixel_size / det_spacing in [0.9429, 1] (FBP_ERR_UNSUPPORTED
+ *       otherwise).  The sinogram is cleared on `stream` first.
+ *  -1   the default: variant 2 where the tile-owned form applies, else 0.
+ * Other values return FBP_ERR_INVALID_ARG.
+ */
+fbp_status radon_forward_variant(const float *slice, float *sino, const fbp_geometry *g,
+                                 int n_slices, int variant, fbp_stream_t stream);
+
+/* Number of forward-projector variants (valid variant values are 0 .. count-1). */
+int radon_forward_variant_count(void);
 
 /* Number of compiled backprojection tile variants, and the shape of one. */
 int fbp_bp_variant_count(void);

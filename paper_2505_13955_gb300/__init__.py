@@ -12,7 +12,7 @@ from __future__ import annotations
 
 _API_NAMES = {
     "Geometry", "filter", "backproject", "radon_forward", "fbp", "fbp_host", "fbp_batched",
-    "bp_variants", "variant_supports", "batched_workspace_bytes", "prepare", "device_status", "release_tables",
+    "bp_variants", "forward_variant_count", "variant_supports", "batched_workspace_bytes", "prepare", "device_status", "release_tables",
     "RadonForward", "RadonBackproject", "radon", "radon_t", "lsq_refine", "FbpError", "lib",
 }
 

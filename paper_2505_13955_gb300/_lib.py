@@ -64,6 +64,8 @@ SIGNATURES = {
     "fbp_backproject_variant": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int,
                                                ctypes.c_float, ctypes.c_int, ctypes.c_int, _vp]),
     "radon_forward": (ctypes.c_int, [_vp, _vp, _G, ctypes.c_int, _vp]),
+    "radon_forward_variant": (ctypes.c_int, [_vp, _vp, _G, ctypes.c_int, ctypes.c_int, _vp]),
+    "radon_forward_variant_count": (ctypes.c_int, []),
     "fbp_backproject_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int,
                                                ctypes.c_float, ctypes.c_int, _vp]),
     "fbp_bp_variant_count": (ctypes.c_int, []),

@@ -144,8 +144,10 @@ def backproject(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None 
 
 
 def radon_forward(img: torch.Tensor, g: Geometry, out: torch.Tensor | None = None,
-                  which: str = "default"):
-    """radon_forward: the matched projector A (transpose of backproject, scale 1)."""
+                  which: str = "default", variant: int = -1):
+    """radon_forward: the matched projector A (transpose of backproject, scale 1).
+    variant -1 = library default, 0 = deterministic gather, 1..3 = tile-owned
+    (floating-point atomics across tiles)."""
     _need(img, "slice", torch.float32)
     S = _slices(img, (g.n, g.n), "slice")
     shape = (g.n_angles, g.n_det) if img.dim() == 2 else (S, g.n_angles, g.n_det)
@@ -154,7 +156,8 @@ def radon_forward(img: torch.Tensor, g: Geometry, out: torch.Tensor | None = Non
     _need(out, "out", torch.float32)
     L = lib(which)
     gc = g.c()
-    st = L.radon_forward(_ptr(img), _ptr(out), ctypes.byref(gc), S, _stream(img.device))
+    st = L.radon_forward_variant(_ptr(img), _ptr(out), ctypes.byref(gc), S, int(variant),
+                                 _stream(img.device))
     _lib.check(st, L, "radon_forward")
     return out
 
@@ -218,6 +221,11 @@ def fbp_host(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32
     for st in streams:
         st.synchronize()
     return out[0] if squeeze and out.dim() == 3 else out
+
+
+def forward_variant_count(which: str = "default") -> int:
+    """Number of radon_forward kernels (0 = gather, 1..3 = tile-owned)."""
+    return int(lib(which).radon_forward_variant_count())
 
 
 def bp_variants() -> list[dict]:

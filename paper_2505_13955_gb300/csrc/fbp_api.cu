@@ -168,10 +168,22 @@ fbp_status fbp_backproject(const void *filt, const float *row_scale, fbp_dtype d
 fbp_status radon_forward(const float *slice, float *sino, const fbp_geometry *g, int n_slices,
                          fbp_stream_t stream)
 {
+    return radon_forward_variant(slice, sino, g, n_slices, -1, stream);
+}
+
+fbp_status radon_forward_variant(const float *slice, float *sino, const fbp_geometry *g,
+                                 int n_slices, int variant, fbp_stream_t stream)
+{
     return guarded([&]() -> fbp_status {
         fbp_status st = check_geometry(g, false, true);
         if (st != FBP_OK) return st;
         if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
+        if (variant < -1 || variant >= fwd_variant_count())
+            return fail(FBP_ERR_INVALID_ARG, "forward variant %d out of range", variant);
+        const double alpha = g->pixel_size / g->det_spacing;
+        if (variant > 0 && !fwd_tile_eligible(alpha))
+            return fail(FBP_ERR_UNSUPPORTED,
+                        "tile forward projector needs pixel_size / det_spacing in [0.9429, 1]");
         if (n_slices == 0) return FBP_OK;
         if (!slice || !sino) return fail(FBP_ERR_INVALID_ARG, "slice or sino is NULL");
         const size_t nin = (size_t)n_slices * g->n * g->n * 4;
@@ -188,11 +200,14 @@ fbp_status radon_forward(const float *slice, float *sino, const fbp_geometry *g,
         a.D = g->n_det;
         a.N = g->n;
         a.S = n_slices;
-        a.alpha = g->pixel_size / g->det_spacing;
+        a.alpha = alpha;
         a.det_center = g->det_center;
+        a.variant = variant;
         return launch_forward(a, stream);
     });
 }
+
+int radon_forward_variant_count(void) { return fwd_variant_count(); }
 
 int fbp_bp_variant_count(void) { return bp_variant_count(); }
 

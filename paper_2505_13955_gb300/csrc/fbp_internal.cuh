@@ -107,7 +107,10 @@ struct FwdLaunch {
     const double2 *cs;
     int K, D, N, S;
     double alpha, det_center;
+    int variant;          // -1 default, 0 gather, 1..3 tile-owned (8 / 16 / 32 bins per warp)
 };
 fbp_status launch_forward(const FwdLaunch &a, cudaStream_t s);
+int fwd_variant_count();
+bool fwd_tile_eligible(double alpha);
 
 }  // namespace fbp

@@ -5,25 +5,28 @@
 // the projector is written as the adjoint of the library's own backprojector,
 // so that least-squares refinement has the exact gradient.)
 //
-// Gather form, one thread per output bin (k, j), no atomics, deterministic:
-// the thread walks the image along the axis where |cos| or |sin| is smaller
-// (rows when |cos th| >= |sin th|) and, on each line of that axis, visits the
-// few pixels whose coordinate lies within one bin of j.  Along the solved
-// axis the support is 2/g pixels wide, g = alpha * max(|cos|, |sin|), so at
-// most ceil(2/g) candidates contribute.  The position of the support on each
-// line moves linearly; it is kept in 32.32 fixed point (exact integer adds),
-// so the weights keep full precision over 8192 lines without FP64 per line:
+// Two forms share one support solve.  For bin j and a line of the image
+// along the axis where |cos| or |sin| is smaller (rows when |cos th| >=
+// |sin th|), the pixels whose coordinate lies within one bin of j form a run
+// of at most ceil(2/g) candidates along the other axis, g = alpha *
+// max(|cos|, |sin|); the run's start moves linearly from line to line and is
+// kept in fixed point, so the weights keep full precision without FP64 per
+// line:
 //   xm(w) = B - slope * w   (first candidate = floor(xm) + 1)
 //   weight_i = max(0, 1 - |g (delta + i) - 1|), delta = 1 - frac(xm).
-// B and slope are formed once per thread in FP64 from the FP64 angle table.
 //
-// A block covers 128 consecutive bins of one angle; their candidates on 32
-// consecutive lines lie in one strip of the image, which the block stages in
-// shared memory with coalesced loads (rows of the strip for the row walk,
-// 32-column segments for the column walk, transposed into shared memory), so
-// every candidate is a shared-memory read.  Pixels outside the image are
-// staged as zeros.  Geometries whose strip would not fit (pixel_size /
-// det_spacing < 1/4) use the same walk with direct global loads.
+// * Gather form (fwd_strip_kernel, fwd_kernel): one thread per output bin
+//   (k, j) walks every line; no atomics, deterministic.  A block covers 128
+//   consecutive bins of one angle; their candidates on 32 consecutive lines
+//   lie in one strip of the image, which the block stages in shared memory
+//   with coalesced loads (rows of the strip for the row walk, 32-column
+//   segments for the column walk, transposed into shared memory).  Pixels
+//   outside the image are staged as zeros.  Geometries whose strip would not
+//   fit (pixel_size / det_spacing < 1/4) use the same walk with direct
+//   global loads.
+// * Tile-owned form (fwd_tile_kernel, below): one block per image tile visits
+//   every angle, so the image is read once per call rather than once per
+//   angle; partial bins are combined with floating-point atomics.
 #include <algorithm>
 #include <cmath>
 
@@ -257,6 +260,194 @@ __global__ void __launch_bounds__(kBins) fwd_strip_kernel(FwdArgs a)
     if (j < a.D) a.sino[((size_t)sl * a.K + k) * a.D + j] = acc;
 }
 
+
+// ---------------------------------------------------------------------------
+// Tile-owned form.  One block per 64 x 64 pixel tile (and slice) stages the
+// tile once in shared memory and visits every angle; per angle it walks only
+// the bins the tile's footprint covers, over the tile's own lines, with the
+// same support solve as above, and adds each bin's partial sum to the
+// sinogram with a global floating-point reduction.  The image is therefore
+// read from memory once per call instead of once per angle, at the price of
+// a summation order over tiles that is not fixed from run to run.
+//
+// Positions on a line are kept in 9.23 fixed point (plus an integer bias of
+// 4, so that floor(P) + 4 is the first candidate's index in the padded
+// tile); each bin's position at its first line is formed exactly from 32.32
+// per-(tile, angle) values computed in FP64, and the per-line step is
+// rounded to 2^-24, so after the at most 64 / LS steps of one walk the
+// position is within 1e-6 pixel.
+//
+// Candidate weights, with e = g * (x1 - P) in (0, g] for the first candidate
+// x1 = floor(P) + 1 and g in [2/3, 1] (pixel / bin ratio alpha in
+// [0.9429, 1]): w0 = e, w1 = 1 - |e + g - 1|, w2 = max(0, 2 - 2g - e); a
+// fourth candidate would have weight max(0, 2 - 3g - e) = 0.
+// ---------------------------------------------------------------------------
+constexpr int kTT = 64;                  // tile side
+constexpr int kTPad = 3;                 // zero border; clamped candidate reads land in it
+constexpr int kTSide = kTT + 2 * kTPad;  // 70
+constexpr int kTPitch = 71;              // odd: a column walk's lanes read distinct banks
+constexpr int kTThreads = 256;
+constexpr int kTChunk = kTThreads;       // angles whose walk parameters are staged together
+constexpr int kFrac = 23;                // fraction bits of a walk position
+constexpr int kBias = 4;
+
+struct alignas(16) TileAngle {
+    long long P0;          // first-candidate position of bin jbase at line 0, 32.32, + kBias
+    long long BJ;          // step per bin, 32.32
+    long long SL;          // step per line (subtracted), 32.32
+    float g;               // alpha * max(|cos|, |sin|)
+    float p0f, bjf, slf;   // P0 (unbiased), BJ, SL as floats, for the line ranges
+    int jbase, W, walk_rows, pad_;
+};
+static_assert(sizeof(TileAngle) == 64, "TileAngle layout");
+
+struct FwdTileArgs {
+    const float *slice;
+    float *sino;
+    const double2 *cs;
+    int K, D, N;
+    double alpha, det_center;
+    int tiles_x;
+    int slice_base;
+};
+
+// Walk parameters of tile (r0, c0) for angle k, in FP64.  Bin j's ray meets
+// line l of the tile (row r0 + l for a row walk, column c0 + l otherwise) at
+// tile-local coordinate t = (j - c_d - cq (l0 + l - m)) / cp - s0 + m, and
+// the bins that any tile pixel touches are floor(u_min) .. floor(u_max) + 1.
+__device__ __forceinline__ TileAngle tile_angle_setup(const FwdTileArgs &a, int k, int r0, int c0)
+{
+    const double2 cs = a.cs[k];
+    const double m = 0.5 * (a.N - 1);
+    const double ax = a.alpha * cs.x, ay = a.alpha * cs.y;
+    const double ua = ax * ((double)c0 - m) + ay * ((double)r0 - m) + a.det_center;
+    const double dx = ax * (kTT - 1), dy = ay * (kTT - 1);
+    const double umin = ua + fmin(0.0, dx) + fmin(0.0, dy);
+    const double umax = ua + fmax(0.0, dx) + fmax(0.0, dy);
+    TileAngle p;
+    p.jbase = (int)floor(umin);
+    p.W = (int)floor(umax) + 2 - p.jbase;
+    p.walk_rows = fabs(cs.x) >= fabs(cs.y);
+    const double cp = p.walk_rows ? ax : ay;          // along the solved axis
+    const double cq = p.walk_rows ? ay : ax;          // along the line axis
+    const double s0 = p.walk_rows ? c0 : r0, l0 = p.walk_rows ? r0 : c0;
+    const double P0 = ((double)p.jbase - a.det_center - cq * (l0 - m)) / cp - s0 + m - 1.0 / fabs(cp);
+    const double BJ = 1.0 / cp, SL = cq / cp;
+    const double two32 = 4294967296.0;
+    p.P0 = __double2ll_rn((P0 + kBias) * two32);
+    p.BJ = __double2ll_rn(BJ * two32);
+    p.SL = __double2ll_rn(SL * two32);
+    p.g = (float)fabs(cp);
+    p.p0f = (float)P0;
+    p.bjf = (float)BJ;
+    p.slf = (float)SL;
+    p.pad_ = 0;
+    return p;
+}
+
+// One lane's walk over lines lo + lsub, lo + lsub + LS, ... <= hi.
+template <int LS, bool ROWS>
+__device__ __forceinline__ float tile_walk(uint32_t tile_s, long long Pb, long long SL, int lo,
+                                           int hi, int lsub, float g)
+{
+    constexpr int LW = ROWS ? kTPitch : 1;   // words between lines
+    constexpr int SW = ROWS ? 1 : kTPitch;   // words between candidates
+    int l = lo + lsub;
+    float acc = 0.f;
+    if (l > hi) return acc;
+    const float twog = 2.f * g, gm1 = g - 1.f, c2 = 2.f - 2.f * g;
+    int P = (int)((Pb - (long long)l * SL) >> (32 - kFrac));
+    const int dP = (int)(((long long)LS * SL + (1LL << (31 - kFrac))) >> (32 - kFrac));
+    uint32_t lb = tile_s + 4u * (uint32_t)((l + kTPad) * LW);
+#pragma unroll 4
+    for (; l <= hi; l += LS) {
+        // first candidate's padded index, clamped into the zero border when
+        // every candidate lies outside the tile (negative -> huge unsigned)
+        const uint32_t c = min((uint32_t)(P >> kFrac), (uint32_t)(kTT + kTPad));
+        const uint32_t ad = lb + c * (4u * SW);
+        const float F = __uint_as_float(((uint32_t)P & 0x7fffffu) | 0x3f800000u);   // 1 + frac(P)
+        const float e = fmaf(-g, F, twog);                                           // g * (2 - F)
+        const float w1 = 1.f - fabsf(e + gm1);
+        const float w2 = fmaxf(0.f, c2 - e);
+        float v0, v1, v2;
+        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v0) : "r"(ad));
+        asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v1) : "r"(ad), "n"(4 * SW));
+        asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v2) : "r"(ad), "n"(8 * SW));
+        acc = fmaf(e, v0, acc);
+        acc = fmaf(w1, v1, acc);
+        acc = fmaf(w2, v2, acc);
+        P -= dP;
+        lb += 4u * LS * LW;
+    }
+    return acc;
+}
+
+template <int BPW>
+__global__ void __launch_bounds__(kTThreads, 4) fwd_tile_kernel(FwdTileArgs a)
+{
+    constexpr int LS = 32 / BPW;             // lines walked side by side in a warp
+    __shared__ float tile[kTSide * kTPitch];
+    __shared__ TileAngle prm[kTChunk];
+    const int N = a.N;
+    const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x - ty * a.tiles_x;
+    const int r0 = ty * kTT, c0 = tx * kTT;
+    const int sl = a.slice_base + blockIdx.y;
+    const float *f = a.slice + (size_t)sl * N * N;
+    for (int i = threadIdx.x; i < kTSide * kTPitch; i += kTThreads) {
+        const int rr = i / kTPitch, cc = i - rr * kTPitch;
+        const int r = r0 + rr - kTPad, c = c0 + cc - kTPad;
+        const bool in = rr >= kTPad && rr < kTPad + kTT && cc >= kTPad && cc < kTPad + kTT &&
+                        r < N && c < N;
+        tile[i] = in ? __ldg(f + (size_t)r * N + c) : 0.f;
+    }
+    const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int bl = lane % BPW, lsub = lane / BPW;
+    for (int k0 = 0; k0 < a.K; k0 += kTChunk) {
+        __syncthreads();                     // tile staged / previous chunk consumed
+        if (k0 + (int)threadIdx.x < a.K)
+            prm[threadIdx.x] = tile_angle_setup(a, k0 + threadIdx.x, r0, c0);
+        __syncthreads();
+        const int kc = min(kTChunk, a.K - k0);
+        for (int ki = warp; ki < kc; ki += kTThreads / 32) {
+            const TileAngle p = prm[ki];
+            float *out = a.sino + ((size_t)sl * a.K + (k0 + ki)) * a.D;
+            const int ng = (p.W + BPW - 1) / BPW;
+            for (int q = 0; q < ng; ++q) {
+                // lines on which some bin of the group has a candidate inside
+                // the tile: max_b P >= -3 and min_b P < T - 1, P = P(b,0) - l SL
+                // (float bounds with slack; excluded lines contribute nothing)
+                const int bA = q * BPW, bB = min(bA + BPW - 1, p.W - 1);
+                const float PA = fmaf((float)bA, p.bjf, p.p0f), PB = fmaf((float)bB, p.bjf, p.p0f);
+                const float Pl = fminf(PA, PB) - 0.01f, Ph = fmaxf(PA, PB) + 0.01f;
+                float lo_f = 0.f, hi_f = (float)(kTT - 1);
+                if (p.slf > 0.f) {
+                    hi_f = fminf(hi_f, (Ph + 3.f) / p.slf);
+                    lo_f = fmaxf(lo_f, (Pl - (float)(kTT - 1)) / p.slf);
+                } else if (p.slf < 0.f) {
+                    lo_f = fmaxf(lo_f, (Ph + 3.f) / p.slf);
+                    hi_f = fminf(hi_f, (Pl - (float)(kTT - 1)) / p.slf);
+                } else if (!(Ph >= -3.f && Pl < (float)(kTT - 1))) {
+                    hi_f = -1.f;
+                }
+                lo_f = fminf(lo_f, (float)kTT);
+                hi_f = fmaxf(hi_f, -1.f);
+                const int lo = max(0, (int)floorf(lo_f) - 1);
+                const int hi = min(kTT - 1, (int)floorf(hi_f) + 1);
+                const int b = bA + bl;
+                const long long Pb = p.P0 + (long long)b * p.BJ;
+                float acc = p.walk_rows ? tile_walk<LS, true>(tile_s, Pb, p.SL, lo, hi, lsub, p.g)
+                                        : tile_walk<LS, false>(tile_s, Pb, p.SL, lo, hi, lsub, p.g);
+#pragma unroll
+                for (int o = BPW; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                const int j = p.jbase + b;
+                if (lsub == 0 && b < p.W && (unsigned)j < (unsigned)a.D && acc != 0.f)
+                    atomicAdd(out + j, acc);
+            }
+        }
+    }
+}
+
 }  // namespace
 
 // Staged strip width for a geometry: candidates of 128 bins over 32 lines
@@ -270,9 +461,51 @@ int fwd_span_pitch(double alpha, int ncmax)
     return (size_t)kLines * pitch * sizeof(float) <= 160 * 1024 ? pitch : 0;
 }
 
+bool fwd_tile_eligible(double alpha)
+{
+    // g = alpha * max(|cos|, |sin|) must lie in [2/3, 1] for the three-candidate weights
+    return alpha >= 0.9429 && alpha <= 1.0;
+}
+
+int fwd_variant_count() { return 4; }
+
+static fbp_status launch_forward_tile(const FwdLaunch &L, int v, cudaStream_t s)
+{
+    if (!fwd_tile_eligible(L.alpha))
+        return fail(FBP_ERR_UNSUPPORTED, "tile forward projector needs pixel_size / det_spacing in [0.9429, 1]");
+    FwdTileArgs a;
+    a.slice = L.slice;
+    a.sino = L.sino;
+    a.cs = L.cs;
+    a.K = L.K;
+    a.D = L.D;
+    a.N = L.N;
+    a.alpha = L.alpha;
+    a.det_center = L.det_center;
+    a.tiles_x = (L.N + kTT - 1) / kTT;
+    const long long tiles = (long long)a.tiles_x * a.tiles_x;
+    if (tiles > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "too many image tiles");
+    FBP_CUDA_TRY(cudaMemsetAsync(L.sino, 0, (size_t)L.S * L.K * L.D * sizeof(float), s));
+    for (int base = 0; base < L.S; base += 65535) {
+        a.slice_base = base;
+        dim3 grid((unsigned)tiles, (unsigned)std::min(65535, L.S - base));
+        switch (v) {
+        case 1: fwd_tile_kernel<8><<<grid, kTThreads, 0, s>>>(a); break;
+        case 2: fwd_tile_kernel<16><<<grid, kTThreads, 0, s>>>(a); break;
+        default: fwd_tile_kernel<32><<<grid, kTThreads, 0, s>>>(a); break;
+        }
+        FBP_CUDA_TRY(cudaGetLastError());
+    }
+    return FBP_OK;
+}
+
 fbp_status launch_forward(const FwdLaunch &L, cudaStream_t s)
 {
     if (L.S <= 0) return FBP_OK;
+    int v = L.variant;
+    if (v < 0) v = fwd_tile_eligible(L.alpha) ? 2 : 0;      // 16 bins x 2 lines per warp measured fastest
+    if (v >= fwd_variant_count()) return fail(FBP_ERR_INVALID_ARG, "forward variant %d out of range", v);
+    if (v > 0) return launch_forward_tile(L, v, s);
     FwdArgs a;
     a.slice = L.slice;
     a.sino = L.sino;

@@ -2,6 +2,8 @@
 adjoint identity between K3 and K2; autograd gradients vs the oracle's FP64
 gradient and vs finite differences; least-squares refinement vs the oracle's
 FP64 run."""
+import math
+
 import numpy as np
 import pytest
 
@@ -42,6 +44,64 @@ def test_forward_matches_oracle(G):
     p = api.radon_forward(to_gpu(x), g)
     ref = oracle.forward(x.astype(np.float64), go)
     assert_within_dr(to_np(p), ref, TOL, str(G))
+
+
+def tile_eligible(G):
+    a = G.get("pixel_size", 1.0) / G.get("det_spacing", 1.0)
+    return 0.9429 <= a <= 1.0
+
+
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("G", GEOMS, ids=lambda G: "x".join(f"{k}{v}" for k, v in G.items()))
+def test_forward_variants_match_oracle(variant, G):
+    """Every forward kernel (0: gather; 1-3: tile-owned with 8/16/32 bins per
+    warp) on every geometry; the tile-owned form refuses pixel/bin ratios
+    outside [0.9429, 1]."""
+    api = fbp_api()
+    g, go = make(api, G)
+    rng = np.random.default_rng(G["N"] + 7 * G["K"])
+    x = rng.standard_normal((2, G["N"], G["N"])).astype(np.float32)
+    if variant > 0 and not tile_eligible(G):
+        with pytest.raises(api.FbpError, match="UNSUPPORTED"):
+            api.radon_forward(to_gpu(x), g, variant=variant)
+        return
+    p = to_np(api.radon_forward(to_gpu(x), g, variant=variant))
+    for s in range(2):
+        ref = oracle.forward(x[s].astype(np.float64), go)
+        assert_within_dr(p[s], ref, TOL, f"variant {variant} {G}")
+
+
+def test_forward_variant_out_of_range_rejected():
+    api = fbp_api()
+    g = api.Geometry(8, 8, 8)
+    x = torch.zeros((8, 8), device="cuda")
+    for v in (-2, api.forward_variant_count()):
+        with pytest.raises(api.FbpError, match="INVALID_ARG"):
+            api.radon_forward(x, g, variant=v)
+
+
+def test_forward_tile_full_size_sampled_angles():
+    """The tile-owned projector at the refinement workload's size and launch
+    (16 slices, N = 1024, 1800 angles), on FBP images of the workload's
+    sinograms: sampled angles (including 0, pi/4, pi/2 and their
+    neighbours, where the walk axis switches) against the oracle, and every
+    bin against the deterministic gather kernel."""
+    api = fbp_api()
+    w = phantoms.WORKLOADS["gd_refine_n1024"]
+    N, K = 1024, 1800
+    g = api.Geometry(K, N, N)
+    sinos = np.stack([phantoms.slice_sinogram(w, i) for i in range(16)])
+    x = api.fbp(to_gpu(sinos), g)
+    p = api.radon_forward(x, g, variant=1)
+    p0 = api.radon_forward(x, g, variant=0)
+    dr = (p0.max() - p0.min()).item()
+    assert (p - p0).abs().max().item() <= 1e-5 * dr
+    pn, xn = to_np(p), to_np(x)
+    for s in (0, 15):
+        for k in (0, 1, 449, 450, 451, 899, 900, 901, 1349, 1350, 1799):
+            go = oracle.Geometry(1, N, N, angle_start=k * (math.pi / K))
+            ref = oracle.forward(xn[s].astype(np.float64), go)[0]
+            assert np.max(np.abs(pn[s, k] - ref)) <= TOL * dr, (s, k)
 
 
 def test_forward_multi_slice_and_mass():

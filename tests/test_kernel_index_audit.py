@@ -310,3 +310,109 @@ def test_forward_strip_n1024_and_n8192_sampled_angles():
     for N, K in ((1024, 1800), (8192, 4096)):
         ks = [0, 1, K // 4 - 1, K // 4, K // 2 - 1, K // 2, K // 2 + 1, 3 * K // 4, K - 1, 777 % K]
         fwd_strip_audit(N, N, K, 1.0, 0.5 * (N - 1), ks)
+
+
+# ---------------------------------------------------------------------------
+# Forward projector, tile-owned form (forward.cu, fwd_tile_kernel): a replay
+# of its fixed-point walk, checked for int32 range, padded-tile indices and
+# coverage (the replayed projection equals the oracle's).
+# ---------------------------------------------------------------------------
+FT, FPAD, FBIAS, FFRAC = 64, 3, 4, 23
+
+
+def fwd_tile_replay(img, K, D, alpha, det_center, bpw):
+    """Returns (projection [K][D], min P, max P, max padded index) of the
+    kernel's arithmetic on image img (N x N)."""
+    N = img.shape[0]
+    LS = 32 // bpw
+    m = 0.5 * (N - 1)
+    tiles_x = -(-N // FT)
+    th = np.arange(K) * (math.pi / K)
+    out = np.zeros((K, D))
+    pmin, pmax, imax = 0, 0, 0
+    two32 = 4294967296.0
+    pad = np.zeros((FT + 2 * FPAD, FT + 2 * FPAD))
+    for ty in range(tiles_x):
+        for tx in range(tiles_x):
+            r0, c0 = ty * FT, tx * FT
+            pad[:] = 0.0
+            blk = img[r0:r0 + FT, c0:c0 + FT]
+            pad[FPAD:FPAD + blk.shape[0], FPAD:FPAD + blk.shape[1]] = blk
+            for k in range(K):
+                cs, sn = math.cos(th[k]), math.sin(th[k])
+                ax, ay = alpha * cs, alpha * sn
+                ua = ax * (c0 - m) + ay * (r0 - m) + det_center
+                dx, dy = ax * (FT - 1), ay * (FT - 1)
+                umin = ua + min(0.0, dx) + min(0.0, dy)
+                umax = ua + max(0.0, dx) + max(0.0, dy)
+                jbase = math.floor(umin)
+                W = math.floor(umax) + 2 - jbase
+                rows = abs(cs) >= abs(sn)
+                cp, cq = (ax, ay) if rows else (ay, ax)
+                s0, l0 = (c0, r0) if rows else (r0, c0)
+                P0 = (jbase - det_center - cq * (l0 - m)) / cp - s0 + m - 1.0 / abs(cp)
+                BJ, SL = 1.0 / cp, cq / cp
+                P0i = int(np.rint((P0 + FBIAS) * two32))
+                BJi = int(np.rint(BJ * two32))
+                SLi = int(np.rint(SL * two32))
+                g = np.float32(abs(cp))
+                p0f, bjf, slf = np.float32(P0), np.float32(BJ), np.float32(SL)
+                dP = (LS * SLi + (1 << (31 - FFRAC))) >> (32 - FFRAC)
+                for q in range(-(-W // bpw)):
+                    bA, bB = q * bpw, min(q * bpw + bpw - 1, W - 1)
+                    PA = np.float32(np.float32(bA) * bjf + p0f)
+                    PB = np.float32(np.float32(bB) * bjf + p0f)
+                    Pl, Ph = np.float32(min(PA, PB) - 0.01), np.float32(max(PA, PB) + 0.01)
+                    lo_f, hi_f = 0.0, float(FT - 1)
+                    if slf > 0:
+                        hi_f = min(hi_f, float(np.float32((Ph + 3) / slf)))
+                        lo_f = max(lo_f, float(np.float32((Pl - (FT - 1)) / slf)))
+                    elif slf < 0:
+                        lo_f = max(lo_f, float(np.float32((Ph + 3) / slf)))
+                        hi_f = min(hi_f, float(np.float32((Pl - (FT - 1)) / slf)))
+                    elif not (Ph >= -3 and Pl < FT - 1):
+                        hi_f = -1.0
+                    lo = max(0, math.floor(min(lo_f, FT)) - 1)
+                    hi = min(FT - 1, math.floor(max(hi_f, -1.0)) + 1)
+                    for bl in range(bpw):
+                        b = bA + bl
+                        Pb = P0i + b * BJi
+                        acc = 0.0
+                        for lsub in range(LS):
+                            l = lo + lsub
+                            if l > hi:
+                                continue
+                            P = (Pb - l * SLi) >> (32 - FFRAC)
+                            while l <= hi:
+                                pmin, pmax = min(pmin, P), max(pmax, P)
+                                st = P >> FFRAC
+                                c = st if 0 <= st <= FT + FPAD else FT + FPAD
+                                imax = max(imax, c + 2)
+                                F = 1.0 + (P & 0x7FFFFF) / 8388608.0
+                                e = float(g) * (2.0 - F)
+                                w = (e, 1.0 - abs(e + float(g) - 1.0), max(0.0, 2.0 - 2.0 * float(g) - e))
+                                for i in range(3):
+                                    v = pad[l + FPAD, c + i] if rows else pad[c + i, l + FPAD]
+                                    acc += w[i] * v
+                                P -= dP
+                                l += LS
+                        j = jbase + b
+                        if b < W and 0 <= j < D:
+                            out[k, j] += acc
+    return out, pmin, pmax, imax
+
+
+@pytest.mark.parametrize("bpw", [8, 32])
+@pytest.mark.parametrize("N,D,K,alpha", [(64, 64, 12, 1.0), (100, 110, 10, 0.95), (130, 128, 8, 1.0)])
+def test_forward_tile_replay_matches_oracle(bpw, N, D, K, alpha):
+    import oracle
+    rng = np.random.default_rng(N + K)
+    img = rng.standard_normal((N, N))
+    dc = 0.5 * (D - 1)
+    out, pmin, pmax, imax = fwd_tile_replay(img, K, D, alpha, dc, bpw)
+    assert -(1 << 31) <= pmin and pmax < (1 << 31)
+    assert -256 * (1 << FFRAC) < pmin and pmax < 256 * (1 << FFRAC)   # 9.23 with the bias
+    assert imax <= FT + 2 * FPAD - 1
+    g = oracle.Geometry(K, D, N, pixel_size=alpha)
+    ref = oracle.forward(img, g)
+    assert np.max(np.abs(out - ref)) <= 1e-5 * np.max(np.abs(ref))
