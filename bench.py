@@ -471,12 +471,14 @@ def run_uniform(args) -> None:
         r = results[dt]
         rpd = roofline_peak(sm_max, dt)
         ach = updates / (r["bp_ms"] / 1e3) / 1e9
+        vdt = resolved_variant(api, g, dt, args.variant)
         line[f"staged_{dt}"] = {
             "value": r["value"], "unit": UNIT, "ratio_to_f32": r["value"] / main["value"],
             "bp_gupdates_per_s": ach, "bp_ratio_to_f32": ach / achieved,
             "roofline_frac": ach / rpd["peak"], "roofline_peak": rpd["peak"],
+            "traffic": captured_traffic(vdt, dt, S),
             "slices_per_s": r["slices_per_s"], "ms_per_step": r["ms_per_step"],
-            "bp_variant": resolved_variant(api, g, dt, args.variant)}
+            "bp_variant": vdt}
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and ws == 1:
