@@ -201,10 +201,10 @@ def bp_source_hash() -> str:
     return h.hexdigest()[:16]
 
 
-def captured_traffic(variant: int, dtype: str, n_slices: int):
+def captured_traffic(variant: int, dtype: str, n_slices: int, n: int, k: int):
     """DRAM bytes per backprojection launch from the committed ncu capture,
     scaled by slices; None when the kernel sources changed since the capture
-    or the launch differs (variant, dtype)."""
+    or the launch differs (variant, dtype, image size, angle count)."""
     try:
         with open(os.path.join(ROOT, "profiles", "bp_traffic.json")) as f:
             entries = json.load(f)
@@ -213,7 +213,7 @@ def captured_traffic(variant: int, dtype: str, n_slices: int):
     for t in entries if isinstance(entries, list) else [entries]:
         if t.get("source_hash") != bp_source_hash() or t.get("dtype") != dtype:
             continue
-        if variant != t.get("variant"):
+        if variant != t.get("variant") or t.get("n") != n or t.get("k") != k:
             continue
         return float(t["dram_bytes_per_slice"]) * n_slices
     return None
@@ -445,7 +445,7 @@ def run_uniform(args) -> None:
     variant = resolved_variant(api, g, args.dtype, args.variant)
     traffic = args.traffic_bytes
     if traffic is None:
-        traffic = captured_traffic(variant, args.dtype, S)
+        traffic = captured_traffic(variant, args.dtype, S, N, K)
     phantom = "Shepp-Logan" if w.phantom == "shepp_logan" else "random ellipses (20-50)"
     noise = f"Poisson {w.photons:g} photons" if w.photons else "noise-free"
     line = base_line(args, ws, main["value"], main["ms_per_step"], DT_LABEL[args.dtype], {
@@ -476,7 +476,7 @@ def run_uniform(args) -> None:
             "value": r["value"], "unit": UNIT, "ratio_to_f32": r["value"] / main["value"],
             "bp_gupdates_per_s": ach, "bp_ratio_to_f32": ach / achieved,
             "roofline_frac": ach / rpd["peak"], "roofline_peak": rpd["peak"],
-            "traffic": captured_traffic(vdt, dt, S),
+            "traffic": captured_traffic(vdt, dt, S, N, K),
             "slices_per_s": r["slices_per_s"], "ms_per_step": r["ms_per_step"],
             "bp_variant": vdt}
     if e2e is not None:
