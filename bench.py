@@ -600,7 +600,7 @@ def run_gd(args) -> None:
         finish({}, ws, rank)
         return
     a_ms, at_ms = T.between(0, 1), T.between(1, 2)
-    fwd_variant = args.fwd_variant if args.fwd_variant >= 0 else 2
+    fwd_variant = args.fwd_variant if args.fwd_variant >= 0 else 4
     sm_max = peaks().get("sm_max_mhz") or 2070.0
     rp = roofline_peak(sm_max, "f32")
     a_rate = S * N * N * K / a_ms / 1e6

@@ -208,13 +208,15 @@ fbp_status radon_forward(const float *slice, float *sino, const fbp_geometry *g,
  * radon_forward with an explicit kernel:
  *   0   gather form: one thread per output bin walks the image; deterministic,
  *       any pixel_size / det_spacing in [1/8, 2.5].
- *   1-3 tile-owned form: one block per 64 x 64 pixel tile visits every angle
- *       and adds per-tile partial bins with floating-point atomics (8, 16 or
- *       32 bins per warp).  The sum over tiles is not in a fixed order, so
+ *   1-5 tile-owned form: one block per 64 x 64 pixel tile visits every angle
+ *       and adds per-tile partial bins with floating-point atomics; 1-3 take
+ *       one slice per block (8, 16 or 32 bins per warp), 4 takes four slices
+ *       per block and 5 two (one shared-memory load serves every slice;
+ *       leftover slices run through the narrower forms).  The sum over tiles is not in a fixed order, so
  *       results may differ between runs in the last bits.  Needs
  *       pixel_size / det_spacing in [0.9429, 1] (FBP_ERR_UNSUPPORTED
  *       otherwise).  The sinogram is cleared on `stream` first.
- *  -1   the default: variant 2 where the tile-owned form applies, else 0.
+ *  -1   the default: the fastest tile-owned variant where it applies, else 0.
  * Other values return FBP_ERR_INVALID_ARG.
  */
 fbp_status radon_forward_variant(const float *slice, float *sino, const fbp_geometry *g,

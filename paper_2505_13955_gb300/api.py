@@ -146,8 +146,9 @@ def backproject(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None 
 def radon_forward(img: torch.Tensor, g: Geometry, out: torch.Tensor | None = None,
                   which: str = "default", variant: int = -1):
     """radon_forward: the matched projector A (transpose of backproject, scale 1).
-    variant -1 = library default, 0 = deterministic gather, 1..3 = tile-owned
-    (floating-point atomics across tiles)."""
+    variant -1 = library default, 0 = deterministic gather, 1..5 = tile-owned
+    (floating-point atomics across tiles; 4 and 5 take four / two slices per
+    block)."""
     _need(img, "slice", torch.float32)
     S = _slices(img, (g.n, g.n), "slice")
     shape = (g.n_angles, g.n_det) if img.dim() == 2 else (S, g.n_angles, g.n_det)
@@ -224,7 +225,7 @@ def fbp_host(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32
 
 
 def forward_variant_count(which: str = "default") -> int:
-    """Number of radon_forward kernels (0 = gather, 1..3 = tile-owned)."""
+    """Number of radon_forward kernels (0 = gather, 1..5 = tile-owned)."""
     return int(lib(which).radon_forward_variant_count())
 
 

@@ -345,62 +345,93 @@ __device__ __forceinline__ TileAngle tile_angle_setup(const FwdTileArgs &a, int 
     return p;
 }
 
-// One lane's walk over lines lo + lsub, lo + lsub + LS, ... <= hi.
-template <int LS, bool ROWS>
-__device__ __forceinline__ float tile_walk(uint32_t tile_s, long long Pb, long long SL, int lo,
-                                           int hi, int lsub, float g)
+// Vector of NS slices' pixels at one tile position (NS = 1, 2 or 4): the
+// multi-slice kernels read the same candidates of NS slices with one 8- or
+// 16-byte shared load and share the position and weight arithmetic.
+template <int NS> struct PixVec;
+template <> struct PixVec<1> { using T = float; };
+template <> struct PixVec<2> { using T = float2; };
+template <> struct PixVec<4> { using T = float4; };
+__device__ __forceinline__ float comp(const float &v, int) { return v; }
+__device__ __forceinline__ float comp(const float2 &v, int s) { return s == 0 ? v.x : v.y; }
+__device__ __forceinline__ float comp(const float4 &v, int s)
 {
-    constexpr int LW = ROWS ? kTPitch : 1;   // words between lines
-    constexpr int SW = ROWS ? 1 : kTPitch;   // words between candidates
+    return s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w;
+}
+__device__ __forceinline__ void set_comp(float &v, int, float x) { v = x; }
+__device__ __forceinline__ void set_comp(float2 &v, int s, float x) { (s == 0 ? v.x : v.y) = x; }
+__device__ __forceinline__ void set_comp(float4 &v, int s, float x)
+{
+    (s == 0 ? v.x : s == 1 ? v.y : s == 2 ? v.z : v.w) = x;
+}
+
+// One lane's walk over lines lo + lsub, lo + lsub + LS, ... <= hi.
+template <int LS, bool ROWS, int NS>
+__device__ __forceinline__ void tile_walk(const typename PixVec<NS>::T *tile, long long Pb,
+                                          long long SL, int lo, int hi, int lsub, float g,
+                                          float (&acc)[NS])
+{
+    using V = typename PixVec<NS>::T;
+    constexpr int LW = ROWS ? kTPitch : 1;   // elements between lines
+    constexpr int SW = ROWS ? 1 : kTPitch;   // elements between candidates
     int l = lo + lsub;
-    float acc = 0.f;
-    if (l > hi) return acc;
+    if (l > hi) return;
     const float twog = 2.f * g, gm1 = g - 1.f, c2 = 2.f - 2.f * g;
     int P = (int)((Pb - (long long)l * SL) >> (32 - kFrac));
     const int dP = (int)(((long long)LS * SL + (1LL << (31 - kFrac))) >> (32 - kFrac));
-    uint32_t lb = tile_s + 4u * (uint32_t)((l + kTPad) * LW);
+    int lb = (l + kTPad) * LW;
 #pragma unroll 4
     for (; l <= hi; l += LS) {
         // first candidate's padded index, clamped into the zero border when
         // every candidate lies outside the tile (negative -> huge unsigned)
         const uint32_t c = min((uint32_t)(P >> kFrac), (uint32_t)(kTT + kTPad));
-        const uint32_t ad = lb + c * (4u * SW);
+        const V *e = tile + lb + (int)c * SW;
         const float F = __uint_as_float(((uint32_t)P & 0x7fffffu) | 0x3f800000u);   // 1 + frac(P)
-        const float e = fmaf(-g, F, twog);                                           // g * (2 - F)
-        const float w1 = 1.f - fabsf(e + gm1);
-        const float w2 = fmaxf(0.f, c2 - e);
-        float v0, v1, v2;
-        asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v0) : "r"(ad));
-        asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v1) : "r"(ad), "n"(4 * SW));
-        asm volatile("ld.shared.f32 %0, [%1+%2];" : "=f"(v2) : "r"(ad), "n"(8 * SW));
-        acc = fmaf(e, v0, acc);
-        acc = fmaf(w1, v1, acc);
-        acc = fmaf(w2, v2, acc);
+        const float w0 = fmaf(-g, F, twog);                                          // g * (2 - F)
+        const float w1 = 1.f - fabsf(w0 + gm1);
+        const float w2 = fmaxf(0.f, c2 - w0);
+        const V v0 = e[0], v1 = e[SW], v2 = e[2 * SW];
+#pragma unroll
+        for (int t = 0; t < NS; ++t) {
+            acc[t] = fmaf(w0, comp(v0, t), acc[t]);
+            acc[t] = fmaf(w1, comp(v1, t), acc[t]);
+            acc[t] = fmaf(w2, comp(v2, t), acc[t]);
+        }
         P -= dP;
-        lb += 4u * LS * LW;
+        lb += LS * LW;
     }
-    return acc;
 }
 
-template <int BPW>
-__global__ void __launch_bounds__(kTThreads, 4) fwd_tile_kernel(FwdTileArgs a)
+template <int NS>
+constexpr size_t tile_bytes() { return ((size_t)kTSide * kTPitch * 4 * NS + 63) / 64 * 64; }
+template <int NS>
+constexpr size_t tile_smem() { return tile_bytes<NS>() + (size_t)kTChunk * sizeof(TileAngle); }
+
+// NS slices per block (slices slice_base + NS * blockIdx.y + [0, NS)).
+template <int BPW, int NS>
+__global__ void __launch_bounds__(kTThreads, NS == 4 ? 2 : 4) fwd_tile_kernel(FwdTileArgs a)
 {
+    using V = typename PixVec<NS>::T;
     constexpr int LS = 32 / BPW;             // lines walked side by side in a warp
-    __shared__ float tile[kTSide * kTPitch];
-    __shared__ TileAngle prm[kTChunk];
+    extern __shared__ __align__(64) unsigned char fwd_smem[];
+    V *tile = reinterpret_cast<V *>(fwd_smem);
+    TileAngle *prm = reinterpret_cast<TileAngle *>(fwd_smem + tile_bytes<NS>());
     const int N = a.N;
     const int ty = blockIdx.x / a.tiles_x, tx = blockIdx.x - ty * a.tiles_x;
     const int r0 = ty * kTT, c0 = tx * kTT;
-    const int sl = a.slice_base + blockIdx.y;
-    const float *f = a.slice + (size_t)sl * N * N;
+    const int sl0 = a.slice_base + NS * blockIdx.y;
+    const float *f = a.slice + (size_t)sl0 * N * N;
     for (int i = threadIdx.x; i < kTSide * kTPitch; i += kTThreads) {
         const int rr = i / kTPitch, cc = i - rr * kTPitch;
         const int r = r0 + rr - kTPad, c = c0 + cc - kTPad;
         const bool in = rr >= kTPad && rr < kTPad + kTT && cc >= kTPad && cc < kTPad + kTT &&
                         r < N && c < N;
-        tile[i] = in ? __ldg(f + (size_t)r * N + c) : 0.f;
+        V v;
+#pragma unroll
+        for (int t = 0; t < NS; ++t)
+            set_comp(v, t, in ? __ldg(f + (size_t)t * N * N + (size_t)r * N + c) : 0.f);
+        tile[i] = v;
     }
-    const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bl = lane % BPW, lsub = lane / BPW;
     for (int k0 = 0; k0 < a.K; k0 += kTChunk) {
@@ -411,7 +442,7 @@ __global__ void __launch_bounds__(kTThreads, 4) fwd_tile_kernel(FwdTileArgs a)
         const int kc = min(kTChunk, a.K - k0);
         for (int ki = warp; ki < kc; ki += kTThreads / 32) {
             const TileAngle p = prm[ki];
-            float *out = a.sino + ((size_t)sl * a.K + (k0 + ki)) * a.D;
+            float *out = a.sino + ((size_t)sl0 * a.K + (k0 + ki)) * a.D;
             const int ng = (p.W + BPW - 1) / BPW;
             for (int q = 0; q < ng; ++q) {
                 // lines on which some bin of the group has a candidate inside
@@ -436,13 +467,22 @@ __global__ void __launch_bounds__(kTThreads, 4) fwd_tile_kernel(FwdTileArgs a)
                 const int hi = min(kTT - 1, (int)floorf(hi_f) + 1);
                 const int b = bA + bl;
                 const long long Pb = p.P0 + (long long)b * p.BJ;
-                float acc = p.walk_rows ? tile_walk<LS, true>(tile_s, Pb, p.SL, lo, hi, lsub, p.g)
-                                        : tile_walk<LS, false>(tile_s, Pb, p.SL, lo, hi, lsub, p.g);
+                float acc[NS];
 #pragma unroll
-                for (int o = BPW; o < 32; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+                for (int t = 0; t < NS; ++t) acc[t] = 0.f;
+                if (p.walk_rows) tile_walk<LS, true, NS>(tile, Pb, p.SL, lo, hi, lsub, p.g, acc);
+                else tile_walk<LS, false, NS>(tile, Pb, p.SL, lo, hi, lsub, p.g, acc);
+#pragma unroll
+                for (int t = 0; t < NS; ++t) {
+#pragma unroll
+                    for (int o = BPW; o < 32; o <<= 1) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
+                }
                 const int j = p.jbase + b;
-                if (lsub == 0 && b < p.W && (unsigned)j < (unsigned)a.D && acc != 0.f)
-                    atomicAdd(out + j, acc);
+                if (lsub == 0 && b < p.W && (unsigned)j < (unsigned)a.D) {
+#pragma unroll
+                    for (int t = 0; t < NS; ++t)
+                        if (acc[t] != 0.f) atomicAdd(out + (size_t)t * a.K * a.D + j, acc[t]);
+                }
             }
         }
     }
@@ -467,8 +507,30 @@ bool fwd_tile_eligible(double alpha)
     return alpha >= 0.9429 && alpha <= 1.0;
 }
 
-int fwd_variant_count() { return 4; }
+int fwd_variant_count() { return 6; }
 
+template <int BPW, int NS>
+static fbp_status launch_tile_group(FwdTileArgs a, int first, int count, unsigned tiles, cudaStream_t s)
+{
+    // count slices from `first`, NS per block
+    const void *kern = reinterpret_cast<const void *>(fwd_tile_kernel<BPW, NS>);
+    constexpr size_t smem = tile_smem<NS>();
+    fbp_status st = ensure_dynamic_smem(kern, smem);
+    if (st != FBP_OK) return st;
+    const int groups = count / NS;
+    for (int g0 = 0; g0 < groups; g0 += 65535) {
+        a.slice_base = first + NS * g0;
+        dim3 grid(tiles, (unsigned)std::min(65535, groups - g0));
+        fwd_tile_kernel<BPW, NS><<<grid, kTThreads, smem, s>>>(a);
+        FBP_CUDA_TRY(cudaGetLastError());
+    }
+    return FBP_OK;
+}
+
+// Variants 1-3: one slice per block, 8 / 16 / 32 bins per warp.  Variant 4:
+// four slices per block (8 bins per warp, one 16-byte load per candidate),
+// variant 5: two slices per block (16 bins per warp); leftover slices of
+// either go through the narrower kernels.
 static fbp_status launch_forward_tile(const FwdLaunch &L, int v, cudaStream_t s)
 {
     if (!fwd_tile_eligible(L.alpha))
@@ -485,25 +547,33 @@ static fbp_status launch_forward_tile(const FwdLaunch &L, int v, cudaStream_t s)
     a.tiles_x = (L.N + kTT - 1) / kTT;
     const long long tiles = (long long)a.tiles_x * a.tiles_x;
     if (tiles > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "too many image tiles");
+    const unsigned nt = (unsigned)tiles;
     FBP_CUDA_TRY(cudaMemsetAsync(L.sino, 0, (size_t)L.S * L.K * L.D * sizeof(float), s));
-    for (int base = 0; base < L.S; base += 65535) {
-        a.slice_base = base;
-        dim3 grid((unsigned)tiles, (unsigned)std::min(65535, L.S - base));
-        switch (v) {
-        case 1: fwd_tile_kernel<8><<<grid, kTThreads, 0, s>>>(a); break;
-        case 2: fwd_tile_kernel<16><<<grid, kTThreads, 0, s>>>(a); break;
-        default: fwd_tile_kernel<32><<<grid, kTThreads, 0, s>>>(a); break;
-        }
-        FBP_CUDA_TRY(cudaGetLastError());
+    fbp_status st = FBP_OK;
+    int done = 0;
+    if (v == 4) {
+        const int n4 = L.S / 4 * 4;
+        if (n4) st = launch_tile_group<8, 4>(a, 0, n4, nt, s);
+        done = n4;
     }
-    return FBP_OK;
+    if (st == FBP_OK && (v == 4 || v == 5)) {
+        const int n2 = (L.S - done) / 2 * 2;
+        if (n2) st = launch_tile_group<16, 2>(a, done, n2, nt, s);
+        done += n2;
+    }
+    if (st != FBP_OK || done == L.S) return st;
+    switch (v) {
+    case 1: return launch_tile_group<8, 1>(a, done, L.S - done, nt, s);
+    case 3: return launch_tile_group<32, 1>(a, done, L.S - done, nt, s);
+    default: return launch_tile_group<16, 1>(a, done, L.S - done, nt, s);
+    }
 }
 
 fbp_status launch_forward(const FwdLaunch &L, cudaStream_t s)
 {
     if (L.S <= 0) return FBP_OK;
     int v = L.variant;
-    if (v < 0) v = fwd_tile_eligible(L.alpha) ? 2 : 0;      // 16 bins x 2 lines per warp measured fastest
+    if (v < 0) v = fwd_tile_eligible(L.alpha) ? 4 : 0;      // four slices per block measured fastest
     if (v >= fwd_variant_count()) return fail(FBP_ERR_INVALID_ARG, "forward variant %d out of range", v);
     if (v > 0) return launch_forward_tile(L, v, s);
     FwdArgs a;

@@ -51,22 +51,24 @@ def tile_eligible(G):
     return 0.9429 <= a <= 1.0
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
 @pytest.mark.parametrize("G", GEOMS, ids=lambda G: "x".join(f"{k}{v}" for k, v in G.items()))
 def test_forward_variants_match_oracle(variant, G):
     """Every forward kernel (0: gather; 1-3: tile-owned with 8/16/32 bins per
-    warp) on every geometry; the tile-owned form refuses pixel/bin ratios
-    outside [0.9429, 1]."""
+    warp; 4: four slices per block; 5: two slices per block) on every
+    geometry, with 7 slices so that the multi-slice variants also run their
+    two- and one-slice remainders; the tile-owned forms refuse pixel/bin
+    ratios outside [0.9429, 1]."""
     api = fbp_api()
     g, go = make(api, G)
     rng = np.random.default_rng(G["N"] + 7 * G["K"])
-    x = rng.standard_normal((2, G["N"], G["N"])).astype(np.float32)
+    x = rng.standard_normal((7, G["N"], G["N"])).astype(np.float32)
     if variant > 0 and not tile_eligible(G):
         with pytest.raises(api.FbpError, match="UNSUPPORTED"):
             api.radon_forward(to_gpu(x), g, variant=variant)
         return
     p = to_np(api.radon_forward(to_gpu(x), g, variant=variant))
-    for s in range(2):
+    for s in range(7):
         ref = oracle.forward(x[s].astype(np.float64), go)
         assert_within_dr(p[s], ref, TOL, f"variant {variant} {G}")
 
@@ -92,10 +94,12 @@ def test_forward_tile_full_size_sampled_angles():
     g = api.Geometry(K, N, N)
     sinos = np.stack([phantoms.slice_sinogram(w, i) for i in range(16)])
     x = api.fbp(to_gpu(sinos), g)
-    p = api.radon_forward(x, g, variant=1)
+    p = api.radon_forward(x, g)
     p0 = api.radon_forward(x, g, variant=0)
     dr = (p0.max() - p0.min()).item()
     assert (p - p0).abs().max().item() <= 1e-5 * dr
+    for v in range(1, api.forward_variant_count()):
+        assert (api.radon_forward(x, g, variant=v) - p0).abs().max().item() <= 1e-5 * dr, v
     pn, xn = to_np(p), to_np(x)
     for s in (0, 15):
         for k in (0, 1, 449, 450, 451, 899, 900, 901, 1349, 1350, 1799):
