@@ -35,7 +35,7 @@ struct FilterBatchItem {        // 56 bytes
     float *row_scale;           // [K] or null
     const float2 *G;            // difference-form spectrum for (D, kind, tau), length L
     const float2 *tw;           // twiddles for L
-    int K, D, L, group_begin;   // group = up to 32/N1 row pairs
+    int K, D, L, group_begin;   // group = one block's filter_pairs_per_block(L) row pairs
 };
 
 struct FilterBatchArgs {
@@ -46,6 +46,7 @@ struct FilterBatchArgs {
 fbp_status launch_bp_persistent(BpBatchArgs &a, int variant, fbp_dtype dtype, cudaStream_t s);
 fbp_status launch_filter_batched(const FilterBatchArgs &a, int total_groups, fbp_dtype dtype,
                                  cudaStream_t s);
+int filter_pairs_per_block(int L);   // row pairs one filter block transforms for length L
 int bp_tile_w(int variant);
 int bp_tile_h(int variant);
 

@@ -332,7 +332,7 @@ fbp_status fbp_batched(const fbp_batch_item *items, int count, fbp_filter_kind k
             f.D = items[i].g.n_det;
             f.L = Ls[i];
             f.group_begin = groups;
-            const int G = 32 / (Ls[i] / 512);
+            const int G = filter_pairs_per_block(Ls[i]);
             const long long pairs = ((long long)f.K + 1) / 2;
             const long long gi = (pairs + G - 1) / G;
             if ((long long)groups + gi > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "batch too large");

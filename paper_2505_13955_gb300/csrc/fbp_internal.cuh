@@ -40,11 +40,25 @@ struct AngleKey {
 // cos/sin of theta_k = start + k*step, k in [0, K), in double precision.
 fbp_status angle_table(const fbp_geometry &g, cudaStream_t s, const double2 **out);
 
+// Filter transform shape: L = R * C, C = 32 * VPL threads per row pair
+// (n = C n1 + n2, k = k1 + R k2, k2 = kr + VPL kl; see filter.cu).
+__host__ __device__ constexpr int fft_R(int L)
+{
+    return L == 512 ? 4 : L <= 2048 ? 8 : L <= 8192 ? 16 : 32;
+}
+__host__ __device__ constexpr int fft_VPL(int L)
+{
+    return L <= 1024 ? 4 : L <= 4096 ? 8 : 16;
+}
+
 // Filter tables for detector width D:
 //   L   = transform length (power of two >= max(512, 2D-1), so L >= 2D; <= 16384)
-//   G   = spectrum of the cumulative (difference-form) kernel, times tau / L
-//         (length L, complex); applied to the row's first differences
-//   tw  = twiddles exp(-2 pi i m / L), m in [0, L) (float2)
+//   G   = spectrum of the cumulative (difference-form) kernel, times tau / L,
+//         complex, in the order the transform's step 2 reads it:
+//         G[(k1 VPL + kr) 32 + l] = spectrum at k = k1 + R (kr + VPL brev5(l))
+//   tw  = twiddle plan (float2), L + C + 32 entries: W_L^{t k1} at k1 C + t,
+//         then W_C^{l kr} at L + 32 kr + l, then W_32^m at L + C + m,
+//         W_M^x = exp(-2 pi i x / M), each rounded once from double
 fbp_status filter_tables(int D, int kind, double tau, cudaStream_t s,
                          const float2 **G, const float2 **tw, int *L);
 int filter_length(int D);   // 0 if D is outside [1, 8192]

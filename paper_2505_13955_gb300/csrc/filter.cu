@@ -1,6 +1,5 @@
 // filter.cu -- K1: the ramp-filter step of FBP (Sec. V-A(c) stage 2,
-// "filtering", after Kak & Slaney ch. 3), as an FFT convolution in shared
-// memory.
+// "filtering", after Kak & Slaney ch. 3), as an FFT convolution.
 //
 // Each projection row p (length D) is linearly convolved with the truncated
 // kernel h (|n| <= D-1):  q[j] = tau * sum_m h[j-m] p[m], j in [0, D).
@@ -15,24 +14,30 @@
 // z = a + i b; IFFT(FFT(z) G) = (a*g) + i (b*g) returns both filtered rows at
 // once, with no real-FFT packing.
 //
-// The length-L transform is split four-step as L = N1 * 512 with
-// n = n1 + N1 * n2 and k = k2 + 512 * k1:
-//   step 1  each warp n1 takes the 512 samples x[n1 + N1 n2]; a lane holds
-//           16 of them in registers (n2 = 16 l + r).  The 32-point DFT over
-//           the lane index l runs as radix-2 butterflies over warp shuffles,
-//           the 16-point DFT over r in registers; then the four-step twiddle
-//           W_L^{n1 k2}.  One shared-memory transpose follows.
-//   step 2  lanes of the group hold the N1 values of one k2; the N1-point
-//           DFT runs over shuffles again, the product with G is taken in
-//           registers, and the inverse N1-point DFT undoes it in place.
-//   step 3  the inverse of step 1 returns the row in natural order.
-// Shared memory holds one padded complex row per row pair; both access
-// patterns (stride 16*N1 and the transpose) are padded to avoid bank
-// conflicts.  Global loads and stores are coalesced and, where alignment
-// allows, 16-byte vectors.
+// The length-L transform is split as L = R * C, C = 32 * VPL, with
+// n = C n1 + n2 and k = k1 + R k2 (R, VPL compile-time per L); a group of C
+// threads transforms one row pair, thread t owning n2 = t:
+//   step 1  thread t loads z[C n1 + t] for every n1 straight from global
+//           memory (coalesced across t), forms the differences, runs the
+//           R-point DFT over n1 in registers, multiplies by W_L^{t k1} and
+//           writes row k1 of an R x C shared buffer.
+//   step 2  each warp takes whole rows k1: lane l holds z[k1][l + 32 r],
+//           r < VPL; the C-point DFT over n2 is a VPL-point DFT in registers,
+//           the twiddle W_C^{l kr}, and a 32-point DFT over lanes (warp
+//           shuffles).  The product with G[k1 + R k2] is taken in registers
+//           and the inverse C-point DFT undoes the forward one in place, so
+//           the spectrum never leaves the warp.
+//   step 3  thread t reads column t, multiplies by W_L^{-t k1}, runs the
+//           inverse R-point DFT and stores its outputs n = C n1 + t < D
+//           straight to global memory (coalesced across t).
+// The shared buffer is read and written row-contiguously in both layouts
+// (row k1 by thread t, row k1 by lane l + 32 r), so no access has a bank
+// conflict and no padding is needed; it is visited four times per pair.
 //
-// The spectrum G already contains tau and 1/L; FP32 throughout, with the
-// spectrum and twiddles rounded once from FP64 tables.
+// The spectrum G already contains tau and 1/L and is stored in step 2's
+// read order; the twiddles come from a plan laid out in the order each step
+// reads them (fbp_internal.cuh), so every table load is coalesced.  FP32
+// throughout, with the spectrum and twiddles rounded once from FP64 tables.
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -58,65 +63,18 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m)
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
-// W16^m = exp(-2 pi i m / 16), m in [0, 8): (cos, -sin)
-__device__ __forceinline__ float2 w16(int m)
-{
-    const float c1 = 0.92387953251128675613f;   // cos(pi/8)
-    const float s1 = 0.38268343236508977173f;   // sin(pi/8)
-    const float r2 = 0.70710678118654752440f;   // cos(pi/4)
-    switch (m & 7) {
-        case 0: return make_float2(1.f, 0.f);
-        case 1: return make_float2(c1, -s1);
-        case 2: return make_float2(r2, -r2);
-        case 3: return make_float2(s1, -c1);
-        case 4: return make_float2(0.f, -1.f);
-        case 5: return make_float2(-s1, -c1);
-        case 6: return make_float2(-r2, -r2);
-        default: return make_float2(-c1, -s1);
-    }
-}
-
-// In-register 16-point DFT, natural order in and out (radix-2 DIT after a
-// compile-time bit-reversal).  INV = true: exponent sign +1, unnormalised.
-template <bool INV>
-__device__ __forceinline__ void dft16(float2 (&v)[16])
-{
-    // bit reversal of 4-bit indices
-    float2 t;
-    t = v[1]; v[1] = v[8]; v[8] = t;
-    t = v[2]; v[2] = v[4]; v[4] = t;
-    t = v[3]; v[3] = v[12]; v[12] = t;
-    t = v[5]; v[5] = v[10]; v[10] = t;
-    t = v[7]; v[7] = v[14]; v[14] = t;
-    t = v[11]; v[11] = v[13]; v[13] = t;
-#pragma unroll
-    for (int h = 1; h < 16; h <<= 1) {
-#pragma unroll
-        for (int blk = 0; blk < 16; blk += 2 * h) {
-#pragma unroll
-            for (int m = 0; m < h; ++m) {
-                float2 w = w16(m * (8 / h));        // W_{2h}^m = W16^{m*16/(2h)}
-                if (INV) w.y = -w.y;
-                float2 b = cmul(v[blk + m + h], w);
-                v[blk + m + h] = csub(v[blk + m], b);
-                v[blk + m] = cadd(v[blk + m], b);
-            }
-        }
-    }
-}
-
 __device__ __forceinline__ int brev5(int x) { return (int)(__brev((unsigned)x) >> 27); }
 
-// Decimation-in-frequency radix-2 DFT over the low `bits` lane bits (forward,
-// natural order in, bit-reversed out), on NV values per lane.
+// Decimation-in-frequency radix-2 DFT over the 32 lanes (forward, natural
+// order in, bit-reversed out), on NV values per lane; w32 = the W_32^m table.
 template <int NV>
-__device__ __forceinline__ void lane_dif(float2 (&v)[NV], int lane, int bits,
-                                         const float2 *__restrict__ tw, int L)
+__device__ __forceinline__ void lane_dif(float2 (&v)[NV], int lane, const float2 *__restrict__ w32t)
 {
-    for (int b = bits - 1; b >= 0; --b) {
+#pragma unroll
+    for (int b = 4; b >= 0; --b) {
         const int h = 1 << b;
         const bool hi = (lane & h) != 0;
-        const float2 w = __ldg(&tw[(lane & (h - 1)) * (L / (2 * h))]);
+        const float2 w = __ldg(&w32t[(lane & (h - 1)) * (16 / h)]);      // W_{2h}^{lane mod h}
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
             float2 o = shfl_xor2(v[i], h);
@@ -125,16 +83,16 @@ __device__ __forceinline__ void lane_dif(float2 (&v)[NV], int lane, int bits,
     }
 }
 
-// Inverse of lane_dif: decimation-in-time over the low `bits` lane bits with
-// conjugate twiddles (bit-reversed in, natural out), unnormalised.
+// Inverse of lane_dif: decimation-in-time over the 32 lanes with conjugate
+// twiddles (bit-reversed in, natural out), unnormalised.
 template <int NV>
-__device__ __forceinline__ void lane_dit_inv(float2 (&v)[NV], int lane, int bits,
-                                             const float2 *__restrict__ tw, int L)
+__device__ __forceinline__ void lane_dit_inv(float2 (&v)[NV], int lane, const float2 *__restrict__ w32t)
 {
-    for (int b = 0; b < bits; ++b) {
+#pragma unroll
+    for (int b = 0; b < 5; ++b) {
         const int h = 1 << b;
         const bool hi = (lane & h) != 0;
-        const float2 w = __ldg(&tw[(lane & (h - 1)) * (L / (2 * h))]);
+        const float2 w = __ldg(&w32t[(lane & (h - 1)) * (16 / h)]);
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
             float2 o = shfl_xor2(v[i], h);
@@ -153,221 +111,233 @@ struct RowPairJob {
 
 template <typename T>
 __device__ __forceinline__ T cvt_out(float x);
-template <> __device__ __forceinline__ float cvt_out<float>(float x) { return x; }
 template <> __device__ __forceinline__ __half cvt_out<__half>(float x) { return __float2half_rn(x); }
 template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(float x) { return __float2bfloat16_rn(x); }
 
-// Store one filtered row (real or imaginary part of the group's buffer);
-// 16-bit types store RNE(q / scale).
-template <typename T, bool IMAG>
-__device__ __forceinline__ void store_row(T *__restrict__ out, const float2 *S, int D, int padsh,
-                                          float scale, bool zero, int tid, int nthr)
+
+// cos(pi j / 16), j in [0, 8]
+__device__ __forceinline__ float cos16(int j)
 {
-    const uintptr_t align = sizeof(T) == 4 ? 15 : 7;
-    const bool vec = ((D & 3) == 0) && ((reinterpret_cast<uintptr_t>(out) & align) == 0);
-    if (vec) {
-        for (int c = tid; c < (D >> 2); c += nthr) {
-            const int n = c << 2;
-            const float2 *s0 = S + n + (n >> padsh);
-            float x[4];
+    switch (j) {
+        case 0: return 1.0f;
+        case 1: return 0.98078528040323044913f;
+        case 2: return 0.92387953251128675613f;
+        case 3: return 0.83146961230254523708f;
+        case 4: return 0.70710678118654752440f;
+        case 5: return 0.55557023301960222474f;
+        case 6: return 0.38268343236508977173f;
+        case 7: return 0.19509032201612826785f;
+        default: return 0.0f;
+    }
+}
+// cos(2 pi m / 32) for any m (folded to a constant when m is)
+__device__ __forceinline__ float cos32(int m)
+{
+    m &= 31;
+    if (m <= 8) return cos16(m);
+    if (m <= 16) return -cos16(16 - m);
+    if (m <= 24) return -cos16(m - 16);
+    return cos16(32 - m);
+}
+// W_32^m = exp(-2 pi i m / 32) = (cos, -sin)
+__device__ __forceinline__ float2 w32(int m) { return make_float2(cos32(m), -cos32(m - 8)); }
+
+template <int M>
+__host__ __device__ constexpr int brev_c(int i)
+{
+    int r = 0;
+    for (int b = 1; b < M; b <<= 1) {
+        r <<= 1;
+        if (i & b) r |= 1;
+    }
+    return r;
+}
+
+// In-register M-point DFT (M a power of two <= 32), natural order in and out
+// (radix-2 decimation in time after a compile-time bit reversal).
+// INV = true: exponent sign +1, unnormalised.
+template <int M, bool INV>
+__device__ __forceinline__ void dft_reg(float2 (&v)[M])
+{
 #pragma unroll
-            for (int i = 0; i < 4; ++i) x[i] = zero ? 0.f : (IMAG ? s0[i].y : s0[i].x);
-            if constexpr (sizeof(T) == 4) {
-                reinterpret_cast<float4 *>(out)[c] = make_float4(x[0], x[1], x[2], x[3]);
-            } else {
-                T y[4];
-#pragma unroll
-                for (int i = 0; i < 4; ++i) y[i] = cvt_out<T>(__fdiv_rn(x[i], scale));
-                reinterpret_cast<uint2 *>(out)[c] = *reinterpret_cast<uint2 *>(y);
-            }
+    for (int i = 0; i < M; ++i) {
+        const int j = brev_c<M>(i);
+        if (j > i) {
+            const float2 t = v[i];
+            v[i] = v[j];
+            v[j] = t;
         }
-    } else {
-        for (int n = tid; n < D; n += nthr) {
-            const float2 v = S[n + (n >> padsh)];
-            const float x = zero ? 0.f : (IMAG ? v.y : v.x);
-            if constexpr (sizeof(T) == 4) out[n] = x;
-            else out[n] = cvt_out<T>(__fdiv_rn(x, scale));
+    }
+#pragma unroll
+    for (int h = 1; h < M; h <<= 1) {
+#pragma unroll
+        for (int blk = 0; blk < M; blk += 2 * h) {
+#pragma unroll
+            for (int m = 0; m < h; ++m) {
+                float2 b = v[blk + m + h];
+                if (m != 0) {                           // W_{2h}^m = W_32^{m * 16 / h}
+                    float2 w = w32(m * (16 / h));
+                    if (INV) w.y = -w.y;
+                    b = cmul(b, w);
+                }
+                v[blk + m + h] = csub(v[blk + m], b);
+                v[blk + m] = cadd(v[blk + m], b);
+            }
         }
     }
 }
 
-// The full row-pair transform for one group of N1 warps.  S points at the
-// group's shared buffer of (L + 32) float2.  All threads of the block call
-// this together (block-wide barriers inside).
-template <int NW, typename T>
-__device__ void filter_group(const RowPairJob &job, bool active, int D, int L, int N1, int logN1,
-                             const float2 *__restrict__ Gs, const float2 *__restrict__ tw,
-                             float2 *S, float *red, int gw, int lane)
+__device__ __forceinline__ void group_sync(int id, int nthreads)
 {
-    const int gtid = gw * 32 + lane;          // thread index inside the group
-    const int gthr = N1 * 32;
-    const int padsh = 4 + logN1;              // one pad slot per 16*N1 samples
-    const int P = 512 + (N1 >= 16 ? 1 : 16 / N1);   // transposed row pitch
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(nthreads) : "memory");
+}
 
-    // ---- load: z[n] = (a[n], b[n]) for n < D, 0 beyond; layout A.  Whether
-    // a and b have any nonzero sample is kept so that an all-zero input row can be
-    // written as exact zeros (the paired transform would otherwise leave
-    // rounding cross-talk from its partner row in it).
-    float in_a = 0.f, in_b = 0.f;
-    if (active) {
-        const bool vec = ((D & 3) == 0) &&
-                         ((reinterpret_cast<uintptr_t>(job.a) & 15) == 0) &&
-                         (!job.b || (reinterpret_cast<uintptr_t>(job.b) & 15) == 0);
-        for (int c = gtid; c < (L >> 2); c += gthr) {
-            const int n = c << 2;
-            float av[4], bv[4];      // first differences p[m] - p[m-1], m = n..n+3 (m <= D)
-            float ra[4], rb[4];      // raw samples p[m] (0 for m >= D), for the zero-row flags
-            if (vec && n + 3 < D) {
-                const float4 x = __ldg(reinterpret_cast<const float4 *>(job.a) + c);
-                const float xm = n > 0 ? __ldg(job.a + n - 1) : 0.f;
-                ra[0] = x.x; ra[1] = x.y; ra[2] = x.z; ra[3] = x.w;
-                av[0] = x.x - xm; av[1] = x.y - x.x; av[2] = x.z - x.y; av[3] = x.w - x.z;
-                if (job.b) {
-                    const float4 y = __ldg(reinterpret_cast<const float4 *>(job.b) + c);
-                    const float ym = n > 0 ? __ldg(job.b + n - 1) : 0.f;
-                    rb[0] = y.x; rb[1] = y.y; rb[2] = y.z; rb[3] = y.w;
-                    bv[0] = y.x - ym; bv[1] = y.y - y.x; bv[2] = y.z - y.y; bv[3] = y.w - y.z;
-                } else {
+constexpr int kFilterThreads = 512;    // threads per block; 512 / C row pairs per block
+
+__host__ __device__ constexpr int group_threads(int L) { return 32 * fft_VPL(L); }
+
+// One row pair by one group of C threads (t = thread index in the group).
+// S: the group's R x C complex buffer; red: 4 * C/32 floats of the group;
+// bar_id: the group's named barrier.
+template <int L, typename T>
+__device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int D,
+                                         const float2 *__restrict__ Gs,
+                                         const float2 *__restrict__ tw, float2 *S, float *red,
+                                         int t, int bar_id)
+{
+    constexpr int R = fft_R(L), VPL = fft_VPL(L);
+    constexpr int C = 32 * VPL;
+    const float2 *__restrict__ w32t = tw + L + C;     // W_32^m
+    constexpr int NWG = C / 32;                 // warps in the group
+    constexpr int RPW = R / NWG;                // rows k1 per warp in step 2
+    static_assert(R * C == L && RPW >= 1 && R % NWG == 0, "shape");
+    const int lane = t & 31, gw = t >> 5;
+
+    // ---- step 1: differences of z[C n1 + t], R-point DFT over n1
+    float2 v[R];
+    bool nz_a = false, nz_b = false;     // any nonzero (or NaN) raw sample in the row
 #pragma unroll
-                    for (int i = 0; i < 4; ++i) rb[i] = bv[i] = 0.f;
-                }
-            } else {
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const int m = n + i;
-                    ra[i] = (m < D) ? __ldg(job.a + m) : 0.f;
-                    rb[i] = (job.b && m < D) ? __ldg(job.b + m) : 0.f;
-                    const float pa = (m >= 1 && m - 1 < D) ? __ldg(job.a + m - 1) : 0.f;
-                    const float pb = (job.b && m >= 1 && m - 1 < D) ? __ldg(job.b + m - 1) : 0.f;
-                    av[i] = (m <= D) ? ra[i] - pa : 0.f;
-                    bv[i] = (m <= D) ? rb[i] - pb : 0.f;
-                }
+    for (int n1 = 0; n1 < R; ++n1) {
+        const int n = C * n1 + t;
+        float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
+        if (active && C * n1 <= D) {              // uniform over the group
+            a = n < D ? __ldg(job.a + n) : 0.f;
+            b = (job.b && n < D) ? __ldg(job.b + n) : 0.f;
+            am = __shfl_up_sync(0xffffffffu, a, 1);
+            bm = __shfl_up_sync(0xffffffffu, b, 1);
+            if (lane == 0) {
+                am = (n >= 1 && n - 1 < D) ? __ldg(job.a + n - 1) : 0.f;
+                bm = (job.b && n >= 1 && n - 1 < D) ? __ldg(job.b + n - 1) : 0.f;
             }
-            float2 *d = S + n + (n >> padsh);
-#pragma unroll
-            for (int i = 0; i < 4; ++i) {
-                d[i] = make_float2(av[i], bv[i]);
-                if (ra[i] != 0.f) in_a = 1.f;   // NaN counts as nonzero
-                if (rb[i] != 0.f) in_b = 1.f;
-            }
+            nz_a |= (a != 0.f);
+            nz_b |= (b != 0.f);
         }
+        v[n1] = make_float2(a - am, b - bm);
     }
+    dft_reg<R, false>(v);
 #pragma unroll
-    for (int o = 16; o; o >>= 1) {
-        in_a = fmaxf(in_a, __shfl_xor_sync(0xffffffffu, in_a, o));
-        in_b = fmaxf(in_b, __shfl_xor_sync(0xffffffffu, in_b, o));
+    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[k1 * C + t]));  // W_L^{t k1}
+#pragma unroll
+    for (int k1 = 0; k1 < R; ++k1) S[k1 * C + t] = v[k1];
+    const unsigned za = __ballot_sync(0xffffffffu, nz_a), zb = __ballot_sync(0xffffffffu, nz_b);
+    if (lane == 0) {
+        red[2 * gw] = za ? 1.f : 0.f;
+        red[2 * gw + 1] = zb ? 1.f : 0.f;
     }
-    if (lane == 0) { red[2 * N1 + 2 * gw] = in_a; red[2 * N1 + 2 * gw + 1] = in_b; }
-    __syncthreads();
+    group_sync(bar_id, C);
     bool zero_a = true, zero_b = true;
-    for (int w = 0; w < N1; ++w) {
-        zero_a = zero_a && !(red[2 * N1 + 2 * w] > 0.f);
-        zero_b = zero_b && !(red[2 * N1 + 2 * w + 1] > 0.f);
+#pragma unroll
+    for (int w = 0; w < NWG; ++w) {
+        zero_a = zero_a && !(red[2 * w] > 0.f);
+        zero_b = zero_b && !(red[2 * w + 1] > 0.f);
     }
 
-    float2 v[16];
-    const int p = brev5(lane);
-    // ---- step 1 (forward): warp n1 = gw
+    // ---- step 2: per row k1, C-point DFT over n2, times G, inverse
     if (active) {
-        const int n1 = gw;
 #pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const int n = n1 + N1 * (16 * lane + r);
-            v[r] = S[n + (n >> padsh)];
-        }
-        lane_dif<16>(v, lane, 5, tw, L);                      // DFT over l -> p (bit-reversed)
+        for (int rr = 0; rr < RPW; ++rr) {
+            const int k1 = gw * RPW + rr;
+            float2 u[VPL];
 #pragma unroll
-        for (int r = 1; r < 16; ++r)                          // W512^{r p}
-            v[r] = cmul(v[r], __ldg(&tw[(r * p * N1) & (L - 1)]));
-        dft16<false>(v);                                      // DFT over r -> q
+            for (int r = 0; r < VPL; ++r) u[r] = S[k1 * C + lane + 32 * r];
+            dft_reg<VPL, false>(u);                                   // r -> kr
+            if (lane) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q) {
-            const int k2 = p + 32 * q;
-            if (n1) v[q] = cmul(v[q], __ldg(&tw[(n1 * k2) & (L - 1)]));   // W_L^{n1 k2}
+                for (int kr = 1; kr < VPL; ++kr) u[kr] = cmul(u[kr], __ldg(&tw[L + 32 * kr + lane]));  // W_C^{l kr}
+            }
+            lane_dif<VPL>(u, lane, w32t);                             // l -> kl = brev5(lane)
+            // G is stored in this order: entry (k1 VPL + kr) 32 + lane is k = k1 + R (kr + VPL kl)
+#pragma unroll
+            for (int kr = 0; kr < VPL; ++kr) u[kr] = cmul(u[kr], __ldg(&Gs[(k1 * VPL + kr) * 32 + lane]));
+            lane_dit_inv<VPL>(u, lane, w32t);                         // kl -> l
+            if (lane) {
+#pragma unroll
+                for (int kr = 1; kr < VPL; ++kr) u[kr] = cmulc(u[kr], __ldg(&tw[L + 32 * kr + lane]));
+            }
+            dft_reg<VPL, true>(u);                                    // kr -> r
+#pragma unroll
+            for (int r = 0; r < VPL; ++r) S[k1 * C + lane + 32 * r] = u[r];
         }
     }
-    __syncthreads();   // every warp has read layout A before it is overwritten
-    if (active) {
-        const int n1 = gw;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) S[n1 * P + p + 32 * q] = v[q];
-    }
-    __syncthreads();
+    group_sync(bar_id, C);
 
-    // ---- step 2: N1-point DFT over lanes, times G, inverse
-    if (active) {
-        const int n1 = lane & (N1 - 1);
-        const int sg = lane >> logN1;
-        const int grp = gw * (32 >> logN1) + sg;              // k2 group, 0..31
+    // ---- step 3: column t, W_L^{-t k1}, inverse R-point DFT over k1
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = S[n1 * P + 32 * r + grp];
-        if (logN1) lane_dif<16>(v, lane, logN1, tw, L);
-        const int k1 = logN1 ? (int)(__brev((unsigned)n1) >> (32 - logN1)) : 0;
+    for (int k1 = 0; k1 < R; ++k1) v[k1] = S[k1 * C + t];
 #pragma unroll
-        for (int r = 0; r < 16; ++r) v[r] = cmul(v[r], __ldg(&Gs[32 * r + grp + 512 * k1]));
-        if (logN1) {
-            lane_dit_inv<16>(v, lane, logN1, tw, L);
-#pragma unroll
-            for (int r = 0; r < 16; ++r)
-                if (n1) v[r] = cmulc(v[r], __ldg(&tw[(n1 * (32 * r + grp)) & (L - 1)]));
-        }
-#pragma unroll
-        for (int r = 0; r < 16; ++r) S[n1 * P + 32 * r + grp] = v[r];
-    }
-    __syncthreads();
-
-    // ---- step 3 (inverse of step 1)
-    if (active) {
-        const int n1 = gw;
-#pragma unroll
-        for (int q = 0; q < 16; ++q) v[q] = S[n1 * P + p + 32 * q];
-        dft16<true>(v);                                       // q -> r
-#pragma unroll
-        for (int r = 1; r < 16; ++r) v[r] = cmulc(v[r], __ldg(&tw[(r * p * N1) & (L - 1)]));
-        lane_dit_inv<16>(v, lane, 5, tw, L);                  // p -> l
-    }
-    __syncthreads();
-    if (active) {
-        const int n1 = gw;
-#pragma unroll
-        for (int r = 0; r < 16; ++r) {
-            const int n = n1 + N1 * (16 * lane + r);
-            S[n + (n >> padsh)] = v[r];
-        }
-    }
-    __syncthreads();
+    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmulc(v[k1], __ldg(&tw[k1 * C + t]));
+    dft_reg<R, true>(v);                                              // k1 -> n1
 
     // ---- store (16-bit: per-row amax scale first)
     float scale_a = 1.f, scale_b = 1.f;
-    if (sizeof(T) != 4) {
+    if constexpr (sizeof(T) != 4) {
         float ma = 0.f, mb = 0.f;
-        if (active)
-            for (int n = gtid; n < D; n += gthr) {
-                float2 z = S[n + (n >> padsh)];
-                ma = fmaxf(ma, fabsf(z.x));
-                mb = fmaxf(mb, fabsf(z.y));
+#pragma unroll
+        for (int n1 = 0; n1 < R; ++n1)
+            if (C * n1 + t < D) {
+                ma = fmaxf(ma, fabsf(v[n1].x));
+                mb = fmaxf(mb, fabsf(v[n1].y));
             }
 #pragma unroll
         for (int o = 16; o; o >>= 1) {
             ma = fmaxf(ma, __shfl_xor_sync(0xffffffffu, ma, o));
             mb = fmaxf(mb, __shfl_xor_sync(0xffffffffu, mb, o));
         }
-        if (lane == 0) { red[2 * gw] = ma; red[2 * gw + 1] = mb; }
-        __syncthreads();
-        if (active) {
-            ma = 0.f; mb = 0.f;
-            for (int w = 0; w < N1; ++w) { ma = fmaxf(ma, red[2 * w]); mb = fmaxf(mb, red[2 * w + 1]); }
-            scale_a = (ma > 0.f && !zero_a) ? ma : 1.f;
-            scale_b = (mb > 0.f && !zero_b) ? mb : 1.f;
-            if (gtid == 0) {
-                job.sa[0] = scale_a;
-                if (job.sb) job.sb[0] = scale_b;
-            }
+        if (lane == 0) {
+            red[2 * NWG + 2 * gw] = ma;
+            red[2 * NWG + 2 * gw + 1] = mb;
+        }
+        group_sync(bar_id, C);
+        ma = 0.f;
+        mb = 0.f;
+#pragma unroll
+        for (int w = 0; w < NWG; ++w) {
+            ma = fmaxf(ma, red[2 * NWG + 2 * w]);
+            mb = fmaxf(mb, red[2 * NWG + 2 * w + 1]);
+        }
+        scale_a = (ma > 0.f && !zero_a) ? ma : 1.f;
+        scale_b = (mb > 0.f && !zero_b) ? mb : 1.f;
+        if (active && t == 0) {
+            job.sa[0] = scale_a;
+            if (job.sb) job.sb[0] = scale_b;
         }
     }
     if (active) {
-        store_row<T, false>(static_cast<T *>(job.qa), S, D, padsh, scale_a, zero_a, gtid, gthr);
-        if (job.qb) store_row<T, true>(static_cast<T *>(job.qb), S, D, padsh, scale_b, zero_b, gtid, gthr);
+        T *qa = static_cast<T *>(job.qa), *qb = static_cast<T *>(job.qb);
+#pragma unroll
+        for (int n1 = 0; n1 < R; ++n1) {
+            const int n = C * n1 + t;
+            if (n < D) {
+                const float xa = zero_a ? 0.f : v[n1].x, xb = zero_b ? 0.f : v[n1].y;
+                if constexpr (sizeof(T) == 4) {
+                    qa[n] = xa;
+                    if (qb) qb[n] = xb;
+                } else {
+                    qa[n] = cvt_out<T>(__fdiv_rn(xa, scale_a));
+                    if (qb) qb[n] = cvt_out<T>(__fdiv_rn(xb, scale_b));
+                }
+            }
+        }
     }
 }
 
@@ -376,108 +346,121 @@ struct FilterArgs {
     void *filt;
     float *row_scale;
     long long rows;
-    int D, L, N1, logN1;
+    int D;
     const float2 *G;
     const float2 *tw;
 };
 
-template <int NW, typename T>
-__global__ void __launch_bounds__(NW * 32) filter_kernel(FilterArgs a)
+__device__ __forceinline__ RowPairJob make_job(const float *sino, void *filt, float *row_scale,
+                                               long long rows, int D, long long pair, size_t esz,
+                                               bool &active)
 {
-    extern __shared__ float2 smem_f2[];
-    __shared__ float red[4 * NW];   // per-warp maxima: output amax, input amax (both rows)
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int G = NW / a.N1;                       // row pairs per block
-    const int g = warp / a.N1, gw = warp % a.N1;
-    const long long pair = (long long)blockIdx.x * G + g;
-    const bool active = 2 * pair < a.rows;
     RowPairJob job;
+    active = 2 * pair < rows;
     const long long ra = 2 * pair, rb = 2 * pair + 1;
-    const size_t esz = sizeof(T);
-    job.a = active ? a.sino + ra * a.D : nullptr;
-    job.b = (active && rb < a.rows) ? a.sino + rb * a.D : nullptr;
-    job.qa = active ? static_cast<char *>(a.filt) + ra * a.D * esz : nullptr;
-    job.qb = (active && rb < a.rows) ? static_cast<char *>(a.filt) + rb * a.D * esz : nullptr;
-    job.sa = (active && a.row_scale) ? a.row_scale + ra : nullptr;
-    job.sb = (active && rb < a.rows && a.row_scale) ? a.row_scale + rb : nullptr;
-    float2 *S = smem_f2 + (size_t)g * (a.L + 32);
-    filter_group<NW, T>(job, active, a.D, a.L, a.N1, a.logN1, a.G, a.tw, S, red + 4 * g * a.N1,
-                        gw, lane);
+    const bool has_b = active && rb < rows;
+    job.a = active ? sino + ra * D : nullptr;
+    job.b = has_b ? sino + rb * D : nullptr;
+    job.qa = active ? static_cast<char *>(filt) + ra * D * esz : nullptr;
+    job.qb = has_b ? static_cast<char *>(filt) + rb * D * esz : nullptr;
+    job.sa = (active && row_scale) ? row_scale + ra : nullptr;
+    job.sb = (has_b && row_scale) ? row_scale + rb : nullptr;
+    return job;
 }
 
-template <int NW, typename T>
-fbp_status launch_nw(const FilterArgs &fa, cudaStream_t s)
+template <int L, typename T>
+__global__ void __launch_bounds__(kFilterThreads) filter_kernel(FilterArgs a)
 {
-    const int G = NW / fa.N1;
+    constexpr int C = group_threads(L);
+    constexpr int GP = kFilterThreads / C;        // row pairs per block
+    extern __shared__ float2 smem_f2[];
+    __shared__ float red[GP][4 * (C / 32)];
+    const int g = threadIdx.x / C, t = threadIdx.x % C;
+    const long long pair = (long long)blockIdx.x * GP + g;
+    bool active;
+    const RowPairJob job = make_job(a.sino, a.filt, a.row_scale, a.rows, a.D, pair, sizeof(T), active);
+    fft_pair<L, T>(job, active, a.D, a.G, a.tw, smem_f2 + (size_t)g * L, red[g], t, 1 + g);
+}
+
+template <int L, typename T>
+fbp_status launch_l(const FilterArgs &fa, cudaStream_t s)
+{
+    constexpr int GP = kFilterThreads / group_threads(L);
     const long long pairs = (fa.rows + 1) / 2;
-    const long long blocks = (pairs + G - 1) / G;
-    const size_t smem = (size_t)G * (fa.L + 32) * sizeof(float2);
-    auto kern = filter_kernel<NW, T>;
+    const long long blocks = (pairs + GP - 1) / GP;
+    const size_t smem = (size_t)GP * L * sizeof(float2);
+    auto kern = filter_kernel<L, T>;
     fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (st != FBP_OK) return st;
     if (blocks > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "too many rows");
-    kern<<<(unsigned)blocks, NW * 32, smem, s>>>(fa);
+    kern<<<(unsigned)blocks, kFilterThreads, smem, s>>>(fa);
     FBP_CUDA_TRY(cudaGetLastError());
     return FBP_OK;
 }
 
 template <typename T>
-fbp_status launch_t(const FilterArgs &fa, cudaStream_t s)
+fbp_status launch_t(const FilterArgs &fa, int L, cudaStream_t s)
 {
-    if (fa.N1 <= 8) return launch_nw<8, T>(fa, s);
-    if (fa.N1 == 16) return launch_nw<16, T>(fa, s);
-    return launch_nw<32, T>(fa, s);
+    switch (L) {
+        case 512: return launch_l<512, T>(fa, s);
+        case 1024: return launch_l<1024, T>(fa, s);
+        case 2048: return launch_l<2048, T>(fa, s);
+        case 4096: return launch_l<4096, T>(fa, s);
+        case 8192: return launch_l<8192, T>(fa, s);
+        case 16384: return launch_l<16384, T>(fa, s);
+    }
+    return fail(FBP_ERR_UNSUPPORTED, "filter length %d", L);
 }
 
-// Ragged batch: one launch over every item's rows.  32 warps per block; an
-// item with transform length L = 512 N1 puts 32/N1 row pairs in a block, so
-// the shared buffer is the same size for every item.
+// Ragged batch: one launch over every item's rows.  A block holds 512 / C
+// row pairs of one item (C = the item's group size), so every block's
+// groups run the same transform; the shared buffer is sized for the batch's
+// longest transform.
 template <typename T>
-__global__ void __launch_bounds__(1024) filter_batched_kernel(FilterBatchArgs a)
+__global__ void __launch_bounds__(kFilterThreads) filter_batched_kernel(FilterBatchArgs a)
 {
     extern __shared__ float2 smem_f2[];
-    __shared__ float red[4 * 32];
+    __shared__ float red[4 * kFilterThreads / 32];     // 4 floats per warp
     int lo = 0, hi = a.count - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
         if (a.items[mid].group_begin <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
     }
     const FilterBatchItem &it = a.items[lo];
-    const int N1 = it.L / 512;
-    int logN1 = 0;
-    while ((1 << logN1) < N1) ++logN1;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int G = 32 / N1;
-    const int g = warp / N1, gw = warp % N1;
-    const long long pair = (long long)(blockIdx.x - it.group_begin) * G + g;
-    const long long rows = it.K;
-    const bool active = 2 * pair < rows;
-    const long long ra = 2 * pair, rb = 2 * pair + 1;
-    RowPairJob job;
-    job.a = active ? it.sino + ra * it.D : nullptr;
-    job.b = (active && rb < rows) ? it.sino + rb * it.D : nullptr;
-    job.qa = active ? static_cast<char *>(it.filt) + ra * it.D * sizeof(T) : nullptr;
-    job.qb = (active && rb < rows) ? static_cast<char *>(it.filt) + rb * it.D * sizeof(T) : nullptr;
-    job.sa = (active && it.row_scale) ? it.row_scale + ra : nullptr;
-    job.sb = (active && rb < rows && it.row_scale) ? it.row_scale + rb : nullptr;
-    float2 *S = smem_f2 + (size_t)g * (it.L + 32);
-    filter_group<32, T>(job, active, it.D, it.L, N1, logN1, it.G, it.tw, S, red + 4 * g * N1, gw, lane);
+    const int C = group_threads(it.L);
+    const int GP = kFilterThreads / C;
+    const int g = threadIdx.x / C, t = threadIdx.x % C;
+    const long long pair = (long long)(blockIdx.x - it.group_begin) * GP + g;
+    bool active;
+    const RowPairJob job = make_job(it.sino, it.filt, it.row_scale, it.K, it.D, pair, sizeof(T), active);
+    float2 *S = smem_f2 + (size_t)g * it.L;
+    float *rd = red + g * 4 * (C / 32);
+    switch (it.L) {
+        case 512: fft_pair<512, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
+        case 1024: fft_pair<1024, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
+        case 2048: fft_pair<2048, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
+        case 4096: fft_pair<4096, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
+        case 8192: fft_pair<8192, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
+        default: fft_pair<16384, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
+    }
 }
 
 template <typename T>
-fbp_status launch_batched_t(const FilterBatchArgs &a, int groups, cudaStream_t s)
+fbp_status launch_batched_t(const FilterBatchArgs &a, int groups, int max_L, cudaStream_t s)
 {
-    // worst case over L: (32/N1) * (512 N1 + 32) float2
-    const size_t smem = (size_t)(16384 + 1024) * sizeof(float2);
+    // (512 / C) pairs x L float2 = 4096 R bytes, largest for the longest L
+    const size_t smem = (size_t)(kFilterThreads / group_threads(max_L)) * max_L * sizeof(float2);
     auto kern = filter_batched_kernel<T>;
     fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (st != FBP_OK) return st;
-    kern<<<groups, 1024, smem, s>>>(a);
+    kern<<<groups, kFilterThreads, smem, s>>>(a);
     FBP_CUDA_TRY(cudaGetLastError());
     return FBP_OK;
 }
 
 }  // namespace
+
+int filter_pairs_per_block(int L) { return kFilterThreads / group_threads(L); }
 
 fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s)
 {
@@ -488,18 +471,12 @@ fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s)
     fa.row_scale = a.row_scale;
     fa.rows = a.rows;
     fa.D = a.D;
-    fa.L = a.L;
-    fa.N1 = a.L / 512;
-    fa.logN1 = 0;
-    while ((1 << fa.logN1) < fa.N1) ++fa.logN1;
     fa.G = a.G;
     fa.tw = a.tw;
-    if (fa.N1 < 1 || fa.N1 > 32 || (1 << fa.logN1) != fa.N1)
-        return fail(FBP_ERR_UNSUPPORTED, "filter length %d", a.L);
     switch (a.dtype) {
-        case FBP_F32: return launch_t<float>(fa, s);
-        case FBP_F16: return launch_t<__half>(fa, s);
-        case FBP_BF16: return launch_t<__nv_bfloat16>(fa, s);
+        case FBP_F32: return launch_t<float>(fa, a.L, s);
+        case FBP_F16: return launch_t<__half>(fa, a.L, s);
+        case FBP_BF16: return launch_t<__nv_bfloat16>(fa, a.L, s);
     }
     return fail(FBP_ERR_INVALID_ARG, "dtype");
 }
@@ -508,10 +485,12 @@ fbp_status launch_filter_batched(const FilterBatchArgs &a, int total_groups, fbp
                                  cudaStream_t s)
 {
     if (total_groups <= 0) return FBP_OK;
+    int max_L = 512;
+    for (int i = 0; i < a.count; ++i) max_L = a.items[i].L > max_L ? a.items[i].L : max_L;
     switch (dtype) {
-        case FBP_F32: return launch_batched_t<float>(a, total_groups, s);
-        case FBP_F16: return launch_batched_t<__half>(a, total_groups, s);
-        case FBP_BF16: return launch_batched_t<__nv_bfloat16>(a, total_groups, s);
+        case FBP_F32: return launch_batched_t<float>(a, total_groups, max_L, s);
+        case FBP_F16: return launch_batched_t<__half>(a, total_groups, max_L, s);
+        case FBP_BF16: return launch_batched_t<__nv_bfloat16>(a, total_groups, max_L, s);
     }
     return fail(FBP_ERR_INVALID_ARG, "dtype");
 }

@@ -156,14 +156,28 @@ __global__ void angle_table_kernel(double2 *cs, int K, double start, double step
     cs[k] = make_double2(c, s);
 }
 
-// exp(-2 pi i m / L), rounded once from double
-__global__ void twiddle_kernel(float2 *tw, int L)
+// The filter's twiddle plan for length L = R C (layout in fbp_internal.cuh),
+// each entry exp(-2 pi i x / M) rounded once from double.
+__global__ void twiddle_kernel(float2 *tw, int L, int R, int C)
 {
-    int m = blockIdx.x * blockDim.x + threadIdx.x;
-    if (m >= L) return;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= L + C + 32) return;
+    long long x;
+    int M;
+    if (o < L) {                       // W_L^{t k1}
+        x = (long long)(o % C) * (o / C);
+        M = L;
+    } else if (o < L + C) {            // W_C^{l kr}
+        const int i = o - L;
+        x = (long long)(i % 32) * (i / 32);
+        M = C;
+    } else {                           // W_32^m
+        x = o - L - C;
+        M = 32;
+    }
     double s, c;
-    sincospi(2.0 * (double)m / (double)L, &s, &c);
-    tw[m] = make_float2((float)c, (float)-s);
+    sincospi(2.0 * (double)(x % M) / (double)M, &s, &c);
+    tw[o] = make_float2((float)c, (float)-s);
 }
 
 // Filter taps h_tau(n), n in [0, D) (the kernel is even), double precision.
@@ -220,8 +234,13 @@ __global__ void spectrum_kernel(double *Hr, const double *h, const double *ctab,
 // (h is even).  Stored as (tau / L) G in float2.
 __global__ void diff_spectrum_kernel(float2 *G, const double *Hr, int D, int L, double tau)
 {
-    int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= L) return;
+    const int o = blockIdx.x * blockDim.x + threadIdx.x;
+    if (o >= L) return;
+    // stored in the transform's step-2 order: o = (k1 VPL + kr) 32 + l
+    const int R = fft_R(L), VPL = fft_VPL(L);
+    const int l = o & 31, kr = (o >> 5) % VPL, k1 = o / (32 * VPL);
+    const int kl = (int)(__brev((unsigned)l) >> 27);
+    const int k = k1 + R * (kr + VPL * kl);
     const double dc = Hr[0];
     double gr, gi;
     if (k == 0) {
@@ -238,7 +257,7 @@ __global__ void diff_spectrum_kernel(float2 *G, const double *Hr, int D, int L, 
         gi = (ni * dr - nr * di) / den;
     }
     const double sc = tau / (double)L;
-    G[k] = make_float2((float)(gr * sc), (float)(gi * sc));
+    G[o] = make_float2((float)(gr * sc), (float)(gi * sc));
 }
 
 // ---------------------------------------------------------------------------
@@ -328,8 +347,9 @@ fbp_status filter_tables(int D, int kind, double tau, cudaStream_t s,
                     D);
     if (tit == g_twiddles.end()) {
         float2 *t = nullptr;
-        FBP_CUDA_TRY(cudaMalloc(&t, sizeof(float2) * (size_t)L));
-        twiddle_kernel<<<(L + 255) / 256, 256, 0, s>>>(t, L);
+        const int C = 32 * fft_VPL(L), n = L + C + 32;
+        FBP_CUDA_TRY(cudaMalloc(&t, sizeof(float2) * (size_t)n));
+        twiddle_kernel<<<(n + 255) / 256, 256, 0, s>>>(t, L, fft_R(L), C);
         cudaError_t e = cudaGetLastError();
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {

@@ -93,38 +93,117 @@ def test_magic_number_rounding_reads_index_from_bits():
     np.testing.assert_array_equal(idx, np.rint(u).astype(np.int64))
 
 
-@pytest.mark.parametrize("N1", [1, 2, 4, 8, 16, 32])
-def test_filter_shared_layouts_fit_buffer(N1):
-    L = 512 * N1
-    size = L + 32
-    logN1 = int(math.log2(N1))
-    padsh = 4 + logN1
-    n = np.arange(L)
-    pos = n + (n >> padsh)
-    assert pos.max() < size
-    # step-1 reads: stride 16*N1 + 1 across lanes -> distinct banks per half-warp
-    for n1 in range(N1):
-        for r in range(16):
-            lanes = np.arange(16)
-            nn = n1 + N1 * (16 * lanes + r)
-            p = nn + (nn >> padsh)
-            assert len(set((2 * p) % 32)) == 16
-    P = 512 + (1 if N1 >= 16 else 16 // N1)
-    assert N1 * P <= size
-    # transposed layout: T(n1, k2) = n1*P + k2 for k2 < 512
-    assert (N1 - 1) * P + 511 < size
-    # step-2 read pattern of a half-warp: n1 = lane & (N1-1), G from lane >> logN1
-    for w in range(N1):
-        lanes = np.arange(16)
-        n1 = lanes & (N1 - 1)
-        sg = lanes >> logN1
-        G = w * (32 >> logN1) + sg
-        p = n1 * P + G
-        assert len(set((2 * p) % 32)) == 16
-    # H index in step 2: 32 r + G + 512 k1 < L
-    assert 32 * 15 + 31 + 512 * (N1 - 1) < L
-    # batched filter: (32 / N1) groups of (L + 32) float2 fit the fixed buffer
-    assert (32 // N1) * size <= 16384 + 1024
+# ---------------------------------------------------------------------------
+# Filter (filter.cu): transform shapes, buffer indices, and a replay of the
+# three-step factorisation and of the in-register radix-2 DFT
+# ---------------------------------------------------------------------------
+FFT_SHAPES = {512: (4, 4), 1024: (8, 4), 2048: (8, 8), 4096: (16, 8), 8192: (16, 16), 16384: (32, 16)}
+
+
+def group_threads(L):
+    return 128 if L in (512, 1024) else 256 if L in (2048, 4096) else 512
+
+
+@pytest.mark.parametrize("L", sorted(FFT_SHAPES))
+def test_filter_shapes_and_indices(L):
+    R, VPL = FFT_SHAPES[L]
+    C = 32 * VPL
+    assert C == group_threads(L) and R * C == L and 512 % C == 0
+    NWG = C // 32
+    assert R % NWG == 0                               # whole rows per warp in step 2
+    t, k1 = np.meshgrid(np.arange(C), np.arange(R))
+    assert (k1 * C + t).max() == L - 1                # buffer S[k1][t]
+    assert (t * k1).max() < L                         # W_L^{t k1} index
+    lane, kr = np.meshgrid(np.arange(32), np.arange(VPL))
+    assert (lane * kr * R).max() < L                  # W_C^{l kr} index
+    kl = np.arange(32)
+    k = k1[:, :1, None] + R * (np.arange(VPL)[None, :, None] + VPL * kl[None, None, :])
+    assert sorted(k.ravel().tolist()) == list(range(L))   # G index covers the spectrum once
+    # batched kernel: (512 / C) pairs x L float2 grows with L, so the longest
+    # item's size bounds every block; 4 reduction floats per warp
+    sizes = [(512 // group_threads(x)) * x for x in sorted(FFT_SHAPES)]
+    assert sizes == sorted(sizes)
+    assert (512 // C) * 4 * NWG == 64
+
+
+@pytest.mark.parametrize("L", sorted(FFT_SHAPES))
+def test_filter_table_layouts(L):
+    """runtime.cu writes G entry o at k = k1 + R (kr + VPL brev5(l)) with
+    l = o % 32, kr = (o / 32) % VPL, k1 = o / (32 VPL); filter.cu reads entry
+    (k1 VPL + kr) 32 + lane.  The twiddle plan has L + C + 32 entries:
+    W_L^{t k1} at k1 C + t, W_C^{l kr} at L + 32 kr + l, W_32^m at L + C + m."""
+    R, VPL = FFT_SHAPES[L]
+    C = 32 * VPL
+    o = np.arange(L)
+    l, kr, k1 = o & 31, (o >> 5) % VPL, o // (32 * VPL)
+    assert np.array_equal((k1 * VPL + kr) * 32 + l, o)
+    brev = np.array([int(format(x, "05b")[::-1], 2) for x in range(32)])
+    k = k1 + R * (kr + VPL * brev[l])
+    assert sorted(k.tolist()) == list(range(L))
+    # twiddle plan: the kernel's reads stay in their sections
+    t, kk = np.meshgrid(np.arange(C), np.arange(R))
+    assert (kk * C + t).max() < L
+    lane, r = np.meshgrid(np.arange(32), np.arange(VPL))
+    assert (L + 32 * r + lane).min() >= L and (L + 32 * r + lane).max() < L + C
+    for h in (1, 2, 4, 8, 16):
+        idx = (np.arange(32) & (h - 1)) * (16 // h)
+        assert idx.max() < 32 and np.array_equal(idx * 2 * h // 32, np.arange(32) & (h - 1))
+
+
+def dft_reg_replay(v, inv):
+    """The kernel's in-register DFT: compile-time bit reversal, then radix-2
+    DIT with twiddle W_32^(m*16/h) at half-size h."""
+    M = len(v)
+    bits = M.bit_length() - 1
+    v = v.copy()
+    rev = [int(format(i, f"0{bits}b")[::-1], 2) if bits else 0 for i in range(M)]
+    v = v[rev]
+    h = 1
+    while h < M:
+        for blk in range(0, M, 2 * h):
+            for m in range(h):
+                w = np.exp(-2j * np.pi * (m * (16 // h)) / 32)
+                if inv:
+                    w = np.conj(w)
+                b = v[blk + m + h] * (w if m else 1.0)
+                v[blk + m + h] = v[blk + m] - b
+                v[blk + m] = v[blk + m] + b
+        h *= 2
+    return v
+
+
+@pytest.mark.parametrize("M", [4, 8, 16, 32])
+def test_filter_register_dft_replay(M):
+    rng = np.random.default_rng(M)
+    x = rng.standard_normal(M) + 1j * rng.standard_normal(M)
+    np.testing.assert_allclose(dft_reg_replay(x, False), np.fft.fft(x), atol=1e-12)
+    np.testing.assert_allclose(dft_reg_replay(x, True), np.fft.ifft(x) * M, atol=1e-12)
+
+
+@pytest.mark.parametrize("L", sorted(FFT_SHAPES))
+def test_filter_three_step_factorisation_replay(L):
+    """Step 1 (R-point DFT over n1, W_L^{t k1}), step 2 per row k1 (VPL-point
+    over r, W_C^{l kr}, 32-point over lanes, times G[k1 + R (kr + VPL kl)],
+    and the inverses), step 3 (W_L^{-t k1}, inverse R-point) equal the
+    circular convolution IFFT(FFT(z) G) * L."""
+    R, VPL = FFT_SHAPES[L]
+    C = 32 * VPL
+    rng = np.random.default_rng(L)
+    z = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    G = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    W = lambda m: np.exp(-2j * np.pi * m / L)
+    tk = np.outer(np.arange(R), np.arange(C))
+    S = np.fft.fft(z.reshape(R, C), axis=0) * W(tk)
+    lk = np.outer(np.arange(VPL), np.arange(32)) * R
+    k2 = np.arange(VPL)[:, None] + VPL * np.arange(32)[None, :]
+    for k1 in range(R):
+        A = np.fft.fft(S[k1].reshape(VPL, 32), axis=0) * W(lk)
+        X = np.fft.fft(A, axis=1) * G[k1 + R * k2]
+        A = np.fft.ifft(X, axis=1) * 32 * np.conj(W(lk))
+        S[k1] = (np.fft.ifft(A, axis=0) * VPL).reshape(-1)
+    out = (np.fft.ifft(S * np.conj(W(tk)), axis=0) * R).reshape(-1)
+    ref = np.fft.ifft(np.fft.fft(z) * G) * L
+    np.testing.assert_allclose(out, ref, atol=1e-9 * np.abs(ref).max())
 
 
 @pytest.mark.parametrize("alpha", [0.125, 0.5, 0.7, 1.0, 2.5])
