@@ -486,6 +486,109 @@ def run_uniform(args) -> None:
     finish(line, ws, rank)
 
 
+def run_pipeline(args) -> None:
+    """Counts to codes (Sec. V-A(c) stages 2-4 on one GPU): one step =
+    fbp_filter_counts (Beer-Lambert + Gaussian blur + ramp filter) and
+    fbp_backproject_u16 (HU window to uint16) over the stack; the plain FP32
+    FBP of the same stack's line integrals is timed in the same run."""
+    import torch
+    from paper_2505_13955_gb300 import api, phantoms
+
+    ws, rank, dev = init_device()
+    w = phantoms.WORKLOADS["fbp_pipeline_n8192"]
+    N, K, S = w.n, w.n_angles, (args.slices or w.n_slices)
+    g = api.Geometry(K, N, N)
+    host = np.empty((S, K, N), dtype=np.float32)
+    for i, s in enumerate(shard_slices(S, rank)):
+        host[i] = phantoms.slice_counts(w, s)
+    counts = torch.from_numpy(host).to(dev)
+    P = phantoms.PIPELINE
+    pre = api.Preprocess(flat_value=w.photons, count_floor=1.0, mu_scale=float(N),
+                         blur_sigma=P["blur_sigma"])
+    win = api.HuWindow(P["mu_water"], P["mu_air"], P["hu_min"], P["hu_max"])
+    filt = torch.empty(counts.shape, dtype=torch.float32, device=dev)
+    codes = torch.empty((S, N, N), dtype=torch.int16, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    api.prepare(g, kind=w.filter, device=dev)
+    updates = S * N * N * K
+    T = Timed(stream, args.steps, args.warmup, n_events=3)
+
+    def step(evs):
+        if evs:
+            evs[0].record(stream)
+        api.filter_counts(counts, g, pre, kind=w.filter, out=filt)
+        if evs:
+            evs[1].record(stream)
+        api.backproject_u16(filt, g, win, out=codes, variant=args.variant)
+        if evs:
+            evs[2].record(stream)
+
+    ms = T.run(step, dev.index)
+    assert api.device_status() == 0
+    per_rank = allgather_floats([ms, float(updates)])
+    rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
+    f_ms, bp_ms, clocks = T.between(0, 1), T.between(1, 2), T.clocks
+
+    # the plain path on line integrals of the same stack, for the ratio
+    out = torch.empty((S, N, N), dtype=torch.float32, device=dev)
+    T2 = Timed(stream, args.steps, args.warmup)
+    lines = -torch.log(counts.clamp_min(1.0) / w.photons) * N     # input preparation, not timed
+
+    def plain(_):
+        api.filter(lines, g, kind=w.filter, out=filt)
+        api.backproject(filt, g, out=out, variant=args.variant)
+
+    plain_ms = T2.run(plain, None)
+    del lines, out
+
+    e2e = None
+    if args.e2e_steps > 0:
+        pin_in = torch.from_numpy(host).pin_memory()
+        pin_out = torch.empty((S, N, N), dtype=torch.int16).pin_memory()
+
+        def e2e_step(_):
+            api.fbp_host(pin_in, g, kind=w.filter, out=pin_out, variant=args.variant, pre=pre, window=win)
+
+        T3 = Timed(stream, args.e2e_steps, 1)
+        t_e2e = T3.run(e2e_step, None)
+        per_rank_e2e = allgather_floats([t_e2e, float(updates)])
+        e2e_rate, _ = aggregate([r[0] for r in per_rank_e2e], [int(r[1]) for r in per_rank_e2e])
+        e2e = {"value": e2e_rate / 1e9, "unit": UNIT, "h2d_bytes_per_step": int(pin_in.numel() * 4),
+               "d2h_bytes_per_step": int(pin_out.numel() * 2), "ms_per_step": t_e2e}
+        del pin_in, pin_out
+
+    if rank != 0:
+        finish({}, ws, rank)
+        return
+    pk = peaks()
+    sm_max = pk.get("sm_max_mhz") or 2070.0
+    rp = roofline_peak(sm_max, "f32")
+    achieved = updates / (bp_ms / 1e3) / 1e9
+    hbm = pk.get("hbm_gbs")
+    fbytes = S * K * N * 8.0                 # counts read + filtered rows written
+    line = base_line(args, ws, rate / 1e9, ms_step, "f32", {
+        "workload": f"{w.name}: S={S} slices per GPU, N=D={N}, K={K}, raw Poisson counts "
+                    f"({w.photons:g} photons), Beer-Lambert + Gaussian blur sigma={P['blur_sigma']} + "
+                    f"Ram-Lak + backprojection + HU window [{P['hu_min']}, {P['hu_max']}] to uint16",
+        "l2": "inputs larger than L2, no flush",
+        "parallelism": f"slices sharded over {ws} GPU(s), no collective",
+        "bp_variant": resolved_variant(api, g, "f32", args.variant)})
+    line.update({
+        "slices_per_s": S * len(per_rank) / (ms_step / 1e3),
+        "filter_counts_ms_per_step": f_ms, "bp_u16_ms_per_step": bp_ms,
+        "filter_counts_gb_per_s": fbytes / (f_ms / 1e3) / 1e9,
+        "filter_counts_hbm_frac": (fbytes / (f_ms / 1e3) / 1e9 / hbm) if hbm else None,
+        "plain_fbp_ms_per_step": plain_ms, "ratio_to_plain_fbp": plain_ms / ms_step,
+        "roofline": {"bound": "alu", "achieved": achieved, "peak": rp["peak"], "unit": UNIT,
+                     "frac": achieved / rp["peak"], "traffic": None, "kernel": BP_KERNEL_REGEX,
+                     "peak_basis": rp["basis"] + " (sm_max_mhz from MEASURED_PEAKS.json)"},
+        "clocks": clocks, "gpu_launches": 2 * args.steps,
+    })
+    if e2e is not None:
+        line["e2e"] = e2e
+    finish(line, ws, rank)
+
+
 def run_ragged(args) -> None:
     """Ragged batch: all items in one fbp_batched call (one filter launch + one
     persistent backprojection launch), captured once in a CUDA graph and
@@ -650,6 +753,8 @@ def main(argv=None):
         run_ragged(args)
     elif args.workload == "gd_refine_n1024":
         run_gd(args)
+    elif args.workload == "fbp_pipeline_n8192":
+        run_pipeline(args)
     else:
         run_uniform(args)
 

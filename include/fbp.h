@@ -169,6 +169,70 @@ fbp_status fbp_backproject_variant(const void *filt, const float *row_scale,
                                    fbp_stream_t stream);
 
 /*
+ * Stage-2 pre-processing fused into the filter (Sec. V-A(c) stage 2: the
+ * Beer-Lambert conversion and a Gaussian blur precede the filtering).  The
+ * paper fixes neither the blur width nor the flat field; they are inputs.
+ */
+typedef struct {
+    const float *flat;   /* device, float [n_det]: incident intensity I0 per detector
+                            bin, or NULL to use flat_value for every bin */
+    float flat_value;    /* I0 when flat is NULL (> 0) */
+    float count_floor;   /* counts are raised to at least this before the log (> 0) */
+    float mu_scale;      /* line integral unit: p = mu_scale * -ln(I / I0) (> 0);
+                            n for line integrals in pixel units of an n-pixel field
+                            of view whose attenuation is given per field width */
+    float blur_sigma;    /* Gaussian blur along the detector, in bins, in [0, 3.875];
+                            0 = none.  Taps exp(-k^2 / (2 sigma^2)), |k| <= floor(4 sigma
+                            + 1/2), normalised to sum 1 in double, zero outside [0, D) */
+} fbp_preprocess;
+
+/*
+ * fbp_filter_counts -- fbp_filter on detector counts: each sample I becomes
+ * p = mu_scale * -ln(max(I, count_floor) / I0), each row is blurred with
+ * the Gaussian, and the result is filtered exactly as fbp_filter filters
+ * line integrals, in one pass (the line integrals are never written to
+ * memory).  counts: device, float [n_slices][K][D]; the other arguments and
+ * errors are fbp_filter's.  FBP_ERR_INVALID_ARG for a NULL pre, a
+ * non-positive floor, scale or flat_value (flat NULL), or sigma outside
+ * [0, 3.875].
+ */
+fbp_status fbp_filter_counts(const float *counts, void *filt, float *row_scale,
+                             fbp_dtype dtype, fbp_filter_kind kind, const fbp_geometry *g,
+                             int n_slices, const fbp_preprocess *pre, fbp_stream_t stream);
+
+/*
+ * Stage-4 output mapping (Sec. V-A(c) stage 4: slices normalised by CT
+ * number (HU) range and quantised to uint16).  HU = 1000 (mu - mu_water) /
+ * (mu_water - mu_air); the window [hu_min, hu_max] maps linearly onto
+ * [0, 65535].
+ */
+typedef struct {
+    double mu_water, mu_air;   /* attenuation of water and air in the slice's units */
+    double hu_min, hu_max;     /* the window, hu_max > hu_min */
+} fbp_hu_window;
+
+/* FP32 coefficients the kernels use: code = clamp(rint(RN(RN(a * mu) + b)),
+ * 0, 65535), rounded to nearest even; a and b are formed in double as
+ * a = 1000 s / (mu_water - mu_air), b = -(1000 mu_water / (mu_water - mu_air)
+ * + hu_min) s, s = 65535 / (hu_max - hu_min), then rounded to float.
+ * FBP_ERR_INVALID_ARG for a NULL argument, a non-finite value,
+ * mu_water == mu_air or hu_max <= hu_min.  Host-only. */
+fbp_status fbp_hu_coefficients(const fbp_hu_window *w, float *a, float *b);
+
+/*
+ * fbp_backproject_u16 -- fbp_backproject_variant with the stage-4 mapping in
+ * the epilogue: each pixel's value scale * sum_k Q_k is mapped to its uint16
+ * code (see fbp_hu_coefficients) instead of being stored as FP32.
+ *   slice  device, uint16 [n_slices][n][n]: receives the codes.
+ * No accumulate mode.  Other arguments and errors as fbp_backproject_variant,
+ * plus fbp_hu_coefficients' errors for the window.
+ */
+fbp_status fbp_backproject_u16(const void *filt, const float *row_scale, fbp_dtype dtype,
+                               unsigned short *slice, const fbp_geometry *g, int n_slices,
+                               float scale, const fbp_hu_window *w, int variant,
+                               fbp_stream_t stream);
+
+/*
  * fbp_backproject_noalloc -- fbp_backproject for callers that cannot
  * allocate device memory.  The paper has no counterpart: this is a library
  * service, not a step of the method.

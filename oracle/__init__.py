@@ -20,9 +20,11 @@ per definition):
 * ``forward``             -- the matched forward projector A (scatter form),
                              whose transpose is ``backproject`` with scale 1.
 
-This module adds the least-squares refinement loop (gradient descent on
-0.5 * ||A x - b||^2, step 1/lambda_max(A^T A) from power iteration) in numpy
-on top of those calls.
+This module adds, in numpy on top of those calls, the least-squares
+refinement loop (gradient descent on 0.5 * ||A x - b||^2, step
+1/lambda_max(A^T A) from power iteration) and the steps on either side of
+the path (Sec. V-A(c) stages 2 and 4): Beer-Lambert conversion of counts,
+a Gaussian blur along the detector, and the HU window quantised to uint16.
 """
 from __future__ import annotations
 
@@ -262,3 +264,80 @@ def gd_refine(x0, b, g: Geometry, eta: float, iters: int):
         x = x - eta * backproject(r, g, scale=1.0)
     losses.append(loss(x, b, g))
     return x, losses
+
+
+# ---------------------------------------------------------------------------
+# The steps on either side of the path (Sec. V-A(c)): stage 2 converts
+# detector counts to line integrals (Beer-Lambert) and blurs them (Gaussian)
+# before filtering; stage 4 maps the reconstructed attenuation to CT numbers
+# (HU) over a window and quantises to uint16.  The paper fixes neither the
+# blur width nor the window: both are parameters here.
+# ---------------------------------------------------------------------------
+def beer_lambert(I, I0, mu_scale: float = 1.0, floor: float = 1.0) -> np.ndarray:
+    """Line integrals from counts by the Beer-Lambert law I = I0 exp(-p):
+    p = mu_scale * -ln(max(I, floor) / I0).  I0 is a scalar or one value per
+    detector bin (broadcast along the last axis)."""
+    I = np.maximum(_f64(I), float(floor))
+    return float(mu_scale) * -np.log(I / _f64(I0))
+
+
+def gaussian_taps(sigma: float) -> np.ndarray:
+    """Weights w_k, |k| <= r, r = floor(4 sigma + 1/2): exp(-k^2 / (2 sigma^2))
+    normalised to sum 1 (sigma = 0: the single tap w_0 = 1)."""
+    if sigma <= 0.0:
+        return np.ones(1)
+    r = int(4.0 * sigma + 0.5)
+    k = np.arange(-r, r + 1, dtype=np.float64)
+    w = np.exp(-(k * k) / (2.0 * sigma * sigma))
+    return w / w.sum()
+
+
+def gaussian_blur(p, sigma: float) -> np.ndarray:
+    """Blur along the detector (last axis), zero outside [0, D):
+    y[j] = sum_k w_k p[j - k]."""
+    p = _f64(p)
+    w = gaussian_taps(sigma)
+    r = (len(w) - 1) // 2
+    D = p.shape[-1]
+    y = np.zeros_like(p)
+    for i, k in enumerate(range(-r, r + 1)):
+        lo, hi = max(0, k), min(D, D + k)          # j with 0 <= j - k < D
+        if lo < hi:
+            y[..., lo:hi] += w[i] * p[..., lo - k:hi - k]
+    return y
+
+
+def preprocess(I, I0, mu_scale: float = 1.0, floor: float = 1.0, sigma: float = 0.0) -> np.ndarray:
+    """Stage-2 pre-processing: Beer-Lambert, then the Gaussian blur."""
+    return gaussian_blur(beer_lambert(I, I0, mu_scale, floor), sigma)
+
+
+def hu(mu, mu_water: float, mu_air: float = 0.0) -> np.ndarray:
+    """CT number: HU = 1000 (mu - mu_water) / (mu_water - mu_air)."""
+    return 1000.0 * (_f64(mu) - mu_water) / (mu_water - mu_air)
+
+
+def hu_codes(mu, mu_water: float, mu_air: float, hu_min: float, hu_max: float) -> np.ndarray:
+    """Stage-4 quantisation in FP64: the HU window [hu_min, hu_max] mapped
+    onto [0, 65535], rounded to nearest (ties to even) and clamped."""
+    x = (hu(mu, mu_water, mu_air) - hu_min) / (hu_max - hu_min) * 65535.0
+    return np.clip(np.rint(x), 0, 65535).astype(np.uint16)
+
+
+def hu_affine(mu_water: float, mu_air: float, hu_min: float, hu_max: float):
+    """(a, b) with code = a * mu + b before rounding, from the definition in
+    FP64: a = 1000 * 65535 / ((mu_water - mu_air)(hu_max - hu_min)),
+    b = -(1000 mu_water / (mu_water - mu_air) + hu_min) * 65535 / (hu_max - hu_min)."""
+    s = 65535.0 / (hu_max - hu_min)
+    a = 1000.0 / (mu_water - mu_air) * s
+    b = -(1000.0 * mu_water / (mu_water - mu_air) + hu_min) * s
+    return a, b
+
+
+def hu_codes_f32(mu32, a32, b32) -> np.ndarray:
+    """The same quantisation taken in FP32 from FP32 values, as a sequence of
+    single roundings: t = RN32(a * mu), t = RN32(t + b), code = clamp(RNE(t))."""
+    mu32 = np.asarray(mu32, dtype=np.float32)
+    t = np.float32(a32) * mu32
+    t = (t + np.float32(b32)).astype(np.float32)
+    return np.clip(np.rint(t), 0, 65535).astype(np.uint16)

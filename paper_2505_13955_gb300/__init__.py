@@ -13,6 +13,7 @@ from __future__ import annotations
 _API_NAMES = {
     "Geometry", "filter", "backproject", "radon_forward", "fbp", "fbp_host", "fbp_batched",
     "bp_variants", "forward_variant_count", "variant_supports", "batched_workspace_bytes", "prepare", "device_status", "release_tables",
+    "Preprocess", "HuWindow", "filter_counts", "hu_coefficients", "backproject_u16", "fbp_counts",
     "RadonForward", "RadonBackproject", "radon", "radon_t", "lsq_refine", "FbpError", "lib",
 }
 

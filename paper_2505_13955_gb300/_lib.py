@@ -53,12 +53,37 @@ class CBpShape(ctypes.Structure):
 
 
 _G = ctypes.POINTER(CGeometry)
+class CPreprocess(ctypes.Structure):
+    _fields_ = [
+        ("flat", ctypes.c_void_p),
+        ("flat_value", ctypes.c_float),
+        ("count_floor", ctypes.c_float),
+        ("mu_scale", ctypes.c_float),
+        ("blur_sigma", ctypes.c_float),
+    ]
+
+
+class CHuWindow(ctypes.Structure):
+    _fields_ = [
+        ("mu_water", ctypes.c_double),
+        ("mu_air", ctypes.c_double),
+        ("hu_min", ctypes.c_double),
+        ("hu_max", ctypes.c_double),
+    ]
+
+
 SIGNATURES = {
     "fbp_version": (ctypes.c_int, []),
     "fbp_geometry_default": (CGeometry, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "fbp_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "fbp_last_error_message": (ctypes.c_char_p, []),
     "fbp_filter": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _G, ctypes.c_int, _vp]),
+    "fbp_filter_counts": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _G, ctypes.c_int,
+                                         ctypes.POINTER(CPreprocess), _vp]),
+    "fbp_hu_coefficients": (ctypes.c_int, [ctypes.POINTER(CHuWindow), ctypes.POINTER(ctypes.c_float),
+                                           ctypes.POINTER(ctypes.c_float)]),
+    "fbp_backproject_u16": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int, ctypes.c_float,
+                                           ctypes.POINTER(CHuWindow), ctypes.c_int, _vp]),
     "fbp_backproject": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int, ctypes.c_float,
                                        ctypes.c_int, _vp]),
     "fbp_backproject_variant": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int,

@@ -115,6 +115,108 @@ def filter(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
     return out, (row_scale if dtype != torch.float32 else None)
 
 
+@dataclass
+class Preprocess:
+    """Stage-2 pre-processing for fbp_filter_counts: p = mu_scale * -ln(max(I,
+    count_floor) / I0) (I0 = `flat` per bin, or `flat_value`), then a Gaussian
+    blur of width blur_sigma bins along the detector."""
+    flat_value: float = 1.0
+    flat: torch.Tensor | None = None
+    count_floor: float = 1.0
+    mu_scale: float = 1.0
+    blur_sigma: float = 0.0
+
+    def c(self):
+        if self.flat is not None:
+            _need(self.flat, "flat", torch.float32)
+        return _lib.CPreprocess(_ptr(self.flat) if self.flat is not None else None,
+                                float(self.flat_value), float(self.count_floor),
+                                float(self.mu_scale), float(self.blur_sigma))
+
+
+@dataclass
+class HuWindow:
+    """Stage-4 mapping: HU = 1000 (mu - mu_water) / (mu_water - mu_air), the
+    window [hu_min, hu_max] onto uint16 codes [0, 65535]."""
+    mu_water: float
+    mu_air: float = 0.0
+    hu_min: float = -1000.0
+    hu_max: float = 3000.0
+
+    def c(self):
+        return _lib.CHuWindow(float(self.mu_water), float(self.mu_air), float(self.hu_min),
+                              float(self.hu_max))
+
+
+def filter_counts(counts: torch.Tensor, g: Geometry, pre: Preprocess, kind="ramlak",
+                  dtype=torch.float32, out: torch.Tensor | None = None,
+                  row_scale: torch.Tensor | None = None, which: str = "default"):
+    """fbp_filter_counts: Beer-Lambert + blur + ramp filter from detector
+    counts in one pass.  Returns (filt, row_scale or None)."""
+    _need(counts, "counts", torch.float32)
+    S = _slices(counts, (g.n_angles, g.n_det), "counts")
+    if out is None:
+        out = torch.empty(counts.shape, dtype=dtype, device=counts.device)
+    _need(out, "out", dtype)
+    if dtype != torch.float32 and row_scale is None:
+        row_scale = torch.empty(counts.shape[:-1], dtype=torch.float32, device=counts.device)
+    L = lib(which)
+    gc, pc = g.c(), pre.c()
+    st = L.fbp_filter_counts(_ptr(counts), _ptr(out), _ptr(row_scale), _DTYPES[dtype], kind_id(kind),
+                             ctypes.byref(gc), S, ctypes.byref(pc), _stream(counts.device))
+    _lib.check(st, L, "fbp_filter_counts")
+    return out, (row_scale if dtype != torch.float32 else None)
+
+
+def hu_coefficients(w: HuWindow, which: str = "default"):
+    """The FP32 (a, b) of code = clamp(rint(RN(RN(a mu) + b)), 0, 65535)."""
+    L = lib(which)
+    wc = w.c()
+    a, b = ctypes.c_float(), ctypes.c_float()
+    _lib.check(L.fbp_hu_coefficients(ctypes.byref(wc), ctypes.byref(a), ctypes.byref(b)), L,
+               "fbp_hu_coefficients")
+    return a.value, b.value
+
+
+def backproject_u16(filt: torch.Tensor, g: Geometry, window: HuWindow,
+                    row_scale: torch.Tensor | None = None, scale: float | None = None,
+                    out: torch.Tensor | None = None, variant: int = -1, which: str = "default"):
+    """fbp_backproject_u16: backprojection with the HU window quantised to
+    uint16 in the epilogue.  Returns an int16-typed tensor holding the uint16
+    codes' bit patterns (``.view(torch.uint16)`` / ``.numpy().view('u2')``)."""
+    _need(filt, "filt")
+    if filt.dtype not in _DTYPES:
+        raise ValueError(f"unsupported filt dtype {filt.dtype}")
+    S = _slices(filt, (g.n_angles, g.n_det), "filt")
+    shape = (g.n, g.n) if filt.dim() == 2 else (S, g.n, g.n)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.int16, device=filt.device)
+    _need(out, "out", torch.int16)
+    if tuple(out.shape) != shape:
+        raise ValueError(f"out has shape {tuple(out.shape)}, expected {shape}")
+    if row_scale is not None:
+        _need(row_scale, "row_scale", torch.float32)
+    if scale is None:
+        scale = g.angle_step
+    L = lib(which)
+    gc, wc = g.c(), window.c()
+    st = L.fbp_backproject_u16(_ptr(filt), _ptr(row_scale), _DTYPES[filt.dtype], _ptr(out),
+                               ctypes.byref(gc), S, float(scale), ctypes.byref(wc), int(variant),
+                               _stream(filt.device))
+    _lib.check(st, L, "fbp_backproject_u16")
+    return out
+
+
+def fbp_counts(counts: torch.Tensor, g: Geometry, pre: Preprocess, window: HuWindow | None = None,
+               kind="ramlak", dtype=torch.float32, variant: int = -1):
+    """The fused reconstruction of Sec. V-A(c) stages 2 and 4: detector counts
+    in, FP32 attenuation (window None) or uint16 HU codes out."""
+    filt, rs = filter_counts(counts, g, pre, kind=kind, dtype=dtype)
+    if window is None:
+        return backproject(filt, g, row_scale=rs, variant=variant)
+    return backproject_u16(filt, g, window, row_scale=rs, variant=variant)
+
+
 def backproject(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None = None,
                 scale: float | None = None, out: torch.Tensor | None = None,
                 accumulate: bool = False, variant: int = -1, which: str = "default"):
@@ -172,8 +274,13 @@ def fbp(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
 
 def fbp_host(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
              out: torch.Tensor | None = None, variant: int = -1, chunk: int = 2,
-             n_streams: int = 3, device=None) -> torch.Tensor:
+             n_streams: int = 3, device=None, pre: "Preprocess | None" = None,
+             window: "HuWindow | None" = None) -> torch.Tensor:
     """FBP of a stack held in host memory: returns (or fills) a host tensor.
+
+    With `pre` the input is detector counts (fbp_filter_counts); with
+    `window` the output is the uint16 HU codes (fbp_backproject_u16), held in
+    an int16 tensor.
 
     The stack is processed in chunks of `chunk` slices on `n_streams` CUDA
     streams; each stream copies its chunk in, runs fbp_filter and
@@ -191,8 +298,9 @@ def fbp_host(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32
     if squeeze:
         sino = sino.unsqueeze(0)
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    odt = torch.int16 if window is not None else torch.float32
     if out is None:
-        out = torch.empty((S, g.n, g.n), dtype=torch.float32, pin_memory=True)
+        out = torch.empty((S, g.n, g.n), dtype=odt, pin_memory=True)
     o3 = out.view(S, g.n, g.n)
     chunk = max(1, min(chunk, S))
     n_streams = max(1, min(n_streams, -(-S // chunk)))
@@ -204,7 +312,7 @@ def fbp_host(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32
                      torch.empty((chunk, g.n_angles, g.n_det), dtype=dtype, device=dev),
                      torch.empty((chunk, g.n_angles), dtype=torch.float32, device=dev)
                      if dtype != torch.float32 else None,
-                     torch.empty((chunk, g.n, g.n), dtype=torch.float32, device=dev)))
+                     torch.empty((chunk, g.n, g.n), dtype=odt, device=dev)))
     for st in streams:
         st.wait_stream(caller)
     for i, i0 in enumerate(range(0, S, chunk)):
@@ -214,10 +322,15 @@ def fbp_host(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32
         d_in, d_filt, d_rs, d_out = bufs[i % n_streams]
         with torch.cuda.stream(st):
             d_in[:n].copy_(sino[i0:i1], non_blocking=True)
-            filter(d_in[:n], g, kind=kind, dtype=dtype, out=d_filt[:n],
-                   row_scale=None if d_rs is None else d_rs[:n])
-            backproject(d_filt[:n], g, row_scale=None if d_rs is None else d_rs[:n],
-                        out=d_out[:n], variant=variant)
+            rs = None if d_rs is None else d_rs[:n]
+            if pre is None:
+                filter(d_in[:n], g, kind=kind, dtype=dtype, out=d_filt[:n], row_scale=rs)
+            else:
+                filter_counts(d_in[:n], g, pre, kind=kind, dtype=dtype, out=d_filt[:n], row_scale=rs)
+            if window is None:
+                backproject(d_filt[:n], g, row_scale=rs, out=d_out[:n], variant=variant)
+            else:
+                backproject_u16(d_filt[:n], g, window, row_scale=rs, out=d_out[:n], variant=variant)
             o3[i0:i1].copy_(d_out[:n], non_blocking=True)
     for st in streams:
         st.synchronize()

@@ -45,6 +45,8 @@ struct BpArgs {
     double alpha, det_center;
     float scale;
     int accumulate;
+    unsigned short *slice16;   // uint16 codes instead of `slice`, or null
+    float hu_a, hu_b;
     int H, W;
     int tiles_x;
     int slice_base;
@@ -62,7 +64,10 @@ __global__ void __launch_bounds__(TXT *TYT) bp_kernel(BpArgs a)
     const size_t kd = (size_t)a.K * a.D;
     j.filt = static_cast<const char *>(a.filt) + (size_t)sl * kd * sizeof(T);
     j.row_scale = a.row_scale ? a.row_scale + (size_t)sl * a.K : nullptr;
-    j.out = a.slice + (size_t)sl * a.N * a.N;
+    j.out = a.slice ? a.slice + (size_t)sl * a.N * a.N : nullptr;
+    j.out16 = a.slice16 ? a.slice16 + (size_t)sl * a.N * a.N : nullptr;
+    j.hu_a = a.hu_a;
+    j.hu_b = a.hu_b;
     j.cs = a.cs;
     j.K = a.K;
     j.D = a.D;
@@ -91,7 +96,10 @@ __global__ void __launch_bounds__(TXT *TYT, (TXT * TYT >= 256) ? 2 : 4) bp_orbit
     const size_t kd = (size_t)a.K * a.D;
     j.filt = static_cast<const char *>(a.filt) + (size_t)sl * kd * sizeof(T);
     j.row_scale = a.row_scale ? a.row_scale + (size_t)sl * a.K : nullptr;
-    j.out = a.slice + (size_t)sl * a.N * a.N;
+    j.out = a.slice ? a.slice + (size_t)sl * a.N * a.N : nullptr;
+    j.out16 = a.slice16 ? a.slice16 + (size_t)sl * a.N * a.N : nullptr;
+    j.hu_a = a.hu_a;
+    j.hu_b = a.hu_b;
     j.cs = a.cs;
     j.K = a.K;
     j.D = a.D;
@@ -137,6 +145,9 @@ fbp_status launch_orbit_shape(const BpLaunch &L, cudaStream_t s, unsigned *statu
     a.det_center = L.det_center;
     a.scale = L.scale;
     a.accumulate = L.accumulate;
+    a.slice16 = L.slice16;
+    a.hu_a = L.hu_a;
+    a.hu_b = L.hu_b;
     a.H = bp_window_half(L.alpha, TILE, TILE);
     a.W = 2 * a.H + 1;
     a.status = status;
@@ -180,6 +191,9 @@ fbp_status launch_shape(const BpLaunch &L, cudaStream_t s, unsigned *status)
     a.det_center = L.det_center;
     a.scale = L.scale;
     a.accumulate = L.accumulate;
+    a.slice16 = L.slice16;
+    a.hu_a = L.hu_a;
+    a.hu_b = L.hu_b;
     a.H = bp_window_half(L.alpha, TW, TH);
     a.W = 2 * a.H + 1;
     a.status = status;
@@ -254,6 +268,8 @@ __global__ void __launch_bounds__(TXT *TYT) bp_persistent_kernel(BpBatchArgs a)
         j.filt = it.filt;
         j.row_scale = it.row_scale;
         j.out = it.slice;
+        j.out16 = nullptr;
+        j.hu_a = j.hu_b = 0.f;
         j.cs = it.cs;
         j.K = it.K;
         j.D = it.D;

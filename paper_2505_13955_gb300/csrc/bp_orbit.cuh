@@ -39,6 +39,8 @@ struct BpOrbitJob {
     const void *filt;          // this slice's [K][D] rows
     const float *row_scale;    // this slice's [K] scales, or null
     float *out;                // this slice's [N][N]
+    unsigned short *out16;     // or, when set, this slice's [N][N] uint16 codes (bp_tile.cuh)
+    float hu_a, hu_b;
     const double2 *cs;         // [K] (only k < K/2 is read)
     int K, D, N;
     double alpha, det_center;
@@ -455,11 +457,8 @@ __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *sme
             const size_t o3 = (size_t)(N - 1 - c) * N + r;
             const size_t os[4] = {o0, o1, o2, o3};
 #pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                float *p = j.out + os[o];
-                const float v = acc[o][iy][ix] * gain;
-                *p = j.accumulate ? *p + v : v;
-            }
+            for (int o = 0; o < 4; ++o)
+                store_pixel(j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, os[o], acc[o][iy][ix] * gain);
         }
     }
 }

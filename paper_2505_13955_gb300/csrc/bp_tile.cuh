@@ -56,6 +56,8 @@ struct BpTileJob {
     const void *filt;          // this slice's [K][D] rows (dtype T)
     const float *row_scale;    // this slice's [K] scales, or null
     float *out;                // this slice's [N][N]
+    unsigned short *out16;     // or, when set, this slice's [N][N] uint16 CT-number codes
+    float hu_a, hu_b;          // code = clamp(rint(RN(RN(hu_a * mu) + hu_b)), 0, 65535)
     const double2 *cs;         // [K] cos, sin (FP64)
     int K, D, N;
     double alpha, det_center;
@@ -65,6 +67,21 @@ struct BpTileJob {
     int x0, y0;                // tile origin (pixels)
     unsigned *status;
 };
+
+// Output of one pixel: the attenuation (written or added), or its stage-4
+// code (Sec. V-A(c): HU window quantised to uint16), taken in FP32 as two
+// single roundings, rounded to nearest even and clamped to [0, 65535].
+__device__ __forceinline__ void store_pixel(float *out, unsigned short *out16, float hu_a, float hu_b,
+                                            int accumulate, size_t idx, float v)
+{
+    if (out16) {
+        const float t = rintf(__fadd_rn(__fmul_rn(hu_a, v), hu_b));
+        out16[idx] = (unsigned short)fminf(fmaxf(t, 0.f), 65535.f);
+    } else {
+        float *o = out + idx;
+        *o = accumulate ? *o + v : v;
+    }
+}
 
 // Shared memory: [KT] float4 per-angle parameters, [KT] int window starts,
 // [KT][W] float2 (a, d) table.
@@ -178,11 +195,9 @@ __device__ __forceinline__ void bp_tile(const BpTileJob &j, unsigned char *smem)
 #pragma unroll
         for (int ix = 0; ix < PX; ++ix) {
             const int c = j.x0 + tx + TXT * ix;
-            if (r < j.N && c < j.N) {
-                float *o = j.out + (size_t)r * j.N + c;
-                const float v = acc[iy][ix] * j.scale;
-                *o = j.accumulate ? *o + v : v;
-            }
+            if (r < j.N && c < j.N)
+                store_pixel(j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, (size_t)r * j.N + c,
+                            acc[iy][ix] * j.scale);
         }
     }
 }

@@ -80,40 +80,127 @@ const char *fbp_status_string(fbp_status s)
 
 const char *fbp_last_error_message(void);
 
+static fbp_status filter_impl(const float *sino, void *filt, float *row_scale, fbp_dtype dtype,
+                              fbp_filter_kind kind, const fbp_geometry *g, int n_slices,
+                              const FilterPre *pre, fbp_stream_t stream)
+{
+    fbp_status st = check_geometry(g, true, false);
+    if (st != FBP_OK) return st;
+    if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
+    if (!kind_ok(kind)) return fail(FBP_ERR_INVALID_ARG, "filter kind %d", (int)kind);
+    if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
+    if (n_slices == 0) return FBP_OK;
+    if (!sino || !filt) return fail(FBP_ERR_INVALID_ARG, "sino or filt is NULL");
+    if (dtype != FBP_F32 && !row_scale)
+        return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit output");
+    const long long rows = (long long)n_slices * g->n_angles;
+    const size_t nin = (size_t)rows * g->n_det * 4, nout = (size_t)rows * g->n_det * dtype_size(dtype);
+    if (overlap(sino, nin, filt, nout)) return fail(FBP_ERR_INVALID_ARG, "filt overlaps sino");
+    const float2 *G = nullptr;
+    const float2 *tw = nullptr;
+    int L = 0;
+    st = filter_tables(g->n_det, kind, g->det_spacing, stream, &G, &tw, &L);
+    if (st != FBP_OK) return st;
+    FilterLaunch a;
+    a.sino = sino;
+    a.filt = filt;
+    a.row_scale = dtype == FBP_F32 ? nullptr : row_scale;
+    a.rows = rows;
+    a.D = g->n_det;
+    a.L = L;
+    a.G = G;
+    a.tw = tw;
+    a.dtype = dtype;
+    a.pre = pre;
+    return launch_filter(a, stream);
+}
+
 fbp_status fbp_filter(const float *sino, void *filt, float *row_scale, fbp_dtype dtype,
                       fbp_filter_kind kind, const fbp_geometry *g, int n_slices,
                       fbp_stream_t stream)
 {
     return guarded([&]() -> fbp_status {
-        fbp_status st = check_geometry(g, true, false);
-        if (st != FBP_OK) return st;
-        if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
-        if (!kind_ok(kind)) return fail(FBP_ERR_INVALID_ARG, "filter kind %d", (int)kind);
-        if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
-        if (n_slices == 0) return FBP_OK;
-        if (!sino || !filt) return fail(FBP_ERR_INVALID_ARG, "sino or filt is NULL");
-        if (dtype != FBP_F32 && !row_scale)
-            return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit output");
-        const long long rows = (long long)n_slices * g->n_angles;
-        const size_t nin = (size_t)rows * g->n_det * 4, nout = (size_t)rows * g->n_det * dtype_size(dtype);
-        if (overlap(sino, nin, filt, nout)) return fail(FBP_ERR_INVALID_ARG, "filt overlaps sino");
-        const float2 *G = nullptr;
-        const float2 *tw = nullptr;
-        int L = 0;
-        st = filter_tables(g->n_det, kind, g->det_spacing, stream, &G, &tw, &L);
-        if (st != FBP_OK) return st;
-        FilterLaunch a;
-        a.sino = sino;
-        a.filt = filt;
-        a.row_scale = dtype == FBP_F32 ? nullptr : row_scale;
-        a.rows = rows;
-        a.D = g->n_det;
-        a.L = L;
-        a.G = G;
-        a.tw = tw;
-        a.dtype = dtype;
-        return launch_filter(a, stream);
+        return filter_impl(sino, filt, row_scale, dtype, kind, g, n_slices, nullptr, stream);
     });
+}
+
+fbp_status fbp_filter_counts(const float *counts, void *filt, float *row_scale, fbp_dtype dtype,
+                             fbp_filter_kind kind, const fbp_geometry *g, int n_slices,
+                             const fbp_preprocess *pre, fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        if (!pre) return fail(FBP_ERR_INVALID_ARG, "pre is NULL");
+        if (!pre->flat && !(pre->flat_value > 0.f && std::isfinite(pre->flat_value)))
+            return fail(FBP_ERR_INVALID_ARG, "flat_value must be positive when flat is NULL");
+        if (!(pre->count_floor > 0.f && std::isfinite(pre->count_floor)))
+            return fail(FBP_ERR_INVALID_ARG, "count_floor must be positive");
+        if (!(pre->mu_scale > 0.f && std::isfinite(pre->mu_scale)))
+            return fail(FBP_ERR_INVALID_ARG, "mu_scale must be positive");
+        if (!(pre->blur_sigma >= 0.f && pre->blur_sigma <= 3.875f))
+            return fail(FBP_ERR_INVALID_ARG, "blur_sigma must lie in [0, 3.875]");
+        FilterPre fp;
+        fp.flat = pre->flat;
+        fp.flat_value = pre->flat_value;
+        fp.floor = pre->count_floor;
+        fp.mu_scale = pre->mu_scale;
+        // taps exp(-k^2 / (2 sigma^2)), |k| <= floor(4 sigma + 1/2), normalised in double
+        const double sg = pre->blur_sigma;
+        fp.blur_radius = sg > 0.0 ? (int)(4.0 * sg + 0.5) : 0;
+        double w[33], sum = 0.0;
+        for (int k = -fp.blur_radius; k <= fp.blur_radius; ++k) {
+            w[k + fp.blur_radius] = sg > 0.0 ? std::exp(-(double)k * k / (2.0 * sg * sg)) : 1.0;
+            sum += w[k + fp.blur_radius];
+        }
+        for (int i = 0; i <= 2 * fp.blur_radius; ++i) fp.taps[i] = (float)(w[i] / sum);
+        if (g && pre->flat && overlap(pre->flat, (size_t)g->n_det * 4, filt,
+                                      (size_t)n_slices * g->n_angles * g->n_det * dtype_size(dtype)))
+            return fail(FBP_ERR_INVALID_ARG, "flat overlaps filt");
+        return filter_impl(counts, filt, row_scale, dtype, kind, g, n_slices, &fp, stream);
+    });
+}
+
+static fbp_status backproject_impl(const void *filt, const float *row_scale, fbp_dtype dtype,
+                                   float *slice, unsigned short *slice16, float hu_a, float hu_b,
+                                   const fbp_geometry *g, int n_slices, float scale,
+                                   int accumulate, int variant, fbp_stream_t stream)
+{
+    fbp_status st = check_geometry(g, false, true);
+    if (st != FBP_OK) return st;
+    if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
+    if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
+    if (variant < -1 || variant >= bp_variant_count())
+        return fail(FBP_ERR_INVALID_ARG, "variant %d", variant);
+    if (!std::isfinite(scale)) return fail(FBP_ERR_INVALID_ARG, "scale is not finite");
+    if (n_slices == 0) return FBP_OK;
+    if (!filt || !(slice || slice16)) return fail(FBP_ERR_INVALID_ARG, "filt or slice is NULL");
+    if (dtype != FBP_F32 && !row_scale)
+        return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit input");
+    const size_t nin = (size_t)n_slices * g->n_angles * g->n_det * dtype_size(dtype);
+    const size_t nout = (size_t)n_slices * g->n * g->n * (slice16 ? 2 : 4);
+    if (overlap(filt, nin, slice16 ? (const void *)slice16 : (const void *)slice, nout))
+        return fail(FBP_ERR_INVALID_ARG, "slice overlaps filt");
+    const double2 *cs = nullptr;
+    st = angle_table(*g, stream, &cs);
+    if (st != FBP_OK) return st;
+    BpLaunch a;
+    a.filt = filt;
+    a.row_scale = dtype == FBP_F32 ? nullptr : row_scale;
+    a.slice = slice;
+    a.cs = cs;
+    a.K = g->n_angles;
+    a.D = g->n_det;
+    a.N = g->n;
+    a.S = n_slices;
+    a.alpha = g->pixel_size / g->det_spacing;
+    a.det_center = g->det_center;
+    a.angle_step = g->angle_step;
+    a.scale = scale;
+    a.accumulate = accumulate ? 1 : 0;
+    a.dtype = dtype;
+    a.slice16 = slice16;
+    a.hu_a = hu_a;
+    a.hu_b = hu_b;
+    return launch_backproject(a, variant, stream);
 }
 
 fbp_status fbp_backproject_variant(const void *filt, const float *row_scale, fbp_dtype dtype,
@@ -121,39 +208,45 @@ fbp_status fbp_backproject_variant(const void *filt, const float *row_scale, fbp
                                    int accumulate, int variant, fbp_stream_t stream)
 {
     return guarded([&]() -> fbp_status {
-        fbp_status st = check_geometry(g, false, true);
+        return backproject_impl(filt, row_scale, dtype, slice, nullptr, 0.f, 0.f, g, n_slices, scale,
+                                accumulate, variant, stream);
+    });
+}
+
+static fbp_status hu_coeffs(const fbp_hu_window *w, float *a, float *b)
+{
+    if (!w) return fail(FBP_ERR_INVALID_ARG, "window is NULL");
+    const double dw = w->mu_water - w->mu_air, dh = w->hu_max - w->hu_min;
+    if (!std::isfinite(w->mu_water) || !std::isfinite(w->mu_air) || !std::isfinite(w->hu_min) ||
+        !std::isfinite(w->hu_max) || !(dw != 0.0) || !(dh > 0.0))
+        return fail(FBP_ERR_INVALID_ARG, "HU window needs finite values, mu_water != mu_air, hu_max > hu_min");
+    // code = (HU - hu_min) / (hu_max - hu_min) * 65535, HU = 1000 (mu - mu_water) / (mu_water - mu_air)
+    const double s = 65535.0 / dh;
+    *a = (float)(1000.0 / dw * s);
+    *b = (float)(-(1000.0 * w->mu_water / dw + w->hu_min) * s);
+    return FBP_OK;
+}
+
+fbp_status fbp_hu_coefficients(const fbp_hu_window *w, float *a, float *b)
+{
+    return guarded([&]() -> fbp_status {
+        if (!a || !b) return fail(FBP_ERR_INVALID_ARG, "a or b is NULL");
+        return hu_coeffs(w, a, b);
+    });
+}
+
+fbp_status fbp_backproject_u16(const void *filt, const float *row_scale, fbp_dtype dtype,
+                               unsigned short *slice, const fbp_geometry *g, int n_slices,
+                               float scale, const fbp_hu_window *w, int variant,
+                               fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        float a = 0.f, b = 0.f;
+        fbp_status st = hu_coeffs(w, &a, &b);
         if (st != FBP_OK) return st;
-        if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
-        if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
-        if (variant < -1 || variant >= bp_variant_count())
-            return fail(FBP_ERR_INVALID_ARG, "variant %d", variant);
-        if (!std::isfinite(scale)) return fail(FBP_ERR_INVALID_ARG, "scale is not finite");
-        if (n_slices == 0) return FBP_OK;
-        if (!filt || !slice) return fail(FBP_ERR_INVALID_ARG, "filt or slice is NULL");
-        if (dtype != FBP_F32 && !row_scale)
-            return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit input");
-        const size_t nin = (size_t)n_slices * g->n_angles * g->n_det * dtype_size(dtype);
-        const size_t nout = (size_t)n_slices * g->n * g->n * 4;
-        if (overlap(filt, nin, slice, nout)) return fail(FBP_ERR_INVALID_ARG, "slice overlaps filt");
-        const double2 *cs = nullptr;
-        st = angle_table(*g, stream, &cs);
-        if (st != FBP_OK) return st;
-        BpLaunch a;
-        a.filt = filt;
-        a.row_scale = dtype == FBP_F32 ? nullptr : row_scale;
-        a.slice = slice;
-        a.cs = cs;
-        a.K = g->n_angles;
-        a.D = g->n_det;
-        a.N = g->n;
-        a.S = n_slices;
-        a.alpha = g->pixel_size / g->det_spacing;
-        a.det_center = g->det_center;
-        a.angle_step = g->angle_step;
-        a.scale = scale;
-        a.accumulate = accumulate ? 1 : 0;
-        a.dtype = dtype;
-        return launch_backproject(a, variant, stream);
+        if (n_slices > 0 && !slice) return fail(FBP_ERR_INVALID_ARG, "slice is NULL");
+        return backproject_impl(filt, row_scale, dtype, nullptr, slice, a, b, g, n_slices, scale, 0,
+                                variant, stream);
     });
 }
 

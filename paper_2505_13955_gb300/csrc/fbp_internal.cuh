@@ -83,8 +83,17 @@ int bp_window_half(double alpha, int tile_w, int tile_h);
 // ---------------------------------------------------------------------------
 // Kernel launchers (defined next to their kernels).
 // ---------------------------------------------------------------------------
+// Stage-2 pre-processing fused into the filter's load (counts -> blurred
+// line integrals); taps w_{-r..r} of the Gaussian, rounded once from double.
+struct FilterPre {
+    const float *flat;     // per-bin I0 [D] (device) or null
+    float flat_value, floor, mu_scale;
+    int blur_radius;       // r <= 16
+    float taps[33];
+};
+
 struct FilterLaunch {
-    const float *sino;     // [rows][D]
+    const float *sino;     // [rows][D] line integrals, or counts when pre is set
     void *filt;            // [rows][D] of dtype
     float *row_scale;      // [rows] (16-bit dtypes)
     long long rows;        // n_slices * K
@@ -92,6 +101,7 @@ struct FilterLaunch {
     const float2 *G;
     const float2 *tw;
     fbp_dtype dtype;
+    const FilterPre *pre = nullptr;
 };
 fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s);
 
@@ -106,6 +116,8 @@ struct BpLaunch {
     float scale;
     int accumulate;
     fbp_dtype dtype;
+    unsigned short *slice16 = nullptr;   // uint16 CT-number codes instead of `slice`
+    float hu_a = 0.f, hu_b = 0.f;        // code = clamp(rint(RN(RN(hu_a * mu) + hu_b)))
 };
 fbp_status launch_backproject(const BpLaunch &a, int variant, cudaStream_t s);
 bool bp_orbit_eligible(const BpLaunch &a, int tile);

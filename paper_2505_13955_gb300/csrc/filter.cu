@@ -196,6 +196,31 @@ constexpr int kFilterThreads = 512;    // threads per block; 512 / C row pairs p
 
 __host__ __device__ constexpr int group_threads(int L) { return 32 * fft_VPL(L); }
 
+// Stage-2 pre-processing fused into the load (Sec. V-A(c)): detector counts
+// I -> line integrals p = mu_scale * -ln(max(I, floor) / I0) (Beer-Lambert),
+// then a Gaussian blur along the detector with taps w_{-r..r} (zero outside
+// [0, D)).  The two rows are staged in the group's buffer, which step 1 then
+// overwrites.
+constexpr int kPrePad = 16;              // zero border of a staged row (>= the blur radius)
+constexpr int kMaxBlurRadius = 16;
+
+struct PreArgs {
+    int on;                              // 0: rows are line integrals already
+    const float *flat;                   // per-bin I0 [D], or null
+    float flat_value, floor, mu_scale;
+    int r;                               // blur radius, 0 = no blur
+    float taps[2 * kMaxBlurRadius + 1];
+};
+
+__device__ __forceinline__ float blur_at(const float *row, int n, const PreArgs &pre)
+{
+    // row[kPrePad + m] = p[m], zero for m outside [0, D)
+    const float *c = row + kPrePad + n;
+    float acc = pre.taps[pre.r] * c[0];
+    for (int k = 1; k <= pre.r; ++k) acc = fmaf(pre.taps[pre.r + k], c[-k] + c[k], acc);
+    return acc;
+}
+
 // One row pair by one group of C threads (t = thread index in the group).
 // S: the group's R x C complex buffer; red: 4 * C/32 floats of the group;
 // bar_id: the group's named barrier.
@@ -203,7 +228,7 @@ template <int L, typename T>
 __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int D,
                                          const float2 *__restrict__ Gs,
                                          const float2 *__restrict__ tw, float2 *S, float *red,
-                                         int t, int bar_id)
+                                         int t, int bar_id, const PreArgs &pre)
 {
     constexpr int R = fft_R(L), VPL = fft_VPL(L);
     constexpr int C = 32 * VPL;
@@ -215,24 +240,61 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
 
     // ---- step 1: differences of z[C n1 + t], R-point DFT over n1
     float2 v[R];
-    bool nz_a = false, nz_b = false;     // any nonzero (or NaN) raw sample in the row
-#pragma unroll
-    for (int n1 = 0; n1 < R; ++n1) {
-        const int n = C * n1 + t;
-        float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
-        if (active && C * n1 <= D) {              // uniform over the group
-            a = n < D ? __ldg(job.a + n) : 0.f;
-            b = (job.b && n < D) ? __ldg(job.b + n) : 0.f;
-            am = __shfl_up_sync(0xffffffffu, a, 1);
-            bm = __shfl_up_sync(0xffffffffu, b, 1);
-            if (lane == 0) {
-                am = (n >= 1 && n - 1 < D) ? __ldg(job.a + n - 1) : 0.f;
-                bm = (job.b && n >= 1 && n - 1 < D) ? __ldg(job.b + n - 1) : 0.f;
+    bool nz_a = false, nz_b = false;     // any nonzero (or NaN) sample in the row
+    if (pre.on) {
+        // stage p for both rows (row stride RS floats, zero borders), then
+        // read blurred values at n = C n1 + t; the buffer is rewritten below
+        float *st = reinterpret_cast<float *>(S);
+        const int RS = D + 2 * kPrePad;
+        for (int i = t; i < 2 * RS; i += C) {
+            const int row = i >= RS, m = i - row * RS - kPrePad;
+            const float *src = row ? job.b : job.a;
+            float p = 0.f;
+            if (active && src && m >= 0 && m < D) {
+                const float I0 = pre.flat ? __ldg(pre.flat + m) : pre.flat_value;
+                p = pre.mu_scale * -logf(__fdiv_rn(fmaxf(__ldg(src + m), pre.floor), I0));
             }
-            nz_a |= (a != 0.f);
-            nz_b |= (b != 0.f);
+            st[i] = p;
         }
-        v[n1] = make_float2(a - am, b - bm);
+        group_sync(bar_id, C);
+#pragma unroll
+        for (int n1 = 0; n1 < R; ++n1) {
+            const int n = C * n1 + t;
+            float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
+            if (active && C * n1 <= D) {          // uniform over the group
+                a = n < D ? blur_at(st, n, pre) : 0.f;
+                b = (job.b && n < D) ? blur_at(st + RS, n, pre) : 0.f;
+                am = __shfl_up_sync(0xffffffffu, a, 1);
+                bm = __shfl_up_sync(0xffffffffu, b, 1);
+                if (lane == 0) {
+                    am = (n >= 1 && n - 1 < D) ? blur_at(st, n - 1, pre) : 0.f;
+                    bm = (job.b && n >= 1 && n - 1 < D) ? blur_at(st + RS, n - 1, pre) : 0.f;
+                }
+                nz_a |= (a != 0.f);
+                nz_b |= (b != 0.f);
+            }
+            v[n1] = make_float2(a - am, b - bm);
+        }
+        group_sync(bar_id, C);                    // staged rows read before S is written
+    } else {
+#pragma unroll
+        for (int n1 = 0; n1 < R; ++n1) {
+            const int n = C * n1 + t;
+            float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
+            if (active && C * n1 <= D) {          // uniform over the group
+                a = n < D ? __ldg(job.a + n) : 0.f;
+                b = (job.b && n < D) ? __ldg(job.b + n) : 0.f;
+                am = __shfl_up_sync(0xffffffffu, a, 1);
+                bm = __shfl_up_sync(0xffffffffu, b, 1);
+                if (lane == 0) {
+                    am = (n >= 1 && n - 1 < D) ? __ldg(job.a + n - 1) : 0.f;
+                    bm = (job.b && n >= 1 && n - 1 < D) ? __ldg(job.b + n - 1) : 0.f;
+                }
+                nz_a |= (a != 0.f);
+                nz_b |= (b != 0.f);
+            }
+            v[n1] = make_float2(a - am, b - bm);
+        }
     }
     dft_reg<R, false>(v);
 #pragma unroll
@@ -342,13 +404,14 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
 }
 
 struct FilterArgs {
-    const float *sino;
+    const float *sino;          // line integrals, or counts when pre.on
     void *filt;
     float *row_scale;
     long long rows;
     int D;
     const float2 *G;
     const float2 *tw;
+    PreArgs pre;
 };
 
 __device__ __forceinline__ RowPairJob make_job(const float *sino, void *filt, float *row_scale,
@@ -379,7 +442,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(FilterArgs a)
     const long long pair = (long long)blockIdx.x * GP + g;
     bool active;
     const RowPairJob job = make_job(a.sino, a.filt, a.row_scale, a.rows, a.D, pair, sizeof(T), active);
-    fft_pair<L, T>(job, active, a.D, a.G, a.tw, smem_f2 + (size_t)g * L, red[g], t, 1 + g);
+    fft_pair<L, T>(job, active, a.D, a.G, a.tw, smem_f2 + (size_t)g * L, red[g], t, 1 + g, a.pre);
 }
 
 template <int L, typename T>
@@ -435,13 +498,16 @@ __global__ void __launch_bounds__(kFilterThreads) filter_batched_kernel(FilterBa
     const RowPairJob job = make_job(it.sino, it.filt, it.row_scale, it.K, it.D, pair, sizeof(T), active);
     float2 *S = smem_f2 + (size_t)g * it.L;
     float *rd = red + g * 4 * (C / 32);
+    PreArgs pre;
+    pre.on = 0;
+    pre.r = 0;
     switch (it.L) {
-        case 512: fft_pair<512, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
-        case 1024: fft_pair<1024, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
-        case 2048: fft_pair<2048, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
-        case 4096: fft_pair<4096, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
-        case 8192: fft_pair<8192, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
-        default: fft_pair<16384, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g); break;
+        case 512: fft_pair<512, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
+        case 1024: fft_pair<1024, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
+        case 2048: fft_pair<2048, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
+        case 4096: fft_pair<4096, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
+        case 8192: fft_pair<8192, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
+        default: fft_pair<16384, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
     }
 }
 
@@ -473,6 +539,20 @@ fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s)
     fa.D = a.D;
     fa.G = a.G;
     fa.tw = a.tw;
+    fa.pre.on = 0;
+    fa.pre.r = 0;
+    if (a.pre) {
+        const FilterPre &p = *a.pre;
+        if (p.blur_radius < 0 || p.blur_radius > kMaxBlurRadius)
+            return fail(FBP_ERR_UNSUPPORTED, "blur radius %d", p.blur_radius);
+        fa.pre.on = 1;
+        fa.pre.flat = p.flat;
+        fa.pre.flat_value = p.flat_value;
+        fa.pre.floor = p.floor;
+        fa.pre.mu_scale = p.mu_scale;
+        fa.pre.r = p.blur_radius;
+        for (int k = 0; k <= 2 * p.blur_radius; ++k) fa.pre.taps[k] = p.taps[k];
+    }
     switch (a.dtype) {
         case FBP_F32: return launch_t<float>(fa, a.L, s);
         case FBP_F16: return launch_t<__half>(fa, a.L, s);

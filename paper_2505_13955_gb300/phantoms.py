@@ -190,8 +190,18 @@ def poisson_noise(p_px: np.ndarray, n: int, photons: float,
     return (n * -np.log(np.maximum(counts, 1) / photons)).astype(np.float32)
 
 
+def poisson_counts(p_px: np.ndarray, n: int, photons: float,
+                   rng: np.random.Generator) -> np.ndarray:
+    """Raw detector counts for line integrals in pixel units: the physical
+    line integral is p_px / n, counts ~ Poisson(photons * exp(-p_px / n)),
+    returned as float32 (the detector's data; converting them back to line
+    integrals is the method's Beer-Lambert step, not the generator's)."""
+    lam = photons * np.exp(-np.asarray(p_px, dtype=np.float64) / n)
+    return rng.poisson(lam).astype(np.float32)
+
+
 # ---------------------------------------------------------------------------
-# The five workloads (slice counts, sizes, angle counts, filters, noise).
+# The workloads (slice counts, sizes, angle counts, filters, noise).
 # ---------------------------------------------------------------------------
 @dataclass
 class Workload:
@@ -206,6 +216,13 @@ class Workload:
     ragged: bool = False
     n_choices: tuple = field(default_factory=tuple)
     k_choices: tuple = field(default_factory=tuple)
+    counts: bool = False        # inputs are raw detector counts (stage-2 pre-processing on)
+
+
+# Parameters of the counts-to-codes workload (the paper leaves the blur width
+# and the HU window open): blur sigma in bins, water / air attenuation in the
+# phantom's density units, the HU window.
+PIPELINE = {"blur_sigma": 1.0, "mu_water": 0.5, "mu_air": 0.0, "hu_min": -1000.0, "hu_max": 3000.0}
 
 
 WORKLOADS = {
@@ -216,6 +233,8 @@ WORKLOADS = {
                                  ragged=True, n_choices=(512, 1024, 2048, 4096),
                                  k_choices=(720, 1800, 3600)),
     "gd_refine_n1024": Workload("gd_refine_n1024", 16, 1024, 1800, "ramlak", "random", 1e4, 5),
+    "fbp_pipeline_n8192": Workload("fbp_pipeline_n8192", 16, 8192, 4096, "ramlak", "random", 1e4, 6,
+                                   counts=True),
 }
 
 
@@ -233,6 +252,13 @@ def slice_spec(w: Workload, i: int):
         n, k = w.n, w.n_angles
     ell = shepp_logan() if w.phantom == "shepp_logan" else random_ellipses(rng)
     return n, k, ell, rng
+
+
+def slice_counts(w: Workload, i: int) -> np.ndarray:
+    """Raw detector counts [K, N] (float32) for slice i of a counts workload."""
+    n, k, ell, rng = slice_spec(w, i)
+    p = sinogram(ell, k, n, n, dtype=np.float64)
+    return poisson_counts(p, n, w.photons, rng)
 
 
 def slice_sinogram(w: Workload, i: int, dtype=np.float32):

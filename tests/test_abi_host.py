@@ -115,6 +115,31 @@ def test_invalid_arguments_are_rejected_without_cuda(L):
     assert L.radon_forward_variant(p, dummy_ptr(), ctypes.byref(half), 0, -1, None) == 0
 
 
+def test_pipeline_entry_points_validate_on_the_host(L):
+    """fbp_filter_counts / fbp_hu_coefficients / fbp_backproject_u16 reject
+    bad arguments before any CUDA call."""
+    g = L.fbp_geometry_default(10, 16, 16)
+    p = dummy_ptr()
+    ok = _lib.CPreprocess(None, 1e4, 1.0, 16.0, 1.0)
+    assert L.fbp_filter_counts(p, dummy_ptr(), None, 0, 0, ctypes.byref(g), 1, None, None) == _lib.FBP_ERR_INVALID_ARG
+    for bad in (_lib.CPreprocess(None, 0.0, 1.0, 16.0, 0.0), _lib.CPreprocess(None, 1e4, 0.0, 16.0, 0.0),
+                _lib.CPreprocess(None, 1e4, 1.0, -1.0, 0.0), _lib.CPreprocess(None, 1e4, 1.0, 16.0, 3.9),
+                _lib.CPreprocess(None, 1e4, 1.0, float("nan"), 0.0)):
+        assert L.fbp_filter_counts(p, dummy_ptr(), None, 0, 0, ctypes.byref(g), 1, ctypes.byref(bad), None) == _lib.FBP_ERR_INVALID_ARG
+    assert L.fbp_filter_counts(p, dummy_ptr(), None, 0, 0, ctypes.byref(g), 0, ctypes.byref(ok), None) == 0
+    a, b = ctypes.c_float(), ctypes.c_float()
+    w = _lib.CHuWindow(0.5, 0.0, -1000.0, 3000.0)
+    assert L.fbp_hu_coefficients(ctypes.byref(w), ctypes.byref(a), ctypes.byref(b)) == 0
+    assert a.value == pytest.approx(1000.0 / 0.5 * 65535.0 / 4000.0, rel=1e-7) and b.value == 0.0
+    for bad in (_lib.CHuWindow(0.5, 0.5, -1000.0, 3000.0), _lib.CHuWindow(0.5, 0.0, 5.0, 5.0),
+                _lib.CHuWindow(float("inf"), 0.0, -1000.0, 3000.0)):
+        assert L.fbp_hu_coefficients(ctypes.byref(bad), ctypes.byref(a), ctypes.byref(b)) == _lib.FBP_ERR_INVALID_ARG
+        assert L.fbp_backproject_u16(p, None, 0, dummy_ptr(), ctypes.byref(g), 1, 1.0, ctypes.byref(bad), -1, None) == _lib.FBP_ERR_INVALID_ARG
+    assert L.fbp_hu_coefficients(None, ctypes.byref(a), ctypes.byref(b)) == _lib.FBP_ERR_INVALID_ARG
+    assert L.fbp_backproject_u16(p, None, 0, None, ctypes.byref(g), 1, 1.0, ctypes.byref(w), -1, None) == _lib.FBP_ERR_INVALID_ARG
+    assert L.fbp_backproject_u16(p, None, 0, dummy_ptr(), ctypes.byref(g), 0, 1.0, ctypes.byref(w), -1, None) == 0
+
+
 def test_batched_workspace_query_and_validation(L):
     items = (_lib.CBatchItem * 3)()
     dims = [(720, 512, 512), (1800, 1024, 1024), (3600, 2048, 2048)]
