@@ -209,15 +209,31 @@ struct PreArgs {
     const float *flat;                   // per-bin I0 [D], or null
     float flat_value, floor, mu_scale;
     int r;                               // blur radius, 0 = no blur
-    float taps[2 * kMaxBlurRadius + 1];
+    float taps[2 * kMaxBlurRadius + 1];  // w_{-r..r}
+    float dtaps[2 * kMaxBlurRadius + 2]; // c_m = w_m - w_{m-1}, m in [-r, r+1]
 };
 
+// Blurred line integral at n (the full, untruncated sum); row[kPrePad + m] = p[m],
+// zero for m outside [0, D) within the border.
 __device__ __forceinline__ float blur_at(const float *row, int n, const PreArgs &pre)
 {
-    // row[kPrePad + m] = p[m], zero for m outside [0, D)
     const float *c = row + kPrePad + n;
     float acc = pre.taps[pre.r] * c[0];
     for (int k = 1; k <= pre.r; ++k) acc = fmaf(pre.taps[pre.r + k], c[-k] + c[k], acc);
+    return acc;
+}
+
+// First difference of the blurred row truncated to [0, D): for 0 < n < D it
+// is sum_m c_m p[n - m]; at n = 0 it is the blur at 0, at n = D minus the
+// blur at D - 1, beyond D zero.
+__device__ __forceinline__ float blur_diff(const float *row, int n, int D, const PreArgs &pre)
+{
+    if (n > D) return 0.f;
+    if (n == 0) return blur_at(row, 0, pre);
+    if (n == D) return -blur_at(row, D - 1, pre);
+    const float *c = row + kPrePad + n;
+    float acc = 0.f;
+    for (int m = -pre.r; m <= pre.r + 1; ++m) acc = fmaf(pre.dtaps[m + pre.r], c[-m], acc);
     return acc;
 }
 
@@ -243,37 +259,47 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
     bool nz_a = false, nz_b = false;     // any nonzero (or NaN) sample in the row
     if (pre.on) {
         // stage p for both rows (row stride RS floats, zero borders), then
-        // read blurred values at n = C n1 + t; the buffer is rewritten below
+        // take differences of the blurred rows at n = C n1 + t; the buffer is
+        // rewritten below
         float *st = reinterpret_cast<float *>(S);
         const int RS = D + 2 * kPrePad;
-        for (int i = t; i < 2 * RS; i += C) {
-            const int row = i >= RS, m = i - row * RS - kPrePad;
+        // positions m = t - kPrePad + C i cover [-kPrePad, D + kPrePad) since
+        // D + 2 kPrePad <= L/2 + 32 <= C (R/2 + 1); every load is issued
+        // before any of them is used
+        constexpr int NST = R / 2 + 1;
+#pragma unroll
+        for (int row = 0; row < 2; ++row) {
             const float *src = row ? job.b : job.a;
-            float p = 0.f;
-            if (active && src && m >= 0 && m < D) {
-                const float I0 = pre.flat ? __ldg(pre.flat + m) : pre.flat_value;
-                p = pre.mu_scale * -logf(__fdiv_rn(fmaxf(__ldg(src + m), pre.floor), I0));
+            float *dst = st + row * RS + kPrePad;
+            float x[NST], f0[NST];
+#pragma unroll
+            for (int i = 0; i < NST; ++i) {
+                const int m = t - kPrePad + C * i;
+                const bool in = active && src && m >= 0 && m < D;
+                x[i] = in ? __ldg(src + m) : 0.f;
+                f0[i] = (in && pre.flat) ? __ldg(pre.flat + m) : pre.flat_value;
             }
-            st[i] = p;
+#pragma unroll
+            for (int i = 0; i < NST; ++i) {
+                const int m = t - kPrePad + C * i;
+                if (m < D + kPrePad) {
+                    const bool in = active && src && m >= 0 && m < D;
+                    dst[m] = in ? pre.mu_scale * -logf(__fdiv_rn(fmaxf(x[i], pre.floor), f0[i])) : 0.f;
+                }
+            }
         }
         group_sync(bar_id, C);
 #pragma unroll
         for (int n1 = 0; n1 < R; ++n1) {
             const int n = C * n1 + t;
-            float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
+            float da = 0.f, db = 0.f;
             if (active && C * n1 <= D) {          // uniform over the group
-                a = n < D ? blur_at(st, n, pre) : 0.f;
-                b = (job.b && n < D) ? blur_at(st + RS, n, pre) : 0.f;
-                am = __shfl_up_sync(0xffffffffu, a, 1);
-                bm = __shfl_up_sync(0xffffffffu, b, 1);
-                if (lane == 0) {
-                    am = (n >= 1 && n - 1 < D) ? blur_at(st, n - 1, pre) : 0.f;
-                    bm = (job.b && n >= 1 && n - 1 < D) ? blur_at(st + RS, n - 1, pre) : 0.f;
-                }
-                nz_a |= (a != 0.f);
-                nz_b |= (b != 0.f);
+                da = blur_diff(st, n, D, pre);
+                if (job.b) db = blur_diff(st + RS, n, D, pre);
+                nz_a |= (da != 0.f);
+                nz_b |= (db != 0.f);
             }
-            v[n1] = make_float2(a - am, b - bm);
+            v[n1] = make_float2(da, db);
         }
         group_sync(bar_id, C);                    // staged rows read before S is written
     } else {
@@ -552,6 +578,8 @@ fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s)
         fa.pre.mu_scale = p.mu_scale;
         fa.pre.r = p.blur_radius;
         for (int k = 0; k <= 2 * p.blur_radius; ++k) fa.pre.taps[k] = p.taps[k];
+        for (int m = 0; m <= 2 * p.blur_radius + 1; ++m)     // c_m = w_m - w_{m-1}
+            fa.pre.dtaps[m] = (m <= 2 * p.blur_radius ? p.taps[m] : 0.f) - (m >= 1 ? p.taps[m - 1] : 0.f);
     }
     switch (a.dtype) {
         case FBP_F32: return launch_t<float>(fa, a.L, s);

@@ -495,3 +495,36 @@ def test_forward_tile_replay_matches_oracle(bpw, N, D, K, alpha):
     g = oracle.Geometry(K, D, N, pixel_size=alpha)
     ref = oracle.forward(img, g)
     assert np.max(np.abs(out - ref)) <= 1e-5 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------------------
+# Fused pre-processing (filter.cu, blur_diff): the first difference of the
+# blurred, truncated row as one (2r+2)-tap filter plus the two end cases
+# ---------------------------------------------------------------------------
+@pytest.mark.parametrize("sigma", [0.0, 0.6, 1.0, 2.5, 3.875])
+@pytest.mark.parametrize("D", [1, 2, 7, 64, 301])
+def test_blur_difference_replay(sigma, D):
+    import oracle
+    rng = np.random.default_rng(D)
+    p = rng.standard_normal(D)
+    w = oracle.gaussian_taps(sigma)
+    r = (len(w) - 1) // 2
+    assert r <= 16                                   # kMaxBlurRadius = kPrePad
+    c = np.append(w, 0.0) - np.insert(w, 0, 0.0)     # c_m = w_m - w_{m-1}, m in [-r, r+1]
+    pad = np.zeros(D + 32)
+    pad[16:16 + D] = p
+
+    def blur_at(n):
+        return sum(w[k + r] * pad[16 + n - k] for k in range(-r, r + 1))
+
+    d = np.zeros(D + 1)
+    for n in range(D + 1):
+        if n == 0:
+            d[n] = blur_at(0)
+        elif n == D:
+            d[n] = -blur_at(D - 1)
+        else:
+            d[n] = sum(c[m + r] * pad[16 + n - m] for m in range(-r, r + 2))
+    pb = oracle.gaussian_blur(p, sigma)
+    ref = np.diff(np.concatenate([[0.0], pb, [0.0]]))
+    np.testing.assert_allclose(d, ref, atol=1e-12)
