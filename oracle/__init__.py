@@ -341,3 +341,53 @@ def hu_codes_f32(mu32, a32, b32) -> np.ndarray:
     t = np.float32(a32) * mu32
     t = (t + np.float32(b32)).astype(np.float32)
     return np.clip(np.rint(t), 0, 65535).astype(np.uint16)
+
+
+# ---------------------------------------------------------------------------
+# Offset scans (Sec. V-A(b): the sample is shifted laterally so that a 360
+# degree scan covers a field of view wider than the detector).  A ray (th, s)
+# and (th + pi, -s) are the same line, so near the rotation axis every line
+# is measured twice and far out on the long side once.  Each row is weighted
+# before filtering by a smooth overlap weight (the paper gives none):
+#   t = +-s (positive towards the long side), Delta = overlap half-width,
+#   w = 0 (t < -Delta), sin^2(pi/4 (1 + t/Delta)) (|t| <= Delta), 1 (t > Delta),
+# so that w(t) + w(-t) = 1 and every line counts once.  The ramp filter
+# spreads a weighted row beyond the detector's short edge, so rows are
+# filtered and backprojected on a virtual detector centred on the axis that
+# spans the long side twice (the physical bins embedded, zeros elsewhere);
+# the backprojection runs over [0, 2 pi) with scale 2 pi / K.
+# ---------------------------------------------------------------------------
+def offset_weight(t, overlap: float) -> np.ndarray:
+    """w(t) for signed distances t (bins) from the axis, positive towards the long side."""
+    t = _f64(t)
+    w = np.where(t > overlap, 1.0, 0.0)
+    mid = np.abs(t) <= overlap
+    w[mid] = np.sin(0.25 * np.pi * (1.0 + t[mid] / overlap)) ** 2
+    return w
+
+
+def offset_virtual(n_det: int, det_center: float, overlap: float):
+    """Virtual detector of an offset scan: (n_virtual, centre, offset, weights)
+    with physical bin j at virtual bin j + offset and the weights per
+    virtual bin.  2 * det_center must be an integer."""
+    long_positive = (n_det - 1 - det_center) >= det_center
+    half = (n_det - 1 - det_center) if long_positive else det_center
+    n_v = int(round(2 * half)) + 1
+    c_v = 0.5 * (n_v - 1)
+    offset = int(round(c_v - det_center)) if long_positive else 0
+    s = np.arange(n_v) - c_v
+    w = offset_weight(s if long_positive else -s, overlap)
+    return n_v, c_v, offset, w
+
+
+def embed_rows(p, n_virtual: int, offset: int) -> np.ndarray:
+    """Rows of physical bins placed at virtual bins [offset, offset + D)."""
+    p = _f64(p)
+    out = np.zeros(p.shape[:-1] + (n_virtual,))
+    out[..., offset:offset + p.shape[-1]] = p
+    return out
+
+
+def fbp_weighted(p, g: Geometry, weights, kind: int = RAMLAK) -> np.ndarray:
+    """FBP of rows weighted per bin before filtering (scale = angle_step)."""
+    return fbp(_f64(p) * _f64(weights)[None, :], g, kind)
