@@ -391,3 +391,22 @@ def embed_rows(p, n_virtual: int, offset: int) -> np.ndarray:
 def fbp_weighted(p, g: Geometry, weights, kind: int = RAMLAK) -> np.ndarray:
     """FBP of rows weighted per bin before filtering (scale = angle_step)."""
     return fbp(_f64(p) * _f64(weights)[None, :], g, kind)
+
+
+def offset_fold(pv, weights) -> np.ndarray:
+    """Fold the weighted virtual rows of a full turn into half-turn rows.
+
+    With K even and angles th_k = th_0 + 2 pi k / K, th_{k + K/2} = th_k + pi,
+    and the line (th + pi, s) is the line (th, -s): on the centred virtual
+    detector the row at th_k + pi, read at the mirrored bin n_v - 1 - i,
+    measures the line that bin i of the row at th_k measures.  So
+        r_k[i] = w[i] p_k[i] + w[n_v - 1 - i] p_{k + K/2}[n_v - 1 - i],  k < K/2,
+    and the FBP of r over th_k, k < K/2 (step 2 pi / K = pi / (K/2), a half
+    turn) equals the weighted full-turn FBP: the ramp kernel is even, so
+    filtering commutes with the mirror, and so does linear interpolation."""
+    pv = _f64(pv)
+    w = _f64(weights)
+    K = pv.shape[-2]
+    if K % 2:
+        raise ValueError("the fold needs an even number of angles")
+    return pv[..., :K // 2, :] * w + (pv[..., K // 2:, :] * w)[..., ::-1]

@@ -80,3 +80,40 @@ def test_offset_scan_equals_the_half_circle_fbp_on_the_virtual_detector():
     f_phys = oracle.fbp_weighted(p_off, oracle.Geometry(K, D, N, angle_step=2 * math.pi / K, det_center=c),
                                  oracle.offset_weight(np.arange(D) - c, delta))
     assert np.abs(f_phys - f_ref)[inside].mean() > 0.01 * dr
+
+
+def test_offset_fold_of_analytic_rows_is_the_half_turn_sinogram():
+    """Noise-free: the folded rows of a full-turn offset scan are the
+    analytic half-turn sinogram of the centred virtual detector (each line's
+    two weights sum to 1 and both samples are the same line integral)."""
+    N = 96
+    D, c, delta = 60, 12.5, 9.0                   # FoV radius 46.5
+    K = 200
+    ell = phantoms.random_ellipses(phantoms.rng_for(17), count_range=(5, 8))
+    p_off = phantoms.sinogram(ell, K, D, N, angle_step=2 * math.pi / K, det_center=c, dtype=np.float64)
+    n_v, c_v, off, w = oracle.offset_virtual(D, c, delta)
+    assert n_v == 94 and off == 34
+    r = oracle.offset_fold(oracle.embed_rows(p_off, n_v, off), w)
+    assert r.shape == (K // 2, n_v)
+    ref = phantoms.sinogram(ell, K // 2, n_v, N, dtype=np.float64)
+    np.testing.assert_allclose(r, ref, atol=1e-10 * np.abs(ref).max())
+    # a wrong mirror (no reversal) or one weight for both halves fails
+    bad = oracle.embed_rows(p_off, n_v, off)[:K // 2] * w + oracle.embed_rows(p_off, n_v, off)[K // 2:] * w
+    assert np.abs(bad - ref).max() > 1e-2 * np.abs(ref).max()
+
+
+def test_offset_fold_then_half_turn_fbp_equals_the_full_turn_fbp():
+    N = 128
+    D, c, delta = 80, 15.5, 12.0
+    K = 240
+    ell = phantoms.random_ellipses(phantoms.rng_for(21), count_range=(6, 10))
+    p_off = phantoms.sinogram(ell, K, D, N, angle_step=2 * math.pi / K, det_center=c, dtype=np.float64)
+    n_v, c_v, off, w = oracle.offset_virtual(D, c, delta)
+    pv = oracle.embed_rows(p_off, n_v, off)
+    f360 = oracle.fbp_weighted(pv, oracle.Geometry(K, n_v, N, angle_step=2 * math.pi / K), w,
+                               oracle.SHEPP_LOGAN)
+    f180 = oracle.fbp(oracle.offset_fold(pv, w), oracle.Geometry(K // 2, n_v, N, angle_step=2 * math.pi / K),
+                      oracle.SHEPP_LOGAN)
+    np.testing.assert_allclose(f180, f360, atol=1e-10 * np.abs(f360).max())
+    with pytest.raises(ValueError):
+        oracle.offset_fold(pv[:-1], w)
