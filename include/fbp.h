@@ -233,6 +233,64 @@ fbp_status fbp_backproject_u16(const void *filt, const float *row_scale, fbp_dty
                                fbp_stream_t stream);
 
 /*
+ * Offset scans (Sec. V-A(b), "Addressing Load Imbalance in XCT Offset
+ * Scans": the sample is shifted laterally so that a full-turn scan images a
+ * field of view wider than the detector).  The rotation axis sits at
+ * det_center, off the detector's centre, and the angles cover a full turn
+ * (n_angles * angle_step = 2 pi).  A line (th + pi, -s) is the line (th, s),
+ * so lines within `overlap` bins of the axis are measured twice and lines
+ * farther out on the long side once.  The paper gives no weighting; this
+ * library weights each sample before filtering with the smooth overlap
+ * weight w(t) = (1 + sin(pi t / (2 overlap))) / 2 for |t| <= overlap, 0 for
+ * t < -overlap and 1 for t > overlap, t the signed distance (bins) of the
+ * sample's line from the axis, positive towards the long side; w(t) + w(-t)
+ * = 1, so every line counts once.  The ramp filter spreads a weighted row
+ * past the detector's short edge, so rows are filtered on a virtual detector
+ * centred on the axis that spans the long side on both sides:
+ *   n_v = 2 * (long side length) + 1 bins (long side = max(c, D-1-c) for
+ *   c = det_center), centre (n_v - 1) / 2, physical bin m at virtual bin
+ *   m + offset (offset = n_v - D when the long side is above c, else 0).
+ */
+typedef struct {
+    double overlap;   /* half-width of the overlap weight, bins, 0 < overlap <=
+                         the short side min(c, D-1-c)                        */
+    int fold;         /* 1: fold the row at th + pi into the row at th (its
+                         mirror, weight 1 - w), giving K/2 half-turn rows; K must
+                         be even.  0: K weighted full-turn rows               */
+} fbp_offset_scan;
+
+/*
+ * fbp_offset_geometry -- the geometry of the rows fbp_filter_offset writes,
+ * for fbp_backproject: n_angles = K/2 (fold) or K, n_det = n_v,
+ * det_center = (n_v - 1)/2; angle_start, angle_step, det_spacing,
+ * pixel_size and n as in g.  Backproject with scale = angle_step: the
+ * weights make each line count once over the full turn.  *offset (may be
+ * NULL) receives the virtual index of physical bin 0.  Host-only, no CUDA
+ * call.  FBP_ERR_INVALID_ARG for a NULL g/o/gv, an invalid geometry, a
+ * det_center outside [0, D-1] or not a multiple of 1/2, overlap outside
+ * (0, short side], angles not covering a full turn (|K angle_step - 2 pi| >
+ * 1e-9 2 pi), or fold with K odd; FBP_ERR_UNSUPPORTED if n_v > 8192.
+ */
+fbp_status fbp_offset_geometry(const fbp_geometry *g, const fbp_offset_scan *o,
+                               fbp_geometry *gv, int *offset);
+
+/*
+ * fbp_filter_offset -- fbp_filter for an offset scan: each physical row is
+ * weighted, embedded in the virtual detector (zero elsewhere), folded when
+ * o->fold is set, and filtered on the virtual detector, in one pass.
+ *   sino   device, float [n_slices][K][D]: line integrals of the physical
+ *          detector (g is the scan's geometry, full turn).
+ *   filt   device, [n_slices][K'][n_v] of `dtype`, K' = K/2 (fold) or K:
+ *          the filtered virtual rows, for fbp_backproject with the geometry
+ *          from fbp_offset_geometry.  May not alias sino.
+ *   row_scale  device, float [n_slices][K'] for F16/BF16 (as fbp_filter).
+ * Errors: fbp_offset_geometry's, then fbp_filter's.
+ */
+fbp_status fbp_filter_offset(const float *sino, void *filt, float *row_scale, fbp_dtype dtype,
+                             fbp_filter_kind kind, const fbp_geometry *g, int n_slices,
+                             const fbp_offset_scan *o, fbp_stream_t stream);
+
+/*
  * fbp_backproject_noalloc -- fbp_backproject for callers that cannot
  * allocate device memory.  The paper has no counterpart: this is a library
  * service, not a step of the method.

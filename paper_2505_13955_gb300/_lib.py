@@ -72,6 +72,10 @@ class CHuWindow(ctypes.Structure):
     ]
 
 
+class COffsetScan(ctypes.Structure):
+    _fields_ = [("overlap", ctypes.c_double), ("fold", ctypes.c_int)]
+
+
 SIGNATURES = {
     "fbp_version": (ctypes.c_int, []),
     "fbp_geometry_default": (CGeometry, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
@@ -80,6 +84,10 @@ SIGNATURES = {
     "fbp_filter": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _G, ctypes.c_int, _vp]),
     "fbp_filter_counts": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _G, ctypes.c_int,
                                          ctypes.POINTER(CPreprocess), _vp]),
+    "fbp_offset_geometry": (ctypes.c_int, [_G, ctypes.POINTER(COffsetScan), _G,
+                                           ctypes.POINTER(ctypes.c_int)]),
+    "fbp_filter_offset": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int, ctypes.c_int, _G, ctypes.c_int,
+                                         ctypes.POINTER(COffsetScan), _vp]),
     "fbp_hu_coefficients": (ctypes.c_int, [ctypes.POINTER(CHuWindow), ctypes.POINTER(ctypes.c_float),
                                            ctypes.POINTER(ctypes.c_float)]),
     "fbp_backproject_u16": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int, ctypes.c_float,

@@ -9,6 +9,7 @@ of the stated dtypes; results are enqueued on the current torch stream.
   radon_forward(img, g)      -> radon_forward    (K3, matched forward projector)
   fbp(sino, g)               -> fbp_filter + fbp_backproject
   fbp_batched(sinos, gs)     -> fbp_batched      (ragged batch, persistent launch)
+  filter_offset(sino, g, ..) -> fbp_filter_offset (full-turn offset scans)
 """
 from __future__ import annotations
 
@@ -215,6 +216,51 @@ def fbp_counts(counts: torch.Tensor, g: Geometry, pre: Preprocess, window: HuWin
     if window is None:
         return backproject(filt, g, row_scale=rs, variant=variant)
     return backproject_u16(filt, g, window, row_scale=rs, variant=variant)
+
+
+def offset_geometry(g: Geometry, overlap: float, fold: bool = True, which: str = "default"):
+    """fbp_offset_geometry: (virtual geometry of the filtered rows, virtual
+    index of physical bin 0) for a full-turn offset scan with geometry g."""
+    L = lib(which)
+    gc, oc, gv = g.c(), _lib.COffsetScan(float(overlap), int(bool(fold))), _lib.CGeometry()
+    off = ctypes.c_int(0)
+    _lib.check(L.fbp_offset_geometry(ctypes.byref(gc), ctypes.byref(oc), ctypes.byref(gv),
+                                     ctypes.byref(off)), L, "fbp_offset_geometry")
+    return Geometry(gv.n_angles, gv.n_det, gv.n, gv.angle_start, gv.angle_step, gv.det_center,
+                    gv.det_spacing, gv.pixel_size), int(off.value)
+
+
+def filter_offset(sino: torch.Tensor, g: Geometry, overlap: float, fold: bool = True, kind="ramlak",
+                  dtype=torch.float32, out: torch.Tensor | None = None,
+                  row_scale: torch.Tensor | None = None, which: str = "default"):
+    """fbp_filter_offset: weight, embed (and fold) the rows of a full-turn
+    offset scan and filter them on the virtual detector.  Returns
+    (filt, row_scale or None, virtual geometry)."""
+    _need(sino, "sino", torch.float32)
+    S = _slices(sino, (g.n_angles, g.n_det), "sino")
+    gv, _ = offset_geometry(g, overlap, fold, which)
+    shape = (gv.n_angles, gv.n_det) if sino.dim() == 2 else (S, gv.n_angles, gv.n_det)
+    if out is None:
+        out = torch.empty(shape, dtype=dtype, device=sino.device)
+    _need(out, "out", dtype)
+    if tuple(out.shape) != shape:
+        raise ValueError(f"out has shape {tuple(out.shape)}, expected {shape}")
+    if dtype != torch.float32 and row_scale is None:
+        row_scale = torch.empty(shape[:-1], dtype=torch.float32, device=sino.device)
+    L = lib(which)
+    gc, oc = g.c(), _lib.COffsetScan(float(overlap), int(bool(fold)))
+    st = L.fbp_filter_offset(_ptr(sino), _ptr(out), _ptr(row_scale), _DTYPES[dtype], kind_id(kind),
+                             ctypes.byref(gc), S, ctypes.byref(oc), _stream(sino.device))
+    _lib.check(st, L, "fbp_filter_offset")
+    return out, (row_scale if dtype != torch.float32 else None), gv
+
+
+def fbp_offset(sino: torch.Tensor, g: Geometry, overlap: float, fold: bool = True, kind="ramlak",
+               dtype=torch.float32, out: torch.Tensor | None = None, variant: int = -1):
+    """FBP of a full-turn offset scan: fbp_filter_offset, then fbp_backproject
+    on the virtual geometry with scale = angle_step."""
+    filt, rs, gv = filter_offset(sino, g, overlap, fold, kind=kind, dtype=dtype)
+    return backproject(filt, gv, row_scale=rs, out=out, variant=variant)
 
 
 def backproject(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None = None,

@@ -159,6 +159,99 @@ fbp_status fbp_filter_counts(const float *counts, void *filt, float *row_scale, 
     });
 }
 
+// Virtual detector of an offset scan (fbp.h, fbp_offset_geometry).
+static fbp_status offset_virtual(const fbp_geometry *g, const fbp_offset_scan *o, fbp_geometry *gv,
+                                 FilterOffset *fo)
+{
+    if (!g || !o || !gv) return fail(FBP_ERR_INVALID_ARG, "g, o or gv is NULL");
+    fbp_status st = check_geometry(g, false, false);
+    if (st != FBP_OK) return st;
+    const double pi = 3.14159265358979323846;
+    const int D = g->n_det, K = g->n_angles;
+    const double c = g->det_center;
+    if (!(c >= 0.0 && c <= D - 1.0) || std::fabs(2.0 * c - std::rint(2.0 * c)) > 1e-9)
+        return fail(FBP_ERR_INVALID_ARG, "offset scan needs det_center in [0, D-1], a multiple of 1/2");
+    if (std::fabs((double)K * g->angle_step - 2.0 * pi) > 1e-9 * 2.0 * pi)
+        return fail(FBP_ERR_INVALID_ARG, "offset scan needs a full turn: n_angles * angle_step = 2 pi");
+    if (o->fold != 0 && o->fold != 1) return fail(FBP_ERR_INVALID_ARG, "fold must be 0 or 1");
+    if (o->fold && K % 2) return fail(FBP_ERR_INVALID_ARG, "fold needs an even number of angles");
+    const bool long_pos = (D - 1 - c) >= c;
+    const double long_side = long_pos ? D - 1 - c : c, short_side = long_pos ? c : D - 1 - c;
+    if (!(o->overlap > 0.0 && o->overlap <= short_side + 1e-12))
+        return fail(FBP_ERR_INVALID_ARG, "overlap %g outside (0, %g]", o->overlap, short_side);
+    const long long nv = (long long)std::llround(2.0 * long_side) + 1;
+    if (nv > 8192) return fail(FBP_ERR_UNSUPPORTED, "virtual detector of %lld bins > 8192", nv);
+    const double cv = 0.5 * (double)(nv - 1);
+    const int off = long_pos ? (int)std::llround(cv - c) : 0;
+    *gv = *g;
+    gv->n_angles = o->fold ? K / 2 : K;
+    gv->n_det = (int)nv;
+    gv->det_center = cv;
+    if (fo) {
+        fo->Dp = D;
+        fo->off = off;
+        fo->fold = o->fold;
+        fo->K_in = K;
+        fo->cv = (float)cv;
+        fo->sgn = long_pos ? 1.f : -1.f;
+        fo->inv_delta = (float)(1.0 / o->overlap);
+    }
+    return FBP_OK;
+}
+
+fbp_status fbp_offset_geometry(const fbp_geometry *g, const fbp_offset_scan *o, fbp_geometry *gv,
+                               int *offset)
+{
+    return guarded([&]() -> fbp_status {
+        FilterOffset fo;
+        fbp_status st = offset_virtual(g, o, gv, &fo);
+        if (st == FBP_OK && offset) *offset = fo.off;
+        return st;
+    });
+}
+
+fbp_status fbp_filter_offset(const float *sino, void *filt, float *row_scale, fbp_dtype dtype,
+                             fbp_filter_kind kind, const fbp_geometry *g, int n_slices,
+                             const fbp_offset_scan *o, fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        fbp_geometry gv;
+        FilterOffset fo;
+        fbp_status st = offset_virtual(g, o, &gv, &fo);
+        if (st != FBP_OK) return st;
+        st = check_geometry(&gv, true, false);
+        if (st != FBP_OK) return st;
+        if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
+        if (!kind_ok(kind)) return fail(FBP_ERR_INVALID_ARG, "filter kind %d", (int)kind);
+        if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
+        if (n_slices == 0) return FBP_OK;
+        if (!sino || !filt) return fail(FBP_ERR_INVALID_ARG, "sino or filt is NULL");
+        if (dtype != FBP_F32 && !row_scale)
+            return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit output");
+        const long long rows = (long long)n_slices * gv.n_angles;
+        const size_t nin = (size_t)n_slices * g->n_angles * g->n_det * 4;
+        const size_t nout = (size_t)rows * gv.n_det * dtype_size(dtype);
+        if (overlap(sino, nin, filt, nout)) return fail(FBP_ERR_INVALID_ARG, "filt overlaps sino");
+        const float2 *G = nullptr;
+        const float2 *tw = nullptr;
+        int L = 0;
+        st = filter_tables(gv.n_det, kind, gv.det_spacing, stream, &G, &tw, &L);
+        if (st != FBP_OK) return st;
+        FilterLaunch a;
+        a.sino = sino;
+        a.filt = filt;
+        a.row_scale = dtype == FBP_F32 ? nullptr : row_scale;
+        a.rows = rows;
+        a.D = gv.n_det;
+        a.L = L;
+        a.G = G;
+        a.tw = tw;
+        a.dtype = dtype;
+        a.offset = &fo;
+        return launch_filter(a, stream);
+    });
+}
+
 static fbp_status backproject_impl(const void *filt, const float *row_scale, fbp_dtype dtype,
                                    float *slice, unsigned short *slice16, float hu_a, float hu_b,
                                    const fbp_geometry *g, int n_slices, float scale,

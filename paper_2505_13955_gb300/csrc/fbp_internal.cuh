@@ -92,6 +92,15 @@ struct FilterPre {
     float taps[33];
 };
 
+// Offset scans: rows of Dp physical bins weighted and embedded in the
+// transform's virtual detector (physical bin m at virtual bin m + off),
+// optionally folded with the row half a turn later (see filter.cu).
+struct FilterOffset {
+    int Dp, off, fold;
+    long long K_in;        // physical rows per slice (even with fold)
+    float cv, sgn, inv_delta;
+};
+
 struct FilterLaunch {
     const float *sino;     // [rows][D] line integrals, or counts when pre is set
     void *filt;            // [rows][D] of dtype
@@ -102,6 +111,7 @@ struct FilterLaunch {
     const float2 *tw;
     fbp_dtype dtype;
     const FilterPre *pre = nullptr;
+    const FilterOffset *offset = nullptr;   // rows = output rows; sino is [S][K_in][Dp]
 };
 fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s);
 

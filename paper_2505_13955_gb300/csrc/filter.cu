@@ -103,8 +103,9 @@ __device__ __forceinline__ void lane_dit_inv(float2 (&v)[NV], int lane, const fl
 }
 
 struct RowPairJob {
-    const float *a;       // first row (length D)
+    const float *a;       // first row (length D; the physical row in offset mode)
     const float *b;       // second row or nullptr
+    const float *a2, *b2; // offset mode with fold: the rows half a turn later
     void *qa, *qb;        // outputs (dtype), qb may be nullptr
     float *sa, *sb;       // row scales (16-bit dtypes) or nullptr
 };
@@ -237,6 +238,48 @@ __device__ __forceinline__ float blur_diff(const float *row, int n, int D, const
     return acc;
 }
 
+// Offset scans (Sec. V-A(b): the sample is shifted laterally and turned a
+// full circle, so the detector covers one side of a wider field of view).
+// The transform runs on a virtual detector of D bins centred on the axis;
+// physical bin m sits at virtual bin m + off.  Each virtual sample is
+// weighted by the smooth overlap weight w(t) = (1 + sin(pi t / (2 Delta))) / 2
+// on |t| <= Delta (0 below, 1 above), t = sgn (n - cv) the signed distance
+// from the axis towards the long side, so w(t) + w(-t) = 1 and each line
+// counts once.  With fold, the row half a turn later is added at the
+// mirrored bin D - 1 - n with weight 1 - w: the line (th + pi, -s) is the
+// line (th, s), so one half-turn row carries both measurements.
+struct OffArgs {
+    int on;                // 0: the rows are the transform's rows
+    int Dp;                // physical bins per row
+    int off;               // virtual index of physical bin 0
+    int fold;              // 1: add the mirrored row half a turn later
+    long long K_in, K_out; // rows per slice read and written (K_out = K_in / 2 with fold)
+    float cv, sgn, inv_delta;
+};
+
+__device__ __forceinline__ float overlap_weight(int n, const OffArgs &o)
+{
+    const float x = o.sgn * ((float)n - o.cv) * o.inv_delta;
+    if (x >= 1.f) return 1.f;
+    if (x <= -1.f) return 0.f;
+    return 0.5f + 0.5f * sinpif(0.5f * x);
+}
+
+// Weighted (and folded) virtual sample n of one row, zero outside [0, D).
+__device__ __forceinline__ float offset_sample(const float *p, const float *p2, int n, int D,
+                                              const OffArgs &o)
+{
+    if (!p || n < 0 || n >= D) return 0.f;
+    const float w = overlap_weight(n, o);
+    const int m = n - o.off;
+    float v = (m >= 0 && m < o.Dp) ? w * __ldg(p + m) : 0.f;
+    if (o.fold) {
+        const int m2 = D - 1 - n - o.off;
+        if (m2 >= 0 && m2 < o.Dp) v = fmaf(1.f - w, __ldg(p2 + m2), v);
+    }
+    return v;
+}
+
 // One row pair by one group of C threads (t = thread index in the group).
 // S: the group's R x C complex buffer; red: 4 * C/32 floats of the group;
 // bar_id: the group's named barrier.
@@ -244,7 +287,7 @@ template <int L, typename T>
 __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int D,
                                          const float2 *__restrict__ Gs,
                                          const float2 *__restrict__ tw, float2 *S, float *red,
-                                         int t, int bar_id, const PreArgs &pre)
+                                         int t, int bar_id, const PreArgs &pre, const OffArgs &off)
 {
     constexpr int R = fft_R(L), VPL = fft_VPL(L);
     constexpr int C = 32 * VPL;
@@ -308,13 +351,23 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
             const int n = C * n1 + t;
             float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
             if (active && C * n1 <= D) {          // uniform over the group
-                a = n < D ? __ldg(job.a + n) : 0.f;
-                b = (job.b && n < D) ? __ldg(job.b + n) : 0.f;
+                if (off.on) {
+                    a = offset_sample(job.a, job.a2, n, D, off);
+                    b = offset_sample(job.b, job.b2, n, D, off);
+                } else {
+                    a = n < D ? __ldg(job.a + n) : 0.f;
+                    b = (job.b && n < D) ? __ldg(job.b + n) : 0.f;
+                }
                 am = __shfl_up_sync(0xffffffffu, a, 1);
                 bm = __shfl_up_sync(0xffffffffu, b, 1);
                 if (lane == 0) {
-                    am = (n >= 1 && n - 1 < D) ? __ldg(job.a + n - 1) : 0.f;
-                    bm = (job.b && n >= 1 && n - 1 < D) ? __ldg(job.b + n - 1) : 0.f;
+                    if (off.on) {
+                        am = offset_sample(job.a, job.a2, n - 1, D, off);
+                        bm = offset_sample(job.b, job.b2, n - 1, D, off);
+                    } else {
+                        am = (n >= 1 && n - 1 < D) ? __ldg(job.a + n - 1) : 0.f;
+                        bm = (job.b && n >= 1 && n - 1 < D) ? __ldg(job.b + n - 1) : 0.f;
+                    }
                 }
                 nz_a |= (a != 0.f);
                 nz_b |= (b != 0.f);
@@ -438,6 +491,7 @@ struct FilterArgs {
     const float2 *G;
     const float2 *tw;
     PreArgs pre;
+    OffArgs off;
 };
 
 __device__ __forceinline__ RowPairJob make_job(const float *sino, void *filt, float *row_scale,
@@ -450,11 +504,34 @@ __device__ __forceinline__ RowPairJob make_job(const float *sino, void *filt, fl
     const bool has_b = active && rb < rows;
     job.a = active ? sino + ra * D : nullptr;
     job.b = has_b ? sino + rb * D : nullptr;
+    job.a2 = job.b2 = nullptr;
     job.qa = active ? static_cast<char *>(filt) + ra * D * esz : nullptr;
     job.qb = has_b ? static_cast<char *>(filt) + rb * D * esz : nullptr;
     job.sa = (active && row_scale) ? row_scale + ra : nullptr;
     job.sb = (has_b && row_scale) ? row_scale + rb : nullptr;
     return job;
+}
+
+// Offset mode: output row r of slice s = r / K_out, angle k = r % K_out reads
+// physical row s K_in + k (and, with fold, s K_in + k + K_in / 2).
+__device__ __forceinline__ void offset_inputs(RowPairJob &job, const float *sino, long long rows,
+                                              long long pair, const OffArgs &o)
+{
+    const long long r[2] = {2 * pair, 2 * pair + 1};
+    const float *in[2] = {nullptr, nullptr}, *in2[2] = {nullptr, nullptr};
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+        if (r[i] < rows) {
+            const long long s = r[i] / o.K_out, k = r[i] - s * o.K_out;
+            const long long src = s * o.K_in + k;
+            in[i] = sino + src * o.Dp;
+            in2[i] = o.fold ? sino + (src + o.K_in / 2) * o.Dp : nullptr;
+        }
+    }
+    job.a = job.a ? in[0] : nullptr;
+    job.b = job.b ? in[1] : nullptr;
+    job.a2 = job.a ? in2[0] : nullptr;
+    job.b2 = job.b ? in2[1] : nullptr;
 }
 
 template <int L, typename T>
@@ -467,8 +544,9 @@ __global__ void __launch_bounds__(kFilterThreads) filter_kernel(FilterArgs a)
     const int g = threadIdx.x / C, t = threadIdx.x % C;
     const long long pair = (long long)blockIdx.x * GP + g;
     bool active;
-    const RowPairJob job = make_job(a.sino, a.filt, a.row_scale, a.rows, a.D, pair, sizeof(T), active);
-    fft_pair<L, T>(job, active, a.D, a.G, a.tw, smem_f2 + (size_t)g * L, red[g], t, 1 + g, a.pre);
+    RowPairJob job = make_job(a.sino, a.filt, a.row_scale, a.rows, a.D, pair, sizeof(T), active);
+    if (a.off.on) offset_inputs(job, a.sino, a.rows, pair, a.off);
+    fft_pair<L, T>(job, active, a.D, a.G, a.tw, smem_f2 + (size_t)g * L, red[g], t, 1 + g, a.pre, a.off);
 }
 
 template <int L, typename T>
@@ -527,13 +605,15 @@ __global__ void __launch_bounds__(kFilterThreads) filter_batched_kernel(FilterBa
     PreArgs pre;
     pre.on = 0;
     pre.r = 0;
+    OffArgs off;
+    off.on = 0;
     switch (it.L) {
-        case 512: fft_pair<512, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
-        case 1024: fft_pair<1024, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
-        case 2048: fft_pair<2048, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
-        case 4096: fft_pair<4096, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
-        case 8192: fft_pair<8192, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
-        default: fft_pair<16384, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre); break;
+        case 512: fft_pair<512, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre, off); break;
+        case 1024: fft_pair<1024, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre, off); break;
+        case 2048: fft_pair<2048, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre, off); break;
+        case 4096: fft_pair<4096, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre, off); break;
+        case 8192: fft_pair<8192, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre, off); break;
+        default: fft_pair<16384, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre, off); break;
     }
 }
 
@@ -567,6 +647,20 @@ fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s)
     fa.tw = a.tw;
     fa.pre.on = 0;
     fa.pre.r = 0;
+    fa.off.on = 0;
+    if (a.offset) {
+        const FilterOffset &o = *a.offset;
+        if (a.pre) return fail(FBP_ERR_UNSUPPORTED, "offset rows from counts");
+        fa.off.on = 1;
+        fa.off.Dp = o.Dp;
+        fa.off.off = o.off;
+        fa.off.fold = o.fold;
+        fa.off.K_in = o.K_in;
+        fa.off.K_out = o.fold ? o.K_in / 2 : o.K_in;
+        fa.off.cv = o.cv;
+        fa.off.sgn = o.sgn;
+        fa.off.inv_delta = o.inv_delta;
+    }
     if (a.pre) {
         const FilterPre &p = *a.pre;
         if (p.blur_radius < 0 || p.blur_radius > kMaxBlurRadius)

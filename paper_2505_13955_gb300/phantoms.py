@@ -17,7 +17,8 @@ Conventions (pixel units, pixel size 1):
   * ellipse parameters live on the unit disk; radius 1 <-> N/2 pixels;
   * pixel [r][c] is centred at X = c - (N-1)/2, Y = r - (N-1)/2;
   * bin j is centred at s_j = j - det_center; det_center defaults to (D-1)/2;
-  * angles theta_k = k * pi / K on [0, pi);
+  * angles theta_k = k * pi / K on [0, pi) (a full turn, 2 pi k / K, for
+    offset scans);
   * a sinogram value is the line integral in density x pixels.
 """
 from __future__ import annotations
@@ -217,6 +218,7 @@ class Workload:
     n_choices: tuple = field(default_factory=tuple)
     k_choices: tuple = field(default_factory=tuple)
     counts: bool = False        # inputs are raw detector counts (stage-2 pre-processing on)
+    offset: tuple | None = None  # full-turn offset scan: (n_det, det_center, overlap in bins)
 
 
 # Parameters of the counts-to-codes workload (the paper leaves the blur width
@@ -235,6 +237,11 @@ WORKLOADS = {
     "gd_refine_n1024": Workload("gd_refine_n1024", 16, 1024, 1800, "ramlak", "random", 1e4, 5),
     "fbp_pipeline_n8192": Workload("fbp_pipeline_n8192", 16, 8192, 4096, "ramlak", "random", 1e4, 6,
                                    counts=True),
+    # offset scan (Sec. V-A(b)): 8192 angles over a full turn, a 4608-bin
+    # detector with the axis at bin 511.5, so it covers the 8192-pixel field
+    # of view's long side (radius 4095.5) and overlaps the axis by 512 bins
+    "fbp_offset_n8192": Workload("fbp_offset_n8192", 16, 8192, 8192, "ramlak", "random", None, 7,
+                                 offset=(4608, 511.5, 256.0)),
 }
 
 
@@ -262,8 +269,12 @@ def slice_counts(w: Workload, i: int) -> np.ndarray:
 
 
 def slice_sinogram(w: Workload, i: int, dtype=np.float32):
-    """Sinogram [K, N] for slice i of workload w, with the workload's noise."""
+    """Sinogram [K, N] for slice i of workload w, with the workload's noise
+    (an offset workload: [K, n_det] over a full turn, axis at det_center)."""
     n, k, ell, rng = slice_spec(w, i)
+    if w.offset is not None:
+        d, c, _ = w.offset
+        return sinogram(ell, k, d, n, angle_step=2.0 * np.pi / k, det_center=c, dtype=dtype)
     if w.photons is None:
         return sinogram(ell, k, n, n, dtype=dtype)
     p = sinogram(ell, k, n, n, dtype=np.float64)
