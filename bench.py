@@ -14,7 +14,9 @@ launch replayed from a CUDA graph, against per-slice launches), and
 gd_refine_n1024 (gradient-descent least squares, 16 slices, N = 1024,
 K = 1800; a step is one iteration, A and A^T), fbp_pipeline_n8192 (detector
 counts to uint16 CT-number codes) and fbp_offset_n8192 (full-turn offset
-scans, 16 slices, 8192 angles, a 4608-bin detector off the axis).
+scans, 16 slices, 8192 angles, a 4608-bin detector off the axis) and
+fbp_mixed_batch (200 normal and offset scans in one persistent launch, work
+queue against the paper's group-and-cyclic order).
 
 Timing: W >= 3 untimed warm-up steps, then exactly K steps bracketed by a
 barrier and torch.cuda.synchronize(), timed with CUDA events on the
@@ -738,6 +740,90 @@ def run_ragged(args) -> None:
     finish(line, ws, rank)
 
 
+def run_mixed(args) -> None:
+    """Normal and offset scans reconstructed together (Sec. V-A(b)): all
+    items in one fbp_batched_scans call (one filter launch + one persistent
+    backprojection launch), captured in a CUDA graph and replayed, once with
+    the atomic work queue and once with the paper's group-and-cyclic order;
+    per-scan launches of the same items are timed in the same run.  Updates
+    are counted once per line (N^2 K for a normal item, N^2 K/2 for an
+    offset item of K full-turn angles)."""
+    import torch
+    from paper_2505_13955_gb300 import api, phantoms
+
+    ws, rank, dev = init_device()
+    w = phantoms.WORKLOADS["fbp_mixed_batch"]
+    S = args.slices or w.n_slices
+    idx = shard_slices(S, rank)
+    sinos, scans = [], []
+    for i in idx:
+        sp = phantoms.scan_spec(w, i)
+        g = api.Geometry(sp["n_angles"], sp["n_det"], sp["n"], angle_step=sp["angle_step"],
+                         det_center=sp["det_center"])
+        sinos.append(torch.from_numpy(phantoms.scan_sinogram(sp)).to(dev))
+        scans.append(api.Scan(g, sp["overlap"], True))
+    rows_geoms = [api.offset_geometry(sc.g, sc.overlap, sc.fold)[0] if sc.overlap else sc.g for sc in scans]
+    for gv in rows_geoms:
+        api.prepare(gv, kind=w.filter, device=dev)
+    updates = sum(g.n * g.n * g.n_angles for g in rows_geoms)
+    n_off = sum(1 for sc in scans if sc.overlap)
+    tdt = getattr(torch, DT[args.dtype])
+    variant = max(0, args.variant)
+    outs = [torch.empty((g.n, g.n), device=dev) for g in rows_geoms]
+    wsp = torch.empty(api.batched_scans_workspace_bytes(sinos, outs, scans, tdt), dtype=torch.uint8,
+                      device=dev)
+    stream = torch.cuda.Stream(dev)
+    res = {}
+    for order in ("queue", "group_cyclic"):
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph, stream=stream):
+            api.fbp_batched_scans(sinos, scans, kind=w.filter, dtype=tdt, variant=variant, order=order,
+                                  outs=outs, workspace=wsp)
+        with torch.cuda.stream(stream):
+            T = Timed(stream, args.steps, args.warmup)
+            res[order] = (T.run(lambda _: graph.replay(), dev.index if order == "queue" else None), T.clocks)
+        del graph
+    with torch.cuda.stream(stream):
+        filts = [torch.empty((g.n_angles, g.n_det), dtype=tdt, device=dev) for g in rows_geoms]
+        rss = [torch.empty((g.n_angles,), device=dev) if args.dtype != "f32" else None for g in rows_geoms]
+
+        def per_scan(_):
+            for s, sc, gv, f, r, o in zip(sinos, scans, rows_geoms, filts, rss, outs):
+                if sc.overlap:
+                    api.filter_offset(s, sc.g, sc.overlap, sc.fold, kind=w.filter, dtype=tdt, out=f,
+                                      row_scale=r)
+                else:
+                    api.filter(s, sc.g, kind=w.filter, dtype=tdt, out=f, row_scale=r)
+                api.backproject(f, gv, row_scale=r, out=o, variant=variant)
+
+        T2 = Timed(stream, max(1, args.steps // 2), args.warmup)
+        ms_single = T2.run(per_scan, None)
+    assert api.device_status() == 0
+    ms, clocks = res["queue"]
+    per_rank = allgather_floats([ms, float(updates)])
+    rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
+    per_rank_c = allgather_floats([res["group_cyclic"][0], float(updates)])
+    rate_c, ms_c = aggregate([r[0] for r in per_rank_c], [int(r[1]) for r in per_rank_c])
+    if rank != 0:
+        finish({}, ws, rank)
+        return
+    line = base_line(args, ws, rate / 1e9, ms_step, DT_LABEL[args.dtype], {
+        "workload": f"{w.name}: {len(idx)} scans per GPU ({n_off} offset: full turn, detector 9N/16 bins "
+                    f"off the axis, folded), N in {w.n_choices}, half-turn K in {w.k_choices}, random "
+                    "ellipses, Ram-Lak; one persistent launch per step, CUDA-graph replay, atomic work queue",
+        "parallelism": f"scans sharded over {ws} GPU(s), no collective",
+        "bp_variant": variant})
+    line.update({"slices_per_s": len(idx) * len(per_rank) / (ms_step / 1e3),
+                 "group_cyclic": {"value": rate_c / 1e9, "unit": UNIT, "ms_per_step": ms_c,
+                                  "ratio_to_queue": ms_step / ms_c},
+                 "per_scan_launches": {"value": updates / (ms_single / 1e3) / 1e9, "unit": UNIT,
+                                       "ms_per_step": ms_single, "launches_per_step": 2 * len(idx)},
+                 "speedup_vs_per_scan": ms_single / ms,
+                 "clocks": clocks, "gpu_launches": 2 * args.steps})
+    finish(line, ws, rank)
+
+
 def run_gd(args) -> None:
     """Least-squares refinement: one step = one gradient-descent iteration
     x <- x - eta A^T (A x - b) over the stack (radon_forward, then
@@ -840,6 +926,8 @@ def main(argv=None):
         run_pipeline(args)
     elif args.workload == "fbp_offset_n8192":
         run_offset(args)
+    elif args.workload == "fbp_mixed_batch":
+        run_mixed(args)
     else:
         run_uniform(args)
 

@@ -378,6 +378,49 @@ fbp_status fbp_batched(const fbp_batch_item *items, int count,
                        void *workspace, size_t ws_bytes, fbp_stream_t stream);
 
 /*
+ * Mixed batches of normal and offset scans (Sec. V-A(b): specimens with
+ * various N_p, N_r, N_c, "both normal scan CT and offset scan CT",
+ * reconstructed simultaneously).  An item with overlap > 0 is a full-turn
+ * offset scan (g as for fbp_filter_offset, weighted and optionally folded on
+ * its virtual detector); overlap == 0 is a normal scan (g as for fbp_filter).
+ */
+typedef struct {
+    const float *sino;   /* device, float [n_angles][n_det]: the scan's rows     */
+    float *slice;        /* device, float [n][n]: the reconstruction             */
+    fbp_geometry g;      /* the scan's geometry                                  */
+    double overlap;      /* 0: normal scan; > 0: offset scan (fbp_offset_scan)   */
+    int fold;            /* offset scans: 1 = fold the half turns (K even)       */
+} fbp_scan_item;
+
+/* Work order of the batch's persistent backprojection launch.  A work unit
+ * is one output tile of one item. */
+typedef enum {
+    FBP_ORDER_QUEUE = 0,        /* items by total cost K n^2, largest first; blocks
+                                   take the next unit from an atomic counter      */
+    FBP_ORDER_GROUP_CYCLIC = 1  /* the paper's group-and-cyclic mapping (Sec.
+                                   V-A(b)): units sorted by cost per unit, so each
+                                   run of P consecutive units (P = resident blocks)
+                                   is a group of similar cost, and block b takes
+                                   units b, b + P, b + 2P, ...: one unit of every
+                                   group, no atomics                              */
+} fbp_batch_order;
+
+/*
+ * fbp_batched_scans -- fbp_batched for mixed items, with a chosen work
+ * order.  Arguments and errors as fbp_batched, plus fbp_offset_geometry's
+ * errors for offset items and FBP_ERR_INVALID_ARG for an unknown order.
+ * Each item's virtual detector must have n_v <= 8192 bins.  The workspace
+ * holds each item's filtered rows ([K'][n_v] for offset items, K' = K/2
+ * when folded).
+ */
+size_t fbp_batched_scans_workspace_bytes(const fbp_scan_item *items, int count,
+                                         fbp_dtype dtype);
+fbp_status fbp_batched_scans(const fbp_scan_item *items, int count,
+                             fbp_filter_kind kind, fbp_dtype dtype, int bp_variant,
+                             fbp_batch_order order, void *workspace, size_t ws_bytes,
+                             fbp_stream_t stream);
+
+/*
  * Device status word.  Kernels never trap: a kernel that detects a fault
  * (a work-queue loop past its iteration cap, or -- in the checked build --
  * an out-of-range table index) records a nonzero code in a device word and

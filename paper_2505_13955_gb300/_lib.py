@@ -72,6 +72,15 @@ class CHuWindow(ctypes.Structure):
     ]
 
 
+class CScanItem(ctypes.Structure):
+    _fields_ = [("sino", _vp), ("slice", _vp), ("g", CGeometry), ("overlap", ctypes.c_double),
+                ("fold", ctypes.c_int)]
+
+
+FBP_ORDER_QUEUE = 0
+FBP_ORDER_GROUP_CYCLIC = 1
+
+
 class COffsetScan(ctypes.Structure):
     _fields_ = [("overlap", ctypes.c_double), ("fold", ctypes.c_int)]
 
@@ -108,6 +117,10 @@ SIGNATURES = {
                                                       ctypes.c_int]),
     "fbp_batched": (ctypes.c_int, [ctypes.POINTER(CBatchItem), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                    ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "fbp_batched_scans_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(CScanItem), ctypes.c_int,
+                                                            ctypes.c_int]),
+    "fbp_batched_scans": (ctypes.c_int, [ctypes.POINTER(CScanItem), ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "fbp_last_device_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "fbp_prepare": (ctypes.c_int, [_G, ctypes.c_int, _vp]),
     "fbp_release_tables": (None, []),

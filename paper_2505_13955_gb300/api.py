@@ -450,6 +450,67 @@ def fbp_batched(sinos: list, geoms: list, kind="ramlak", dtype=torch.float32, va
     return outs
 
 
+_ORDERS = {"queue": _lib.FBP_ORDER_QUEUE, "group_cyclic": _lib.FBP_ORDER_GROUP_CYCLIC}
+
+
+@dataclass
+class Scan:
+    """One item of a mixed batch: a normal scan (overlap 0) or a full-turn
+    offset scan (overlap > 0, folded when `fold`)."""
+    g: Geometry
+    overlap: float = 0.0
+    fold: bool = True
+
+
+def _scan_items(sinos, outs, scans):
+    arr = (_lib.CScanItem * len(sinos))()
+    for i, (s, o, sc) in enumerate(zip(sinos, outs, scans)):
+        arr[i].sino = s.data_ptr()
+        arr[i].slice = o.data_ptr()
+        arr[i].g = sc.g.c()
+        arr[i].overlap = float(sc.overlap)
+        arr[i].fold = int(bool(sc.fold))
+    return arr
+
+
+def fbp_batched_scans(sinos: list, scans: list, kind="ramlak", dtype=torch.float32, variant: int = -1,
+                      order: str = "queue", outs: list | None = None,
+                      workspace: torch.Tensor | None = None):
+    """fbp_batched_scans: a ragged batch of normal and offset scans in one
+    filter launch and one persistent backprojection launch, with the work
+    order "queue" (atomic work queue, largest items first) or "group_cyclic"
+    (static cyclic assignment of cost-sorted tiles).  Returns the slices."""
+    if len(sinos) != len(scans):
+        raise ValueError("sinos and scans differ in length")
+    for i, (s, sc) in enumerate(zip(sinos, scans)):
+        _need(s, f"sinos[{i}]", torch.float32)
+        _slices(s, (sc.g.n_angles, sc.g.n_det), f"sinos[{i}]")
+    dev = sinos[0].device
+    if outs is None:
+        outs = [torch.empty((sc.g.n, sc.g.n), dtype=torch.float32, device=dev) for sc in scans]
+    items = _scan_items(sinos, outs, scans)
+    L = lib()
+    need = L.fbp_batched_scans_workspace_bytes(items, len(sinos), _DTYPES[dtype])
+    if need == 0:
+        raise FbpError(_lib.FBP_ERR_INVALID_ARG,
+                       "fbp_batched_scans: " + L.fbp_last_error_message().decode())
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=dev)
+    st = L.fbp_batched_scans(items, len(sinos), kind_id(kind), _DTYPES[dtype], int(variant),
+                             _ORDERS[order], _ptr(workspace), workspace.numel(), _stream(dev))
+    _lib.check(st, L, "fbp_batched_scans")
+    return outs
+
+
+def batched_scans_workspace_bytes(sinos, outs, scans, dtype=torch.float32) -> int:
+    L = lib()
+    n = L.fbp_batched_scans_workspace_bytes(_scan_items(sinos, outs, scans), len(sinos), _DTYPES[dtype])
+    if n == 0:
+        raise FbpError(_lib.FBP_ERR_INVALID_ARG,
+                       "fbp_batched_scans_workspace_bytes: " + L.fbp_last_error_message().decode())
+    return int(n)
+
+
 def prepare(g: Geometry, kind="ramlak", device=None):
     """Build the geometry's constant tables now (before CUDA graph capture)."""
     L = lib()

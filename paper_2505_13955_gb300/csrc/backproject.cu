@@ -247,10 +247,16 @@ __global__ void __launch_bounds__(TXT *TYT) bp_persistent_kernel(BpBatchArgs a)
     __shared__ int s_unit;
     constexpr int TW = TXT * PX, TH = TYT * PY;
     for (int iter = 0;; ++iter) {
-        if (threadIdx.x == 0) s_unit = atomicAdd(a.counter, 1);
-        __syncthreads();
-        const int u = s_unit;
-        __syncthreads();
+        int u;
+        if (a.cyclic) {
+            const long long uc = (long long)blockIdx.x + (long long)iter * gridDim.x;
+            u = uc < a.total_units ? (int)uc : a.total_units;
+        } else {
+            if (threadIdx.x == 0) s_unit = atomicAdd(a.counter, 1);
+            __syncthreads();
+            u = s_unit;
+            __syncthreads();
+        }
         if (u >= a.total_units) break;
         if (iter > a.total_units) {
             if (threadIdx.x == 0) atomicCAS(a.status, 0u, (unsigned)FAULT_QUEUE_CAP);

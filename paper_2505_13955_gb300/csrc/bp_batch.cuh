@@ -25,17 +25,23 @@ struct BpBatchItem {            // one slice of the batch, 80 bytes
 struct BpBatchArgs {
     BpBatchItem items[kMaxBatch];
     int count, total_units, max_H;
+    int cyclic;                 // 1: block b takes units b, b + P, b + 2P (P = grid); 0: atomic queue
     int *counter;               // work-queue counter (workspace), zeroed before launch
     unsigned *status;
 };
 
-struct FilterBatchItem {        // 56 bytes
-    const float *sino;          // [K][D]
+struct FilterBatchItem {        // 88 bytes
+    const float *sino;          // [K][D], or the offset scan's [K_in][Dp] physical rows
     void *filt;                 // [K][D] in the workspace
     float *row_scale;           // [K] or null
     const float2 *G;            // difference-form spectrum for (D, kind, tau), length L
     const float2 *tw;           // twiddles for L
     int K, D, L, group_begin;   // group = one block's filter_pairs_per_block(L) row pairs
+    // offset scans (Dp > 0): physical bins, virtual index of bin 0, fold,
+    // physical rows, virtual centre, side sign and 1 / overlap (filter.cu)
+    int Dp, off, fold, K_in;
+    float cv, sgn, inv_delta;
+    int pad_;
 };
 
 struct FilterBatchArgs {

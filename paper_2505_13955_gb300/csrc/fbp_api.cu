@@ -424,46 +424,206 @@ fbp_status fbp_bp_variant_info(int variant, fbp_bp_shape *out)
 }
 
 // ---------------------------------------------------------------------------
-// Ragged batches
+// Ragged batches (normal and offset scans)
 // ---------------------------------------------------------------------------
-static fbp_status check_items(const fbp_batch_item *items, int count)
+struct ScanPlan {
+    const float *sino;
+    float *slice;
+    fbp_geometry g;        // the scan's geometry
+    fbp_geometry gb;       // geometry of the filtered rows (virtual detector for offset scans)
+    bool offset;
+    FilterOffset fo;
+};
+
+static fbp_status plan_items(const fbp_scan_item *items, int count, std::vector<ScanPlan> *plan)
 {
     if (!items) return fail(FBP_ERR_INVALID_ARG, "items is NULL");
     if (count < 1 || count > kMaxBatch)
         return fail(FBP_ERR_INVALID_ARG, "count %d outside [1, %d]", count, kMaxBatch);
+    plan->resize(count);
     for (int i = 0; i < count; ++i) {
-        fbp_status st = check_geometry(&items[i].g, true, true);
+        ScanPlan &p = (*plan)[i];
+        p.sino = items[i].sino;
+        p.slice = items[i].slice;
+        p.g = items[i].g;
+        p.offset = items[i].overlap != 0.0;
+        p.fo = FilterOffset{};
+        fbp_status st = FBP_OK;
+        if (p.offset) {
+            fbp_offset_scan o;
+            o.overlap = items[i].overlap;
+            o.fold = items[i].fold;
+            st = offset_virtual(&items[i].g, &o, &p.gb, &p.fo);
+            if (st == FBP_OK) st = check_geometry(&p.gb, true, true);
+        } else {
+            p.gb = items[i].g;
+            st = check_geometry(&items[i].g, true, true);
+        }
         if (st != FBP_OK) {
             const std::string why = fbp_last_error_message();
             return fail(st, "item %d: %s", i, why.c_str());
         }
-        if (!items[i].sino || !items[i].slice)
-            return fail(FBP_ERR_INVALID_ARG, "item %d: sino or slice is NULL", i);
+        if (!p.sino || !p.slice) return fail(FBP_ERR_INVALID_ARG, "item %d: sino or slice is NULL", i);
     }
     return FBP_OK;
 }
 
 // Workspace: [256 B: queue counter] then, per item, its filtered rows and
 // (16-bit dtypes) its row scales, each 256-byte aligned.
-static size_t workspace_layout(const fbp_batch_item *items, int count, fbp_dtype dtype,
+static size_t workspace_layout(const std::vector<ScanPlan> &plan, fbp_dtype dtype,
                                std::vector<size_t> *filt_off, std::vector<size_t> *scale_off)
 {
     size_t off = 256;
-    for (int i = 0; i < count; ++i) {
-        const size_t rows = (size_t)items[i].g.n_angles;
+    for (const ScanPlan &p : plan) {
+        const size_t rows = (size_t)p.gb.n_angles;
         if (filt_off) filt_off->push_back(off);
-        off += align256(rows * items[i].g.n_det * dtype_size(dtype));
+        off += align256(rows * p.gb.n_det * dtype_size(dtype));
         if (scale_off) scale_off->push_back(dtype == FBP_F32 ? 0 : off);
         if (dtype != FBP_F32) off += align256(rows * 4);
     }
     return off;
 }
 
+static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kind kind,
+                               fbp_dtype dtype, int bp_variant, int order, void *workspace,
+                               size_t ws_bytes, fbp_stream_t stream)
+{
+    const int count = (int)plan.size();
+    if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
+    if (!kind_ok(kind)) return fail(FBP_ERR_INVALID_ARG, "filter kind %d", (int)kind);
+    if (bp_variant < -1 || bp_variant >= bp_variant_count())
+        return fail(FBP_ERR_INVALID_ARG, "variant %d", bp_variant);
+    if (order != FBP_ORDER_QUEUE && order != FBP_ORDER_GROUP_CYCLIC)
+        return fail(FBP_ERR_INVALID_ARG, "order %d", order);
+    const int variant = bp_variant < 0 ? 0 : bp_variant;
+    std::vector<size_t> foff, soff;
+    const size_t need = workspace_layout(plan, dtype, &foff, &soff);
+    if (!workspace) return fail(FBP_ERR_WORKSPACE, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255)
+        return fail(FBP_ERR_WORKSPACE, "workspace is not 256-byte aligned");
+    if (ws_bytes < need)
+        return fail(FBP_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", ws_bytes, need);
+    char *ws = static_cast<char *>(workspace);
+    unsigned *status = nullptr;
+    fbp_status st = device_status_word(&status);
+    if (st != FBP_OK) return st;
+
+    // tables (all before any launch, so a failure enqueues nothing)
+    std::vector<const double2 *> cs(count);
+    std::vector<const float2 *> Gs(count);
+    std::vector<const float2 *> tws(count);
+    std::vector<int> Ls(count);
+    for (int i = 0; i < count; ++i) {
+        st = angle_table(plan[i].gb, stream, &cs[i]);
+        if (st != FBP_OK) return st;
+        st = filter_tables(plan[i].gb.n_det, kind, plan[i].gb.det_spacing, stream, &Gs[i], &tws[i], &Ls[i]);
+        if (st != FBP_OK) return st;
+    }
+
+    // filter descriptors, in item order
+    auto *fa = new FilterBatchArgs();
+    std::unique_ptr<FilterBatchArgs> fa_owner(fa);
+    int groups = 0;
+    for (int i = 0; i < count; ++i) {
+        const ScanPlan &p = plan[i];
+        FilterBatchItem &f = fa->items[i];
+        f.sino = p.sino;
+        f.filt = ws + foff[i];
+        f.row_scale = dtype == FBP_F32 ? nullptr : reinterpret_cast<float *>(ws + soff[i]);
+        f.G = Gs[i];
+        f.tw = tws[i];
+        f.K = p.gb.n_angles;
+        f.D = p.gb.n_det;
+        f.L = Ls[i];
+        f.group_begin = groups;
+        f.Dp = p.offset ? p.fo.Dp : 0;
+        f.off = p.offset ? p.fo.off : 0;
+        f.fold = p.offset ? p.fo.fold : 0;
+        f.K_in = p.offset ? (int)p.fo.K_in : f.K;
+        f.cv = p.fo.cv;
+        f.sgn = p.fo.sgn;
+        f.inv_delta = p.fo.inv_delta;
+        f.pad_ = 0;
+        const int G = filter_pairs_per_block(Ls[i]);
+        const long long pairs = ((long long)f.K + 1) / 2;
+        const long long gi = (pairs + G - 1) / G;
+        if ((long long)groups + gi > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "batch too large");
+        groups += (int)gi;
+    }
+    fa->count = count;
+
+    // backprojection descriptors.  Queue: items by total cost K n^2, largest
+    // first.  Group-cyclic: by cost per unit (K per tile), largest first, so
+    // every run of P consecutive units holds units of similar cost.
+    std::vector<int> idx(count);
+    std::iota(idx.begin(), idx.end(), 0);
+    std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
+        const fbp_geometry &a = plan[x].gb, &b = plan[y].gb;
+        if (order == FBP_ORDER_GROUP_CYCLIC) return a.n_angles > b.n_angles;
+        return (long long)a.n_angles * a.n * a.n > (long long)b.n_angles * b.n * b.n;
+    });
+    auto *ba = new BpBatchArgs();
+    std::unique_ptr<BpBatchArgs> ba_owner(ba);
+    const int TW = bp_tile_w(variant), TH = bp_tile_h(variant);
+    long long units = 0;
+    int max_H = 0;
+    for (int r = 0; r < count; ++r) {
+        const int i = idx[r];
+        const fbp_geometry &g = plan[i].gb;
+        BpBatchItem &b = ba->items[r];
+        b.filt = ws + foff[i];
+        b.row_scale = dtype == FBP_F32 ? nullptr : reinterpret_cast<const float *>(ws + soff[i]);
+        b.slice = plan[i].slice;
+        b.cs = cs[i];
+        b.alpha = g.pixel_size / g.det_spacing;
+        b.det_center = g.det_center;
+        b.K = g.n_angles;
+        b.D = g.n_det;
+        b.N = g.n;
+        b.scale = (float)g.angle_step;
+        b.tiles_x = (g.n + TW - 1) / TW;
+        b.H = bp_window_half(b.alpha, TW, TH);
+        b.unit_begin = (int)units;
+        b.pad_ = 0;
+        max_H = std::max(max_H, b.H);
+        units += (long long)b.tiles_x * ((g.n + TH - 1) / TH);
+        if (units > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "batch too large");
+    }
+    ba->count = count;
+    ba->total_units = (int)units;
+    ba->max_H = max_H;
+    ba->cyclic = order == FBP_ORDER_GROUP_CYCLIC ? 1 : 0;
+    ba->counter = reinterpret_cast<int *>(ws);
+    ba->status = status;
+
+    if (!ba->cyclic) FBP_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), stream));
+    st = launch_filter_batched(*fa, groups, dtype, stream);
+    if (st != FBP_OK) return st;
+    return launch_bp_persistent(*ba, variant, dtype, stream);
+}
+
+static fbp_status plan_plain(const fbp_batch_item *items, int count, std::vector<ScanPlan> *plan)
+{
+    if (!items) return fail(FBP_ERR_INVALID_ARG, "items is NULL");
+    if (count < 1 || count > kMaxBatch)
+        return fail(FBP_ERR_INVALID_ARG, "count %d outside [1, %d]", count, kMaxBatch);
+    std::vector<fbp_scan_item> scans(count);
+    for (int i = 0; i < count; ++i) {
+        scans[i].sino = items[i].sino;
+        scans[i].slice = items[i].slice;
+        scans[i].g = items[i].g;
+        scans[i].overlap = 0.0;
+        scans[i].fold = 0;
+    }
+    return plan_items(scans.data(), count, plan);
+}
+
 size_t fbp_batched_workspace_bytes(const fbp_batch_item *items, int count, fbp_dtype dtype)
 {
     clear_error();
-    if (!dtype_ok(dtype) || check_items(items, count) != FBP_OK) return 0;
-    return workspace_layout(items, count, dtype, nullptr, nullptr);
+    std::vector<ScanPlan> plan;
+    if (!dtype_ok(dtype) || plan_plain(items, count, &plan) != FBP_OK) return 0;
+    return workspace_layout(plan, dtype, nullptr, nullptr);
 }
 
 fbp_status fbp_batched(const fbp_batch_item *items, int count, fbp_filter_kind kind,
@@ -471,105 +631,30 @@ fbp_status fbp_batched(const fbp_batch_item *items, int count, fbp_filter_kind k
                        fbp_stream_t stream)
 {
     return guarded([&]() -> fbp_status {
-        fbp_status st = check_items(items, count);
+        std::vector<ScanPlan> plan;
+        fbp_status st = plan_plain(items, count, &plan);
         if (st != FBP_OK) return st;
-        if (!dtype_ok(dtype)) return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
-        if (!kind_ok(kind)) return fail(FBP_ERR_INVALID_ARG, "filter kind %d", (int)kind);
-        if (bp_variant < -1 || bp_variant >= bp_variant_count())
-            return fail(FBP_ERR_INVALID_ARG, "variant %d", bp_variant);
-        const int variant = bp_variant < 0 ? 0 : bp_variant;
-        std::vector<size_t> foff, soff;
-        const size_t need = workspace_layout(items, count, dtype, &foff, &soff);
-        if (!workspace) return fail(FBP_ERR_WORKSPACE, "workspace is NULL");
-        if (reinterpret_cast<uintptr_t>(workspace) & 255)
-            return fail(FBP_ERR_WORKSPACE, "workspace is not 256-byte aligned");
-        if (ws_bytes < need)
-            return fail(FBP_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", ws_bytes, need);
-        char *ws = static_cast<char *>(workspace);
-        unsigned *status = nullptr;
-        st = device_status_word(&status);
+        return batched_impl(plan, kind, dtype, bp_variant, FBP_ORDER_QUEUE, workspace, ws_bytes, stream);
+    });
+}
+
+size_t fbp_batched_scans_workspace_bytes(const fbp_scan_item *items, int count, fbp_dtype dtype)
+{
+    clear_error();
+    std::vector<ScanPlan> plan;
+    if (!dtype_ok(dtype) || plan_items(items, count, &plan) != FBP_OK) return 0;
+    return workspace_layout(plan, dtype, nullptr, nullptr);
+}
+
+fbp_status fbp_batched_scans(const fbp_scan_item *items, int count, fbp_filter_kind kind,
+                             fbp_dtype dtype, int bp_variant, fbp_batch_order order,
+                             void *workspace, size_t ws_bytes, fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        std::vector<ScanPlan> plan;
+        fbp_status st = plan_items(items, count, &plan);
         if (st != FBP_OK) return st;
-
-        // tables (all before any launch, so a failure enqueues nothing)
-        std::vector<const double2 *> cs(count);
-        std::vector<const float2 *> Gs(count);
-        std::vector<const float2 *> tws(count);
-        std::vector<int> Ls(count);
-        for (int i = 0; i < count; ++i) {
-            st = angle_table(items[i].g, stream, &cs[i]);
-            if (st != FBP_OK) return st;
-            st = filter_tables(items[i].g.n_det, kind, items[i].g.det_spacing, stream, &Gs[i],
-                               &tws[i], &Ls[i]);
-            if (st != FBP_OK) return st;
-        }
-
-        // filter descriptors, in item order
-        auto *fa = new FilterBatchArgs();
-        std::unique_ptr<FilterBatchArgs> fa_owner(fa);
-        int groups = 0;
-        for (int i = 0; i < count; ++i) {
-            FilterBatchItem &f = fa->items[i];
-            f.sino = items[i].sino;
-            f.filt = ws + foff[i];
-            f.row_scale = dtype == FBP_F32 ? nullptr : reinterpret_cast<float *>(ws + soff[i]);
-            f.G = Gs[i];
-            f.tw = tws[i];
-            f.K = items[i].g.n_angles;
-            f.D = items[i].g.n_det;
-            f.L = Ls[i];
-            f.group_begin = groups;
-            const int G = filter_pairs_per_block(Ls[i]);
-            const long long pairs = ((long long)f.K + 1) / 2;
-            const long long gi = (pairs + G - 1) / G;
-            if ((long long)groups + gi > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "batch too large");
-            groups += (int)gi;
-        }
-        fa->count = count;
-
-        // backprojection descriptors: items by angle count, largest first
-        std::vector<int> order(count);
-        std::iota(order.begin(), order.end(), 0);
-        std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
-            return (long long)items[x].g.n_angles * items[x].g.n * items[x].g.n >
-                   (long long)items[y].g.n_angles * items[y].g.n * items[y].g.n;
-        });
-        auto *ba = new BpBatchArgs();
-        std::unique_ptr<BpBatchArgs> ba_owner(ba);
-        const int TW = bp_tile_w(variant), TH = bp_tile_h(variant);
-        long long units = 0;
-        int max_H = 0;
-        for (int r = 0; r < count; ++r) {
-            const int i = order[r];
-            const fbp_geometry &g = items[i].g;
-            BpBatchItem &b = ba->items[r];
-            b.filt = ws + foff[i];
-            b.row_scale = dtype == FBP_F32 ? nullptr : reinterpret_cast<const float *>(ws + soff[i]);
-            b.slice = items[i].slice;
-            b.cs = cs[i];
-            b.alpha = g.pixel_size / g.det_spacing;
-            b.det_center = g.det_center;
-            b.K = g.n_angles;
-            b.D = g.n_det;
-            b.N = g.n;
-            b.scale = (float)g.angle_step;
-            b.tiles_x = (g.n + TW - 1) / TW;
-            b.H = bp_window_half(b.alpha, TW, TH);
-            b.unit_begin = (int)units;
-            b.pad_ = 0;
-            max_H = std::max(max_H, b.H);
-            units += (long long)b.tiles_x * ((g.n + TH - 1) / TH);
-            if (units > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "batch too large");
-        }
-        ba->count = count;
-        ba->total_units = (int)units;
-        ba->max_H = max_H;
-        ba->counter = reinterpret_cast<int *>(ws);
-        ba->status = status;
-
-        FBP_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), stream));
-        st = launch_filter_batched(*fa, groups, dtype, stream);
-        if (st != FBP_OK) return st;
-        return launch_bp_persistent(*ba, variant, dtype, stream);
+        return batched_impl(plan, kind, dtype, bp_variant, (int)order, workspace, ws_bytes, stream);
     });
 }
 

@@ -345,29 +345,39 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
             v[n1] = make_float2(da, db);
         }
         group_sync(bar_id, C);                    // staged rows read before S is written
+    } else if (off.on) {
+        // offset scans: weighted (and folded) virtual samples, then differences
+#pragma unroll
+        for (int n1 = 0; n1 < R; ++n1) {
+            const int n = C * n1 + t;
+            float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
+            if (active && C * n1 <= D) {          // uniform over the group
+                a = offset_sample(job.a, job.a2, n, D, off);
+                b = offset_sample(job.b, job.b2, n, D, off);
+                am = __shfl_up_sync(0xffffffffu, a, 1);
+                bm = __shfl_up_sync(0xffffffffu, b, 1);
+                if (lane == 0) {
+                    am = offset_sample(job.a, job.a2, n - 1, D, off);
+                    bm = offset_sample(job.b, job.b2, n - 1, D, off);
+                }
+                nz_a |= (a != 0.f);
+                nz_b |= (b != 0.f);
+            }
+            v[n1] = make_float2(a - am, b - bm);
+        }
     } else {
 #pragma unroll
         for (int n1 = 0; n1 < R; ++n1) {
             const int n = C * n1 + t;
             float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
             if (active && C * n1 <= D) {          // uniform over the group
-                if (off.on) {
-                    a = offset_sample(job.a, job.a2, n, D, off);
-                    b = offset_sample(job.b, job.b2, n, D, off);
-                } else {
-                    a = n < D ? __ldg(job.a + n) : 0.f;
-                    b = (job.b && n < D) ? __ldg(job.b + n) : 0.f;
-                }
+                a = n < D ? __ldg(job.a + n) : 0.f;
+                b = (job.b && n < D) ? __ldg(job.b + n) : 0.f;
                 am = __shfl_up_sync(0xffffffffu, a, 1);
                 bm = __shfl_up_sync(0xffffffffu, b, 1);
                 if (lane == 0) {
-                    if (off.on) {
-                        am = offset_sample(job.a, job.a2, n - 1, D, off);
-                        bm = offset_sample(job.b, job.b2, n - 1, D, off);
-                    } else {
-                        am = (n >= 1 && n - 1 < D) ? __ldg(job.a + n - 1) : 0.f;
-                        bm = (job.b && n >= 1 && n - 1 < D) ? __ldg(job.b + n - 1) : 0.f;
-                    }
+                    am = (n >= 1 && n - 1 < D) ? __ldg(job.a + n - 1) : 0.f;
+                    bm = (job.b && n >= 1 && n - 1 < D) ? __ldg(job.b + n - 1) : 0.f;
                 }
                 nz_a |= (a != 0.f);
                 nz_b |= (b != 0.f);
@@ -599,7 +609,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_batched_kernel(FilterBa
     const int g = threadIdx.x / C, t = threadIdx.x % C;
     const long long pair = (long long)(blockIdx.x - it.group_begin) * GP + g;
     bool active;
-    const RowPairJob job = make_job(it.sino, it.filt, it.row_scale, it.K, it.D, pair, sizeof(T), active);
+    RowPairJob job = make_job(it.sino, it.filt, it.row_scale, it.K, it.D, pair, sizeof(T), active);
     float2 *S = smem_f2 + (size_t)g * it.L;
     float *rd = red + g * 4 * (C / 32);
     PreArgs pre;
@@ -607,6 +617,23 @@ __global__ void __launch_bounds__(kFilterThreads) filter_batched_kernel(FilterBa
     pre.r = 0;
     OffArgs off;
     off.on = 0;
+    if (it.Dp > 0) {
+        off.on = 1;
+        off.Dp = it.Dp;
+        off.off = it.off;
+        off.fold = it.fold;
+        off.K_in = it.K_in;
+        off.K_out = it.K;
+        off.cv = it.cv;
+        off.sgn = it.sgn;
+        off.inv_delta = it.inv_delta;
+        RowPairJob oj = job;
+        offset_inputs(oj, it.sino, it.K, pair, off);
+        job.a = oj.a;
+        job.b = oj.b;
+        job.a2 = oj.a2;
+        job.b2 = oj.b2;
+    }
     switch (it.L) {
         case 512: fft_pair<512, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre, off); break;
         case 1024: fft_pair<1024, T>(job, active, it.D, it.G, it.tw, S, rd, t, 1 + g, pre, off); break;

@@ -219,6 +219,7 @@ class Workload:
     k_choices: tuple = field(default_factory=tuple)
     counts: bool = False        # inputs are raw detector counts (stage-2 pre-processing on)
     offset: tuple | None = None  # full-turn offset scan: (n_det, det_center, overlap in bins)
+    offset_fraction: float = 0.0  # ragged: share of items that are offset scans
 
 
 # Parameters of the counts-to-codes workload (the paper leaves the blur width
@@ -242,6 +243,11 @@ WORKLOADS = {
     # of view's long side (radius 4095.5) and overlaps the axis by 512 bins
     "fbp_offset_n8192": Workload("fbp_offset_n8192", 16, 8192, 8192, "ramlak", "random", None, 7,
                                  offset=(4608, 511.5, 256.0)),
+    # normal and offset scans reconstructed together (Sec. V-A(b)): as the
+    # ragged batch, about a third of the items offset scans (scan_spec)
+    "fbp_mixed_batch": Workload("fbp_mixed_batch", 200, 0, 0, "ramlak", "random", None, 8,
+                                ragged=True, n_choices=(512, 1024, 2048, 4096),
+                                k_choices=(720, 1800, 3600), offset_fraction=1.0 / 3.0),
 }
 
 
@@ -259,6 +265,28 @@ def slice_spec(w: Workload, i: int):
         n, k = w.n, w.n_angles
     ell = shepp_logan() if w.phantom == "shepp_logan" else random_ellipses(rng)
     return n, k, ell, rng
+
+
+def scan_spec(w: Workload, i: int) -> dict:
+    """Item i of a mixed batch: n, the half-turn angle count k, ellipses, and
+    whether it is an offset scan.  An offset item has 2k angles over a full
+    turn on a detector of 9n/16 bins with the axis at bin n/16 - 1/2 (it
+    covers the long side of the n-pixel field of view) and overlap n/32 bins;
+    a normal item has k angles over a half turn on n centred bins."""
+    n, k, ell, rng = slice_spec(w, i)
+    offset = bool(rng.uniform() < w.offset_fraction)
+    if offset:
+        return {"n": n, "k": k, "ell": ell, "offset": True, "n_angles": 2 * k,
+                "n_det": 9 * n // 16, "det_center": n / 16 - 0.5, "overlap": n / 32,
+                "angle_step": 2.0 * np.pi / (2 * k)}
+    return {"n": n, "k": k, "ell": ell, "offset": False, "n_angles": k, "n_det": n,
+            "det_center": 0.5 * (n - 1), "overlap": 0.0, "angle_step": np.pi / k}
+
+
+def scan_sinogram(spec: dict, dtype=np.float32) -> np.ndarray:
+    """Noise-free analytic rows [n_angles, n_det] of a scan_spec item."""
+    return sinogram(spec["ell"], spec["n_angles"], spec["n_det"], spec["n"],
+                    angle_step=spec["angle_step"], det_center=spec["det_center"], dtype=dtype)
 
 
 def slice_counts(w: Workload, i: int) -> np.ndarray:

@@ -79,3 +79,28 @@ def test_filter_offset_validates_before_any_cuda_call(L):
                                None) == _lib.FBP_ERR_INVALID_ARG          # filt overlaps sino
     assert "overlaps" in L.fbp_last_error_message().decode()
     assert L.fbp_filter_offset(p, p, None, 0, 0, ctypes.byref(g), 0, ctypes.byref(o), None) == 0  # nothing to do
+
+
+def test_batched_scans_validate_before_any_cuda_call(L):
+    g = scan(L, 360, 64, 64, 10.0)
+    items = (_lib.CScanItem * 2)()
+    for it in items:
+        it.sino, it.slice, it.g, it.overlap, it.fold = 0x1000, 0x2000, g, 6.0, 1
+    items[1].g = L.fbp_geometry_default(90, 64, 64)
+    items[1].overlap = 0.0
+    n = L.fbp_batched_scans_workspace_bytes(items, 2, 0)
+    # counter block, then 180 folded rows of the virtual detector, then 90 x 64 rows
+    n_v = oracle.offset_virtual(64, 10.0, 6.0)[0]
+    assert n_v == 107
+    assert n == 256 + ((180 * n_v * 4 + 255) // 256) * 256 + 90 * 64 * 4
+    ws = ctypes.c_void_p(0x100000)
+    assert L.fbp_batched_scans(items, 2, 0, 0, -1, 7, ws, n, None) == _lib.FBP_ERR_INVALID_ARG   # order
+    assert L.fbp_batched_scans(items, 2, 0, 0, -1, 1, ws, n - 1, None) == _lib.FBP_ERR_WORKSPACE
+    items[0].overlap = 20.0                                                   # > short side
+    assert L.fbp_batched_scans(items, 2, 0, 0, -1, 1, ws, n, None) == _lib.FBP_ERR_INVALID_ARG
+    assert "item 0" in L.fbp_last_error_message().decode()
+    assert L.fbp_batched_scans_workspace_bytes(items, 2, 0) == 0
+    items[0].overlap = 6.0
+    items[1].sino = None
+    assert L.fbp_batched_scans(items, 2, 0, 0, -1, 0, ws, n, None) == _lib.FBP_ERR_INVALID_ARG
+    assert L.fbp_batched_scans(None, 2, 0, 0, -1, 0, ws, n, None) == _lib.FBP_ERR_INVALID_ARG
