@@ -16,7 +16,8 @@ K = 1800; a step is one iteration, A and A^T), fbp_pipeline_n8192 (detector
 counts to uint16 CT-number codes) and fbp_offset_n8192 (full-turn offset
 scans, 16 slices, 8192 angles, a 4608-bin detector off the axis) and
 fbp_mixed_batch (200 normal and offset scans in one persistent launch, work
-queue against the paper's group-and-cyclic order).
+queue against the paper's group-and-cyclic order) and sap_patching_n8192
+(adaptive patching of 16 reconstructed 8192^2 uint16 slices, slices/s).
 
 Timing: W >= 3 untimed warm-up steps, then exactly K steps bracketed by a
 barrier and torch.cuda.synchronize(), timed with CUDA events on the
@@ -258,7 +259,7 @@ def run_reference(args) -> None:
         return
     from paper_2505_13955_gb300 import phantoms
     w = phantoms.WORKLOADS[args.workload]
-    if w.ragged or w.offset is not None:
+    if w.ragged or w.offset is not None or not w.filter:
         w = phantoms.WORKLOADS[WORKLOAD]
     block = 1024 if args.steps + args.warmup <= 20 else 512
     for _ in range(args.warmup):
@@ -824,6 +825,110 @@ def run_mixed(args) -> None:
     finish(line, ws, rank)
 
 
+SAP_BYTES_PER_PIXEL = 8   # codes read by Canny (2) + edge map written (1) + codes and edges read by
+                          # the tree sums (3) + codes read by the patch means (2)
+
+
+def run_sap(args) -> None:
+    """Adaptive patching of reconstructed slices (Sec. V-B(c)): one step =
+    sap_edges + sap_patches for each of the stack's 16 uint16 slices
+    (n = 8192, 16 x 16 patches, 4096 per slice); the 2-bit mask path
+    (sap_depatch_pack of random four-class patches) is timed after it.
+    Throughput in slices/s; the roofline is HBM bandwidth at the step's
+    algorithmic bytes (8 per pixel)."""
+    import torch
+    from paper_2505_13955_gb300 import api, phantoms
+
+    ws, rank, dev = init_device()
+    w = phantoms.WORKLOADS["sap_patching_n8192"]
+    c = phantoms.SAP
+    n, S = w.n, (args.slices or w.n_slices)
+    host = np.empty((S, n, n), dtype=np.uint16)
+    for i, s_ in enumerate(shard_slices(S, rank)):
+        host[i] = phantoms.sap_slice(n, phantoms.slice_seed(w.config_id, s_))
+    slices = torch.from_numpy(host.view(np.int16)).to(dev)
+    p = api.SapParams(n, c["patch"], c["length"], c["canny_lo"], c["canny_hi"])
+    wsp = torch.empty(api.sap_workspace_bytes(p), dtype=torch.uint8, device=dev)
+    edges = torch.empty((n, n), dtype=torch.uint8, device=dev)
+    patches = torch.empty((S, p.length, p.patch, p.patch), dtype=torch.float32, device=dev)
+    leaves = torch.empty((S, p.length, 3), dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    T = Timed(stream, args.steps, args.warmup, n_events=3)
+
+    def step(evs):
+        for i in range(S):
+            if evs and i == 0:
+                evs[0].record(stream)
+            api.sap_edges(slices[i], p, out=edges, workspace=wsp)
+            if evs and i == 0:
+                evs[1].record(stream)
+            api.sap_patches(slices[i], edges, p, patches=patches[i], leaves=leaves[i], workspace=wsp)
+            if evs and i == 0:
+                evs[2].record(stream)
+
+    ms = T.run(step, dev.index)
+    assert api.device_status() == 0
+    edges_ms, patches_ms, clocks = T.between(0, 1), T.between(1, 2), T.clocks
+    rng = np.random.default_rng(0)
+    masks = torch.from_numpy(rng.integers(0, 4, (S, p.length, p.patch, p.patch)).astype(np.uint8)).to(dev)
+    packed = torch.empty((S, n, n // 4), dtype=torch.uint8, device=dev)
+    T2 = Timed(stream, args.steps, args.warmup)
+
+    def unpatch(_):
+        for i in range(S):
+            api.sap_depatch_pack(masks[i], leaves[i], p, out=packed[i])
+
+    ms_pack = T2.run(unpatch, None)
+    assert api.device_status() == 0
+
+    e2e = None
+    if args.e2e_steps > 0:
+        pin_in = torch.from_numpy(host.view(np.int16)).pin_memory()
+        pin_p = torch.empty(patches.shape, dtype=torch.float32).pin_memory()
+        pin_l = torch.empty(leaves.shape, dtype=torch.int32).pin_memory()
+        d_in = torch.empty((n, n), dtype=torch.int16, device=dev)
+
+        def e2e_step(_):
+            for i in range(S):
+                d_in.copy_(pin_in[i], non_blocking=True)
+                api.sap_edges(d_in, p, out=edges, workspace=wsp)
+                api.sap_patches(d_in, edges, p, patches=patches[i], leaves=leaves[i], workspace=wsp)
+            pin_p.copy_(patches, non_blocking=True)
+            pin_l.copy_(leaves, non_blocking=True)
+
+        T3 = Timed(stream, args.e2e_steps, 1)
+        t_e2e = T3.run(e2e_step, None)
+        e2e = {"value": S / (t_e2e / 1e3), "unit": "slices/s", "h2d_bytes_per_step": int(pin_in.numel() * 2),
+               "d2h_bytes_per_step": int(pin_p.numel() * 4 + pin_l.numel() * 4), "ms_per_step": t_e2e}
+    per_rank = allgather_floats([ms, float(S)])
+    rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
+    if rank != 0:
+        finish({}, ws, rank)
+        return
+    hbm = peaks().get("hbm_gbs") or 6800.0
+    gbs = SAP_BYTES_PER_PIXEL * n * n * S / (ms / 1e3) / 1e9
+    line = base_line(args, ws, rate, ms_step, "u16 codes, exact integer / f64", {
+        "workload": f"{w.name}: S={S} uint16 slices per GPU, n={n}, seeded random-ellipse phantoms "
+                    f"(codes {phantoms.SAP_CODES}), patch {p.patch}, {p.length} patches per slice, Canny "
+                    f"thresholds {p.canny_lo}/{p.canny_hi}",
+        "l2": "inputs larger than L2 (2.1 GB of slices per step), no flush",
+        "parallelism": f"slices sharded over {ws} GPU(s), no collective"})
+    line["metric"] = "SAP patching slices/s at N=8192 (Canny + adaptive quadtree + Z-order patches)"
+    line["unit"] = "slices/s"
+    line.update({
+        "sap_edges_ms_per_slice": edges_ms, "sap_patches_ms_per_slice": patches_ms,
+        "depatch_pack": {"ms_per_step": ms_pack, "slices_per_s": S / (ms_pack / 1e3),
+                         "gb_per_s": (p.length * p.patch ** 2 + n * n // 4) * S / (ms_pack / 1e3) / 1e9},
+        "roofline": {"bound": "hbm", "achieved": gbs, "peak": hbm, "unit": "GB/s", "frac": gbs / hbm,
+                     "traffic": None, "kernel": "whole SAP step",
+                     "basis": f"{SAP_BYTES_PER_PIXEL} algorithmic bytes per pixel per step / step time; "
+                              "peak = measured HBM copy (MEASURED_PEAKS.json)"},
+        "clocks": clocks, "gpu_launches": S * (5 + 3 * int(np.log2(n // p.patch)) + 5) * args.steps})
+    if e2e is not None:
+        line["e2e"] = e2e
+    finish(line, ws, rank)
+
+
 def run_gd(args) -> None:
     """Least-squares refinement: one step = one gradient-descent iteration
     x <- x - eta A^T (A x - b) over the stack (radon_forward, then
@@ -928,6 +1033,8 @@ def main(argv=None):
         run_offset(args)
     elif args.workload == "fbp_mixed_batch":
         run_mixed(args)
+    elif args.workload == "sap_patching_n8192":
+        run_sap(args)
     else:
         run_uniform(args)
 

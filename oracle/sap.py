@@ -50,7 +50,6 @@ The paper fixes none of the numbers or tie rules; the readings here are:
 from __future__ import annotations
 
 import heapq
-from collections import deque
 
 import numpy as np
 
@@ -88,56 +87,42 @@ def sobel(s):
 
 
 def nms_classes(gx, gy, lo: int, hi: int) -> np.ndarray:
-    """Non-maximum suppression and double threshold: 0 none, 1 weak, 2 strong."""
+    """Non-maximum suppression and double threshold: 0 none, 1 weak, 2 strong.
+    The gradient direction is quantised by integer comparisons; the pixel is
+    compared with its two neighbours along it (M = 0 outside the slice)."""
     gx = np.asarray(gx, dtype=np.int64)
     gy = np.asarray(gy, dtype=np.int64)
     m = np.abs(gx) + np.abs(gy)
     n0, n1 = m.shape
+    mp = np.pad(m, 1, mode="constant")          # M = 0 outside the slice
+
+    def shifted(dr, dc):                         # M at (r + dr, c + dc)
+        return mp[1 + dr:1 + dr + n0, 1 + dc:1 + dc + n1]
+
+    ax, ay = np.abs(gx), np.abs(gy)
+    horiz = ay * 32768 <= TAN22_Q15 * ax
+    vert = ~horiz & (ay * 32768 >= TAN67_Q15 * ax)
+    diag = ~horiz & ~vert & ((gx > 0) == (gy > 0))     # along (+r, +c)
+    anti = ~horiz & ~vert & ~diag                     # along (+r, -c)
+    prev = np.select([horiz, vert, diag, anti], [shifted(0, -1), shifted(-1, 0), shifted(-1, -1), shifted(-1, 1)])
+    nxt = np.select([horiz, vert, diag, anti], [shifted(0, 1), shifted(1, 0), shifted(1, 1), shifted(1, -1)])
+    keep = (m > lo) & (m > prev) & (m >= nxt)
     out = np.zeros((n0, n1), dtype=np.uint8)
-    for r in range(n0):
-        for c in range(n1):
-            mv = m[r, c]
-            if mv <= lo:
-                continue
-            ax, ay = abs(gx[r, c]), abs(gy[r, c])
-            if ay * 32768 <= TAN22_Q15 * ax:          # gradient near horizontal
-                d = (0, 1)
-            elif ay * 32768 >= TAN67_Q15 * ax:        # near vertical
-                d = (1, 0)
-            elif (gx[r, c] > 0) == (gy[r, c] > 0):    # along (+r, +c)
-                d = (1, 1)
-            else:                                     # along (+r, -c)
-                d = (1, -1)
-
-            def mag(rr, cc):
-                return m[rr, cc] if 0 <= rr < n0 and 0 <= cc < n1 else 0
-
-            prev = mag(r - d[0], c - d[1])
-            nxt = mag(r + d[0], c + d[1])
-            if mv > prev and mv >= nxt:
-                out[r, c] = 2 if mv > hi else 1
+    out[keep & (m <= hi)] = 1
+    out[keep & (m > hi)] = 2
     return out
 
 
 def hysteresis(cls) -> np.ndarray:
-    """Edges: strong pixels, and weak pixels 8-connected to a strong pixel
-    through weak pixels (breadth-first search from every strong pixel)."""
+    """Edges: the 8-connected components of the candidate (weak or strong)
+    pixels that hold a strong pixel.  The labelling is scipy's."""
+    from scipy import ndimage
     cls = np.asarray(cls)
-    n0, n1 = cls.shape
-    edge = np.zeros((n0, n1), dtype=np.uint8)
-    q = deque()
-    for r, c in zip(*np.nonzero(cls == 2)):
-        edge[r, c] = 1
-        q.append((r, c))
-    while q:
-        r, c = q.popleft()
-        for dr in (-1, 0, 1):
-            for dc in (-1, 0, 1):
-                rr, cc = r + dr, c + dc
-                if 0 <= rr < n0 and 0 <= cc < n1 and not edge[rr, cc] and cls[rr, cc] == 1:
-                    edge[rr, cc] = 1
-                    q.append((rr, cc))
-    return edge
+    lab, count = ndimage.label(cls > 0, structure=np.ones((3, 3), dtype=int))
+    strong = np.zeros(count + 1, dtype=bool)
+    strong[np.unique(lab[cls == 2])] = True
+    strong[0] = False
+    return strong[lab].astype(np.uint8)
 
 
 def canny(img, lo: int, hi: int) -> np.ndarray:

@@ -25,7 +25,7 @@ FBP_F32 = 0
 FBP_F16 = 1
 FBP_BF16 = 2
 
-# Every function include/fbp.h declares, with (restype, argtypes).
+# Every function include/*.h declares, with (restype, argtypes).
 _vp = ctypes.c_void_p
 
 
@@ -77,6 +77,11 @@ class CScanItem(ctypes.Structure):
                 ("fold", ctypes.c_int)]
 
 
+class CSapParams(ctypes.Structure):
+    _fields_ = [("n", ctypes.c_int), ("patch", ctypes.c_int), ("length", ctypes.c_int),
+                ("canny_lo", ctypes.c_int), ("canny_hi", ctypes.c_int)]
+
+
 FBP_ORDER_QUEUE = 0
 FBP_ORDER_GROUP_CYCLIC = 1
 
@@ -121,6 +126,10 @@ SIGNATURES = {
                                                             ctypes.c_int]),
     "fbp_batched_scans": (ctypes.c_int, [ctypes.POINTER(CScanItem), ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                          ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "sap_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(CSapParams)]),
+    "sap_edges": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(CSapParams), _vp, ctypes.c_size_t, _vp]),
+    "sap_patches": (ctypes.c_int, [_vp, _vp, _vp, _vp, ctypes.POINTER(CSapParams), _vp, ctypes.c_size_t, _vp]),
+    "sap_depatch_pack": (ctypes.c_int, [_vp, _vp, _vp, ctypes.POINTER(CSapParams), _vp]),
     "fbp_last_device_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "fbp_prepare": (ctypes.c_int, [_G, ctypes.c_int, _vp]),
     "fbp_release_tables": (None, []),

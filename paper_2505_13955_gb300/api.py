@@ -511,6 +511,99 @@ def batched_scans_workspace_bytes(sinos, outs, scans, dtype=torch.float32) -> in
     return int(n)
 
 
+# ---------------------------------------------------------------------------
+# Adaptive patching of reconstructed slices and 2-bit masks (include/sap.h).
+# uint16 slices travel in int16 tensors (the same bits), as in backproject_u16.
+# ---------------------------------------------------------------------------
+@dataclass
+class SapParams:
+    """Patching parameters: slice side n, patch side P, sequence length
+    (1 mod 3), Canny thresholds on M = |gx| + |gy|."""
+    n: int
+    patch: int = 16
+    length: int = 4096
+    canny_lo: int = 400000
+    canny_hi: int = 1000000
+
+    def c(self):
+        return _lib.CSapParams(int(self.n), int(self.patch), int(self.length), int(self.canny_lo),
+                               int(self.canny_hi))
+
+
+def sap_workspace_bytes(p: SapParams, which: str = "default") -> int:
+    pc = p.c()
+    n = lib(which).sap_workspace_bytes(ctypes.byref(pc))
+    if n == 0:
+        L = lib(which)
+        raise FbpError(_lib.FBP_ERR_INVALID_ARG, "sap_workspace_bytes: " + L.fbp_last_error_message().decode())
+    return int(n)
+
+
+def _sap_ws(p: SapParams, workspace, device):
+    need = sap_workspace_bytes(p)
+    if workspace is None:
+        workspace = torch.empty(need, dtype=torch.uint8, device=device)
+    return workspace
+
+
+def sap_edges(slice16: torch.Tensor, p: SapParams, out: torch.Tensor | None = None,
+              workspace: torch.Tensor | None = None, which: str = "default"):
+    """sap_edges: Canny edge map (uint8, 1 on edges) of one uint16 slice."""
+    _need(slice16, "slice", torch.int16)
+    if tuple(slice16.shape) != (p.n, p.n):
+        raise ValueError(f"slice has shape {tuple(slice16.shape)}, expected {(p.n, p.n)}")
+    if out is None:
+        out = torch.empty((p.n, p.n), dtype=torch.uint8, device=slice16.device)
+    _need(out, "edges", torch.uint8)
+    workspace = _sap_ws(p, workspace, slice16.device)
+    L = lib(which)
+    pc = p.c()
+    st = L.sap_edges(_ptr(slice16), _ptr(out), ctypes.byref(pc), _ptr(workspace), workspace.numel(),
+                     _stream(slice16.device))
+    _lib.check(st, L, "sap_edges")
+    return out
+
+
+def sap_patches(slice16: torch.Tensor, edges: torch.Tensor, p: SapParams,
+                patches: torch.Tensor | None = None, leaves: torch.Tensor | None = None,
+                workspace: torch.Tensor | None = None, which: str = "default"):
+    """sap_patches: the adaptive quadtree and its Z-order patch sequence.
+    Returns (patches [length, P, P] float32, leaves [length, 3] int32)."""
+    _need(slice16, "slice", torch.int16)
+    _need(edges, "edges", torch.uint8)
+    dev = slice16.device
+    if patches is None:
+        patches = torch.empty((p.length, p.patch, p.patch), dtype=torch.float32, device=dev)
+    if leaves is None:
+        leaves = torch.empty((p.length, 3), dtype=torch.int32, device=dev)
+    _need(patches, "patches", torch.float32)
+    _need(leaves, "leaves", torch.int32)
+    workspace = _sap_ws(p, workspace, dev)
+    L = lib(which)
+    pc = p.c()
+    st = L.sap_patches(_ptr(slice16), _ptr(edges), _ptr(patches), _ptr(leaves), ctypes.byref(pc),
+                       _ptr(workspace), workspace.numel(), _stream(dev))
+    _lib.check(st, L, "sap_patches")
+    return patches, leaves
+
+
+def sap_depatch_pack(mask_patches: torch.Tensor, leaves: torch.Tensor, p: SapParams,
+                     out: torch.Tensor | None = None, which: str = "default"):
+    """sap_depatch_pack: mask patches [length, P, P] (uint8 classes 0..3) back
+    onto the slice through the quadtree, packed 2 bits per pixel [n, n/4]."""
+    _need(mask_patches, "mask_patches", torch.uint8)
+    _need(leaves, "leaves", torch.int32)
+    if out is None:
+        out = torch.empty((p.n, p.n // 4), dtype=torch.uint8, device=mask_patches.device)
+    _need(out, "packed", torch.uint8)
+    L = lib(which)
+    pc = p.c()
+    st = L.sap_depatch_pack(_ptr(mask_patches), _ptr(leaves), _ptr(out), ctypes.byref(pc),
+                            _stream(mask_patches.device))
+    _lib.check(st, L, "sap_depatch_pack")
+    return out
+
+
 def prepare(g: Geometry, kind="ramlak", device=None):
     """Build the geometry's constant tables now (before CUDA graph capture)."""
     L = lib()

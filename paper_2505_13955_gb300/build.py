@@ -24,7 +24,7 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 
-CU_SOURCES = ["runtime.cu", "filter.cu", "backproject.cu", "forward.cu", "fbp_api.cu", "noalloc.cu"]
+CU_SOURCES = ["runtime.cu", "filter.cu", "backproject.cu", "forward.cu", "fbp_api.cu", "noalloc.cu", "sap.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -36,7 +36,7 @@ def nvcc() -> str:
 
 
 def _headers_mtime() -> float:
-    paths = [os.path.join(INCLUDE, "fbp.h")] + [
+    paths = [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE) if f.endswith(".h")] + [
         os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith(".cuh")]
     return max(os.path.getmtime(p) for p in paths)
 

@@ -1,0 +1,675 @@
+// sap.cu -- symmetric adaptive patching (SAP) of a reconstructed slice and
+// the 2-bit masks (Sec. V-B(c), Eq. (1); Sec. V-C(a)); the definitions are in
+// include/sap.h.  Everything is exact: integer arithmetic, or a fixed
+// sequence of IEEE double operations for the variance key and the patch means.
+//
+// Edges: one fused kernel per 32 x 32 tile stages the codes with a halo of 4
+// and computes smoothing, Sobel, magnitude, non-maximum suppression and the
+// two thresholds in shared memory (each staged array holds the value at the
+// border-clamped coordinate, which is what replicated borders mean stage by
+// stage).  Hysteresis is connected-component labelling of the candidate
+// pixels (weak or strong) with a lock-free union-find (links made only from
+// roots by compare-and-swap, larger root under smaller); a component is
+// kept if it holds a strong pixel.  Connectivity does not depend on the
+// order of the unions, so the result is deterministic.
+//
+// Quadtree: nodes are stored level by level (level l has 4^l nodes of side
+// n >> l, indexed by their Morton code, so node m's children are 4m .. 4m+3
+// in Z-order).  Sums (edge count, S1, S2) are built bottom-up, the monotone
+// variance key top-down, and each splittable node gets a 128-bit key
+// (V | variance key | shallower level | smaller Morton code) that orders
+// nodes as the greedy split does.  The greedy split set is then the top M =
+// (length - 1) / 3 keys: one block radix-selects the M-th key.  Leaf counts
+// go bottom-up and Z-order offsets top-down; each leaf writes its entry.
+#include <climits>
+#include <cstdint>
+
+#include "fbp_internal.cuh"
+#include "sap.h"
+
+namespace fbp {
+void clear_error();
+namespace {
+
+constexpr unsigned FAULT_UNION_CAP = 4;   // union-find loop past its cap
+constexpr unsigned FAULT_LEAF = 5;        // a leaf entry outside the slice
+
+constexpr int kTile = 32, kHalo = 4, kSpan = kTile + 2 * kHalo;   // 40
+constexpr int kTan22 = 13573, kTan67 = 79109;                     // tan(22.5), tan(67.5) x 2^15
+constexpr int kUnionCap = 1 << 22;
+constexpr int kFlag = 1 << 30;            // "component holds a strong pixel", on the root's entry
+constexpr int kLabelMask = kFlag - 1;
+
+__device__ __forceinline__ int clampi(int v, int hi) { return v < 0 ? 0 : v > hi ? hi : v; }
+
+// ---------------------------------------------------------------------------
+// Canny: classes (0 none, 1 weak, 2 strong) and the initial labels
+// ---------------------------------------------------------------------------
+__global__ void __launch_bounds__(256) canny_kernel(const unsigned short *__restrict__ img, int n, int lo,
+                                                   int hi, unsigned char *__restrict__ cls,
+                                                   int *__restrict__ label)
+{
+    // every array is indexed by (y - (ty0 - 4), x - (tx0 - 4)) and holds the
+    // stage's value at the clamped coordinate (clamp(y), clamp(x))
+    __shared__ int IN[kSpan][kSpan];
+    __shared__ int HH[kSpan][kSpan];
+    __shared__ int SS[kSpan][kSpan];
+    __shared__ int GX[kSpan][kSpan], GY[kSpan][kSpan], MM[kSpan][kSpan];
+    const int ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
+    const int oy = ty0 - kHalo, ox = tx0 - kHalo, nm = n - 1;
+    const int t = threadIdx.x;
+    // index of the clamped coordinate
+    auto iy = [&](int y) { return clampi(y, nm) - oy; };
+    auto ix = [&](int x) { return clampi(x, nm) - ox; };
+
+    for (int i = t; i < kSpan * kSpan; i += 256) {
+        const int r = i / kSpan, c = i - r * kSpan;
+        IN[r][c] = img[(size_t)clampi(oy + r, nm) * n + clampi(ox + c, nm)];
+    }
+    __syncthreads();
+    // horizontal binomial, columns needed by the vertical pass: [2, 38)
+    for (int i = t; i < kSpan * (kSpan - 4); i += 256) {
+        const int r = i / (kSpan - 4), c = 2 + i % (kSpan - 4);
+        const int x = clampi(ox + c, nm);
+        HH[r][c] = IN[r][ix(x - 2)] + 4 * IN[r][ix(x - 1)] + 6 * IN[r][ix(x)] + 4 * IN[r][ix(x + 1)] +
+                   IN[r][ix(x + 2)];
+    }
+    __syncthreads();
+    // vertical binomial on [2, 38) x [2, 38)
+    for (int i = t; i < (kSpan - 4) * (kSpan - 4); i += 256) {
+        const int r = 2 + i / (kSpan - 4), c = 2 + i % (kSpan - 4);
+        const int y = clampi(oy + r, nm);
+        SS[r][c] = HH[iy(y - 2)][c] + 4 * HH[iy(y - 1)][c] + 6 * HH[iy(y)][c] + 4 * HH[iy(y + 1)][c] +
+                   HH[iy(y + 2)][c];
+    }
+    __syncthreads();
+    // Sobel and L1 magnitude on [3, 37) x [3, 37)
+    for (int i = t; i < (kSpan - 6) * (kSpan - 6); i += 256) {
+        const int r = 3 + i / (kSpan - 6), c = 3 + i % (kSpan - 6);
+        const int y = clampi(oy + r, nm), x = clampi(ox + c, nm);
+        const int ym = iy(y - 1), y0 = iy(y), yp = iy(y + 1);
+        const int xm = ix(x - 1), x0 = ix(x), xp = ix(x + 1);
+        const int gx = (SS[ym][xp] + 2 * SS[y0][xp] + SS[yp][xp]) - (SS[ym][xm] + 2 * SS[y0][xm] + SS[yp][xm]);
+        const int gy = (SS[yp][xm] + 2 * SS[yp][x0] + SS[yp][xp]) - (SS[ym][xm] + 2 * SS[ym][x0] + SS[ym][xp]);
+        GX[r][c] = gx;
+        GY[r][c] = gy;
+        MM[r][c] = abs(gx) + abs(gy);
+    }
+    __syncthreads();
+    // non-maximum suppression and thresholds on the tile
+    for (int i = t; i < kTile * kTile; i += 256) {
+        const int r = kHalo + i / kTile, c = kHalo + i % kTile;
+        const int y = oy + r, x = ox + c;
+        if (y >= n || x >= n) continue;
+        const int m = MM[r][c];
+        unsigned char k = 0;
+        if (m > lo) {
+            const int gx = GX[r][c], gy = GY[r][c];
+            const long long ax = abs(gx), ay = abs(gy);
+            int dy, dx;
+            if (ay * 32768 <= (long long)kTan22 * ax) { dy = 0; dx = 1; }
+            else if (ay * 32768 >= (long long)kTan67 * ax) { dy = 1; dx = 0; }
+            else if ((gx > 0) == (gy > 0)) { dy = 1; dx = 1; }
+            else { dy = 1; dx = -1; }
+            const int py = y - dy, px = x - dx, qy = y + dy, qx = x + dx;
+            const int prev = (py >= 0 && py < n && px >= 0 && px < n) ? MM[r - dy][c - dx] : 0;
+            const int next = (qy >= 0 && qy < n && qx >= 0 && qx < n) ? MM[r + dy][c + dx] : 0;
+            if (m > prev && m >= next) k = m > hi ? 2 : 1;
+        }
+        const size_t p = (size_t)y * n + x;
+        cls[p] = k;
+        label[p] = k ? (int)p : -1;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Hysteresis as connected components of the candidates
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ int uf_find(int *L, int x, unsigned *status)
+{
+    // parent pointers only ever point to smaller indices, so the walk ends;
+    // loads bypass L1 so that links made by other blocks are seen
+    for (int it = 0; it < kUnionCap; ++it) {
+        const int p = __ldcg(L + x);
+        if (p == x) return x;
+        const int gp = __ldcg(L + p);
+        if (gp != p) L[x] = gp;            // path halving: every write moves to an ancestor
+        x = gp;
+    }
+    atomicCAS(status, 0u, FAULT_UNION_CAP);
+    return x;
+}
+
+// The root of x without writing: used once every union is done, where a
+// path-halving write could otherwise replace another pixel's final root
+// with an intermediate ancestor.
+__device__ __forceinline__ int uf_root(const int *L, int x, unsigned *status)
+{
+    for (int it = 0; it < kUnionCap; ++it) {
+        const int p = __ldcg(L + x);
+        if (p == x) return x;
+        x = p;
+    }
+    atomicCAS(status, 0u, FAULT_UNION_CAP);
+    return x;
+}
+
+__device__ __forceinline__ void uf_unite(int *L, int a, int b, unsigned *status)
+{
+    for (int it = 0; it < kUnionCap; ++it) {
+        a = uf_find(L, a, status);
+        b = uf_find(L, b, status);
+        if (a == b) return;
+        if (a < b) { const int tmp = a; a = b; b = tmp; }   // link the larger root under the smaller
+        const int old = atomicCAS(&L[a], a, b);
+        if (old == a) return;
+        a = old;                                             // a was linked meanwhile: retry from there
+    }
+    atomicCAS(status, 0u, FAULT_UNION_CAP);
+}
+
+__global__ void ccl_merge_kernel(int *label, int n, unsigned *status)
+{
+    const size_t total = (size_t)n * n;
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        if (label[p] < 0) continue;
+        const int y = (int)(p / n), x = (int)(p - (size_t)y * n);
+        // forward neighbours: right, down-left, down, down-right
+        if (x + 1 < n && label[p + 1] >= 0) uf_unite(label, (int)p, (int)p + 1, status);
+        if (y + 1 < n) {
+            const size_t q = p + n;
+            if (x > 0 && label[q - 1] >= 0) uf_unite(label, (int)p, (int)(q - 1), status);
+            if (label[q] >= 0) uf_unite(label, (int)p, (int)q, status);
+            if (x + 1 < n && label[q + 1] >= 0) uf_unite(label, (int)p, (int)(q + 1), status);
+        }
+    }
+}
+
+__global__ void ccl_flatten_kernel(int *label, size_t total, unsigned *status)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x)
+        if (label[p] >= 0) label[p] = uf_root(label, (int)p, status);   // only thread p writes entry p
+}
+
+__global__ void ccl_mark_kernel(int *label, const unsigned char *cls, size_t total)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x)
+        if (cls[p] == 2) atomicOr(&label[label[p] & kLabelMask], kFlag);
+}
+
+__global__ void ccl_output_kernel(const int *label, unsigned char *edges, size_t total)
+{
+    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
+        const int l = label[p];
+        edges[p] = (l >= 0 && (label[l & kLabelMask] & kFlag)) ? 1 : 0;
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Quadtree
+// ---------------------------------------------------------------------------
+__host__ __device__ constexpr long long level_base(int l) { return ((1LL << (2 * l)) - 1) / 3; }
+
+__device__ __forceinline__ unsigned compact1(unsigned long long v)   // even bits -> integer
+{
+    v &= 0x5555555555555555ULL;
+    v = (v | (v >> 1)) & 0x3333333333333333ULL;
+    v = (v | (v >> 2)) & 0x0f0f0f0f0f0f0f0fULL;
+    v = (v | (v >> 4)) & 0x00ff00ff00ff00ffULL;
+    v = (v | (v >> 8)) & 0x0000ffff0000ffffULL;
+    v = (v | (v >> 16)) & 0x00000000ffffffffULL;
+    return (unsigned)v;
+}
+
+struct TreeArgs {
+    const unsigned short *img;
+    const unsigned char *edges;
+    int n, P, L;                 // slice side, patch side, finest level (side P)
+    int *V;                      // [T] edge counts
+    long long *S1, *S2;          // [T] sums of codes and of squared codes
+    double *KE;                  // [Ns] monotone variance keys
+    ulonglong2 *K;               // [Ns] 128-bit keys (x = high word)
+    unsigned char *split;        // [Ns]
+    int *cnt, *off;              // [T] leaf counts, Z-order offsets
+    ulonglong2 *thr;             // [1] the M-th largest key
+    long long M;                 // splits
+    int length;
+    int *leaves;                 // [length][3]
+    unsigned *status;
+};
+
+__global__ void stats_leaf_kernel(TreeArgs a)
+{
+    const long long count = 1LL << (2 * a.L);
+    const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    const int X = (int)compact1((unsigned long long)m), Y = (int)compact1((unsigned long long)m >> 1);
+    const int x0 = X * a.P, y0 = Y * a.P;
+    int v = 0;
+    long long s1 = 0, s2 = 0;
+    for (int r = 0; r < a.P; ++r) {
+        const size_t row = (size_t)(y0 + r) * a.n + x0;
+        unsigned r1 = 0;
+        unsigned long long r2 = 0;
+        for (int c = 0; c < a.P; ++c) {
+            const unsigned x = a.img[row + c];
+            r1 += x;
+            r2 += (unsigned long long)x * x;
+            v += a.edges[row + c] ? 1 : 0;
+        }
+        s1 += r1;
+        s2 += (long long)r2;
+    }
+    const long long idx = level_base(a.L) + m;
+    a.V[idx] = v;
+    a.S1[idx] = s1;
+    a.S2[idx] = s2;
+}
+
+__global__ void stats_up_kernel(TreeArgs a, int l)
+{
+    const long long count = 1LL << (2 * l);
+    const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    const long long c0 = level_base(l + 1) + 4 * m, idx = level_base(l) + m;
+    a.V[idx] = a.V[c0] + a.V[c0 + 1] + a.V[c0 + 2] + a.V[c0 + 3];
+    a.S1[idx] = a.S1[c0] + a.S1[c0 + 1] + a.S1[c0 + 2] + a.S1[c0 + 3];
+    a.S2[idx] = a.S2[c0] + a.S2[c0 + 1] + a.S2[c0 + 2] + a.S2[c0 + 3];
+}
+
+// order-preserving map of a double to an unsigned integer
+__device__ __forceinline__ unsigned long long sortable(double d)
+{
+    const long long b = __double_as_longlong(d);
+    return b < 0 ? ~(unsigned long long)b : (unsigned long long)b | (1ULL << 63);
+}
+
+__global__ void keys_kernel(TreeArgs a, int l)
+{
+    const long long count = 1LL << (2 * l);
+    const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    const long long idx = level_base(l) + m;
+    const long long side = (long long)a.n >> l;
+    // d(S2) - d(S1) * d(S1) / d(n), each operation rounded once
+    const double s1 = __ll2double_rn(a.S1[idx]);
+    const double t = __ddiv_rn(__dmul_rn(s1, s1), __ll2double_rn(side * side));
+    double ke = __dsub_rn(__ll2double_rn(a.S2[idx]), t);
+    if (l > 0) ke = fmin(ke, a.KE[level_base(l - 1) + (m >> 2)]);
+    a.KE[idx] = ke;
+    const unsigned long long s = sortable(ke);
+    const unsigned long long mort = (unsigned long long)m << (2 * (a.L - l));   // corner in units of P
+    ulonglong2 k;
+    k.x = ((unsigned long long)a.V[idx] << 35) | (s >> 29);
+    k.y = ((s & ((1ULL << 29) - 1)) << 35) | ((unsigned long long)(15 - l) << 31) | (0x7fffffffULL - mort);
+    a.K[idx] = k;
+}
+
+// The M-th largest of the Ns keys, by MSB-first radix selection (8-bit
+// digits) in one block.
+__global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns)
+{
+    __shared__ unsigned hist[256];
+    __shared__ unsigned long long pre_x, pre_y, msk_x, msk_y;
+    __shared__ long long krem;
+    const int t = threadIdx.x;
+    if (t == 0) {
+        pre_x = pre_y = msk_x = msk_y = 0;
+        krem = a.M;
+    }
+    if (a.M <= 0) {
+        if (t == 0) *a.thr = make_ulonglong2(~0ULL, ~0ULL);   // above every key (their top bit is 0)
+        return;
+    }
+    for (int pass = 0; pass < 16; ++pass) {
+        for (int i = t; i < 256; i += 1024) hist[i] = 0;
+        __syncthreads();
+        const bool hi_word = pass < 8;
+        const int sh = 56 - 8 * (pass & 7);
+        const unsigned long long px = pre_x, py = pre_y, mx = msk_x, my = msk_y;
+        for (long long i = t; i < Ns; i += 1024) {
+            const ulonglong2 k = a.K[i];
+            if ((k.x & mx) == px && (k.y & my) == py)
+                atomicAdd(&hist[(unsigned)(((hi_word ? k.x : k.y) >> sh) & 0xff)], 1u);
+        }
+        __syncthreads();
+        if (t == 0) {
+            long long cum = 0;
+            int d = 255;
+            for (; d > 0; --d) {
+                if (cum + hist[d] >= krem) break;
+                cum += hist[d];
+            }
+            krem -= cum;
+            if (hi_word) {
+                pre_x |= (unsigned long long)d << sh;
+                msk_x |= 0xffULL << sh;
+            } else {
+                pre_y |= (unsigned long long)d << sh;
+                msk_y |= 0xffULL << sh;
+            }
+        }
+        __syncthreads();
+    }
+    if (t == 0) *a.thr = make_ulonglong2(pre_x, pre_y);
+}
+
+__device__ __forceinline__ bool key_ge(ulonglong2 k, ulonglong2 t)
+{
+    return k.x > t.x || (k.x == t.x && k.y >= t.y);
+}
+
+// bottom-up: split flags (levels < L) and leaf counts
+__global__ void counts_kernel(TreeArgs a, int l)
+{
+    const long long count = 1LL << (2 * l);
+    const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    const long long idx = level_base(l) + m;
+    if (l == a.L) {
+        a.cnt[idx] = 1;
+        return;
+    }
+    const bool sp = key_ge(a.K[idx], *a.thr);
+    a.split[idx] = sp ? 1 : 0;
+    const long long c0 = level_base(l + 1) + 4 * m;
+    a.cnt[idx] = sp ? a.cnt[c0] + a.cnt[c0 + 1] + a.cnt[c0 + 2] + a.cnt[c0 + 3] : 1;
+}
+
+// top-down: Z-order offsets, and the leaves' entries
+__global__ void offsets_kernel(TreeArgs a, int l)
+{
+    const long long count = 1LL << (2 * l);
+    const long long m = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (m >= count) return;
+    const long long idx = level_base(l) + m;
+    bool reached = true;
+    int o = 0;
+    if (l > 0) {
+        const long long pidx = level_base(l - 1) + (m >> 2);
+        reached = a.split[pidx] != 0;
+        o = a.off[pidx];
+        const long long c0 = level_base(l) + (m & ~3LL);
+        for (long long j = c0; j < idx; ++j) o += a.cnt[j];
+    }
+    a.off[idx] = o;
+    const bool leaf = reached && (l == a.L || a.split[idx] == 0);
+    if (!leaf) return;
+    if (o < 0 || o >= a.length) {
+        atomicCAS(a.status, 0u, FAULT_LEAF);
+        return;
+    }
+    const int s = a.n >> l;
+    a.leaves[3 * o + 0] = (int)compact1((unsigned long long)m) * s;
+    a.leaves[3 * o + 1] = (int)compact1((unsigned long long)m >> 1) * s;
+    a.leaves[3 * o + 2] = s;
+}
+
+__device__ __forceinline__ bool leaf_ok(int x0, int y0, int s, int n, int P)
+{
+    return s >= P && s <= n && (s & (s - 1)) == 0 && x0 >= 0 && y0 >= 0 && x0 % s == 0 && y0 % s == 0 &&
+           x0 <= n - s && y0 <= n - s;
+}
+
+// one thread per patch element: the mean of its f x f block
+__global__ void extract_kernel(TreeArgs a, float *patches)
+{
+    const int P = a.P;
+    const long long total = (long long)a.length * P * P;
+    const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    if (e >= total) return;
+    const int i = (int)(e / (P * P)), rc = (int)(e - (long long)i * P * P);
+    const int r = rc / P, c = rc - r * P;
+    const int x0 = a.leaves[3 * i], y0 = a.leaves[3 * i + 1], s = a.leaves[3 * i + 2];
+    if (!leaf_ok(x0, y0, s, a.n, P)) {
+        atomicCAS(a.status, 0u, FAULT_LEAF);
+        return;
+    }
+    const int f = s / P;
+    long long sum = 0;
+    for (int yy = 0; yy < f; ++yy) {
+        const unsigned short *row = a.img + (size_t)(y0 + r * f + yy) * a.n + x0 + c * f;
+        unsigned rs = 0;
+        for (int xx = 0; xx < f; ++xx) rs += row[xx];
+        sum += rs;
+    }
+    patches[e] = __double2float_rn(__ddiv_rn(__ll2double_rn(sum), __ll2double_rn((long long)f * f)));
+}
+
+// one block per (leaf, row phase): writes the leaf's packed bytes
+constexpr int kRowPhases = 16;
+__global__ void __launch_bounds__(256) depatch_pack_kernel(const unsigned char *mask, const int *leaves, int n,
+                                                          int P, unsigned char *packed, unsigned *status)
+{
+    const int i = blockIdx.x;
+    const int x0 = leaves[3 * i], y0 = leaves[3 * i + 1], s = leaves[3 * i + 2];
+    if (!leaf_ok(x0, y0, s, n, P)) {
+        if (threadIdx.x == 0 && blockIdx.y == 0) atomicCAS(status, 0u, FAULT_LEAF);
+        return;
+    }
+    const int f = s / P, nb = s / 4;
+    const unsigned char *mp = mask + (size_t)i * P * P;
+    for (int yy = blockIdx.y; yy < s; yy += kRowPhases) {
+        const unsigned char *prow = mp + (size_t)(yy / f) * P;
+        unsigned char *out = packed + (size_t)(y0 + yy) * (n / 4) + x0 / 4;
+        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+            unsigned b = 0;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) b |= (unsigned)(prow[(4 * k + q) / f] & 3) << (2 * q);
+            out[k] = (unsigned char)b;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+int log2i(int v)
+{
+    int l = 0;
+    while ((1 << l) < v) ++l;
+    return l;
+}
+
+fbp_status check_params(const sap_params *p)
+{
+    if (!p) return fail(FBP_ERR_INVALID_ARG, "params is NULL");
+    if (p->n < 16 || p->n > 16384 || (p->n & (p->n - 1)))
+        return fail(FBP_ERR_INVALID_ARG, "n = %d must be a power of two in [16, 16384]", p->n);
+    if (p->patch != 4 && p->patch != 8 && p->patch != 16 && p->patch != 32 && p->patch != 64)
+        return fail(FBP_ERR_INVALID_ARG, "patch = %d must be 4, 8, 16, 32 or 64", p->patch);
+    if (p->patch > p->n) return fail(FBP_ERR_INVALID_ARG, "patch %d > n %d", p->patch, p->n);
+    const long long cells = (long long)(p->n / p->patch) * (p->n / p->patch);
+    if (p->length < 1 || p->length > cells || (p->length - 1) % 3)
+        return fail(FBP_ERR_INVALID_ARG, "length %d must be 1 mod 3 and in [1, %lld]", p->length, cells);
+    if (p->canny_lo < 0 || p->canny_hi < p->canny_lo)
+        return fail(FBP_ERR_INVALID_ARG, "need 0 <= canny_lo <= canny_hi");
+    return FBP_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+struct Layout {
+    size_t label, cls, edges_end;                                  // sap_edges
+    size_t V, S1, S2, KE, K, split, cnt, off, thr, tree_end;       // sap_patches
+    long long T, Ns;
+    int L;
+};
+
+Layout layout(const sap_params &p)
+{
+    Layout o{};
+    const size_t px = (size_t)p.n * p.n;
+    o.label = 0;
+    o.cls = align256(px * 4);
+    o.edges_end = o.cls + align256(px);
+    o.L = log2i(p.n / p.patch);
+    o.T = level_base(o.L + 1);
+    o.Ns = level_base(o.L);
+    size_t q = 0;
+    o.V = q;     q += align256((size_t)o.T * 4);
+    o.S1 = q;    q += align256((size_t)o.T * 8);
+    o.S2 = q;    q += align256((size_t)o.T * 8);
+    o.KE = q;    q += align256((size_t)(o.Ns ? o.Ns : 1) * 8);
+    o.K = q;     q += align256((size_t)(o.Ns ? o.Ns : 1) * 16);
+    o.split = q; q += align256((size_t)(o.Ns ? o.Ns : 1));
+    o.cnt = q;   q += align256((size_t)o.T * 4);
+    o.off = q;   q += align256((size_t)o.T * 4);
+    o.thr = q;   q += 256;
+    o.tree_end = q;
+    return o;
+}
+
+fbp_status check_ws(void *ws, size_t bytes, size_t need)
+{
+    if (!ws) return fail(FBP_ERR_WORKSPACE, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(ws) & 255) return fail(FBP_ERR_WORKSPACE, "workspace is not 256-byte aligned");
+    if (bytes < need) return fail(FBP_ERR_WORKSPACE, "workspace has %zu bytes, needs %zu", bytes, need);
+    return FBP_OK;
+}
+
+unsigned grid_for(long long items, int threads)
+{
+    const long long g = (items + threads - 1) / threads;
+    return (unsigned)(g < 1 ? 1 : g);
+}
+
+template <typename F>
+fbp_status guarded(F &&f)
+{
+    clear_error();
+    try {
+        return f();
+    } catch (...) {
+        return fail(FBP_ERR_CUDA, "unexpected host exception");
+    }
+}
+
+}  // namespace
+}  // namespace fbp
+
+using namespace fbp;
+
+extern "C" {
+
+size_t sap_workspace_bytes(const sap_params *p)
+{
+    if (check_params(p) != FBP_OK) return 0;
+    const Layout o = layout(*p);
+    return o.edges_end > o.tree_end ? o.edges_end : o.tree_end;
+}
+
+fbp_status sap_edges(const unsigned short *slice, unsigned char *edges, const sap_params *p, void *workspace,
+                     size_t ws_bytes, fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        fbp_status st = check_params(p);
+        if (st != FBP_OK) return st;
+        if (!slice || !edges) return fail(FBP_ERR_INVALID_ARG, "slice or edges is NULL");
+        st = check_ws(workspace, ws_bytes, sap_workspace_bytes(p));
+        if (st != FBP_OK) return st;
+        unsigned *status = nullptr;
+        st = device_status_word(&status);
+        if (st != FBP_OK) return st;
+        const Layout o = layout(*p);
+        char *ws = static_cast<char *>(workspace);
+        int *label = reinterpret_cast<int *>(ws + o.label);
+        unsigned char *cls = reinterpret_cast<unsigned char *>(ws + o.cls);
+        const int n = p->n;
+        const size_t total = (size_t)n * n;
+        dim3 tiles((n + kTile - 1) / kTile, (n + kTile - 1) / kTile);
+        canny_kernel<<<tiles, 256, 0, stream>>>(slice, n, p->canny_lo, p->canny_hi, cls, label);
+        FBP_CUDA_TRY(cudaGetLastError());
+        const unsigned g = grid_for((long long)total, 256) > 152u * 16u ? 152u * 16u : grid_for((long long)total, 256);
+        ccl_merge_kernel<<<g, 256, 0, stream>>>(label, n, status);
+        FBP_CUDA_TRY(cudaGetLastError());
+        ccl_flatten_kernel<<<g, 256, 0, stream>>>(label, total, status);
+        FBP_CUDA_TRY(cudaGetLastError());
+        ccl_mark_kernel<<<g, 256, 0, stream>>>(label, cls, total);
+        FBP_CUDA_TRY(cudaGetLastError());
+        ccl_output_kernel<<<g, 256, 0, stream>>>(label, edges, total);
+        FBP_CUDA_TRY(cudaGetLastError());
+        return FBP_OK;
+    });
+}
+
+fbp_status sap_patches(const unsigned short *slice, const unsigned char *edges, float *patches, int *leaves,
+                       const sap_params *p, void *workspace, size_t ws_bytes, fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        fbp_status st = check_params(p);
+        if (st != FBP_OK) return st;
+        if (!slice || !edges || !patches || !leaves)
+            return fail(FBP_ERR_INVALID_ARG, "slice, edges, patches or leaves is NULL");
+        st = check_ws(workspace, ws_bytes, sap_workspace_bytes(p));
+        if (st != FBP_OK) return st;
+        unsigned *status = nullptr;
+        st = device_status_word(&status);
+        if (st != FBP_OK) return st;
+        const Layout o = layout(*p);
+        char *ws = static_cast<char *>(workspace);
+        TreeArgs a;
+        a.img = slice;
+        a.edges = edges;
+        a.n = p->n;
+        a.P = p->patch;
+        a.L = o.L;
+        a.V = reinterpret_cast<int *>(ws + o.V);
+        a.S1 = reinterpret_cast<long long *>(ws + o.S1);
+        a.S2 = reinterpret_cast<long long *>(ws + o.S2);
+        a.KE = reinterpret_cast<double *>(ws + o.KE);
+        a.K = reinterpret_cast<ulonglong2 *>(ws + o.K);
+        a.split = reinterpret_cast<unsigned char *>(ws + o.split);
+        a.cnt = reinterpret_cast<int *>(ws + o.cnt);
+        a.off = reinterpret_cast<int *>(ws + o.off);
+        a.thr = reinterpret_cast<ulonglong2 *>(ws + o.thr);
+        a.M = (p->length - 1) / 3;
+        a.length = p->length;
+        a.leaves = leaves;
+        a.status = status;
+        const int L = o.L;
+        stats_leaf_kernel<<<grid_for(1LL << (2 * L), 256), 256, 0, stream>>>(a);
+        FBP_CUDA_TRY(cudaGetLastError());
+        for (int l = L - 1; l >= 0; --l) {
+            stats_up_kernel<<<grid_for(1LL << (2 * l), 256), 256, 0, stream>>>(a, l);
+            FBP_CUDA_TRY(cudaGetLastError());
+        }
+        for (int l = 0; l < L; ++l) {
+            keys_kernel<<<grid_for(1LL << (2 * l), 256), 256, 0, stream>>>(a, l);
+            FBP_CUDA_TRY(cudaGetLastError());
+        }
+        select_kernel<<<1, 1024, 0, stream>>>(a, o.Ns);
+        FBP_CUDA_TRY(cudaGetLastError());
+        for (int l = L; l >= 0; --l) {
+            counts_kernel<<<grid_for(1LL << (2 * l), 256), 256, 0, stream>>>(a, l);
+            FBP_CUDA_TRY(cudaGetLastError());
+        }
+        for (int l = 0; l <= L; ++l) {
+            offsets_kernel<<<grid_for(1LL << (2 * l), 256), 256, 0, stream>>>(a, l);
+            FBP_CUDA_TRY(cudaGetLastError());
+        }
+        extract_kernel<<<grid_for((long long)p->length * p->patch * p->patch, 256), 256, 0, stream>>>(a, patches);
+        FBP_CUDA_TRY(cudaGetLastError());
+        return FBP_OK;
+    });
+}
+
+fbp_status sap_depatch_pack(const unsigned char *mask_patches, const int *leaves, unsigned char *packed,
+                            const sap_params *p, fbp_stream_t stream)
+{
+    return guarded([&]() -> fbp_status {
+        fbp_status st = check_params(p);
+        if (st != FBP_OK) return st;
+        if (!mask_patches || !leaves || !packed)
+            return fail(FBP_ERR_INVALID_ARG, "mask_patches, leaves or packed is NULL");
+        unsigned *status = nullptr;
+        st = device_status_word(&status);
+        if (st != FBP_OK) return st;
+        dim3 grid((unsigned)p->length, kRowPhases);
+        depatch_pack_kernel<<<grid, 256, 0, stream>>>(mask_patches, leaves, p->n, p->patch, packed, status);
+        FBP_CUDA_TRY(cudaGetLastError());
+        return FBP_OK;
+    });
+}
+
+}  // extern "C"

@@ -248,6 +248,8 @@ WORKLOADS = {
     "fbp_mixed_batch": Workload("fbp_mixed_batch", 200, 0, 0, "ramlak", "random", None, 8,
                                 ragged=True, n_choices=(512, 1024, 2048, 4096),
                                 k_choices=(720, 1800, 3600), offset_fraction=1.0 / 3.0),
+    # adaptive patching of reconstructed 8192^2 slices (sap_slice, SAP)
+    "sap_patching_n8192": Workload("sap_patching_n8192", 16, 8192, 0, "", "random", None, 9),
 }
 
 
@@ -287,6 +289,27 @@ def scan_sinogram(spec: dict, dtype=np.float32) -> np.ndarray:
     """Noise-free analytic rows [n_angles, n_det] of a scan_spec item."""
     return sinogram(spec["ell"], spec["n_angles"], spec["n_det"], spec["n"],
                     angle_step=spec["angle_step"], det_center=spec["det_center"], dtype=dtype)
+
+
+# Adaptive patching of reconstructed slices (Sec. V-B(c)): the stage-4
+# output is a slice of uint16 codes.  Synthetic stand-in: a random-ellipse
+# phantom rasterised at n pixels, densities mapped linearly to codes
+# (SAP_CODES: code = offset + scale * density), plus Gaussian noise of
+# sigma codes, rounded and clipped to [0, 65535].
+SAP_CODES = {"offset": 8000.0, "scale": 20000.0, "sigma": 150.0}
+# Patching parameters of the workload (the paper fixes none): patch side,
+# sequence length (1 mod 3), Canny thresholds on M = |gx| + |gy|.
+SAP = {"patch": 16, "length": 4096, "canny_lo": 400000, "canny_hi": 1000000}
+
+
+def sap_slice(n: int, seed: int) -> np.ndarray:
+    """uint16 codes [n, n] of a seeded random-ellipse slice (see SAP_CODES)."""
+    rng = rng_for(seed)
+    ell = random_ellipses(rng)
+    dens = image(ell, n)
+    c = SAP_CODES
+    x = c["offset"] + c["scale"] * dens + rng.normal(0.0, c["sigma"], dens.shape)
+    return np.clip(np.rint(x), 0, 65535).astype(np.uint16)
 
 
 def slice_counts(w: Workload, i: int) -> np.ndarray:

@@ -20,7 +20,8 @@ def L():
 
 
 def declared_functions():
-    src = open(os.path.join(ROOT, "include", "fbp.h")).read()
+    inc = os.path.join(ROOT, "include")
+    src = "".join(open(os.path.join(inc, f)).read() for f in sorted(os.listdir(inc)) if f.endswith(".h"))
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     names = re.findall(r"^[A-Za-z_][\w \*]*?\b(\w+)\s*\(", src, flags=re.M)
     return sorted(set(n for n in names if n not in ("if", "sizeof")))

@@ -82,6 +82,62 @@ def test_hysteresis_keeps_weak_chains_touching_a_strong_pixel():
     assert set(zip(*np.nonzero(e))) == {(2, 1), (3, 2), (4, 3), (4, 4), (5, 5), (0, 10)}
 
 
+def nms_loops(gx, gy, lo, hi):
+    """Brute force: the suppression rule pixel by pixel."""
+    m = np.abs(gx) + np.abs(gy)
+    n0, n1 = m.shape
+    out = np.zeros((n0, n1), dtype=np.uint8)
+    for r in range(n0):
+        for c in range(n1):
+            if m[r, c] <= lo:
+                continue
+            ax, ay = abs(int(gx[r, c])), abs(int(gy[r, c]))
+            if ay * 32768 <= 13573 * ax:
+                d = (0, 1)
+            elif ay * 32768 >= 79109 * ax:
+                d = (1, 0)
+            elif (gx[r, c] > 0) == (gy[r, c] > 0):
+                d = (1, 1)
+            else:
+                d = (1, -1)
+            mag = [m[rr, cc] if 0 <= rr < n0 and 0 <= cc < n1 else 0
+                   for rr, cc in ((r - d[0], c - d[1]), (r + d[0], c + d[1]))]
+            if m[r, c] > mag[0] and m[r, c] >= mag[1]:
+                out[r, c] = 2 if m[r, c] > hi else 1
+    return out
+
+
+def hysteresis_bfs(cls):
+    """Brute force: grow from every strong pixel through weak 8-neighbours."""
+    n0, n1 = cls.shape
+    edge = np.zeros((n0, n1), dtype=np.uint8)
+    stack = [(int(r), int(c)) for r, c in zip(*np.nonzero(cls == 2))]
+    for r, c in stack:
+        edge[r, c] = 1
+    while stack:
+        r, c = stack.pop()
+        for dr in (-1, 0, 1):
+            for dc in (-1, 0, 1):
+                rr, cc = r + dr, c + dc
+                if 0 <= rr < n0 and 0 <= cc < n1 and not edge[rr, cc] and cls[rr, cc] == 1:
+                    edge[rr, cc] = 1
+                    stack.append((rr, cc))
+    return edge
+
+
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_vectorised_suppression_and_labelling_equal_brute_force(seed):
+    img = random_slice(48, seed)
+    gx, gy = sap.sobel(sap.smooth(img))
+    m = np.abs(gx) + np.abs(gy)
+    lo, hi = int(np.percentile(m, 60)), int(np.percentile(m, 90))
+    cls = sap.nms_classes(gx, gy, lo, hi)
+    np.testing.assert_array_equal(cls, nms_loops(gx, gy, lo, hi))
+    np.testing.assert_array_equal(sap.hysteresis(cls), hysteresis_bfs(cls))
+    e = sap.hysteresis(cls)
+    assert np.all(e[cls == 2] == 1) and np.all(e[cls == 0] == 0) and (cls == 2).sum() > 0
+
+
 def test_morton_interleave():
     assert [sap.morton(x, y) for x, y in [(0, 0), (1, 0), (0, 1), (1, 1), (2, 0), (3, 5)]] == [0, 1, 2, 3, 4, 39]
 
