@@ -43,34 +43,56 @@ constexpr int kLabelMask = kFlag - 1;
 __device__ __forceinline__ int clampi(int v, int hi) { return v < 0 ? 0 : v > hi ? hi : v; }
 
 // ---------------------------------------------------------------------------
-// Canny: classes (0 none, 1 weak, 2 strong) and the initial labels
+// Canny: classes (0 none, 1 weak, 2 strong), the edge map cleared, and the
+// candidates appended to a list with their labels initialised
 // ---------------------------------------------------------------------------
-__global__ void __launch_bounds__(256) canny_kernel(const unsigned short *__restrict__ img, int n, int lo,
-                                                   int hi, unsigned char *__restrict__ cls,
-                                                   int *__restrict__ label)
-{
-    // every array is indexed by (y - (ty0 - 4), x - (tx0 - 4)) and holds the
-    // stage's value at the clamped coordinate (clamp(y), clamp(x))
-    __shared__ int IN[kSpan][kSpan];
-    __shared__ int HH[kSpan][kSpan];
-    __shared__ int SS[kSpan][kSpan];
-    __shared__ int GX[kSpan][kSpan], GY[kSpan][kSpan], MM[kSpan][kSpan];
-    const int ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
-    const int oy = ty0 - kHalo, ox = tx0 - kHalo, nm = n - 1;
-    const int t = threadIdx.x;
-    // index of the clamped coordinate
-    auto iy = [&](int y) { return clampi(y, nm) - oy; };
-    auto ix = [&](int x) { return clampi(x, nm) - ox; };
+template <bool CLAMP>
+__device__ __forceinline__ int cl(int v, int nm) { return CLAMP ? clampi(v, nm) : v; }
 
-    for (int i = t; i < kSpan * kSpan; i += 256) {
-        const int r = i / kSpan, c = i - r * kSpan;
-        IN[r][c] = img[(size_t)clampi(oy + r, nm) * n + clampi(ox + c, nm)];
+struct CannyArgs {
+    const unsigned short *img;
+    int n, lo, hi;
+    int vec;                     // img is 8-byte aligned: interior tiles load 4 codes at a time
+    unsigned char *cls, *edges;
+    int *label, *list, *count;
+};
+
+// every staged array is indexed by (y - (ty0 - 4), x - (tx0 - 4)) and holds
+// the stage's value at the clamped coordinate (clamp(y), clamp(x)); in an
+// interior tile (CLAMP false) no coordinate needs clamping
+template <bool CLAMP>
+__device__ __forceinline__ void canny_tile(const CannyArgs &a, int (*IN)[kSpan], int (*HH)[kSpan],
+                                           int (*SS)[kSpan], int (*GX)[kSpan], int (*GY)[kSpan],
+                                           int (*MM)[kSpan])
+{
+    const int n = a.n, nm = n - 1;
+    const int ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
+    const int oy = ty0 - kHalo, ox = tx0 - kHalo;
+    const int t = threadIdx.x, lane = t & 31;
+    auto iy = [&](int y) { return cl<CLAMP>(y, nm) - oy; };
+    auto ix = [&](int x) { return cl<CLAMP>(x, nm) - ox; };
+
+    if (CLAMP) {
+        for (int i = t; i < kSpan * kSpan; i += 256) {
+            const int r = i / kSpan, c = i - r * kSpan;
+            IN[r][c] = a.img[(size_t)clampi(oy + r, nm) * n + clampi(ox + c, nm)];
+        }
+    } else {
+        // rows of 40 codes from an 8-byte aligned start (ox = 32 bx - 4): 10 x 8 bytes
+        for (int i = t; i < kSpan * (kSpan / 4); i += 256) {
+            const int r = i / (kSpan / 4), c4 = i - r * (kSpan / 4);
+            const uint2 v = *reinterpret_cast<const uint2 *>(a.img + (size_t)(oy + r) * n + ox + 4 * c4);
+            IN[r][4 * c4 + 0] = (int)(v.x & 0xffffu);
+            IN[r][4 * c4 + 1] = (int)(v.x >> 16);
+            IN[r][4 * c4 + 2] = (int)(v.y & 0xffffu);
+            IN[r][4 * c4 + 3] = (int)(v.y >> 16);
+        }
     }
     __syncthreads();
     // horizontal binomial, columns needed by the vertical pass: [2, 38)
     for (int i = t; i < kSpan * (kSpan - 4); i += 256) {
         const int r = i / (kSpan - 4), c = 2 + i % (kSpan - 4);
-        const int x = clampi(ox + c, nm);
+        const int x = cl<CLAMP>(ox + c, nm);
         HH[r][c] = IN[r][ix(x - 2)] + 4 * IN[r][ix(x - 1)] + 6 * IN[r][ix(x)] + 4 * IN[r][ix(x + 1)] +
                    IN[r][ix(x + 2)];
     }
@@ -78,7 +100,7 @@ __global__ void __launch_bounds__(256) canny_kernel(const unsigned short *__rest
     // vertical binomial on [2, 38) x [2, 38)
     for (int i = t; i < (kSpan - 4) * (kSpan - 4); i += 256) {
         const int r = 2 + i / (kSpan - 4), c = 2 + i % (kSpan - 4);
-        const int y = clampi(oy + r, nm);
+        const int y = cl<CLAMP>(oy + r, nm);
         SS[r][c] = HH[iy(y - 2)][c] + 4 * HH[iy(y - 1)][c] + 6 * HH[iy(y)][c] + 4 * HH[iy(y + 1)][c] +
                    HH[iy(y + 2)][c];
     }
@@ -86,7 +108,7 @@ __global__ void __launch_bounds__(256) canny_kernel(const unsigned short *__rest
     // Sobel and L1 magnitude on [3, 37) x [3, 37)
     for (int i = t; i < (kSpan - 6) * (kSpan - 6); i += 256) {
         const int r = 3 + i / (kSpan - 6), c = 3 + i % (kSpan - 6);
-        const int y = clampi(oy + r, nm), x = clampi(ox + c, nm);
+        const int y = cl<CLAMP>(oy + r, nm), x = cl<CLAMP>(ox + c, nm);
         const int ym = iy(y - 1), y0 = iy(y), yp = iy(y + 1);
         const int xm = ix(x - 1), x0 = ix(x), xp = ix(x + 1);
         const int gx = (SS[ym][xp] + 2 * SS[y0][xp] + SS[yp][xp]) - (SS[ym][xm] + 2 * SS[y0][xm] + SS[yp][xm]);
@@ -96,14 +118,15 @@ __global__ void __launch_bounds__(256) canny_kernel(const unsigned short *__rest
         MM[r][c] = abs(gx) + abs(gy);
     }
     __syncthreads();
-    // non-maximum suppression and thresholds on the tile
+    // non-maximum suppression and thresholds on the tile; every thread runs
+    // all four rounds (1024 pixels / 256 threads) so the warp votes are full
     for (int i = t; i < kTile * kTile; i += 256) {
         const int r = kHalo + i / kTile, c = kHalo + i % kTile;
         const int y = oy + r, x = ox + c;
-        if (y >= n || x >= n) continue;
-        const int m = MM[r][c];
+        const bool inside = y < n && x < n;
         unsigned char k = 0;
-        if (m > lo) {
+        const int m = MM[r][c];
+        if (inside && m > a.lo) {
             const int gx = GX[r][c], gy = GY[r][c];
             const long long ax = abs(gx), ay = abs(gy);
             int dy, dx;
@@ -114,12 +137,35 @@ __global__ void __launch_bounds__(256) canny_kernel(const unsigned short *__rest
             const int py = y - dy, px = x - dx, qy = y + dy, qx = x + dx;
             const int prev = (py >= 0 && py < n && px >= 0 && px < n) ? MM[r - dy][c - dx] : 0;
             const int next = (qy >= 0 && qy < n && qx >= 0 && qx < n) ? MM[r + dy][c + dx] : 0;
-            if (m > prev && m >= next) k = m > hi ? 2 : 1;
+            if (m > prev && m >= next) k = m > a.hi ? 2 : 1;
         }
         const size_t p = (size_t)y * n + x;
-        cls[p] = k;
-        label[p] = k ? (int)p : -1;
+        if (inside) {
+            a.cls[p] = k;
+            a.edges[p] = 0;
+        }
+        const unsigned vote = __ballot_sync(0xffffffffu, k != 0);
+        int base = 0;
+        if (lane == 0 && vote) base = atomicAdd(a.count, __popc(vote));
+        base = __shfl_sync(0xffffffffu, base, 0);
+        if (k) {
+            a.list[base + __popc(vote & ((1u << lane) - 1))] = (int)p;
+            a.label[p] = (int)p;
+        }
     }
+}
+
+__global__ void __launch_bounds__(256) canny_kernel(CannyArgs a)
+{
+    __shared__ int IN[kSpan][kSpan];
+    __shared__ int HH[kSpan][kSpan];
+    __shared__ int SS[kSpan][kSpan];
+    __shared__ int GX[kSpan][kSpan], GY[kSpan][kSpan], MM[kSpan][kSpan];
+    const int oy = (int)blockIdx.y * kTile - kHalo, ox = (int)blockIdx.x * kTile - kHalo;
+    if (a.vec && oy >= 0 && ox >= 0 && oy + kSpan <= a.n && ox + kSpan <= a.n)
+        canny_tile<false>(a, IN, HH, SS, GX, GY, MM);
+    else
+        canny_tile<true>(a, IN, HH, SS, GX, GY, MM);
 }
 
 // ---------------------------------------------------------------------------
@@ -168,40 +214,49 @@ __device__ __forceinline__ void uf_unite(int *L, int a, int b, unsigned *status)
     atomicCAS(status, 0u, FAULT_UNION_CAP);
 }
 
-__global__ void ccl_merge_kernel(int *label, int n, unsigned *status)
+// The passes below visit the candidates only (the list canny_kernel wrote).
+__global__ void ccl_merge_kernel(const int *list, const int *count, const unsigned char *cls, int *label,
+                                 int n, unsigned *status)
 {
-    const size_t total = (size_t)n * n;
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
-        if (label[p] < 0) continue;
-        const int y = (int)(p / n), x = (int)(p - (size_t)y * n);
+    const int c = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+        const int p = list[i];
+        const int y = p / n, x = p - y * n;
         // forward neighbours: right, down-left, down, down-right
-        if (x + 1 < n && label[p + 1] >= 0) uf_unite(label, (int)p, (int)p + 1, status);
+        if (x + 1 < n && cls[p + 1]) uf_unite(label, p, p + 1, status);
         if (y + 1 < n) {
-            const size_t q = p + n;
-            if (x > 0 && label[q - 1] >= 0) uf_unite(label, (int)p, (int)(q - 1), status);
-            if (label[q] >= 0) uf_unite(label, (int)p, (int)q, status);
-            if (x + 1 < n && label[q + 1] >= 0) uf_unite(label, (int)p, (int)(q + 1), status);
+            const int q = p + n;
+            if (x > 0 && cls[q - 1]) uf_unite(label, p, q - 1, status);
+            if (cls[q]) uf_unite(label, p, q, status);
+            if (x + 1 < n && cls[q + 1]) uf_unite(label, p, q + 1, status);
         }
     }
 }
 
-__global__ void ccl_flatten_kernel(int *label, size_t total, unsigned *status)
+__global__ void ccl_flatten_kernel(const int *list, const int *count, int *label, unsigned *status)
 {
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x)
-        if (label[p] >= 0) label[p] = uf_root(label, (int)p, status);   // only thread p writes entry p
+    const int c = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+        const int p = list[i];
+        label[p] = uf_root(label, p, status);      // only this thread writes entry p
+    }
 }
 
-__global__ void ccl_mark_kernel(int *label, const unsigned char *cls, size_t total)
+__global__ void ccl_mark_kernel(const int *list, const int *count, const unsigned char *cls, int *label)
 {
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x)
+    const int c = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+        const int p = list[i];
         if (cls[p] == 2) atomicOr(&label[label[p] & kLabelMask], kFlag);
+    }
 }
 
-__global__ void ccl_output_kernel(const int *label, unsigned char *edges, size_t total)
+__global__ void ccl_output_kernel(const int *list, const int *count, const int *label, unsigned char *edges)
 {
-    for (size_t p = blockIdx.x * (size_t)blockDim.x + threadIdx.x; p < total; p += (size_t)gridDim.x * blockDim.x) {
-        const int l = label[p];
-        edges[p] = (l >= 0 && (label[l & kLabelMask] & kFlag)) ? 1 : 0;
+    const int c = *count;
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < c; i += gridDim.x * blockDim.x) {
+        const int p = list[i];
+        if (label[label[p] & kLabelMask] & kFlag) edges[p] = 1;
     }
 }
 
@@ -306,52 +361,85 @@ __global__ void keys_kernel(TreeArgs a, int l)
 }
 
 // The M-th largest of the Ns keys, by MSB-first radix selection (8-bit
-// digits) in one block.
-__global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns)
+// digits) in one block: each pass counts the digit of every remaining key
+// (per-warp histograms, one atomic per distinct digit in a warp), picks the
+// digit holding the M-th largest, and copies the keys with that digit to the
+// other buffer, so later passes see only the keys that can still be it.
+__device__ __forceinline__ unsigned digit_of(ulonglong2 k, int pass)
 {
-    __shared__ unsigned hist[256];
-    __shared__ unsigned long long pre_x, pre_y, msk_x, msk_y;
-    __shared__ long long krem;
-    const int t = threadIdx.x;
-    if (t == 0) {
-        pre_x = pre_y = msk_x = msk_y = 0;
-        krem = a.M;
-    }
+    const int sh = 56 - 8 * (pass & 7);
+    return (unsigned)(((pass < 8 ? k.x : k.y) >> sh) & 0xff);
+}
+
+__global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns, ulonglong2 *bufB,
+                                                      ulonglong2 *bufC)
+{
+    __shared__ unsigned hist[32][256];
+    __shared__ unsigned tot[256];
+    __shared__ unsigned s_digit, s_next, s_pos;
+    __shared__ long long s_krem;
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     if (a.M <= 0) {
         if (t == 0) *a.thr = make_ulonglong2(~0ULL, ~0ULL);   // above every key (their top bit is 0)
         return;
     }
+    if (t == 0) s_krem = a.M;
+    const ulonglong2 *src = a.K;
+    ulonglong2 *dst = bufB;
+    long long cnt = Ns;
+    unsigned long long tx = 0, ty = 0;
     for (int pass = 0; pass < 16; ++pass) {
-        for (int i = t; i < 256; i += 1024) hist[i] = 0;
+        for (int i = t; i < 32 * 256; i += 1024) (&hist[0][0])[i] = 0;
         __syncthreads();
-        const bool hi_word = pass < 8;
-        const int sh = 56 - 8 * (pass & 7);
-        const unsigned long long px = pre_x, py = pre_y, mx = msk_x, my = msk_y;
-        for (long long i = t; i < Ns; i += 1024) {
-            const ulonglong2 k = a.K[i];
-            if ((k.x & mx) == px && (k.y & my) == py)
-                atomicAdd(&hist[(unsigned)(((hi_word ? k.x : k.y) >> sh) & 0xff)], 1u);
+        // every warp runs the same number of rounds, so the warp-wide votes see all lanes
+        for (long long b0 = 0; b0 < cnt; b0 += 1024) {
+            const long long i = b0 + t;
+            const bool valid = i < cnt;
+            const unsigned d = valid ? digit_of(src[i], pass) : 256u;
+            const unsigned same = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == __ffs(same) - 1) atomicAdd(&hist[warp][d], __popc(same));
+        }
+        __syncthreads();
+        if (t < 256) {
+            unsigned v = 0;
+            for (int w = 0; w < 32; ++w) v += hist[w][t];
+            tot[t] = v;
         }
         __syncthreads();
         if (t == 0) {
             long long cum = 0;
             int d = 255;
             for (; d > 0; --d) {
-                if (cum + hist[d] >= krem) break;
-                cum += hist[d];
+                if (cum + tot[d] >= s_krem) break;
+                cum += tot[d];
             }
-            krem -= cum;
-            if (hi_word) {
-                pre_x |= (unsigned long long)d << sh;
-                msk_x |= 0xffULL << sh;
-            } else {
-                pre_y |= (unsigned long long)d << sh;
-                msk_y |= 0xffULL << sh;
-            }
+            s_krem -= cum;
+            s_digit = (unsigned)d;
+            s_next = tot[d];
+            s_pos = 0;
         }
         __syncthreads();
+        const unsigned d = s_digit;
+        if (pass < 8) tx |= (unsigned long long)d << (56 - 8 * pass);
+        else ty |= (unsigned long long)d << (56 - 8 * (pass - 8));
+        if (pass == 15) break;
+        for (long long b0 = 0; b0 < cnt; b0 += 1024) {
+            const long long i = b0 + t;
+            const bool valid = i < cnt;
+            const ulonglong2 k = valid ? src[i] : make_ulonglong2(0, 0);
+            const bool keep = valid && digit_of(k, pass) == d;
+            const unsigned vote = __ballot_sync(0xffffffffu, keep);
+            unsigned base = 0;
+            if (lane == 0 && vote) base = atomicAdd(&s_pos, __popc(vote));
+            base = __shfl_sync(0xffffffffu, base, 0);
+            if (keep) dst[base + __popc(vote & ((1u << lane) - 1))] = k;
+        }
+        __syncthreads();
+        cnt = s_next;
+        src = dst;
+        dst = dst == bufB ? bufC : bufB;
     }
-    if (t == 0) *a.thr = make_ulonglong2(pre_x, pre_y);
+    if (t == 0) *a.thr = make_ulonglong2(tx, ty);
 }
 
 __device__ __forceinline__ bool key_ge(ulonglong2 k, ulonglong2 t)
@@ -411,7 +499,20 @@ __device__ __forceinline__ bool leaf_ok(int x0, int y0, int s, int n, int P)
            x0 <= n - s && y0 <= n - s;
 }
 
-// one thread per patch element: the mean of its f x f block
+__device__ __forceinline__ unsigned long long spread1(unsigned v)      // integer -> even bits
+{
+    unsigned long long x = v;
+    x = (x | (x << 16)) & 0x0000ffff0000ffffULL;
+    x = (x | (x << 8)) & 0x00ff00ff00ff00ffULL;
+    x = (x | (x << 4)) & 0x0f0f0f0f0f0f0f0fULL;
+    x = (x | (x << 2)) & 0x3333333333333333ULL;
+    x = (x | (x << 1)) & 0x5555555555555555ULL;
+    return x;
+}
+
+// one thread per patch element: the mean of its f x f block.  A block of
+// side f >= P is a quadtree node, whose exact sum S1 is already in the
+// pyramid; smaller blocks (f < P) are summed from the codes.
 __global__ void extract_kernel(TreeArgs a, float *patches)
 {
     const int P = a.P;
@@ -427,19 +528,29 @@ __global__ void extract_kernel(TreeArgs a, float *patches)
     }
     const int f = s / P;
     long long sum = 0;
-    for (int yy = 0; yy < f; ++yy) {
-        const unsigned short *row = a.img + (size_t)(y0 + r * f + yy) * a.n + x0 + c * f;
-        unsigned rs = 0;
-        for (int xx = 0; xx < f; ++xx) rs += row[xx];
-        sum += rs;
+    if (f >= P) {
+        const int lf = (__ffs(a.n) - 1) - (__ffs(f) - 1);          // level whose side is f
+        const unsigned bx = (unsigned)(x0 / f + c), by = (unsigned)(y0 / f + r);
+        sum = a.S1[level_base(lf) + (long long)(spread1(bx) | (spread1(by) << 1))];
+    } else {
+        for (int yy = 0; yy < f; ++yy) {
+            const unsigned short *row = a.img + (size_t)(y0 + r * f + yy) * a.n + x0 + c * f;
+            unsigned rs = 0;
+            for (int xx = 0; xx < f; ++xx) rs += row[xx];
+            sum += rs;
+        }
     }
     patches[e] = __double2float_rn(__ddiv_rn(__ll2double_rn(sum), __ll2double_rn((long long)f * f)));
 }
 
-// one block per (leaf, row phase): writes the leaf's packed bytes
-constexpr int kRowPhases = 16;
-__global__ void __launch_bounds__(256) depatch_pack_kernel(const unsigned char *mask, const int *leaves, int n,
-                                                          int P, unsigned char *packed, unsigned *status)
+// one block per (leaf, row phase): writes the leaf's packed bytes, a 4-byte
+// word (16 pixels) at a time where the leaf is at least 16 pixels wide.
+// f = s / P is a power of two, so patch coordinates are shifts; where
+// f >= 16 one patch value covers the whole word.
+constexpr int kRowPhases = 4;
+__global__ void __launch_bounds__(128) depatch_pack_kernel(const unsigned char *mask, const int *leaves, int n,
+                                                          int P, unsigned char *packed, int words,
+                                                          unsigned *status)
 {
     const int i = blockIdx.x;
     const int x0 = leaves[3 * i], y0 = leaves[3 * i + 1], s = leaves[3 * i + 2];
@@ -447,16 +558,35 @@ __global__ void __launch_bounds__(256) depatch_pack_kernel(const unsigned char *
         if (threadIdx.x == 0 && blockIdx.y == 0) atomicCAS(status, 0u, FAULT_LEAF);
         return;
     }
-    const int f = s / P, nb = s / 4;
+    const int by = blockIdx.y;
+    if (by >= s) return;
+    const int lf = (__ffs(s) - 1) - (__ffs(P) - 1);             // log2 f
+    const int rows = (s - by + kRowPhases - 1) / kRowPhases;     // rows by, by + 4, ... < s
     const unsigned char *mp = mask + (size_t)i * P * P;
-    for (int yy = blockIdx.y; yy < s; yy += kRowPhases) {
-        const unsigned char *prow = mp + (size_t)(yy / f) * P;
-        unsigned char *out = packed + (size_t)(y0 + yy) * (n / 4) + x0 / 4;
-        for (int k = threadIdx.x; k < nb; k += blockDim.x) {
+    if (words && s >= 16) {
+        const int wpr = s >> 4;
+        for (int it = threadIdx.x; it < rows * wpr; it += blockDim.x) {
+            const int yy = by + kRowPhases * (it / wpr), w = it % wpr;
+            const unsigned char *prow = mp + (size_t)(yy >> lf) * P;
+            unsigned v;
+            if (lf >= 4) {
+                v = (unsigned)(prow[(16 * w) >> lf] & 3) * 0x55555555u;     // one value, 16 copies
+            } else {
+                v = 0;
+#pragma unroll
+                for (int q = 0; q < 16; ++q) v |= (unsigned)(prow[(16 * w + q) >> lf] & 3) << (2 * q);
+            }
+            *reinterpret_cast<unsigned *>(packed + (size_t)(y0 + yy) * (n / 4) + x0 / 4 + 4 * w) = v;
+        }
+    } else {
+        const int bpr = s / 4;
+        for (int it = threadIdx.x; it < rows * bpr; it += blockDim.x) {
+            const int yy = by + kRowPhases * (it / bpr), k = it % bpr;
+            const unsigned char *prow = mp + (size_t)(yy >> lf) * P;
             unsigned b = 0;
 #pragma unroll
-            for (int q = 0; q < 4; ++q) b |= (unsigned)(prow[(4 * k + q) / f] & 3) << (2 * q);
-            out[k] = (unsigned char)b;
+            for (int q = 0; q < 4; ++q) b |= (unsigned)(prow[(4 * k + q) >> lf] & 3) << (2 * q);
+            packed[(size_t)(y0 + yy) * (n / 4) + x0 / 4 + k] = (unsigned char)b;
         }
     }
 }
@@ -490,8 +620,8 @@ fbp_status check_params(const sap_params *p)
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct Layout {
-    size_t label, cls, edges_end;                                  // sap_edges
-    size_t V, S1, S2, KE, K, split, cnt, off, thr, tree_end;       // sap_patches
+    size_t label, cls, list, count, edges_end;                     // sap_edges
+    size_t V, S1, S2, KE, K, KB, KC, split, cnt, off, thr, tree_end;   // sap_patches
     long long T, Ns;
     int L;
 };
@@ -501,8 +631,10 @@ Layout layout(const sap_params &p)
     Layout o{};
     const size_t px = (size_t)p.n * p.n;
     o.label = 0;
-    o.cls = align256(px * 4);
-    o.edges_end = o.cls + align256(px);
+    o.list = align256(px * 4);
+    o.cls = o.list + align256(px * 4);
+    o.count = o.cls + align256(px);
+    o.edges_end = o.count + 256;
     o.L = log2i(p.n / p.patch);
     o.T = level_base(o.L + 1);
     o.Ns = level_base(o.L);
@@ -512,6 +644,8 @@ Layout layout(const sap_params &p)
     o.S2 = q;    q += align256((size_t)o.T * 8);
     o.KE = q;    q += align256((size_t)(o.Ns ? o.Ns : 1) * 8);
     o.K = q;     q += align256((size_t)(o.Ns ? o.Ns : 1) * 16);
+    o.KB = q;    q += align256((size_t)(o.Ns ? o.Ns : 1) * 16);
+    o.KC = q;    q += align256((size_t)(o.Ns ? o.Ns : 1) * 16);
     o.split = q; q += align256((size_t)(o.Ns ? o.Ns : 1));
     o.cnt = q;   q += align256((size_t)o.T * 4);
     o.off = q;   q += align256((size_t)o.T * 4);
@@ -573,21 +707,30 @@ fbp_status sap_edges(const unsigned short *slice, unsigned char *edges, const sa
         if (st != FBP_OK) return st;
         const Layout o = layout(*p);
         char *ws = static_cast<char *>(workspace);
-        int *label = reinterpret_cast<int *>(ws + o.label);
-        unsigned char *cls = reinterpret_cast<unsigned char *>(ws + o.cls);
+        CannyArgs ca;
+        ca.img = slice;
+        ca.n = p->n;
+        ca.lo = p->canny_lo;
+        ca.hi = p->canny_hi;
+        ca.vec = (reinterpret_cast<uintptr_t>(slice) & 7) == 0 ? 1 : 0;
+        ca.cls = reinterpret_cast<unsigned char *>(ws + o.cls);
+        ca.edges = edges;
+        ca.label = reinterpret_cast<int *>(ws + o.label);
+        ca.list = reinterpret_cast<int *>(ws + o.list);
+        ca.count = reinterpret_cast<int *>(ws + o.count);
         const int n = p->n;
-        const size_t total = (size_t)n * n;
+        FBP_CUDA_TRY(cudaMemsetAsync(ca.count, 0, sizeof(int), stream));
         dim3 tiles((n + kTile - 1) / kTile, (n + kTile - 1) / kTile);
-        canny_kernel<<<tiles, 256, 0, stream>>>(slice, n, p->canny_lo, p->canny_hi, cls, label);
+        canny_kernel<<<tiles, 256, 0, stream>>>(ca);
         FBP_CUDA_TRY(cudaGetLastError());
-        const unsigned g = grid_for((long long)total, 256) > 152u * 16u ? 152u * 16u : grid_for((long long)total, 256);
-        ccl_merge_kernel<<<g, 256, 0, stream>>>(label, n, status);
+        const unsigned g = 152u * 8u;        // grid-stride over the candidate list
+        ccl_merge_kernel<<<g, 256, 0, stream>>>(ca.list, ca.count, ca.cls, ca.label, n, status);
         FBP_CUDA_TRY(cudaGetLastError());
-        ccl_flatten_kernel<<<g, 256, 0, stream>>>(label, total, status);
+        ccl_flatten_kernel<<<g, 256, 0, stream>>>(ca.list, ca.count, ca.label, status);
         FBP_CUDA_TRY(cudaGetLastError());
-        ccl_mark_kernel<<<g, 256, 0, stream>>>(label, cls, total);
+        ccl_mark_kernel<<<g, 256, 0, stream>>>(ca.list, ca.count, ca.cls, ca.label);
         FBP_CUDA_TRY(cudaGetLastError());
-        ccl_output_kernel<<<g, 256, 0, stream>>>(label, edges, total);
+        ccl_output_kernel<<<g, 256, 0, stream>>>(ca.list, ca.count, ca.label, edges);
         FBP_CUDA_TRY(cudaGetLastError());
         return FBP_OK;
     });
@@ -638,7 +781,8 @@ fbp_status sap_patches(const unsigned short *slice, const unsigned char *edges, 
             keys_kernel<<<grid_for(1LL << (2 * l), 256), 256, 0, stream>>>(a, l);
             FBP_CUDA_TRY(cudaGetLastError());
         }
-        select_kernel<<<1, 1024, 0, stream>>>(a, o.Ns);
+        select_kernel<<<1, 1024, 0, stream>>>(a, o.Ns, reinterpret_cast<ulonglong2 *>(ws + o.KB),
+                                              reinterpret_cast<ulonglong2 *>(ws + o.KC));
         FBP_CUDA_TRY(cudaGetLastError());
         for (int l = L; l >= 0; --l) {
             counts_kernel<<<grid_for(1LL << (2 * l), 256), 256, 0, stream>>>(a, l);
@@ -666,7 +810,8 @@ fbp_status sap_depatch_pack(const unsigned char *mask_patches, const int *leaves
         st = device_status_word(&status);
         if (st != FBP_OK) return st;
         dim3 grid((unsigned)p->length, kRowPhases);
-        depatch_pack_kernel<<<grid, 256, 0, stream>>>(mask_patches, leaves, p->n, p->patch, packed, status);
+        const int words = (reinterpret_cast<uintptr_t>(packed) & 3) == 0 ? 1 : 0;
+        depatch_pack_kernel<<<grid, 128, 0, stream>>>(mask_patches, leaves, p->n, p->patch, packed, words, status);
         FBP_CUDA_TRY(cudaGetLastError());
         return FBP_OK;
     });
