@@ -57,14 +57,22 @@ struct CannyArgs {
     int *label, *list, *count;
 };
 
-// every staged array is indexed by (y - (ty0 - 4), x - (tx0 - 4)) and holds
+// Every staged array is indexed by (y - (ty0 - 4), x - (tx0 - 4)) and holds
 // the stage's value at the clamped coordinate (clamp(y), clamp(x)); in an
-// interior tile (CLAMP false) no coordinate needs clamping
+// interior tile (CLAMP false) no coordinate needs clamping.  Each stage walks
+// a region W wide with a linear thread index; a warp that wraps into the
+// next row is conflict-free when the row stride S satisfies S = W (mod 32),
+// so each array's stride matches the width its main reader walks: the
+// input and the horizontal pass are read 36 wide (S = 68), the smoothed
+// image 34 wide (S = 66), the magnitude 32 wide (S = 64).  The gradients
+// reuse the first two buffers, which are dead by then.
+constexpr int kSin = 68, kShh = 68, kSss = 66, kSmm = 64;
+constexpr int kCannySmem = kSpan * (kSin + kShh + kSss + kSmm);   // ints
+
 template <bool CLAMP>
-__device__ __forceinline__ void canny_tile(const CannyArgs &a, int (*IN)[kSpan], int (*HH)[kSpan],
-                                           int (*SS)[kSpan], int (*GX)[kSpan], int (*GY)[kSpan],
-                                           int (*MM)[kSpan])
+__device__ __forceinline__ void canny_tile(const CannyArgs &a, int *IN, int *HH, int *SS, int *MM)
 {
+    int *GX = IN, *GY = HH;
     const int n = a.n, nm = n - 1;
     const int ty0 = blockIdx.y * kTile, tx0 = blockIdx.x * kTile;
     const int oy = ty0 - kHalo, ox = tx0 - kHalo;
@@ -75,17 +83,16 @@ __device__ __forceinline__ void canny_tile(const CannyArgs &a, int (*IN)[kSpan],
     if (CLAMP) {
         for (int i = t; i < kSpan * kSpan; i += 256) {
             const int r = i / kSpan, c = i - r * kSpan;
-            IN[r][c] = a.img[(size_t)clampi(oy + r, nm) * n + clampi(ox + c, nm)];
+            IN[r * kSin + c] = a.img[(size_t)clampi(oy + r, nm) * n + clampi(ox + c, nm)];
         }
     } else {
-        // rows of 40 codes from an 8-byte aligned start (ox = 32 bx - 4): 10 x 8 bytes
+        // rows of 40 codes from an 8-byte aligned start (ox = 32 bx - 4): 10 x 8 bytes,
+        // stored as one 16-byte vector (the row stride is a multiple of 4 words)
         for (int i = t; i < kSpan * (kSpan / 4); i += 256) {
             const int r = i / (kSpan / 4), c4 = i - r * (kSpan / 4);
             const uint2 v = *reinterpret_cast<const uint2 *>(a.img + (size_t)(oy + r) * n + ox + 4 * c4);
-            IN[r][4 * c4 + 0] = (int)(v.x & 0xffffu);
-            IN[r][4 * c4 + 1] = (int)(v.x >> 16);
-            IN[r][4 * c4 + 2] = (int)(v.y & 0xffffu);
-            IN[r][4 * c4 + 3] = (int)(v.y >> 16);
+            *reinterpret_cast<int4 *>(IN + r * kSin + 4 * c4) =
+                make_int4((int)(v.x & 0xffffu), (int)(v.x >> 16), (int)(v.y & 0xffffu), (int)(v.y >> 16));
         }
     }
     __syncthreads();
@@ -93,29 +100,30 @@ __device__ __forceinline__ void canny_tile(const CannyArgs &a, int (*IN)[kSpan],
     for (int i = t; i < kSpan * (kSpan - 4); i += 256) {
         const int r = i / (kSpan - 4), c = 2 + i % (kSpan - 4);
         const int x = cl<CLAMP>(ox + c, nm);
-        HH[r][c] = IN[r][ix(x - 2)] + 4 * IN[r][ix(x - 1)] + 6 * IN[r][ix(x)] + 4 * IN[r][ix(x + 1)] +
-                   IN[r][ix(x + 2)];
+        const int *row = IN + r * kSin;
+        HH[r * kShh + c] = row[ix(x - 2)] + 4 * row[ix(x - 1)] + 6 * row[ix(x)] + 4 * row[ix(x + 1)] +
+                           row[ix(x + 2)];
     }
     __syncthreads();
     // vertical binomial on [2, 38) x [2, 38)
     for (int i = t; i < (kSpan - 4) * (kSpan - 4); i += 256) {
         const int r = 2 + i / (kSpan - 4), c = 2 + i % (kSpan - 4);
         const int y = cl<CLAMP>(oy + r, nm);
-        SS[r][c] = HH[iy(y - 2)][c] + 4 * HH[iy(y - 1)][c] + 6 * HH[iy(y)][c] + 4 * HH[iy(y + 1)][c] +
-                   HH[iy(y + 2)][c];
+        SS[r * kSss + c] = HH[iy(y - 2) * kShh + c] + 4 * HH[iy(y - 1) * kShh + c] + 6 * HH[iy(y) * kShh + c] +
+                           4 * HH[iy(y + 1) * kShh + c] + HH[iy(y + 2) * kShh + c];
     }
     __syncthreads();
     // Sobel and L1 magnitude on [3, 37) x [3, 37)
     for (int i = t; i < (kSpan - 6) * (kSpan - 6); i += 256) {
         const int r = 3 + i / (kSpan - 6), c = 3 + i % (kSpan - 6);
         const int y = cl<CLAMP>(oy + r, nm), x = cl<CLAMP>(ox + c, nm);
-        const int ym = iy(y - 1), y0 = iy(y), yp = iy(y + 1);
+        const int *rm = SS + iy(y - 1) * kSss, *r0 = SS + iy(y) * kSss, *rp = SS + iy(y + 1) * kSss;
         const int xm = ix(x - 1), x0 = ix(x), xp = ix(x + 1);
-        const int gx = (SS[ym][xp] + 2 * SS[y0][xp] + SS[yp][xp]) - (SS[ym][xm] + 2 * SS[y0][xm] + SS[yp][xm]);
-        const int gy = (SS[yp][xm] + 2 * SS[yp][x0] + SS[yp][xp]) - (SS[ym][xm] + 2 * SS[ym][x0] + SS[ym][xp]);
-        GX[r][c] = gx;
-        GY[r][c] = gy;
-        MM[r][c] = abs(gx) + abs(gy);
+        const int gx = (rm[xp] + 2 * r0[xp] + rp[xp]) - (rm[xm] + 2 * r0[xm] + rp[xm]);
+        const int gy = (rp[xm] + 2 * rp[x0] + rp[xp]) - (rm[xm] + 2 * rm[x0] + rm[xp]);
+        GX[r * kSin + c] = gx;
+        GY[r * kShh + c] = gy;
+        MM[r * kSmm + c] = abs(gx) + abs(gy);
     }
     __syncthreads();
     // non-maximum suppression and thresholds on the tile; every thread runs
@@ -125,9 +133,9 @@ __device__ __forceinline__ void canny_tile(const CannyArgs &a, int (*IN)[kSpan],
         const int y = oy + r, x = ox + c;
         const bool inside = y < n && x < n;
         unsigned char k = 0;
-        const int m = MM[r][c];
+        const int m = MM[r * kSmm + c];
         if (inside && m > a.lo) {
-            const int gx = GX[r][c], gy = GY[r][c];
+            const int gx = GX[r * kSin + c], gy = GY[r * kShh + c];
             const long long ax = abs(gx), ay = abs(gy);
             int dy, dx;
             if (ay * 32768 <= (long long)kTan22 * ax) { dy = 0; dx = 1; }
@@ -135,8 +143,8 @@ __device__ __forceinline__ void canny_tile(const CannyArgs &a, int (*IN)[kSpan],
             else if ((gx > 0) == (gy > 0)) { dy = 1; dx = 1; }
             else { dy = 1; dx = -1; }
             const int py = y - dy, px = x - dx, qy = y + dy, qx = x + dx;
-            const int prev = (py >= 0 && py < n && px >= 0 && px < n) ? MM[r - dy][c - dx] : 0;
-            const int next = (qy >= 0 && qy < n && qx >= 0 && qx < n) ? MM[r + dy][c + dx] : 0;
+            const int prev = (py >= 0 && py < n && px >= 0 && px < n) ? MM[(r - dy) * kSmm + c - dx] : 0;
+            const int next = (qy >= 0 && qy < n && qx >= 0 && qx < n) ? MM[(r + dy) * kSmm + c + dx] : 0;
             if (m > prev && m >= next) k = m > a.hi ? 2 : 1;
         }
         const size_t p = (size_t)y * n + x;
@@ -157,15 +165,13 @@ __device__ __forceinline__ void canny_tile(const CannyArgs &a, int (*IN)[kSpan],
 
 __global__ void __launch_bounds__(256) canny_kernel(CannyArgs a)
 {
-    __shared__ int IN[kSpan][kSpan];
-    __shared__ int HH[kSpan][kSpan];
-    __shared__ int SS[kSpan][kSpan];
-    __shared__ int GX[kSpan][kSpan], GY[kSpan][kSpan], MM[kSpan][kSpan];
+    __shared__ __align__(16) int smem[kCannySmem];
+    int *IN = smem, *HH = IN + kSpan * kSin, *SS = HH + kSpan * kShh, *MM = SS + kSpan * kSss;
     const int oy = (int)blockIdx.y * kTile - kHalo, ox = (int)blockIdx.x * kTile - kHalo;
     if (a.vec && oy >= 0 && ox >= 0 && oy + kSpan <= a.n && ox + kSpan <= a.n)
-        canny_tile<false>(a, IN, HH, SS, GX, GY, MM);
+        canny_tile<false>(a, IN, HH, SS, MM);
     else
-        canny_tile<true>(a, IN, HH, SS, GX, GY, MM);
+        canny_tile<true>(a, IN, HH, SS, MM);
 }
 
 // ---------------------------------------------------------------------------
@@ -423,6 +429,7 @@ __global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns, 
         if (pass < 8) tx |= (unsigned long long)d << (56 - 8 * pass);
         else ty |= (unsigned long long)d << (56 - 8 * (pass - 8));
         if (pass == 15) break;
+        if ((long long)s_next == cnt) continue;     // every key has this digit: nothing to drop
         for (long long b0 = 0; b0 < cnt; b0 += 1024) {
             const long long i = b0 + t;
             const bool valid = i < cnt;
