@@ -422,10 +422,14 @@ fbp_status fbp_batched_scans(const fbp_scan_item *items, int count,
 
 /*
  * Device status word.  Kernels never trap: a kernel that detects a fault
- * (a work-queue loop past its iteration cap, or -- in the checked build --
- * an out-of-range table index) records a nonzero code in a device word and
- * returns.  This call synchronises `stream`, reads and clears the word, and
- * returns FBP_OK or FBP_ERR_DEVICE_STATUS (code in *code if non-NULL).
+ * records a nonzero code in a device word and returns.  Codes: 1 a
+ * work-queue loop past its iteration cap; 2 (checked build) an
+ * interpolation index outside the staged table; 3 reserved; 4 a
+ * union-find loop of the patching kernels (sap.h) past its cap; 5 a
+ * quadtree leaf entry outside the slice (sap.h).  The
+ * first fault recorded stays until read.  This call synchronises `stream`,
+ * reads and clears the word, and returns FBP_OK or FBP_ERR_DEVICE_STATUS
+ * (code in *code if non-NULL).
  */
 fbp_status fbp_last_device_status(fbp_stream_t stream, int *code);
 

@@ -26,7 +26,9 @@ enum DeviceFault : unsigned {
     FAULT_NONE = 0,
     FAULT_QUEUE_CAP = 1,      // persistent work loop ran past its iteration cap
     FAULT_TABLE_INDEX = 2,    // checked build: interpolation index outside the staged window
-    FAULT_FILTER_SHAPE = 3,   // filter kernel got an unsupported transform length
+    FAULT_RESERVED_3 = 3,     // unused: transform lengths are checked on the host
+    FAULT_UNION_CAP = 4,      // patching: a union-find loop ran past its cap
+    FAULT_LEAF = 5,           // patching: a quadtree leaf entry outside the slice
 };
 fbp_status device_status_word(unsigned **out);   // current device
 

@@ -31,9 +31,6 @@ namespace fbp {
 void clear_error();
 namespace {
 
-constexpr unsigned FAULT_UNION_CAP = 4;   // union-find loop past its cap
-constexpr unsigned FAULT_LEAF = 5;        // a leaf entry outside the slice
-
 constexpr int kTile = 32, kHalo = 4, kSpan = kTile + 2 * kHalo;   // 40
 constexpr int kTan22 = 13573, kTan67 = 79109;                     // tan(22.5), tan(67.5) x 2^15
 constexpr int kUnionCap = 1 << 22;
@@ -188,7 +185,7 @@ __device__ __forceinline__ int uf_find(int *L, int x, unsigned *status)
         if (gp != p) L[x] = gp;            // path halving: every write moves to an ancestor
         x = gp;
     }
-    atomicCAS(status, 0u, FAULT_UNION_CAP);
+    atomicCAS(status, 0u, (unsigned)FAULT_UNION_CAP);
     return x;
 }
 
@@ -202,7 +199,7 @@ __device__ __forceinline__ int uf_root(const int *L, int x, unsigned *status)
         if (p == x) return x;
         x = p;
     }
-    atomicCAS(status, 0u, FAULT_UNION_CAP);
+    atomicCAS(status, 0u, (unsigned)FAULT_UNION_CAP);
     return x;
 }
 
@@ -217,7 +214,7 @@ __device__ __forceinline__ void uf_unite(int *L, int a, int b, unsigned *status)
         if (old == a) return;
         a = old;                                             // a was linked meanwhile: retry from there
     }
-    atomicCAS(status, 0u, FAULT_UNION_CAP);
+    atomicCAS(status, 0u, (unsigned)FAULT_UNION_CAP);
 }
 
 // The passes below visit the candidates only (the list canny_kernel wrote).
@@ -491,7 +488,7 @@ __global__ void offsets_kernel(TreeArgs a, int l)
     const bool leaf = reached && (l == a.L || a.split[idx] == 0);
     if (!leaf) return;
     if (o < 0 || o >= a.length) {
-        atomicCAS(a.status, 0u, FAULT_LEAF);
+        atomicCAS(a.status, 0u, (unsigned)FAULT_LEAF);
         return;
     }
     const int s = a.n >> l;
@@ -530,7 +527,7 @@ __global__ void extract_kernel(TreeArgs a, float *patches)
     const int r = rc / P, c = rc - r * P;
     const int x0 = a.leaves[3 * i], y0 = a.leaves[3 * i + 1], s = a.leaves[3 * i + 2];
     if (!leaf_ok(x0, y0, s, a.n, P)) {
-        atomicCAS(a.status, 0u, FAULT_LEAF);
+        atomicCAS(a.status, 0u, (unsigned)FAULT_LEAF);
         return;
     }
     const int f = s / P;
@@ -562,7 +559,7 @@ __global__ void __launch_bounds__(128) depatch_pack_kernel(const unsigned char *
     const int i = blockIdx.x;
     const int x0 = leaves[3 * i], y0 = leaves[3 * i + 1], s = leaves[3 * i + 2];
     if (!leaf_ok(x0, y0, s, n, P)) {
-        if (threadIdx.x == 0 && blockIdx.y == 0) atomicCAS(status, 0u, FAULT_LEAF);
+        if (threadIdx.x == 0 && blockIdx.y == 0) atomicCAS(status, 0u, (unsigned)FAULT_LEAF);
         return;
     }
     const int by = blockIdx.y;
