@@ -420,6 +420,19 @@ def run_uniform(args) -> None:
                        "slices_per_s": S * len(per_rank) / (ms_step / 1e3)}
         del filt, rs
 
+    # the texture-unit backprojection (the measured alternative to staged
+    # tables): backprojection only, on the same FP32 rows
+    tex = None
+    tvs = [v["variant"] for v in api.bp_variants() if v["texture"]]
+    if args.texture and tvs and api.variant_supports(tvs[0], g):
+        filt, _ = api.filter(sino, g, kind=w.filter)
+        Tt = Timed(stream, 2, args.warmup)
+        ms_tex = Tt.run(lambda _: api.backproject(filt, g, out=out, variant=tvs[0]), None)
+        assert api.device_status() == 0
+        tex = {"variant": tvs[0], "bp_ms_per_step": ms_tex,
+               "bp_gupdates_per_s": updates / (ms_tex / 1e3) / 1e9}
+        del filt
+
     e2e = None
     if args.e2e_steps > 0:
         tdt = getattr(torch, DT[args.dtype])
@@ -484,6 +497,9 @@ def run_uniform(args) -> None:
             "traffic": captured_traffic(vdt, dt, S, N, K),
             "slices_per_s": r["slices_per_s"], "ms_per_step": r["ms_per_step"],
             "bp_variant": vdt}
+    if tex is not None:
+        tex["ratio_to_table"] = tex["bp_gupdates_per_s"] / achieved
+        line["texture_alternative"] = tex
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and ws == 1:
@@ -1015,6 +1031,8 @@ def main(argv=None):
     ap.add_argument("--slices", type=int, default=None,
                     help="slices per GPU (default: the workload's); small cases for profiling")
     ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--texture", action=argparse.BooleanOptionalAction, default=True,
+                    help="also time the texture-unit backprojection (FP32 rows) in the same run")
     ap.add_argument("--cpu-block", type=int, default=1024)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None,

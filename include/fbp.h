@@ -110,6 +110,15 @@ typedef struct {
     int packed16;        /* 1: 16-bit rows only; interpolates two rows with
                             one packed 16-bit FMA (the interpolated value is
                             rounded to the 16-bit type, then summed in FP32) */
+    int texture;         /* 1: interpolates with the texture unit's linear
+                            filtering instead of staged tables (FP32 rows, D a
+                            multiple of 8, K <= 65000, `filt` aligned for a
+                            texture: 512 bytes on current GPUs; slices are bound
+                            in groups of up to 65000 rows); its fraction is
+                            quantised to 8 bits,
+                            and the call synchronises `stream` before it returns
+                            (so it cannot be captured in a CUDA graph).  Never
+                            the default; kept as the measured alternative   */
 } fbp_bp_shape;
 
 /* Library version (major*10000 + minor*100 + patch). */

@@ -49,7 +49,7 @@ class CBatchItem(ctypes.Structure):
 class CBpShape(ctypes.Structure):
     _fields_ = [("angle_tile", ctypes.c_int), ("tile_x", ctypes.c_int), ("tile_y", ctypes.c_int),
                 ("px", ctypes.c_int), ("py", ctypes.c_int), ("threads", ctypes.c_int),
-                ("symmetric", ctypes.c_int), ("packed16", ctypes.c_int)]
+                ("symmetric", ctypes.c_int), ("packed16", ctypes.c_int), ("texture", ctypes.c_int)]
 
 
 _G = ctypes.POINTER(CGeometry)

@@ -396,7 +396,8 @@ def bp_variants() -> list[dict]:
         _lib.check(L.fbp_bp_variant_info(v, ctypes.byref(s)), L, "fbp_bp_variant_info")
         out.append({"variant": v, "angle_tile": s.angle_tile, "tile_x": s.tile_x,
                     "tile_y": s.tile_y, "px": s.px, "py": s.py, "threads": s.threads,
-                    "symmetric": bool(s.symmetric), "packed16": bool(s.packed16)})
+                    "symmetric": bool(s.symmetric), "packed16": bool(s.packed16),
+                    "texture": bool(s.texture)})
     return out
 
 

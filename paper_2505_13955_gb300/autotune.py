@@ -101,7 +101,9 @@ def tune_single(g: api.Geometry, dtype=torch.float32, reps: int = 3, force: bool
     rows = torch.randn((g.n_angles, g.n_det), device="cuda", generator=gen)
     filt, rs = api.filter(rows, g, dtype=dtype)
     out = torch.empty((g.n, g.n), device="cuda")
-    cands = variants if variants is not None else range(len(api.bp_variants()))
+    # the texture-unit variant synchronises on every call and is never the
+    # default: it is timed only when asked for explicitly
+    cands = variants if variants is not None else [s["variant"] for s in api.bp_variants() if not s["texture"]]
     times = {}
     for v in cands:
         if not api.variant_supports(v, g, dtype):
@@ -128,7 +130,8 @@ def tune_batched(sinos, geoms, dtype=torch.float32, reps: int = 2, force: bool =
     ws = torch.empty(api.batched_workspace_bytes(sinos, outs, geoms, dtype), dtype=torch.uint8,
                      device="cuda")
     shapes = api.bp_variants()
-    cands = variants if variants is not None else [s["variant"] for s in shapes if not s["symmetric"]]
+    cands = variants if variants is not None else [s["variant"] for s in shapes
+                                                   if not s["symmetric"] and not s["texture"]]
     times = {}
     for v in cands:
         try:

@@ -24,7 +24,8 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 
-CU_SOURCES = ["runtime.cu", "filter.cu", "backproject.cu", "forward.cu", "fbp_api.cu", "noalloc.cu", "sap.cu"]
+CU_SOURCES = ["runtime.cu", "filter.cu", "backproject.cu", "forward.cu", "fbp_api.cu", "noalloc.cu", "sap.cu",
+              "bp_texture.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -315,7 +315,8 @@ fbp_status launch_persistent_shape(BpBatchArgs &a, int sms, cudaStream_t s)
 template <typename T>
 fbp_status launch_persistent_t(BpBatchArgs &a, int v, int sms, cudaStream_t s)
 {
-    if (kShapes[v].orbit) return fail(FBP_ERR_UNSUPPORTED, "variant %d is not available for ragged batches", v);
+    if (v < 0 || v >= kNumShapes || kShapes[v].orbit)
+        return fail(FBP_ERR_UNSUPPORTED, "variant %d is not available for ragged batches", v);
     switch (v) {
         case 0: return launch_persistent_shape<0, T>(a, sms, s);
         case 1: return launch_persistent_shape<1, T>(a, sms, s);
@@ -329,11 +330,26 @@ fbp_status launch_persistent_t(BpBatchArgs &a, int v, int sms, cudaStream_t s)
 
 }  // namespace
 
-int bp_variant_count() { return kNumShapes; }
+// One more variant after the table's: the texture-unit kernel (bp_texture.cu).
+constexpr int kTextureVariant = kNumShapes;
+
+int bp_variant_count() { return kNumShapes + 1; }
 
 bool bp_variant_shape(int v, fbp_bp_shape *out)
 {
-    if (v < 0 || v >= kNumShapes || !out) return false;
+    if (!out) return false;
+    if (v == kTextureVariant) {
+        out->angle_tile = 256;
+        out->tile_x = out->tile_y = 64;
+        out->px = out->py = 4;
+        out->threads = 256;
+        out->symmetric = 0;
+        out->packed16 = 0;
+        out->texture = 1;
+        return true;
+    }
+    if (v < 0 || v >= kNumShapes) return false;
+    out->texture = 0;
     const ShapeDesc &d = kShapes[v];
     out->angle_tile = d.kt;
     out->tile_x = d.txt * d.px;
@@ -347,8 +363,8 @@ bool bp_variant_shape(int v, fbp_bp_shape *out)
     return true;
 }
 
-int bp_tile_w(int v) { return kShapes[v].txt * kShapes[v].px; }
-int bp_tile_h(int v) { return kShapes[v].tyt * kShapes[v].py; }
+int bp_tile_w(int v) { return v >= 0 && v < kNumShapes ? kShapes[v].txt * kShapes[v].px : 64; }
+int bp_tile_h(int v) { return v >= 0 && v < kNumShapes ? kShapes[v].tyt * kShapes[v].py : 64; }
 
 bool bp_orbit_eligible(const BpLaunch &L, int tile)
 {
@@ -375,6 +391,7 @@ size_t variant_smem(const BpLaunch &L)
 
 bool bp_variant_fits(int v, const BpLaunch &L)
 {
+    if (v == kTextureVariant) return bp_texture_shape_ok(L);
     size_t smem = 0;
     switch (v) {
         case 0: smem = variant_smem<0>(L); break;
@@ -416,6 +433,7 @@ fbp_status launch_backproject(const BpLaunch &L, int variant, cudaStream_t s)
 {
     if (L.S <= 0) return FBP_OK;
     if (variant < 0) variant = bp_default_variant(L);
+    if (variant == kTextureVariant) return launch_backproject_texture(L, s);
     unsigned *status = nullptr;
     fbp_status st = device_status_word(&status);
     if (st != FBP_OK) return st;

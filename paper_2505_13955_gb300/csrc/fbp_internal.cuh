@@ -138,6 +138,10 @@ int bp_default_variant(const BpLaunch &a);
 int bp_variant_count();
 bool bp_variant_shape(int v, fbp_bp_shape *out);
 size_t bp_smem_bytes(int v, int W);
+// The texture-unit variant (bp_texture.cu): eligibility and launch.  The
+// launch synchronises `s` before releasing its texture objects.
+bool bp_texture_shape_ok(const BpLaunch &a);
+fbp_status launch_backproject_texture(const BpLaunch &a, cudaStream_t s);
 
 struct FwdLaunch {
     const float *slice;   // [S][N][N]

@@ -48,7 +48,7 @@ def test_backproject_matches_oracle(G):
 
 
 @pytest.mark.parametrize("variant", range(12))
-def test_every_variant_matches_oracle(variant):
+def test_every_table_variant_matches_oracle(variant):
     api = fbp_api()
     shape = api.bp_variants()[variant]
     if shape["packed16"]:
