@@ -365,9 +365,11 @@ __global__ void keys_kernel(TreeArgs a, int l)
 
 // The M-th largest of the Ns keys, by MSB-first radix selection (8-bit
 // digits) in one block: each pass counts the digit of every remaining key
-// (per-warp histograms, one atomic per distinct digit in a warp), picks the
-// digit holding the M-th largest, and copies the keys with that digit to the
-// other buffer, so later passes see only the keys that can still be it.
+// (per-warp histograms, one atomic per distinct digit in a warp) and picks
+// the digit holding the M-th largest.  The remaining keys are those that
+// match the digits chosen so far; when a pass drops at least a quarter of
+// them they are copied to the other buffer (later passes read fewer keys),
+// otherwise they stay in place and later passes check the prefix.
 __device__ __forceinline__ unsigned digit_of(ulonglong2 k, int pass)
 {
     const int sh = 56 - 8 * (pass & 7);
@@ -389,16 +391,22 @@ __global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns, 
     if (t == 0) s_krem = a.M;
     const ulonglong2 *src = a.K;
     ulonglong2 *dst = bufB;
-    long long cnt = Ns;
-    unsigned long long tx = 0, ty = 0;
+    long long cnt = Ns;                               // keys in src (some may not match the prefix)
+    long long live = Ns;                              // keys matching the prefix
+    unsigned long long tx = 0, ty = 0, mx = 0, my = 0;   // prefix and its mask
     for (int pass = 0; pass < 16; ++pass) {
         for (int i = t; i < 32 * 256; i += 1024) (&hist[0][0])[i] = 0;
         __syncthreads();
         // every warp runs the same number of rounds, so the warp-wide votes see all lanes
         for (long long b0 = 0; b0 < cnt; b0 += 1024) {
             const long long i = b0 + t;
-            const bool valid = i < cnt;
-            const unsigned d = valid ? digit_of(src[i], pass) : 256u;
+            bool valid = i < cnt;
+            ulonglong2 k = make_ulonglong2(0, 0);
+            if (valid) {
+                k = src[i];
+                valid = (k.x & mx) == tx && (k.y & my) == ty;
+            }
+            const unsigned d = valid ? digit_of(k, pass) : 256u;
             const unsigned same = __match_any_sync(0xffffffffu, d);
             if (valid && lane == __ffs(same) - 1) atomicAdd(&hist[warp][d], __popc(same));
         }
@@ -423,15 +431,28 @@ __global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns, 
         }
         __syncthreads();
         const unsigned d = s_digit;
-        if (pass < 8) tx |= (unsigned long long)d << (56 - 8 * pass);
-        else ty |= (unsigned long long)d << (56 - 8 * (pass - 8));
+        const int sh = 56 - 8 * (pass & 7);
+        if (pass < 8) {
+            tx |= (unsigned long long)d << sh;
+            mx |= 0xffULL << sh;
+        } else {
+            ty |= (unsigned long long)d << sh;
+            my |= 0xffULL << sh;
+        }
+        const long long next = s_next;
         if (pass == 15) break;
-        if ((long long)s_next == cnt) continue;     // every key has this digit: nothing to drop
+        if (4 * (live - next) < live) {               // drops under a quarter: keep the keys in place
+            live = next;
+            continue;
+        }
         for (long long b0 = 0; b0 < cnt; b0 += 1024) {
             const long long i = b0 + t;
-            const bool valid = i < cnt;
-            const ulonglong2 k = valid ? src[i] : make_ulonglong2(0, 0);
-            const bool keep = valid && digit_of(k, pass) == d;
+            bool keep = false;
+            ulonglong2 k = make_ulonglong2(0, 0);
+            if (i < cnt) {
+                k = src[i];
+                keep = (k.x & mx) == tx && (k.y & my) == ty;
+            }
             const unsigned vote = __ballot_sync(0xffffffffu, keep);
             unsigned base = 0;
             if (lane == 0 && vote) base = atomicAdd(&s_pos, __popc(vote));
@@ -439,7 +460,7 @@ __global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns, 
             if (keep) dst[base + __popc(vote & ((1u << lane) - 1))] = k;
         }
         __syncthreads();
-        cnt = s_next;
+        cnt = live = next;
         src = dst;
         dst = dst == bufB ? bufC : bufB;
     }
