@@ -435,7 +435,8 @@ fbp_status fbp_batched_scans(const fbp_scan_item *items, int count,
  * work-queue loop past its iteration cap; 2 (checked build) an
  * interpolation index outside the staged table; 3 reserved; 4 a
  * union-find loop of the patching kernels (sap.h) past its cap; 5 a
- * quadtree leaf entry outside the slice (sap.h).  The
+ * quadtree leaf entry outside the slice (sap.h); 6 a wait of the streamed
+ * filter for its row copy past its cap.  The
  * first fault recorded stays until read.  This call synchronises `stream`,
  * reads and clears the word, and returns FBP_OK or FBP_ERR_DEVICE_STATUS
  * (code in *code if non-NULL).

@@ -29,6 +29,7 @@ enum DeviceFault : unsigned {
     FAULT_RESERVED_3 = 3,     // unused: transform lengths are checked on the host
     FAULT_UNION_CAP = 4,      // patching: a union-find loop ran past its cap
     FAULT_LEAF = 5,           // patching: a quadtree leaf entry outside the slice
+    FAULT_STREAM_WAIT = 6,    // streamed filter: a wait for its row copy ran past its cap
 };
 fbp_status device_status_word(unsigned **out);   // current device
 

@@ -38,6 +38,8 @@
 // read order; the twiddles come from a plan laid out in the order each step
 // reads them (fbp_internal.cuh), so every table load is coalesced.  FP32
 // throughout, with the spectrum and twiddles rounded once from FP64 tables.
+#include <algorithm>
+
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
 
@@ -280,14 +282,54 @@ __device__ __forceinline__ float offset_sample(const float *p, const float *p2, 
     return v;
 }
 
+// Streamed rows (filter_stream_kernel): the next row pair is copied into a
+// shared staging buffer by the bulk-copy (TMA) engine while the current pair
+// is transformed; completion is signalled on an mbarrier.
+struct StreamNext {
+    bool issue;                  // a next pair exists
+    const float *src;            // its first row (16-byte aligned)
+    unsigned bytes;              // 4 D per row, a multiple of 16
+    uint32_t stage, mbar;        // shared addresses of the staging buffer and the mbarrier
+};
+
+__device__ __forceinline__ void bulk_rows(const StreamNext &nx)
+{
+    // the staging buffer was last read through the generic proxy: order those
+    // reads before the asynchronous copy overwrites it
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(nx.mbar), "r"(nx.bytes)
+                 : "memory");
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(nx.stage), "l"(nx.src), "r"(nx.bytes), "r"(nx.mbar)
+                 : "memory");
+}
+
+// Wait for the mbarrier phase with the given parity; false after `cap` polls.
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, unsigned parity, long long cap)
+{
+    for (long long it = 0; it < cap; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
 // One row pair by one group of C threads (t = thread index in the group).
 // S: the group's R x C complex buffer; red: 4 * C/32 floats of the group;
 // bar_id: the group's named barrier.
-template <int L, typename T>
+// STAGED: job.a / job.b point to the rows in shared memory (filled by the
+// bulk-copy engine); after step 1 has read them, thread 0 starts the copy
+// described by *nx into the same buffer.
+template <int L, typename T, bool STAGED = false>
 __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int D,
                                          const float2 *__restrict__ Gs,
                                          const float2 *__restrict__ tw, float2 *S, float *red,
-                                         int t, int bar_id, const PreArgs &pre, const OffArgs &off)
+                                         int t, int bar_id, const PreArgs &pre, const OffArgs &off,
+                                         const StreamNext *nx = nullptr)
 {
     constexpr int R = fft_R(L), VPL = fft_VPL(L);
     constexpr int C = 32 * VPL;
@@ -345,6 +387,25 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
             v[n1] = make_float2(da, db);
         }
         group_sync(bar_id, C);                    // staged rows read before S is written
+    } else if (STAGED) {
+        // rows already in shared memory: each difference reads its two samples
+        const float *sa = job.a, *sb = job.b;
+#pragma unroll
+        for (int n1 = 0; n1 < R; ++n1) {
+            const int n = C * n1 + t;
+            float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
+            if (C * n1 <= D) {                    // uniform over the group
+                a = n < D ? sa[n] : 0.f;
+                am = (n >= 1 && n - 1 < D) ? sa[n - 1] : 0.f;
+                if (sb) {
+                    b = n < D ? sb[n] : 0.f;
+                    bm = (n >= 1 && n - 1 < D) ? sb[n - 1] : 0.f;
+                }
+                nz_a |= (a != 0.f);
+                nz_b |= (b != 0.f);
+            }
+            v[n1] = make_float2(a - am, b - bm);
+        }
     } else if (off.on) {
         // offset scans: weighted (and folded) virtual samples, then differences
 #pragma unroll
@@ -396,6 +457,9 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         red[2 * gw + 1] = zb ? 1.f : 0.f;
     }
     group_sync(bar_id, C);
+    if constexpr (STAGED) {
+        if (t == 0 && nx->issue) bulk_rows(*nx);     // step 1 is done with the staged rows
+    }
     bool zero_a = true, zero_b = true;
 #pragma unroll
     for (int w = 0; w < NWG; ++w) {
@@ -575,6 +639,92 @@ fbp_status launch_l(const FilterArgs &fa, cudaStream_t s)
     return FBP_OK;
 }
 
+// Persistent, streamed form for the lengths with one row pair per block
+// (L = 8192, 16384): one block per SM walks the row pairs; the bulk-copy
+// engine brings pair i+1's rows into a staging buffer beside the transform
+// buffer while pair i is transformed.  Plain line-integral rows only, D a
+// multiple of 4 and 16-byte aligned rows.  A wait past its cap records
+// FAULT_STREAM_WAIT and ends the block (after waiting, also capped, for its
+// copy in flight).
+constexpr long long kStreamWaitCap = 1LL << 22;   // a 64 KB copy needs ~100 polls
+
+template <int L, typename T>
+__global__ void __launch_bounds__(kFilterThreads) filter_stream_kernel(FilterArgs a, unsigned *status)
+{
+    static_assert(group_threads(L) == kFilterThreads, "one row pair per block");
+    extern __shared__ __align__(128) float2 smem_f2[];
+    __shared__ float red[4 * (kFilterThreads / 32)];
+    __shared__ __align__(8) unsigned long long mbar_store;
+    float2 *S = smem_f2;
+    float *stage = reinterpret_cast<float *>(smem_f2 + L);         // 2 D floats (D <= L / 2)
+    const int t = threadIdx.x;
+    const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&mbar_store);
+    const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
+    const long long pairs = (a.rows + 1) / 2;
+    auto next_of = [&](long long p) {
+        StreamNext nx;
+        nx.issue = p < pairs;
+        const long long r0 = 2 * p;
+        const int nrows = (r0 + 1 < a.rows) ? 2 : 1;
+        nx.src = a.sino + (nx.issue ? r0 : 0) * a.D;
+        nx.bytes = (unsigned)(nrows * a.D * 4);
+        nx.stage = stage_s;
+        nx.mbar = mbar;
+        return nx;
+    };
+    if (t == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    long long pair = blockIdx.x;
+    if (t == 0 && pair < pairs) bulk_rows(next_of(pair));
+    unsigned parity = 0;
+    bool pending = pair < pairs;            // a copy this block issued is in flight
+    for (; pair < pairs; pair += gridDim.x) {
+        if (!mbar_wait(mbar, parity, kStreamWaitCap)) {
+            if (t == 0) atomicCAS(status, 0u, (unsigned)FAULT_STREAM_WAIT);
+            break;
+        }
+        parity ^= 1u;
+        bool active;
+        RowPairJob job = make_job(a.sino, a.filt, a.row_scale, a.rows, a.D, pair, sizeof(T), active);
+        job.a = stage;
+        job.b = job.b ? stage + a.D : nullptr;
+        const StreamNext nx = next_of(pair + gridDim.x);
+        pending = nx.issue;
+        fft_pair<L, T, true>(job, true, a.D, a.G, a.tw, S, red, t, 1, a.pre, a.off, &nx);   // pre, off: off
+    }
+    if (pending) mbar_wait(mbar, parity, kStreamWaitCap);   // only after a failed wait
+}
+
+template <int L, typename T>
+fbp_status launch_stream_l(const FilterArgs &fa, unsigned *status, cudaStream_t s)
+{
+    const size_t smem = (size_t)L * sizeof(float2) + (size_t)L * sizeof(float);
+    auto kern = filter_stream_kernel<L, T>;
+    fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
+    if (st != FBP_OK) return st;
+    int per_sm = 0;
+    st = blocks_per_sm(reinterpret_cast<const void *>(kern), kFilterThreads, smem, &per_sm);
+    if (st != FBP_OK) return st;
+    int dev = 0, sms = 0;
+    FBP_CUDA_TRY(cudaGetDevice(&dev));
+    FBP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const long long pairs = (fa.rows + 1) / 2;
+    const long long grid = std::max(1LL, std::min<long long>(pairs, (long long)sms * std::max(1, per_sm)));
+    kern<<<(unsigned)grid, kFilterThreads, smem, s>>>(fa, status);
+    FBP_CUDA_TRY(cudaGetLastError());
+    return FBP_OK;
+}
+
+template <typename T>
+fbp_status launch_stream_t(const FilterArgs &fa, int L, unsigned *status, cudaStream_t s)
+{
+    if (L == 8192) return launch_stream_l<8192, T>(fa, status, s);
+    return launch_stream_l<16384, T>(fa, status, s);
+}
+
 template <typename T>
 fbp_status launch_t(const FilterArgs &fa, int L, cudaStream_t s)
 {
@@ -701,6 +851,19 @@ fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s)
         for (int k = 0; k <= 2 * p.blur_radius; ++k) fa.pre.taps[k] = p.taps[k];
         for (int m = 0; m <= 2 * p.blur_radius + 1; ++m)     // c_m = w_m - w_{m-1}
             fa.pre.dtaps[m] = (m <= 2 * p.blur_radius ? p.taps[m] : 0.f) - (m >= 1 ? p.taps[m - 1] : 0.f);
+    }
+    const bool streamed = !a.pre && !a.offset && (a.L == 8192 || a.L == 16384) && a.D % 4 == 0 &&
+                          (reinterpret_cast<uintptr_t>(a.sino) & 15) == 0;
+    if (streamed) {
+        unsigned *status = nullptr;
+        fbp_status st = device_status_word(&status);
+        if (st != FBP_OK) return st;
+        switch (a.dtype) {
+            case FBP_F32: return launch_stream_t<float>(fa, a.L, status, s);
+            case FBP_F16: return launch_stream_t<__half>(fa, a.L, status, s);
+            case FBP_BF16: return launch_stream_t<__nv_bfloat16>(fa, a.L, status, s);
+        }
+        return fail(FBP_ERR_INVALID_ARG, "dtype");
     }
     switch (a.dtype) {
         case FBP_F32: return launch_t<float>(fa, a.L, s);

@@ -105,3 +105,33 @@ def test_filter_large_line_integrals_difference_form(D, K):
     ref = oracle.filter(p.astype(np.float64))
     err = np.max(np.abs(to_np(q) - ref)) / np.max(np.abs(ref))
     assert err <= 1e-5, err
+
+
+@pytest.mark.parametrize("D", [8192, 4096, 3000])
+@pytest.mark.parametrize("rows", [1, 7, 610])
+def test_streamed_filter_equals_the_plain_kernel(D, rows):
+    """At the one-pair-per-block lengths the library streams 16-byte aligned
+    rows through the bulk-copy engine (filter_stream_kernel); rows that are
+    not 16-byte aligned take the plain kernel.  Both compute the same
+    arithmetic in the same order, so the results are bit-identical, and both
+    match the oracle."""
+    api = fbp_api()
+    rng = np.random.default_rng(D + rows)
+    p = (rng.standard_normal((rows, D)) * 40).astype(np.float32)
+    g = api.Geometry(rows, D, D)
+    aligned = to_gpu(p)
+    buf = torch.empty(rows * D + 1, device="cuda")
+    buf[1:] = aligned.reshape(-1)
+    shifted = buf[1:].view(rows, D)                       # 4 bytes past an aligned address
+    assert aligned.data_ptr() % 16 == 0 and shifted.data_ptr() % 16 == 4
+    q1, _ = api.filter(aligned, g)
+    q2, _ = api.filter(shifted, g)
+    assert torch.equal(q1, q2)
+    assert api.device_status() == 0
+    if rows <= 7:
+        ref = oracle.filter(p.astype(np.float64))
+        assert_within_dr(to_np(q1), ref, 2e-5, "streamed filter")
+    for dt in (torch.float16, torch.bfloat16):
+        a1, s1 = api.filter(aligned, g, dtype=dt)
+        a2, s2 = api.filter(shifted, g, dtype=dt)
+        assert torch.equal(a1, a2) and torch.equal(s1, s2)
