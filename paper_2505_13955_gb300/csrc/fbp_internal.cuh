@@ -58,7 +58,8 @@ __host__ __device__ constexpr int fft_VPL(int L)
 //   L   = transform length (power of two >= max(512, 2D-1), so L >= 2D; <= 16384)
 //   G   = spectrum of the cumulative (difference-form) kernel, times tau / L,
 //         complex, in the order the transform's step 2 reads it:
-//         G[(k1 VPL + kr) 32 + l] = spectrum at k = k1 + R (kr + VPL brev5(l))
+//         G[(k1 VPL + kr) 32 + l] = spectrum at k = k1 + R (kr + VPL brev5(l)),
+//         brev5 = the 5-bit reversal of the lane index
 //   tw  = twiddle plan (float2), L + C + 32 entries: W_L^{t k1} at k1 C + t,
 //         then W_C^{l kr} at L + 32 kr + l, then W_32^m at L + C + m,
 //         W_M^x = exp(-2 pi i x / M), each rounded once from double

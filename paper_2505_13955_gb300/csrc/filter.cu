@@ -65,7 +65,6 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m)
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
 
-__device__ __forceinline__ int brev5(int x) { return (int)(__brev((unsigned)x) >> 27); }
 
 // Decimation-in-frequency radix-2 DFT over the 32 lanes (forward, natural
 // order in, bit-reversed out), on NV values per lane; w32 = the W_32^m table.
@@ -480,7 +479,7 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
 #pragma unroll
                 for (int kr = 1; kr < VPL; ++kr) u[kr] = cmul(u[kr], __ldg(&tw[L + 32 * kr + lane]));  // W_C^{l kr}
             }
-            lane_dif<VPL>(u, lane, w32t);                             // l -> kl = brev5(lane)
+            lane_dif<VPL>(u, lane, w32t);                             // l -> kl = bit-reversed lane (5 bits)
             // G is stored in this order: entry (k1 VPL + kr) 32 + lane is k = k1 + R (kr + VPL kl)
 #pragma unroll
             for (int kr = 0; kr < VPL; ++kr) u[kr] = cmul(u[kr], __ldg(&Gs[(k1 * VPL + kr) * 32 + lane]));
