@@ -253,6 +253,66 @@ def cpu_sample(w, block: int) -> dict:
             "seconds": t2 - t0}
 
 
+def cpu_sample_offset(w, block: int) -> dict:
+    """Oracle on one offset-scan slice: weight, embed and fold its rows,
+    filter all folded rows, backproject a block x block pixel square over
+    all folded angles; whole-slice time extrapolated by pixel count."""
+    import oracle
+    from paper_2505_13955_gb300 import phantoms
+    D, c, delta = w.offset
+    N, K = w.n, w.n_angles
+    p = phantoms.slice_sinogram(w, 0).astype(np.float64)
+    t0 = time.perf_counter()
+    n_v, c_v, off, wt = oracle.offset_virtual(D, c, delta)
+    q = oracle.filter(oracle.offset_fold(oracle.embed_rows(p, n_v, off), wt))
+    t1 = time.perf_counter()
+    block = min(block, N)
+    c0 = N // 2 - block // 2
+    rr, cc = np.meshgrid(np.arange(c0, c0 + block), np.arange(c0, c0 + block), indexing="ij")
+    oracle.backproject_pixels(q, oracle.Geometry(K // 2, n_v, N, angle_step=2 * np.pi / K), rr.ravel(), cc.ravel())
+    t2 = time.perf_counter()
+    t_slice = (t1 - t0) + (t2 - t1) * (N * N) / (block * block)
+    return {"value": N * N * (K // 2) / t_slice / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"1 offset slice: weight + fold + filter all {K // 2} folded rows ({t1 - t0:.2f} s) + "
+                      f"backproject a {block}x{block} block ({t2 - t1:.2f} s), extrapolated to the full slice"}
+
+
+def cpu_sample_gd(w) -> dict:
+    """Oracle FP64 gradient A^T (A x - b) of one slice (one GD iteration's work)."""
+    import oracle
+    from paper_2505_13955_gb300 import phantoms
+    N, K = w.n, w.n_angles
+    b = phantoms.slice_sinogram(w, 0).astype(np.float64)
+    g = oracle.Geometry(K, N, N)
+    x = np.zeros((N, N))
+    t0 = time.perf_counter()
+    oracle.gradient(x, b, g)
+    t1 = time.perf_counter()
+    return {"value": 2 * N * N * K / (t1 - t0) / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle", "sample": f"one FP64 gradient A^T (A x - b) of 1 slice N={N} K={K} ({t1 - t0:.2f} s)"}
+
+
+def cpu_sample_sap(n_sample: int, n: int) -> dict:
+    """Oracle patching (Canny, greedy quadtree, patch means) of one
+    n_sample^2 slice, scaled to n^2 slices by pixel count."""
+    from oracle import sap
+    from paper_2505_13955_gb300 import phantoms
+    c = phantoms.SAP
+    img = phantoms.sap_slice(n_sample, 12345)
+    length = min(c["length"], 1 + 3 * (((n_sample // c["patch"]) ** 2 - 1) // 3))
+    t0 = time.perf_counter()
+    e = sap.canny(img, c["canny_lo"], c["canny_hi"])
+    leaves, _ = sap.quadtree(img, e, c["patch"], length)
+    sap.extract_patches(img, leaves, c["patch"])
+    t1 = time.perf_counter()
+    per_slice = (t1 - t0) * (n * n) / (n_sample * n_sample)
+    from oracle import num_threads
+    return {"value": 1.0 / per_slice, "unit": "slices/s", "cores": num_threads(), "kind": "oracle",
+            "sample": f"Canny + quadtree ({length} patches) + patch means of one {n_sample}^2 slice "
+                      f"({t1 - t0:.2f} s), scaled to {n}^2 by pixel count"}
+
+
 def run_reference(args) -> None:
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -688,6 +748,8 @@ def run_offset(args) -> None:
         "speedup_fold_vs_unfolded": unf["ms_per_step"] / main["ms_per_step"],
         "clocks": main["clocks"], "gpu_launches": 2 * args.steps,
     })
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_sample_offset(w, args.cpu_block)
     finish(line, ws, rank)
 
 
@@ -942,6 +1004,8 @@ def run_sap(args) -> None:
         "clocks": clocks, "gpu_launches": S * (5 + 3 * int(np.log2(n // p.patch)) + 5) * args.steps})
     if e2e is not None:
         line["e2e"] = e2e
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_sample_sap(2048, n)
     finish(line, ws, rank)
 
 
@@ -1036,6 +1100,8 @@ def run_gd(args) -> None:
                               "peak_basis": rp["basis"] + " (sm_max_mhz from MEASURED_PEAKS.json)"},
                  "refine_50": refine,
                  "eta": eta, "clocks": T.clocks, "gpu_launches": 2 * args.steps})
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_sample_gd(w)
     finish(line, ws, rank)
 
 
