@@ -39,6 +39,7 @@
 // reads them (fbp_internal.cuh), so every table load is coalesced.  FP32
 // throughout, with the spectrum and twiddles rounded once from FP64 tables.
 #include <algorithm>
+#include <cstdlib>
 
 #include <cuda_fp16.h>
 #include <cuda_bf16.h>
@@ -304,12 +305,14 @@ __device__ __forceinline__ void bulk_rows(const StreamNext &nx)
 }
 
 // Wait for the mbarrier phase with the given parity; false after `cap` polls.
+// The non-blocking test form keeps every poll short, so the cap bounds the
+// time (4M polls: well under a second).
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, unsigned parity, long long cap)
 {
     for (long long it = 0; it < cap; ++it) {
         uint32_t done;
         asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
                      "selp.u32 %0, 1, 0, p;\n\t}"
                      : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
         if (done) return true;
@@ -645,10 +648,14 @@ fbp_status launch_l(const FilterArgs &fa, cudaStream_t s)
 // multiple of 4 and 16-byte aligned rows.  A wait past its cap records
 // FAULT_STREAM_WAIT and ends the block (after waiting, also capped, for its
 // copy in flight).
-constexpr long long kStreamWaitCap = 1LL << 22;   // a 64 KB copy needs ~100 polls
+constexpr long long kStreamWaitCap = 1LL << 22;   // a 64 KB copy needs ~1000 polls at most
 
+// skip_copies (failure-detection tests only): no row copy is issued, so
+// every wait runs out at its cap, records FAULT_STREAM_WAIT and the block
+// returns; nothing is written.
 template <int L, typename T>
-__global__ void __launch_bounds__(kFilterThreads) filter_stream_kernel(FilterArgs a, unsigned *status)
+__global__ void __launch_bounds__(kFilterThreads) filter_stream_kernel(FilterArgs a, unsigned *status,
+                                                                      int skip_copies)
 {
     static_assert(group_threads(L) == kFilterThreads, "one row pair per block");
     extern __shared__ __align__(128) float2 smem_f2[];
@@ -677,11 +684,14 @@ __global__ void __launch_bounds__(kFilterThreads) filter_stream_kernel(FilterArg
     }
     __syncthreads();
     long long pair = blockIdx.x;
-    if (t == 0 && pair < pairs) bulk_rows(next_of(pair));
+    if (t == 0 && pair < pairs && !skip_copies) bulk_rows(next_of(pair));
     unsigned parity = 0;
-    bool pending = pair < pairs;            // a copy this block issued is in flight
+    bool pending = pair < pairs && !skip_copies;   // a copy this block issued is in flight
     for (; pair < pairs; pair += gridDim.x) {
-        if (!mbar_wait(mbar, parity, kStreamWaitCap)) {
+        // the decision is block-wide, so no thread reaches the transform's
+        // barriers while another has left
+        const bool ok = mbar_wait(mbar, parity, kStreamWaitCap);
+        if (__syncthreads_or(!ok)) {
             if (t == 0) atomicCAS(status, 0u, (unsigned)FAULT_STREAM_WAIT);
             break;
         }
@@ -698,7 +708,7 @@ __global__ void __launch_bounds__(kFilterThreads) filter_stream_kernel(FilterArg
 }
 
 template <int L, typename T>
-fbp_status launch_stream_l(const FilterArgs &fa, unsigned *status, cudaStream_t s)
+fbp_status launch_stream_l(const FilterArgs &fa, unsigned *status, int skip_copies, cudaStream_t s)
 {
     const size_t smem = (size_t)L * sizeof(float2) + (size_t)L * sizeof(float);
     auto kern = filter_stream_kernel<L, T>;
@@ -712,16 +722,16 @@ fbp_status launch_stream_l(const FilterArgs &fa, unsigned *status, cudaStream_t 
     FBP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const long long pairs = (fa.rows + 1) / 2;
     const long long grid = std::max(1LL, std::min<long long>(pairs, (long long)sms * std::max(1, per_sm)));
-    kern<<<(unsigned)grid, kFilterThreads, smem, s>>>(fa, status);
+    kern<<<(unsigned)grid, kFilterThreads, smem, s>>>(fa, status, skip_copies);
     FBP_CUDA_TRY(cudaGetLastError());
     return FBP_OK;
 }
 
 template <typename T>
-fbp_status launch_stream_t(const FilterArgs &fa, int L, unsigned *status, cudaStream_t s)
+fbp_status launch_stream_t(const FilterArgs &fa, int L, unsigned *status, int skip, cudaStream_t s)
 {
-    if (L == 8192) return launch_stream_l<8192, T>(fa, status, s);
-    return launch_stream_l<16384, T>(fa, status, s);
+    if (L == 8192) return launch_stream_l<8192, T>(fa, status, skip, s);
+    return launch_stream_l<16384, T>(fa, status, skip, s);
 }
 
 template <typename T>
@@ -857,10 +867,14 @@ fbp_status launch_filter(const FilterLaunch &a, cudaStream_t s)
         unsigned *status = nullptr;
         fbp_status st = device_status_word(&status);
         if (st != FBP_OK) return st;
+        // failure-detection tests set FBP_TEST_STREAM_NO_COPY=1 so that the
+        // kernel's waits run out (see filter_stream_kernel)
+        const char *env = std::getenv("FBP_TEST_STREAM_NO_COPY");
+        const int skip = (env && env[0] == '1') ? 1 : 0;
         switch (a.dtype) {
-            case FBP_F32: return launch_stream_t<float>(fa, a.L, status, s);
-            case FBP_F16: return launch_stream_t<__half>(fa, a.L, status, s);
-            case FBP_BF16: return launch_stream_t<__nv_bfloat16>(fa, a.L, status, s);
+            case FBP_F32: return launch_stream_t<float>(fa, a.L, status, skip, s);
+            case FBP_F16: return launch_stream_t<__half>(fa, a.L, status, skip, s);
+            case FBP_BF16: return launch_stream_t<__nv_bfloat16>(fa, a.L, status, skip, s);
         }
         return fail(FBP_ERR_INVALID_ARG, "dtype");
     }

@@ -135,3 +135,23 @@ def test_streamed_filter_equals_the_plain_kernel(D, rows):
         a1, s1 = api.filter(aligned, g, dtype=dt)
         a2, s2 = api.filter(shifted, g, dtype=dt)
         assert torch.equal(a1, a2) and torch.equal(s1, s2)
+
+
+def test_streamed_filter_wait_runs_out_and_reports(monkeypatch):
+    """Failure detection without a fault: with FBP_TEST_STREAM_NO_COPY=1 the
+    streamed filter issues no row copy, so each block's capped wait on its
+    mbarrier runs out; the kernel records code 6 in the device status word
+    and returns.  The context stays usable: the next call is correct."""
+    api = fbp_api()
+    rng = np.random.default_rng(6)
+    p = rng.standard_normal((8, 8192)).astype(np.float32)
+    g = api.Geometry(8, 8192, 8192)
+    x = to_gpu(p)
+    assert api.device_status() == 0
+    monkeypatch.setenv("FBP_TEST_STREAM_NO_COPY", "1")
+    api.filter(x, g)
+    assert api.device_status() == 6
+    monkeypatch.delenv("FBP_TEST_STREAM_NO_COPY")
+    q, _ = api.filter(x, g)
+    assert api.device_status() == 0
+    assert_within_dr(to_np(q), oracle.filter(p.astype(np.float64)), 2e-5, "after the timeout")
