@@ -605,6 +605,51 @@ def sap_depatch_pack(mask_patches: torch.Tensor, leaves: torch.Tensor, p: SapPar
     return out
 
 
+def sap_host(slices: torch.Tensor, p: SapParams, patches: torch.Tensor | None = None,
+             leaves: torch.Tensor | None = None, n_streams: int = 2, device=None):
+    """Adaptive patching of a stack of uint16 slices held in host memory
+    (int16 tensor [S, n, n], pinned for asynchronous copies): each slice is
+    copied in, patched (sap_edges + sap_patches) and its patches and leaves
+    copied out, on `n_streams` streams so that one slice's copies overlap
+    another's kernels.  Returns host (patches [S, length, P, P],
+    leaves [S, length, 3]); blocks until they are filled."""
+    if slices.is_cuda:
+        raise ValueError("sap_host takes a host tensor; use sap_edges / sap_patches on device tensors")
+    if slices.dtype != torch.int16 or not slices.is_contiguous() or slices.dim() != 3:
+        raise ValueError("slices must be a contiguous int16 tensor [S, n, n]")
+    S = int(slices.shape[0])
+    if tuple(slices.shape[1:]) != (p.n, p.n):
+        raise ValueError(f"slices have shape {tuple(slices.shape)}, expected [S, {p.n}, {p.n}]")
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    if patches is None:
+        patches = torch.empty((S, p.length, p.patch, p.patch), dtype=torch.float32, pin_memory=True)
+    if leaves is None:
+        leaves = torch.empty((S, p.length, 3), dtype=torch.int32, pin_memory=True)
+    n_streams = max(1, min(n_streams, S))
+    caller = torch.cuda.current_stream(dev)
+    streams = [torch.cuda.Stream(dev) for _ in range(n_streams)]
+    need = sap_workspace_bytes(p)
+    bufs = [(torch.empty((p.n, p.n), dtype=torch.int16, device=dev),
+             torch.empty((p.n, p.n), dtype=torch.uint8, device=dev),
+             torch.empty(need, dtype=torch.uint8, device=dev),
+             torch.empty((p.length, p.patch, p.patch), dtype=torch.float32, device=dev),
+             torch.empty((p.length, 3), dtype=torch.int32, device=dev)) for _ in range(n_streams)]
+    for st in streams:
+        st.wait_stream(caller)
+    for i in range(S):
+        st = streams[i % n_streams]
+        d_in, d_e, d_ws, d_p, d_l = bufs[i % n_streams]
+        with torch.cuda.stream(st):
+            d_in.copy_(slices[i], non_blocking=True)
+            sap_edges(d_in, p, out=d_e, workspace=d_ws)
+            sap_patches(d_in, d_e, p, patches=d_p, leaves=d_l, workspace=d_ws)
+            patches[i].copy_(d_p, non_blocking=True)
+            leaves[i].copy_(d_l, non_blocking=True)
+    for st in streams:
+        st.synchronize()
+    return patches, leaves
+
+
 def prepare(g: Geometry, kind="ramlak", device=None):
     """Build the geometry's constant tables now (before CUDA graph capture)."""
     L = lib()

@@ -71,6 +71,25 @@ def test_patches_match_oracle(n, P, length, seed):
     assert api.device_status() == 0
 
 
+def test_host_stack_overlapped_streams_match_oracle():
+    """sap_host: a stack of pinned host slices through two streams gives,
+    slice by slice, the oracle's leaves and patches (odd count: one stream
+    takes an extra slice)."""
+    api = fbp_api()
+    n, P, length, S = 128, 8, 97, 5
+    imgs = np.stack([random_slice(n, 40 + i) for i in range(S)])
+    lo, hi = thresholds(imgs[0])
+    p = api.SapParams(n, P, length, lo, hi)
+    host = torch.from_numpy(imgs.view(np.int16)).pin_memory()
+    patches, leaves = api.sap_host(host, p)
+    assert not patches.is_cuda and not leaves.is_cuda
+    for i in range(S):
+        ref_leaves, _ = sap.quadtree(imgs[i], sap.canny(imgs[i], lo, hi), P, length)
+        np.testing.assert_array_equal(leaves[i].numpy(), np.array(ref_leaves, dtype=np.int32).reshape(-1, 3))
+        np.testing.assert_array_equal(patches[i].numpy(), sap.extract_patches(imgs[i], ref_leaves, P))
+    assert api.device_status() == 0
+
+
 def test_constant_slice_splits_by_morton_order():
     """No edges and no variance: every key ties, so the order is level, then
     Morton code -- the tree is the first splits of a breadth-first Z-order."""

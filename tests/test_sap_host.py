@@ -46,3 +46,18 @@ def test_workspace_size_and_checks(L):
     assert L.sap_patches(q, q, None, q, ctypes.byref(p), ws, need, None) == _lib.FBP_ERR_INVALID_ARG
     assert L.sap_edges(None, q, ctypes.byref(p), ws, need, None) == _lib.FBP_ERR_INVALID_ARG
     assert L.sap_edges(q, q, None, ws, need, None) == _lib.FBP_ERR_INVALID_ARG
+
+
+def test_host_stack_call_checks_its_arguments():
+    """sap_host validates the host stack before touching a device."""
+    import torch
+    from paper_2505_13955_gb300 import api
+    p = api.SapParams(64, 8, 10, 1, 2)
+    with pytest.raises(ValueError):
+        api.sap_host(torch.zeros((2, 64, 64), dtype=torch.int32), p)
+    with pytest.raises(ValueError):
+        api.sap_host(torch.zeros((2, 64, 32), dtype=torch.int16), p)
+    with pytest.raises(ValueError):
+        api.sap_host(torch.zeros((64, 64), dtype=torch.int16), p)
+    with pytest.raises(ValueError):
+        api.sap_host(torch.zeros((2, 64, 128), dtype=torch.int16)[:, :, ::2], p)
