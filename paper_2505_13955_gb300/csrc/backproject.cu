@@ -17,22 +17,27 @@ namespace {
 // Compiled tile shapes: threads TXT x TYT, pixels per thread PX x PY,
 // angles (generic) or angle pairs (orbit) per staged tile KT.  Orbit shapes
 // use the 90-degree symmetry (bp_orbit.cuh) and need the standard geometry.
+// minb: resident blocks per SM the orbit kernels are compiled for (the
+// register cap is 65536 / (minb x threads)).  Variant 7 runs six 128-thread
+// blocks (80 registers, 8 bytes of spill): 24 warps per SM instead of 16 hide
+// more shared-load latency, +3 % over four blocks at N = 8192 (seven blocks
+// spill 68 bytes, eight fit 64 registers without spill but measure between).
 struct ShapeDesc {
-    int txt, tyt, px, py, kt, orbit, packed;
+    int txt, tyt, px, py, kt, orbit, packed, minb;
 };
 constexpr ShapeDesc kShapes[] = {
-    {16, 16, 4, 4, 32, 0, 0},   // 0: 64 x 64 tile
-    {16, 16, 4, 4, 16, 0, 0},   // 1
-    {16, 16, 4, 2, 32, 0, 0},   // 2: 64 x 32
-    {16, 16, 2, 4, 32, 0, 0},   // 3: 32 x 64
-    {16, 16, 4, 4, 64, 0, 0},   // 4
-    {32, 8, 2, 8, 32, 0, 0},    // 5: 64 x 64, warps 4 x 2
-    {16, 8, 2, 4, 16, 1, 0},    // 6: orbit of 32 x 32 tiles, 16 angle pairs per stage
-    {16, 8, 2, 4, 8, 1, 0},     // 7: orbit of 32 x 32 tiles, 8 pairs
-    {16, 16, 4, 4, 8, 1, 0},    // 8: orbit of 64 x 64 tiles, 8 pairs
-    {16, 8, 2, 4, 32, 1, 0},    // 9: orbit of 32 x 32 tiles, 32 pairs
-    {16, 16, 4, 4, 8, 1, 1},    // 10: as 8, packed pair arithmetic (16-bit rows only)
-    {16, 8, 2, 4, 16, 1, 1},    // 11: as 6, packed pair arithmetic (16-bit rows only)
+    {16, 16, 4, 4, 32, 0, 0, 0},   // 0: 64 x 64 tile
+    {16, 16, 4, 4, 16, 0, 0, 0},   // 1
+    {16, 16, 4, 2, 32, 0, 0, 0},   // 2: 64 x 32
+    {16, 16, 2, 4, 32, 0, 0, 0},   // 3: 32 x 64
+    {16, 16, 4, 4, 64, 0, 0, 0},   // 4
+    {32, 8, 2, 8, 32, 0, 0, 0},    // 5: 64 x 64, warps 4 x 2
+    {16, 8, 2, 4, 16, 1, 0, 4},    // 6: orbit of 32 x 32 tiles, 16 angle pairs per stage
+    {16, 8, 2, 4, 8, 1, 0, 6},     // 7: orbit of 32 x 32 tiles, 8 pairs
+    {16, 16, 4, 4, 8, 1, 0, 2},    // 8: orbit of 64 x 64 tiles, 8 pairs
+    {16, 8, 2, 4, 32, 1, 0, 4},    // 9: orbit of 32 x 32 tiles, 32 pairs
+    {16, 16, 4, 4, 8, 1, 1, 2},    // 10: as 8, packed pair arithmetic (16-bit rows only)
+    {16, 8, 2, 4, 16, 1, 1, 4},    // 11: as 6, packed pair arithmetic (16-bit rows only)
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -84,8 +89,8 @@ __global__ void __launch_bounds__(TXT *TYT) bp_kernel(BpArgs a)
     bp_tile<TXT, TYT, PX, PY, KT, T, CHECKED>(j, bp_smem);
 }
 
-template <int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED, bool PACKED>
-__global__ void __launch_bounds__(TXT *TYT, (TXT * TYT >= 256) ? 2 : 4) bp_orbit_kernel(BpArgs a)
+template <int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED, bool PACKED, int MINB>
+__global__ void __launch_bounds__(TXT *TYT, MINB) bp_orbit_kernel(BpArgs a)
 {
     extern __shared__ __align__(16) unsigned char bp_smem[];
     constexpr int TILE = TXT * PX;
@@ -132,7 +137,8 @@ fbp_status launch_orbit_shape(const BpLaunch &L, cudaStream_t s, unsigned *statu
     constexpr bool kPacked = sd.packed && sizeof(T) == 2;
     if (sd.packed && sizeof(T) != 2)
         return fail(FBP_ERR_UNSUPPORTED, "variant %d is for 16-bit rows", V);
-    auto kern = bp_orbit_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, T, kChecked, kPacked>;
+    static_assert(sd.minb >= 1, "orbit shapes state their blocks per SM");
+    auto kern = bp_orbit_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, T, kChecked, kPacked, sd.minb>;
     BpArgs a;
     a.filt = L.filt;
     a.row_scale = L.row_scale;
