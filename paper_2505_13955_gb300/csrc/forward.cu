@@ -286,8 +286,12 @@ constexpr int kTT = 64;                  // tile side
 constexpr int kTPad = 3;                 // zero border; clamped candidate reads land in it
 constexpr int kTSide = kTT + 2 * kTPad;  // 70
 constexpr int kTPitch = 71;              // odd: a column walk's lanes read distinct banks
-constexpr int kTThreads = 256;
-constexpr int kTChunk = kTThreads;       // angles whose walk parameters are staged together
+// Threads per block: the four-slice form runs 384 (12 warps; 79 registers,
+// so two blocks -- as many as its 80 KB tile allows -- give 24 warps per SM
+// to cover the shared-load latency: 2.12 -> 2.27 Tupdates/s at N = 1024,
+// K = 1800); the one- and two-slice forms run 256, four blocks per SM.
+// Each thread stages one angle's walk parameters per chunk.
+template <int NS> constexpr int tile_threads() { return NS == 4 ? 384 : 256; }
 constexpr int kFrac = 23;                // fraction bits of a walk position
 constexpr int kBias = 4;
 
@@ -411,13 +415,15 @@ __device__ __forceinline__ void tile_walk(const typename PixVec<NS>::T *tile, lo
 template <int NS>
 constexpr size_t tile_bytes() { return ((size_t)kTSide * kTPitch * 4 * NS + 63) / 64 * 64; }
 template <int NS>
-constexpr size_t tile_smem() { return tile_bytes<NS>() + (size_t)kTChunk * sizeof(TileAngle); }
+constexpr size_t tile_smem() { return tile_bytes<NS>() + (size_t)tile_threads<NS>() * sizeof(TileAngle); }
 
 // NS slices per block (slices slice_base + NS * blockIdx.y + [0, NS)).
 template <int BPW, int NS>
-__global__ void __launch_bounds__(kTThreads, NS == 4 ? 2 : 4) fwd_tile_kernel(FwdTileArgs a)
+__global__ void __launch_bounds__(tile_threads<NS>(), NS == 4 ? 2 : 4) fwd_tile_kernel(FwdTileArgs a)
 {
     using V = typename PixVec<NS>::T;
+    constexpr int kTThreads = tile_threads<NS>();
+    constexpr int kTChunk = kTThreads;       // angles whose walk parameters are staged together
     constexpr int LS = 32 / BPW;             // lines walked side by side in a warp
     extern __shared__ __align__(64) unsigned char fwd_smem[];
     V *tile = reinterpret_cast<V *>(fwd_smem);
@@ -527,7 +533,7 @@ static fbp_status launch_tile_group(FwdTileArgs a, int first, int count, unsigne
     for (int g0 = 0; g0 < groups; g0 += 65535) {
         a.slice_base = first + NS * g0;
         dim3 grid(tiles, (unsigned)std::min(65535, groups - g0));
-        fwd_tile_kernel<BPW, NS><<<grid, kTThreads, smem, s>>>(a);
+        fwd_tile_kernel<BPW, NS><<<grid, tile_threads<NS>(), smem, s>>>(a);
         FBP_CUDA_TRY(cudaGetLastError());
     }
     return FBP_OK;
