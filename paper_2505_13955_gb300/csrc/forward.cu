@@ -395,12 +395,19 @@ __device__ __forceinline__ void tile_walk(const typename PixVec<NS>::T *tile, lo
         const float w1 = 1.f - fabsf(w0 + gm1);
         const float w2 = fmaxf(0.f, c2 - w0);
         // the third candidate carries weight only when e < 2 - 2g (a quarter
-        // of the (bin, line) pairs over a half turn): its load is skipped otherwise
+        // of the (bin, line) pairs over a half turn): the multi-slice forms
+        // skip its 8- or 16-byte load otherwise; the one-slice form loads it
+        // always (a 4-byte read inside the padded tile, weight 0), which
+        // costs fewer instructions than the predicate
         const V v0 = e[0], v1 = e[SW];
         V v2;
+        if constexpr (NS == 1) {
+            v2 = e[2 * SW];
+        } else {
 #pragma unroll
-        for (int t = 0; t < NS; ++t) set_comp(v2, t, 0.f);
-        if (w2 > 0.f) v2 = e[2 * SW];
+            for (int t = 0; t < NS; ++t) set_comp(v2, t, 0.f);
+            if (w2 > 0.f) v2 = e[2 * SW];
+        }
 #pragma unroll
         for (int t = 0; t < NS; ++t) {
             acc[t] = fmaf(w0, comp(v0, t), acc[t]);
