@@ -528,3 +528,17 @@ def test_blur_difference_replay(sigma, D):
     pb = oracle.gaussian_blur(p, sigma)
     ref = np.diff(np.concatenate([[0.0], pb, [0.0]]))
     np.testing.assert_allclose(d, ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("NS,threads,blocks", [(1, 256, 4), (2, 256, 4), (4, 384, 2)])
+def test_forward_tile_shared_memory_allows_its_blocks_per_sm(NS, threads, blocks):
+    """fwd_tile_kernel's dynamic shared memory -- the padded 70 x 71 tile of
+    NS-slice vectors plus one 64-byte walk record per thread -- fits one
+    block (227 KB) and the blocks per SM its launch bounds ask for (228 KB
+    per SM, 1 KB reserved per block)."""
+    side, pitch = 70, 71
+    tile = (side * pitch * 4 * NS + 63) // 64 * 64
+    smem = tile + threads * 64
+    assert smem <= 227 * 1024
+    assert blocks * (smem + 1024) <= 228 * 1024
+    assert threads % 32 == 0
