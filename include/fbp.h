@@ -343,8 +343,9 @@ fbp_status radon_forward(const float *slice, float *sino, const fbp_geometry *g,
  *       and adds per-tile partial bins with floating-point atomics; 1-3 take
  *       one slice per block (8, 16 or 32 bins per warp), 4 takes four slices
  *       per block and 5 two (one shared-memory load serves every slice;
- *       leftover slices run through the narrower forms).  The sum over tiles is not in a fixed order, so
- *       results may differ between runs in the last bits.  Needs
+ *       leftover slices run through the narrower forms).  The sum over
+ *       tiles is not in a fixed order, so results may differ between runs
+ *       in the last bits.  Needs
  *       pixel_size / det_spacing in [0.9429, 1] (FBP_ERR_UNSUPPORTED
  *       otherwise).  The sinogram is cleared on `stream` first.
  *  -1   the default: the fastest tile-owned variant where it applies, else 0.
