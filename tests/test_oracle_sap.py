@@ -165,6 +165,19 @@ def test_hand_worked_quadtree():
     assert splits[2] == (4, 4, 4)
 
 
+def test_ties_go_to_the_shallower_node_then_the_smaller_morton_code():
+    """16 x 16 constant slice, no edges, P = 2: every V and variance key
+    ties.  Split 1 takes the root; split 2 the level-1 node with the smallest
+    Morton code, (0, 0, 8); split 3 must take another level-1 node, (8, 0, 8),
+    not one of the level-2 children (0, 0, 4) ... just created."""
+    img = np.full((16, 16), 1234, dtype=np.uint16)
+    edges = np.zeros((16, 16), dtype=np.uint8)
+    leaves, splits = sap.quadtree(img, edges, 2, 10)
+    assert splits == [(0, 0, 16), (0, 0, 8), (8, 0, 8)]
+    assert leaves == [(0, 0, 4), (4, 0, 4), (0, 4, 4), (4, 4, 4),
+                      (8, 0, 4), (12, 0, 4), (8, 4, 4), (12, 4, 4), (0, 8, 8), (8, 8, 8)]
+
+
 def random_slice(n, seed):
     rng = np.random.default_rng(seed)
     img = rng.integers(0, 3000, (n, n)).astype(np.uint16)
