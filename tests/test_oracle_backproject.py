@@ -66,6 +66,25 @@ def test_backprojection_of_constant_is_pi_on_disk(N, K):
     assert np.all(f[R > 0.5 * (N - 1) + 1.0] < np.pi)
 
 
+@pytest.mark.parametrize("pixel_size,det_spacing", [(0.75, 1.5), (1.5, 1.0), (1.0, 1.25)])
+def test_backprojection_of_constant_scales_with_pixel_over_bin_size(pixel_size, det_spacing):
+    """u = alpha (X cos + Y sin) + c_d with alpha = pixel_size / det_spacing:
+    a constant row of D bins covers a pixel at radius R at every angle when
+    alpha R <= (D - 1)/2 (value pi), and misses it at the angles where
+    |alpha R cos(theta - phi)| > (D + 1)/2, which exist once alpha R > (D + 1)/2
+    (value below pi)."""
+    N, D, K = 32, 16, 12
+    alpha = pixel_size / det_spacing
+    g = Geometry(K, D, N, pixel_size=pixel_size, det_spacing=det_spacing)
+    f = oracle.backproject(np.ones((K, D)), g)
+    X = np.arange(N) - 0.5 * (N - 1)
+    R = np.hypot(*np.meshgrid(X, X))
+    inside, outside = alpha * R <= 0.5 * (D - 1), alpha * R > 0.5 * (D + 1) + 0.5
+    assert inside.sum() > 20 and outside.sum() > 20
+    np.testing.assert_allclose(f[inside], np.pi, rtol=1e-13)
+    assert np.all(f[outside] < np.pi - 0.1)
+
+
 def dense_forward(g: Geometry) -> np.ndarray:
     N = g.n
     A = np.empty((g.n_angles * g.n_det, N * N))
