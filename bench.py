@@ -392,6 +392,13 @@ class Timed:
     def between(self, i: int, j: int) -> float:
         return float(np.mean([e[i].elapsed_time(e[j]) for e in self.ev]))
 
+    def spread(self, i: int, j: int) -> dict:
+        """Median, min and max over the timed steps of the time from event i
+        to event j of each step."""
+        t = [e[i].elapsed_time(e[j]) for e in self.ev]
+        return {"median": float(np.median(t)), "min": float(np.min(t)), "max": float(np.max(t)),
+                "n": len(t)}
+
 
 def init_device():
     import torch
@@ -476,7 +483,7 @@ def run_uniform(args) -> None:
         per_rank = allgather_floats([ms, float(updates)])
         rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
         results[dt] = {"value": rate / 1e9, "ms_per_step": ms_step, "bp_ms": T.between(1, 2),
-                       "filter_ms": T.between(0, 1), "clocks": T.clocks,
+                       "filter_ms": T.between(0, 1), "step_spread": T.spread(0, 2), "clocks": T.clocks,
                        "slices_per_s": S * len(per_rank) / (ms_step / 1e3)}
         del filt, rs
 
@@ -536,6 +543,8 @@ def run_uniform(args) -> None:
     line.update({
         "slices_per_s": main["slices_per_s"],
         "bp_ms_per_step": main["bp_ms"], "filter_ms_per_step": main["filter_ms"],
+        # filter + backprojection time of each timed step (CUDA events)
+        "step_ms_spread": main["step_spread"],
         "bp_gupdates_per_s": achieved,
         "roofline": {"bound": "alu", "achieved": achieved, "peak": rp["peak"], "unit": UNIT,
                      "frac": achieved / rp["peak"], "traffic": traffic,

@@ -58,3 +58,42 @@ def test_two_rank_sharding_and_aggregation():
 def test_aggregate_single_rank():
     rate, t = bench.aggregate([80.0], [1000])
     assert t == 80.0 and rate == pytest.approx(1000 / 0.08)
+
+
+class _FakeEvent:
+    """Stands in for torch.cuda.Event on a CPU host: each record() advances
+    a shared clock by 1 ms before taking the time."""
+    clock = 0.0
+
+    def __init__(self, enable_timing=False):
+        self.t = None
+
+    def record(self, stream=None):
+        _FakeEvent.clock += 1.0
+        self.t = _FakeEvent.clock
+
+    def elapsed_time(self, other):
+        return other.t - self.t
+
+
+def test_timed_reports_each_steps_time_and_their_spread(monkeypatch):
+    import torch
+    monkeypatch.setattr(torch.cuda, "Event", _FakeEvent)
+    monkeypatch.setattr(torch.cuda, "synchronize", lambda *a, **k: None)
+    T = bench.Timed(None, steps=5, warmup=3, n_events=2)
+    work = iter([1.0, 3.0, 2.0, 5.0, 4.0])
+    calls = []
+
+    def step(evs):
+        calls.append(evs is not None)
+        if evs:
+            evs[0].record()
+            _FakeEvent.clock += next(work)
+            evs[1].record()
+
+    ms = T.run(step, None)
+    assert calls == [False] * 3 + [True] * 5                 # warm-up steps record nothing
+    # each step spans its work + 1 ms of the second record; 5 steps + the bracketing events
+    assert T.spread(0, 1) == {"median": 4.0, "min": 2.0, "max": 6.0, "n": 5}
+    assert T.between(0, 1) == 4.0
+    assert ms == (15.0 + 10.0 + 1.0) / 5
