@@ -102,7 +102,10 @@ fbp_status sap_patches(const unsigned short *slice, const unsigned char *edges, 
  *   leaves        device, int [length][3] as written by sap_patches.
  *   packed        device, uint8 [n][n / 4]: receives the 2-bit mask.
  * The leaves must tile the slice (as sap_patches writes them); nothing else
- * is written.  No workspace.
+ * is written.  A leaf that lies outside the slice, or whose side is not
+ * P 2^j or whose corner is not a multiple of its side, is skipped and
+ * recorded in the device status word (code 5, fbp_last_device_status); the
+ * other leaves are still written.  No workspace.
  */
 fbp_status sap_depatch_pack(const unsigned char *mask_patches, const int *leaves,
                             unsigned char *packed, const sap_params *p, fbp_stream_t stream);
