@@ -97,3 +97,24 @@ def test_timed_reports_each_steps_time_and_their_spread(monkeypatch):
     assert T.spread(0, 1) == {"median": 4.0, "min": 2.0, "max": 6.0, "n": 5}
     assert T.between(0, 1) == 4.0
     assert ms == (15.0 + 10.0 + 1.0) / 5
+
+
+@pytest.mark.slow
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` times the FP64 oracle on the host cores
+    (no GPU involved) and prints one JSON line with the contract's keys."""
+    import json
+    import subprocess
+    import sys
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    r = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "3"],
+                       cwd=root, capture_output=True, text=True, timeout=600)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["unit"] == "Gupdates/s" and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["steps"] == 1 and d["warmup"] >= 3
+    cb = d["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
