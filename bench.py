@@ -54,6 +54,7 @@ if ROOT not in sys.path:
 
 METRIC = "backprojection Gupdates/s & slices/s at N=8192; % of roofline vs plain FP32 FBP"
 UNIT = "Gupdates/s"
+SAP_METRIC = "SAP patching slices/s at N=8192 (Canny + adaptive quadtree + Z-order patches)"
 WORKLOAD = "fbp_precision_n8192"
 SMS = 152
 FP32_LANES = 128
@@ -319,29 +320,44 @@ def run_reference(args) -> None:
         return
     from paper_2505_13955_gb300 import phantoms
     w = phantoms.WORKLOADS[args.workload]
-    if w.ragged or w.offset is not None or not w.filter:
-        w = phantoms.WORKLOADS[WORKLOAD]
     block = 1024 if args.steps + args.warmup <= 20 else 512
+    metric, unit = METRIC, UNIT
+    # each workload's oracle sample, in its own metric: (sample function, seconds per slice from a value)
+    if w.name == "sap_patching_n8192":
+        metric, unit = SAP_METRIC, "slices/s"
+        fn, slice_seconds = (lambda _b: cpu_sample_sap(2048, w.n)), (lambda v: 1.0 / v)
+        what = f"{w.name}: S={w.n_slices} uint16 slices, n={w.n}"
+    elif w.name == "gd_refine_n1024":
+        fn, slice_seconds = (lambda _b: cpu_sample_gd(w)), (lambda v: 2 * w.n * w.n * w.n_angles / (v * 1e9))
+        what = f"{w.name}: S={w.n_slices} N=D={w.n} K={w.n_angles}, one gradient step per slice"
+    elif w.offset is not None and not w.ragged:
+        fn = lambda b: cpu_sample_offset(w, b)
+        slice_seconds = lambda v: w.n * w.n * (w.n_angles // 2) / (v * 1e9)
+        what = f"{w.name}: S={w.n_slices} N={w.n} K={w.n_angles} over a full turn, folded"
+    else:
+        if w.ragged or not w.filter:
+            w = phantoms.WORKLOADS[WORKLOAD]      # ragged batches: per-update cost of the uniform stack
+        fn, slice_seconds = (lambda b: cpu_sample(w, b)), (lambda v: w.n * w.n * w.n_angles / (v * 1e9))
+        what = f"{w.name}: S={w.n_slices} N=D={w.n} K={w.n_angles} random ellipses, {w.filter}"
     for _ in range(args.warmup):
-        cpu_sample(w, block // 2)
+        fn(block // 2)
     vals = []
     sample = None
     for _ in range(args.steps):
-        r = cpu_sample(w, block)
+        r = fn(block)
         vals.append(r["value"])
         sample = r
     value = float(np.median(vals))
-    slice_s = w.n * w.n * w.n_angles / (value * 1e9)
+    slice_s = slice_seconds(value)
     line = {
-        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+        "impl": "reference", "metric": metric, "value": value, "unit": unit, "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * slice_s * w.n_slices, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": {"workload": f"{w.name}: S={w.n_slices} N=D={w.n} K={w.n_angles} "
-                   f"random ellipses, {w.filter}", "sample": "see cpu_baseline"},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": sample["cores"], "kind": "oracle",
+        "config": {"workload": what, "sample": "see cpu_baseline"},
+        "cpu_baseline": {"value": value, "unit": unit, "cores": sample["cores"], "kind": "oracle",
                          "sample": sample["sample"]},
-        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+        "e2e": {"value": value, "unit": unit, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "slices_per_s": 1.0 / slice_s,
     }
     print(json.dumps(line), flush=True)
@@ -995,7 +1011,7 @@ def run_sap(args) -> None:
                     f"thresholds {p.canny_lo}/{p.canny_hi}",
         "l2": "inputs larger than L2 (2.1 GB of slices per step), no flush",
         "parallelism": f"slices sharded over {ws} GPU(s), no collective"})
-    line["metric"] = "SAP patching slices/s at N=8192 (Canny + adaptive quadtree + Z-order patches)"
+    line["metric"] = SAP_METRIC
     line["unit"] = "slices/s"
     line.update({
         "sap_edges_ms_per_slice": edges_ms, "sap_patches_ms_per_slice": patches_ms,
