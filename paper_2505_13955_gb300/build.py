@@ -24,8 +24,12 @@ CSRC = os.path.join(HERE, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(HERE, "_build")
 
-CU_SOURCES = ["runtime.cu", "filter.cu", "backproject.cu", "forward.cu", "fbp_api.cu", "noalloc.cu", "sap.cu",
-              "bp_texture.cu"]
+FILTER_UNITS = [f"filter_{fam}_{dt}.cu" for fam in ("plain", "stream", "batched")
+                for dt in ("f32", "f16", "bf16")]
+CU_SOURCES = ["runtime.cu", "filter.cu", *FILTER_UNITS, "backproject.cu", "forward.cu", "fbp_api.cu",
+              "noalloc.cu", "sap.cu", "bp_texture.cu"]
+# only these translation units read FBP_CHECKED; the checked twin shares every other object
+CHECKED_SOURCES = ["backproject.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -51,23 +55,18 @@ def _compile(src: str, obj: str, defines: list[str]) -> None:
         raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
 
 
-def build_cuda(name: str = "libfbp.so", defines: list[str] | None = None,
-               force: bool = False, jobs: int | None = None) -> str:
-    defines = defines or []
-    out = os.path.join(HERE, name)
-    srcs = [os.path.join(CSRC, s) for s in CU_SOURCES]
-    newest = max([os.path.getmtime(s) for s in srcs] + [_headers_mtime(),
-                                                       os.path.getmtime(__file__)])
-    if not force and os.path.exists(out) and os.path.getmtime(out) >= newest:
-        return out
-    tag = name.replace(".so", "")
+def _objects(tag: str, sources: list[str], defines: list[str], ex) -> list:
     bdir = os.path.join(BUILD, tag)
     os.makedirs(bdir, exist_ok=True)
-    objs = [os.path.join(bdir, s.replace(".cu", ".o")) for s in CU_SOURCES]
-    with cf.ThreadPoolExecutor(max_workers=jobs or min(len(CU_SOURCES), os.cpu_count() or 4)) as ex:
-        futs = [ex.submit(_compile, s, o, defines) for s, o in zip(CU_SOURCES, objs)]
-        for f in futs:
-            f.result()
+    out = []
+    for src in sources:
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
+        out.append((obj, ex.submit(_compile, src, obj, defines)))
+    return out
+
+
+def _link(name: str, objs: list[str]) -> str:
+    out = os.path.join(HERE, name)
     tmp = out + ".tmp%d" % os.getpid()
     cmd = [nvcc(), *ARCH, "-shared", "-cudart", "static", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -77,12 +76,31 @@ def build_cuda(name: str = "libfbp.so", defines: list[str] | None = None,
     return out
 
 
+def build_cuda(force: bool = False, jobs: int | None = None) -> list[str]:
+    """libfbp.so and libfbp_checked.so: every translation unit compiled once
+    (in parallel), CHECKED_SOURCES a second time with -DFBP_CHECKED."""
+    names = ("libfbp.so", "libfbp_checked.so")
+    srcs = [os.path.join(CSRC, s) for s in CU_SOURCES]
+    newest = max([os.path.getmtime(s) for s in srcs] + [_headers_mtime(), os.path.getmtime(__file__)])
+    outs = [os.path.join(HERE, n) for n in names]
+    if not force and all(os.path.exists(o) and os.path.getmtime(o) >= newest for o in outs):
+        return outs
+    with cf.ThreadPoolExecutor(max_workers=jobs or os.cpu_count() or 4) as ex:
+        # the longest units first, so the pool stays busy
+        order = sorted(CU_SOURCES, key=lambda s: (not s.startswith("filter_"), s))
+        plain = dict(_objects("libfbp", order, [], ex))
+        checked = dict(_objects("libfbp_checked", CHECKED_SOURCES, ["-DFBP_CHECKED"], ex))
+        for fut in list(plain.values()) + list(checked.values()):
+            fut.result()
+    objs = [os.path.join(BUILD, "libfbp", s.replace(".cu", ".o")) for s in CU_SOURCES]
+    objs_checked = [os.path.join(BUILD, "libfbp_checked", s.replace(".cu", ".o")) if s in CHECKED_SOURCES
+                    else o for s, o in zip(CU_SOURCES, objs)]
+    return [_link(names[0], objs), _link(names[1], objs_checked)]
+
+
 def build_all(force: bool = False) -> list[str]:
     from . import phantoms
-    with cf.ThreadPoolExecutor(max_workers=2) as ex:
-        a = ex.submit(build_cuda, "libfbp.so", [], force)
-        b = ex.submit(build_cuda, "libfbp_checked.so", ["-DFBP_CHECKED"], force)
-        outs = [a.result(), b.result()]
+    outs = build_cuda(force=force)
     outs.append(phantoms.build(force=force))
     return outs
 

@@ -15,7 +15,7 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 @pytest.fixture(scope="module")
 def L():
     from paper_2505_13955_gb300 import build
-    build.build_cuda("libfbp.so")
+    build.build_cuda()
     return _lib.load()
 
 

@@ -148,7 +148,7 @@ def test_fbp_shepp_logan_n256_vs_oracle_and_phantom():
 
 def test_checked_build_reports_no_fault_on_valid_geometries():
     from paper_2505_13955_gb300 import build
-    build.build_cuda("libfbp_checked.so", ["-DFBP_CHECKED"])
+    build.build_cuda()
     api = fbp_api()
     assert api.device_status("checked") == 0
     extra = [dict(K=70, D=230, N=256, pixel_size=0.9), dict(K=64, D=300, N=256, pixel_size=2.4),

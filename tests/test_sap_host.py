@@ -10,7 +10,7 @@ from paper_2505_13955_gb300 import _lib
 @pytest.fixture(scope="module")
 def L():
     from paper_2505_13955_gb300 import build
-    build.build_cuda("libfbp.so")
+    build.build_cuda()
     return _lib.load()
 
 
