@@ -56,25 +56,57 @@ METRIC = "backprojection Gupdates/s & slices/s at N=8192; % of roofline vs plain
 UNIT = "Gupdates/s"
 SAP_METRIC = "SAP patching slices/s at N=8192 (Canny + adaptive quadtree + Z-order patches)"
 WORKLOAD = "fbp_precision_n8192"
-SMS = 152
-FP32_LANES = 128
+FP32_LANES = 128                # nominal FP32 lanes per SM
 ALU_OPS_PER_UPDATE = 4          # coordinate step, fraction, interpolate, accumulate
-SHARED_BYTES_PER_CLK = 128      # shared-memory load bandwidth per SM
+SHARED_BYTES_PER_CLK = 128      # nominal shared-memory load bandwidth per SM
 SAMPLES_PER_UPDATE = 2          # linear interpolation reads two detector samples
 BP_KERNEL_REGEX = "bp_kernel|bp_orbit_kernel"
 
 
-def roofline_peak(sm_mhz: float, dtype: str) -> dict:
-    """Backprojection ceilings in updates/s: the FP32 ALU ceiling
-    (lanes x SMs x clock / 4 ops) and the on-chip load ceiling
-    (128 B/clk/SM / (2 samples x sample bytes)); the roofline is the lower."""
+def roofline_peak(sm_mhz: float, dtype: str, sms: int, onchip: dict | None = None) -> dict:
+    """Backprojection ceilings in Gupdates/s at `sm_mhz`: the FP32 ALU ceiling
+    (FMA lane operations per SM clock x SMs x clock / 4 ops) and the
+    shared-load ceiling (bytes per SM clock x SMs x clock / (2 samples x
+    sample bytes)), each from the nominal per-SM rates (128 lanes, 128 B) and,
+    when `onchip` is given, from the rates measured on this GPU
+    (fbp_measure_onchip_peaks).  The roofline is the lower of the two, taken
+    from the measured rates when there are any."""
     sample_bytes = 4 if dtype == "f32" else 2
-    c_alu = SMS * FP32_LANES * sm_mhz * 1e6 / ALU_OPS_PER_UPDATE
-    c_lds = SMS * SHARED_BYTES_PER_CLK * sm_mhz * 1e6 / (SAMPLES_PER_UPDATE * sample_bytes)
-    return {"c_alu": c_alu / 1e9, "c_lds": c_lds / 1e9, "peak": min(c_alu, c_lds) / 1e9,
-            "basis": f"min(C_alu = {SMS} SMs x {FP32_LANES} FP32 lanes x {sm_mhz:.0f} MHz / "
-                     f"{ALU_OPS_PER_UPDATE} ops, C_lds = {SMS} x {SHARED_BYTES_PER_CLK} B/clk x "
-                     f"{sm_mhz:.0f} MHz / ({SAMPLES_PER_UPDATE} x {sample_bytes} B)) per update"}
+    clk = sm_mhz * 1e6
+
+    def ceil(lanes, lds_b):
+        c_alu = sms * lanes * clk / ALU_OPS_PER_UPDATE / 1e9
+        c_lds = sms * lds_b * clk / (SAMPLES_PER_UPDATE * sample_bytes) / 1e9
+        return c_alu, c_lds
+
+    c_alu, c_lds = ceil(FP32_LANES, SHARED_BYTES_PER_CLK)
+    out = {"c_alu_nominal": c_alu, "c_lds_nominal": c_lds, "peak_nominal": min(c_alu, c_lds),
+           "sms": sms, "sm_mhz": sm_mhz}
+    basis = (f"min(C_alu = {sms} SMs x {{lanes}} FP32 FMA/clk x {sm_mhz:.0f} MHz / {ALU_OPS_PER_UPDATE} ops, "
+             f"C_lds = {sms} SMs x {{lds}} B/clk x {sm_mhz:.0f} MHz / ({SAMPLES_PER_UPDATE} x {sample_bytes} B)) "
+             "per update")
+    if onchip:
+        m_alu, m_lds = ceil(onchip["fma_per_clk_per_sm"], onchip["lds_bytes_per_clk_per_sm"])
+        out.update({"c_alu": m_alu, "c_lds": m_lds, "peak": min(m_alu, m_lds),
+                    "bound": "lds" if m_lds <= m_alu else "alu", "measured": True,
+                    "basis": basis.format(lanes=f"{onchip['fma_per_clk_per_sm']:.1f} (measured)",
+                                          lds=f"{onchip['lds_bytes_per_clk_per_sm']:.1f} (measured)")})
+    else:
+        out.update({"c_alu": c_alu, "c_lds": c_lds, "peak": min(c_alu, c_lds),
+                    "bound": "lds" if c_lds <= c_alu else "alu", "measured": False,
+                    "basis": basis.format(lanes=FP32_LANES, lds=SHARED_BYTES_PER_CLK) + " (nominal)"})
+    return out
+
+
+def roofline_entry(achieved: float, rp: dict, kernel: str, traffic=None, **extra) -> dict:
+    """The line's roofline object for an updates-per-second kernel."""
+    r = {"bound": rp["bound"], "achieved": achieved, "peak": rp["peak"], "unit": UNIT,
+         "frac": achieved / rp["peak"], "traffic": traffic, "kernel": kernel,
+         "c_alu": rp["c_alu"], "c_lds": rp["c_lds"],
+         "peak_nominal": rp["peak_nominal"], "frac_nominal": achieved / rp["peak_nominal"],
+         "peak_basis": rp["basis"] + f", sm_max_mhz {rp['sm_mhz']:.0f} from MEASURED_PEAKS.json"}
+    r.update(extra)
+    return r
 
 
 # ---------------------------------------------------------------------------
@@ -254,6 +286,35 @@ def cpu_sample(w, block: int) -> dict:
             "seconds": t2 - t0}
 
 
+def cpu_sample_pipeline(w, block: int) -> dict:
+    """Oracle on one counts slice: Beer-Lambert + Gaussian blur and filtering
+    of all K rows, backprojection of a block x block pixel square over all
+    angles and its uint16 codes; whole-slice time extrapolated by pixel
+    count (as cpu_sample)."""
+    import oracle
+    from paper_2505_13955_gb300 import phantoms
+    P = phantoms.PIPELINE
+    N, K = w.n, w.n_angles
+    I = phantoms.slice_counts(w, 0).astype(np.float64)
+    g = oracle.Geometry(K, N, N)
+    t0 = time.perf_counter()
+    p = oracle.preprocess(I, w.photons, mu_scale=float(N), floor=1.0, sigma=P["blur_sigma"])
+    q = oracle.filter(p, oracle.RAMLAK)
+    t1 = time.perf_counter()
+    block = min(block, N)
+    c0 = N // 2 - block // 2
+    rr, cc = np.meshgrid(np.arange(c0, c0 + block), np.arange(c0, c0 + block), indexing="ij")
+    mu = oracle.backproject_pixels(q, g, rr.ravel(), cc.ravel())
+    oracle.hu_codes(mu, P["mu_water"], P["mu_air"], P["hu_min"], P["hu_max"])
+    t2 = time.perf_counter()
+    t_slice = (t1 - t0) + (t2 - t1) * (N * N) / (block * block)
+    return {"value": N * N * K / t_slice / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"1 counts slice N={N} K={K}: Beer-Lambert + blur + filter of all {K} rows "
+                      f"({t1 - t0:.2f} s) + backprojection and uint16 codes of a {block}x{block} pixel "
+                      f"block over all angles ({t2 - t1:.2f} s), extrapolated to the full slice"}
+
+
 def cpu_sample_offset(w, block: int) -> dict:
     """Oracle on one offset-scan slice: weight, embed and fold its rows,
     filter all folded rows, backproject a block x block pixel square over
@@ -422,18 +483,29 @@ def init_device():
     ws, rank, local = dist_env()
     if ws > 1:
         torch.cuda.set_device(local)
-        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+        if not dist.is_initialized():
+            dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     else:
         torch.cuda.set_device(0)
     return ws, rank, torch.device("cuda", torch.cuda.current_device())
 
 
-def finish(line: dict, ws: int, rank: int):
-    import torch.distributed as dist
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if ws > 1:
-        dist.destroy_process_group()
+_ONCHIP: dict = {}
+
+
+def device_ceilings(dev) -> tuple[float, int, dict | None]:
+    """(sm_max_mhz from MEASURED_PEAKS.json, the device's SM count, the on-chip
+    rates measured on it by fbp_measure_onchip_peaks, once per process)."""
+    import torch
+    from paper_2505_13955_gb300 import api
+    if dev.index not in _ONCHIP:
+        try:
+            _ONCHIP[dev.index] = api.measure_onchip_peaks(dev)
+        except Exception as e:           # the nominal ceilings stand in, and the line says so
+            print(f"on-chip probe failed: {e}", file=sys.stderr)
+            _ONCHIP[dev.index] = None
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    return peaks().get("sm_max_mhz") or 2070.0, sms, _ONCHIP[dev.index]
 
 
 def base_line(args, ws, value, ms_step, dtype_label, config) -> dict:
@@ -536,12 +608,10 @@ def run_uniform(args) -> None:
         del pin_in, pin_out
 
     if rank != 0:
-        finish({}, ws, rank)
-        return
+        return None
     main = results[args.dtype]
-    pk = peaks()
-    sm_max = pk.get("sm_max_mhz") or 2070.0
-    rp = roofline_peak(sm_max, args.dtype)
+    sm_max, sms, onchip = device_ceilings(dev)
+    rp = roofline_peak(sm_max, args.dtype, sms, onchip)
     achieved = updates / (main["bp_ms"] / 1e3) / 1e9
     variant = resolved_variant(api, g, args.dtype, args.variant)
     traffic = args.traffic_bytes
@@ -562,23 +632,23 @@ def run_uniform(args) -> None:
         # filter + backprojection time of each timed step (CUDA events)
         "step_ms_spread": main["step_spread"],
         "bp_gupdates_per_s": achieved,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": rp["peak"], "unit": UNIT,
-                     "frac": achieved / rp["peak"], "traffic": traffic,
-                     "kernel": BP_KERNEL_REGEX, "c_alu": rp["c_alu"], "c_lds": rp["c_lds"],
-                     "peak_basis": rp["basis"] + " (sm_max_mhz from MEASURED_PEAKS.json)",
-                     "traffic_basis": "ncu dram bytes per slice x slices, kernel unchanged since capture"},
+        "roofline": roofline_entry(achieved, rp, BP_KERNEL_REGEX, traffic,
+                                   traffic_basis="ncu dram bytes per slice x slices, kernel unchanged "
+                                                 "since capture (null otherwise)"),
+        "onchip_measured": onchip,
         "clocks": main["clocks"],
         "gpu_launches": 2 * args.steps,
     })
     for dt in dtypes[1:]:
         r = results[dt]
-        rpd = roofline_peak(sm_max, dt)
+        rpd = roofline_peak(sm_max, dt, sms, onchip)
         ach = updates / (r["bp_ms"] / 1e3) / 1e9
         vdt = resolved_variant(api, g, dt, args.variant)
         line[f"staged_{dt}"] = {
             "value": r["value"], "unit": UNIT, "ratio_to_f32": r["value"] / main["value"],
             "bp_gupdates_per_s": ach, "bp_ratio_to_f32": ach / achieved,
             "roofline_frac": ach / rpd["peak"], "roofline_peak": rpd["peak"],
+            "roofline_frac_nominal": ach / rpd["peak_nominal"], "roofline_bound": rpd["bound"],
             "traffic": captured_traffic(vdt, dt, S, N, K),
             "slices_per_s": r["slices_per_s"], "ms_per_step": r["ms_per_step"],
             "bp_variant": vdt}
@@ -589,7 +659,7 @@ def run_uniform(args) -> None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = {k: v for k, v in cpu_sample(w, args.cpu_block).items() if k != "seconds"}
-    finish(line, ws, rank)
+    return line
 
 
 def run_pipeline(args) -> None:
@@ -664,11 +734,10 @@ def run_pipeline(args) -> None:
         del pin_in, pin_out
 
     if rank != 0:
-        finish({}, ws, rank)
-        return
+        return None
     pk = peaks()
-    sm_max = pk.get("sm_max_mhz") or 2070.0
-    rp = roofline_peak(sm_max, "f32")
+    sm_max, sms, onchip = device_ceilings(dev)
+    rp = roofline_peak(sm_max, "f32", sms, onchip)
     achieved = updates / (bp_ms / 1e3) / 1e9
     hbm = pk.get("hbm_gbs")
     fbytes = S * K * N * 8.0                 # counts read + filtered rows written
@@ -685,14 +754,14 @@ def run_pipeline(args) -> None:
         "filter_counts_gb_per_s": fbytes / (f_ms / 1e3) / 1e9,
         "filter_counts_hbm_frac": (fbytes / (f_ms / 1e3) / 1e9 / hbm) if hbm else None,
         "plain_fbp_ms_per_step": plain_ms, "ratio_to_plain_fbp": plain_ms / ms_step,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": rp["peak"], "unit": UNIT,
-                     "frac": achieved / rp["peak"], "traffic": None, "kernel": BP_KERNEL_REGEX,
-                     "peak_basis": rp["basis"] + " (sm_max_mhz from MEASURED_PEAKS.json)"},
+        "roofline": roofline_entry(achieved, rp, BP_KERNEL_REGEX),
         "clocks": clocks, "gpu_launches": 2 * args.steps,
     })
     if e2e is not None:
         line["e2e"] = e2e
-    finish(line, ws, rank)
+    if not args.no_cpu_baseline and ws == 1:
+        line["cpu_baseline"] = cpu_sample_pipeline(w, args.cpu_block)
+    return line
 
 
 def run_offset(args) -> None:
@@ -744,11 +813,10 @@ def run_offset(args) -> None:
                          "slices_per_s": S * len(per_rank) / (ms_step / 1e3)}
         del filt
     if rank != 0:
-        finish({}, ws, rank)
-        return
+        return None
     main, unf = results[True], results[False]
-    sm_max = peaks().get("sm_max_mhz") or 2070.0
-    rp = roofline_peak(sm_max, "f32")
+    sm_max, sms, onchip = device_ceilings(dev)
+    rp = roofline_peak(sm_max, "f32", sms, onchip)
     achieved = updates / (main["bp_ms"] / 1e3) / 1e9
     gv = main["gv"]
     line = base_line(args, ws, main["value"], main["ms_per_step"], "f32", {
@@ -763,10 +831,7 @@ def run_offset(args) -> None:
         "slices_per_s": main["slices_per_s"],
         "filter_offset_ms_per_step": main["filter_ms"], "bp_ms_per_step": main["bp_ms"],
         "bp_gupdates_per_s": achieved,
-        "roofline": {"bound": "alu", "achieved": achieved, "peak": rp["peak"], "unit": UNIT,
-                     "frac": achieved / rp["peak"], "traffic": None, "kernel": BP_KERNEL_REGEX,
-                     "c_alu": rp["c_alu"], "c_lds": rp["c_lds"],
-                     "peak_basis": rp["basis"] + " (sm_max_mhz from MEASURED_PEAKS.json)"},
+        "roofline": roofline_entry(achieved, rp, BP_KERNEL_REGEX),
         "unfolded": {"value": unf["value"], "unit": UNIT, "ms_per_step": unf["ms_per_step"],
                      "filter_offset_ms_per_step": unf["filter_ms"], "bp_ms_per_step": unf["bp_ms"],
                      "bp_variant": unf["variant"], "slices_per_s": unf["slices_per_s"]},
@@ -775,7 +840,7 @@ def run_offset(args) -> None:
     })
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_sample_offset(w, args.cpu_block)
-    finish(line, ws, rank)
+    return line
 
 
 def run_ragged(args) -> None:
@@ -813,23 +878,25 @@ def run_ragged(args) -> None:
         T = Timed(stream, args.steps, args.warmup)
         ms = T.run(lambda _: graph.replay(), dev.index)
         clocks = T.clocks
-        # per-slice launches, same stream, same tile variant
+        # per-slice launches on the same stream: with the library's default
+        # kernel for each slice (the baseline), and with the batch's tile variant
         filts = [torch.empty_like(s, dtype=tdt) for s in sinos]
         rss = [torch.empty((g.n_angles,), device=dev) if args.dtype != "f32" else None for g in geoms]
 
-        def per_slice(_):
-            for s, g, f, r, o in zip(sinos, geoms, filts, rss, outs):
-                api.filter(s, g, kind=w.filter, dtype=tdt, out=f, row_scale=r)
-                api.backproject(f, g, row_scale=r, out=o, variant=variant)
+        def per_slice_with(v):
+            def run(_):
+                for s, g, f, r, o in zip(sinos, geoms, filts, rss, outs):
+                    api.filter(s, g, kind=w.filter, dtype=tdt, out=f, row_scale=r)
+                    api.backproject(f, g, row_scale=r, out=o, variant=v)
+            return run
 
-        T2 = Timed(stream, max(1, args.steps // 2), args.warmup)
-        ms_single = T2.run(per_slice, None)
+        ms_single = Timed(stream, max(1, args.steps // 2), args.warmup).run(per_slice_with(-1), None)
+        ms_same = Timed(stream, max(1, args.steps // 2), args.warmup).run(per_slice_with(variant), None)
     assert api.device_status() == 0
     per_rank = allgather_floats([ms, float(updates)])
     rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
     if rank != 0:
-        finish({}, ws, rank)
-        return
+        return None
     line = base_line(args, ws, rate / 1e9, ms_step, DT_LABEL[args.dtype], {
         "workload": f"{w.name}: {len(idx)} slices per GPU, N in {w.n_choices}, K in {w.k_choices}, "
                     "random ellipses, Ram-Lak; one persistent launch per step, CUDA-graph replay",
@@ -837,11 +904,13 @@ def run_ragged(args) -> None:
         "bp_variant": variant, "autotune": tuned})
     line.update({"slices_per_s": len(idx) * len(per_rank) / (ms_step / 1e3),
                  "per_slice_launches": {"value": updates / (ms_single / 1e3) / 1e9, "unit": UNIT,
-                                        "ms_per_step": ms_single,
+                                        "ms_per_step": ms_single, "bp_variant": "library default per slice",
                                         "launches_per_step": 2 * len(idx)},
                  "speedup_vs_per_slice": ms_single / ms,
+                 "per_slice_launches_same_variant": {"value": updates / (ms_same / 1e3) / 1e9, "unit": UNIT,
+                                                     "ms_per_step": ms_same, "bp_variant": variant},
                  "clocks": clocks, "gpu_launches": 2 * args.steps})
-    finish(line, ws, rank)
+    return line
 
 
 def run_mixed(args) -> None:
@@ -893,13 +962,14 @@ def run_mixed(args) -> None:
         rss = [torch.empty((g.n_angles,), device=dev) if args.dtype != "f32" else None for g in rows_geoms]
 
         def per_scan(_):
+            # each scan alone with the library's default kernel
             for s, sc, gv, f, r, o in zip(sinos, scans, rows_geoms, filts, rss, outs):
                 if sc.overlap:
                     api.filter_offset(s, sc.g, sc.overlap, sc.fold, kind=w.filter, dtype=tdt, out=f,
                                       row_scale=r)
                 else:
                     api.filter(s, sc.g, kind=w.filter, dtype=tdt, out=f, row_scale=r)
-                api.backproject(f, gv, row_scale=r, out=o, variant=variant)
+                api.backproject(f, gv, row_scale=r, out=o, variant=-1)
 
         T2 = Timed(stream, max(1, args.steps // 2), args.warmup)
         ms_single = T2.run(per_scan, None)
@@ -910,8 +980,7 @@ def run_mixed(args) -> None:
     per_rank_c = allgather_floats([res["group_cyclic"][0], float(updates)])
     rate_c, ms_c = aggregate([r[0] for r in per_rank_c], [int(r[1]) for r in per_rank_c])
     if rank != 0:
-        finish({}, ws, rank)
-        return
+        return None
     line = base_line(args, ws, rate / 1e9, ms_step, DT_LABEL[args.dtype], {
         "workload": f"{w.name}: {len(idx)} scans per GPU ({n_off} offset: full turn, detector 9N/16 bins "
                     f"off the axis, folded), N in {w.n_choices}, half-turn K in {w.k_choices}, random "
@@ -922,10 +991,11 @@ def run_mixed(args) -> None:
                  "group_cyclic": {"value": rate_c / 1e9, "unit": UNIT, "ms_per_step": ms_c,
                                   "ratio_to_queue": ms_step / ms_c},
                  "per_scan_launches": {"value": updates / (ms_single / 1e3) / 1e9, "unit": UNIT,
-                                       "ms_per_step": ms_single, "launches_per_step": 2 * len(idx)},
+                                       "ms_per_step": ms_single, "bp_variant": "library default per scan",
+                                       "launches_per_step": 2 * len(idx)},
                  "speedup_vs_per_scan": ms_single / ms,
                  "clocks": clocks, "gpu_launches": 2 * args.steps})
-    finish(line, ws, rank)
+    return line
 
 
 SAP_BYTES_PER_PIXEL = 8   # codes read by Canny (2) + edge map written (1) + codes and edges read by
@@ -1001,8 +1071,7 @@ def run_sap(args) -> None:
     per_rank = allgather_floats([ms, float(S)])
     rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
     if rank != 0:
-        finish({}, ws, rank)
-        return
+        return None
     hbm = peaks().get("hbm_gbs") or 6800.0
     gbs = SAP_BYTES_PER_PIXEL * n * n * S / (ms / 1e3) / 1e9
     line = base_line(args, ws, rate, ms_step, "u16 codes, exact integer / f64", {
@@ -1025,8 +1094,8 @@ def run_sap(args) -> None:
     if e2e is not None:
         line["e2e"] = e2e
     if not args.no_cpu_baseline and ws == 1:
-        line["cpu_baseline"] = cpu_sample_sap(2048, n)
-    finish(line, ws, rank)
+        line["cpu_baseline"] = cpu_sample_sap(max(256, min(2048, args.cpu_block)), n)
+    return line
 
 
 def run_gd(args) -> None:
@@ -1097,12 +1166,11 @@ def run_gd(args) -> None:
     per_rank = allgather_floats([ms, float(updates)])
     rate, ms_step = aggregate([r_[0] for r_ in per_rank], [int(r_[1]) for r_ in per_rank])
     if rank != 0:
-        finish({}, ws, rank)
-        return
+        return None
     a_ms, at_ms = T.between(0, 1), T.between(1, 2)
     fwd_variant = args.fwd_variant if args.fwd_variant >= 0 else 4
-    sm_max = peaks().get("sm_max_mhz") or 2070.0
-    rp = roofline_peak(sm_max, "f32")
+    sm_max, sms, onchip = device_ceilings(dev)
+    rp = roofline_peak(sm_max, "f32", sms, onchip)
     a_rate = S * N * N * K / a_ms / 1e6
     line = base_line(args, ws, rate / 1e9, ms_step, "f32", {
         "workload": f"{w.name}: S={S} slices per GPU, N=D={N}, K={K}, Poisson 1e4 photons, "
@@ -1113,16 +1181,74 @@ def run_gd(args) -> None:
                  "adjoint_AT": {"ms": at_ms, "gupdates_per_s": S * N * N * K / at_ms / 1e6},
                  # the forward projector dominates the step; it has the
                  # backprojection's per-update accounting (one pixel-angle pair)
-                 "roofline": {"bound": "alu", "achieved": a_rate, "peak": rp["peak"], "unit": UNIT,
-                              "frac": a_rate / rp["peak"], "traffic": None,
-                              "kernel": "fwd_tile_kernel" if fwd_variant else "fwd_strip_kernel",
-                              "c_alu": rp["c_alu"], "c_lds": rp["c_lds"],
-                              "peak_basis": rp["basis"] + " (sm_max_mhz from MEASURED_PEAKS.json)"},
+                 "roofline": roofline_entry(a_rate, rp, "fwd_tile_kernel" if fwd_variant else "fwd_strip_kernel"),
                  "refine_50": refine,
                  "eta": eta, "clocks": T.clocks, "gpu_launches": 2 * args.steps})
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_sample_gd(w)
-    finish(line, ws, rank)
+    return line
+
+
+RUNNERS = {
+    "fbp_ragged_batch": run_ragged,
+    "gd_refine_n1024": run_gd,
+    "fbp_pipeline_n8192": run_pipeline,
+    "fbp_offset_n8192": run_offset,
+    "fbp_mixed_batch": run_mixed,
+    "sap_patching_n8192": run_sap,
+}
+
+# Compact runs of the other workloads after the headline (one GPU): the key,
+# the workload, and what differs from the headline's arguments.  Slice counts
+# below a workload's own are stated in its config ("slices_per_gpu").
+SUB_RECORDS = (
+    ("config1_fbp_single_n256", "fbp_single_n256",
+     dict(steps=200, e2e_steps=20, all_dtypes=False, texture=False, cpu_block=256)),
+    ("config2_fbp_stack_n2048", "fbp_stack_n2048",
+     dict(steps=5, e2e_steps=1, all_dtypes=True, texture=False, cpu_block=256)),
+    ("config4_fbp_ragged_batch", "fbp_ragged_batch", dict(steps=5)),
+    ("config5_gd_refine_n1024", "gd_refine_n1024", dict(steps=5)),
+    ("f1_pipeline_n8192", "fbp_pipeline_n8192", dict(steps=3, slices=4, e2e_steps=1, cpu_block=256)),
+    ("f2_offset_n8192", "fbp_offset_n8192", dict(steps=4, slices=4, cpu_block=256)),
+    ("f3_mixed_batch", "fbp_mixed_batch", dict(steps=5)),
+    ("f4_sap_patching_n8192", "sap_patching_n8192", dict(steps=3, slices=4, e2e_steps=1, cpu_block=1024)),
+)
+SUB_DROP = ("n_gpus", "higher_is_better", "scaling", "vs_baseline", "data")
+
+
+def run_sub_records(args, head: dict) -> dict:
+    """Every other workload in a compact form (fewer steps, fewer slices for
+    the 8192^2 counts, offset and patching stacks), each with its own value,
+    step time, roofline where one applies, CPU baseline and clocks."""
+    import copy
+    import torch
+    out = {}
+    for key, workload, over in SUB_RECORDS:
+        a = copy.copy(args)
+        a.workload, a.warmup, a.variant, a.fwd_variant = workload, 3, -1, -1
+        a.dtype, a.traffic_bytes, a.slices, a.sub_records = "f32", None, None, False
+        for name, v in over.items():
+            setattr(a, name, v)
+        t0 = time.perf_counter()
+        try:
+            sub = RUNNERS.get(workload, run_uniform)(a)
+        except Exception as e:           # one workload's failure must not hide the others
+            sub = {"error": f"{type(e).__name__}: {e}"}
+        torch.cuda.empty_cache()
+        if sub is None:
+            continue
+        for name in SUB_DROP:
+            sub.pop(name, None)
+        if a.slices is not None and "config" in sub:
+            sub["config"]["slices_per_gpu"] = a.slices
+        if "cpu_baseline" not in sub and "error" not in sub and "cpu_baseline" in head \
+                and workload in ("fbp_ragged_batch", "fbp_mixed_batch"):
+            cb = dict(head["cpu_baseline"])
+            cb["sample"] = "the headline stack's oracle sample (per-update cost): " + cb["sample"]
+            sub["cpu_baseline"] = cb
+        sub["wall_s"] = time.perf_counter() - t0
+        out[key] = sub
+    return out
 
 
 def main(argv=None):
@@ -1147,24 +1273,23 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--traffic-bytes", type=float, default=None,
                     help="DRAM bytes per backprojection launch from an ncu capture")
+    ap.add_argument("--sub-records", action=argparse.BooleanOptionalAction, default=True,
+                    help="after the headline workload (one GPU), also run every other workload "
+                         "in a compact form and attach its line under sub_records")
     args = ap.parse_args(argv)
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up steps
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == "fbp_ragged_batch":
-        run_ragged(args)
-    elif args.workload == "gd_refine_n1024":
-        run_gd(args)
-    elif args.workload == "fbp_pipeline_n8192":
-        run_pipeline(args)
-    elif args.workload == "fbp_offset_n8192":
-        run_offset(args)
-    elif args.workload == "fbp_mixed_batch":
-        run_mixed(args)
-    elif args.workload == "sap_patching_n8192":
-        run_sap(args)
-    else:
-        run_uniform(args)
+        return
+    ws, rank, _ = init_device()
+    line = RUNNERS.get(args.workload, run_uniform)(args)
+    if args.sub_records and args.workload == WORKLOAD and ws == 1 and line is not None:
+        line["sub_records"] = run_sub_records(args, line)
+    if rank == 0 and line is not None:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
 
 
 if __name__ == "__main__":

@@ -452,6 +452,31 @@ fbp_status fbp_prepare(const fbp_geometry *g, int kind, fbp_stream_t stream);
 /* Free every cached table on every device (synchronises those devices). */
 void fbp_release_tables(void);
 
+/*
+ * Measured on-chip ceilings of the current device, for the roofline of the
+ * backprojection and the forward projector (the paper has no counterpart:
+ * this is a measurement service).  Both kernels are bound by the path that
+ * carries shared-memory loads into registers and by the FP32 lanes, so
+ * their ceilings are per-SM rates rather than HBM bandwidth.  Two probe
+ * kernels run on every SM (eight 256-thread blocks each): conflict-free
+ * 16-byte shared loads, and eight independent FP32 FMA chains per thread;
+ * each SM's cycles come from its own clock64 counter, so the rates are per
+ * clock and per SM, whatever clock the GPU ran at (median over SMs).
+ *   lds_bytes_per_clk_per_sm  bytes delivered by ld.shared.v4 per SM cycle
+ *   fma_per_clk_per_sm        FP32 FMA lane operations per SM cycle
+ *   sm_clock_mhz              cycles / event time of the shared-load probe
+ *   sm_count                  multiprocessors of the device
+ * Synchronous (runs on the legacy default stream and waits, ~10 ms); not for
+ * stream capture.  Returns FBP_ERR_INVALID_ARG for a NULL out.
+ */
+typedef struct {
+    double lds_bytes_per_clk_per_sm;
+    double fma_per_clk_per_sm;
+    double sm_clock_mhz;
+    int sm_count;
+} fbp_onchip_peaks;
+fbp_status fbp_measure_onchip_peaks(fbp_onchip_peaks *out);
+
 #ifdef __cplusplus
 }
 #endif

@@ -86,6 +86,11 @@ FBP_ORDER_QUEUE = 0
 FBP_ORDER_GROUP_CYCLIC = 1
 
 
+class COnchipPeaks(ctypes.Structure):
+    _fields_ = [("lds_bytes_per_clk_per_sm", ctypes.c_double), ("fma_per_clk_per_sm", ctypes.c_double),
+                ("sm_clock_mhz", ctypes.c_double), ("sm_count", ctypes.c_int)]
+
+
 class COffsetScan(ctypes.Structure):
     _fields_ = [("overlap", ctypes.c_double), ("fold", ctypes.c_int)]
 
@@ -133,6 +138,7 @@ SIGNATURES = {
     "fbp_last_device_status": (ctypes.c_int, [_vp, ctypes.POINTER(ctypes.c_int)]),
     "fbp_prepare": (ctypes.c_int, [_G, ctypes.c_int, _vp]),
     "fbp_release_tables": (None, []),
+    "fbp_measure_onchip_peaks": (ctypes.c_int, [ctypes.POINTER(COnchipPeaks)]),
 }
 
 _libs: dict[str, ctypes.CDLL] = {}

@@ -674,6 +674,20 @@ def release_tables():
     lib().fbp_release_tables()
 
 
+def measure_onchip_peaks(device=None) -> dict:
+    """Measured per-SM ceilings of the device (fbp_measure_onchip_peaks):
+    shared-load bytes and FP32 FMA lane operations per SM clock, the SM
+    clock seen during the probe, and the SM count."""
+    L = lib()
+    dev = torch.device("cuda") if device is None else torch.device(device)
+    out = _lib.COnchipPeaks()
+    with torch.cuda.device(dev):
+        _lib.check(L.fbp_measure_onchip_peaks(ctypes.byref(out)), L, "fbp_measure_onchip_peaks")
+    return {"lds_bytes_per_clk_per_sm": out.lds_bytes_per_clk_per_sm,
+            "fma_per_clk_per_sm": out.fma_per_clk_per_sm,
+            "sm_clock_mhz": out.sm_clock_mhz, "sm_count": out.sm_count}
+
+
 # ---------------------------------------------------------------------------
 # Differentiation: A and A^T as a torch.autograd.Function pair.
 # ---------------------------------------------------------------------------

@@ -118,3 +118,62 @@ def test_reference_arm_prints_one_contract_line():
     cb = d["cpu_baseline"]
     assert cb["kind"] == "oracle" and cb["cores"] >= 1 and cb["value"] == d["value"] and cb["sample"]
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
+
+
+def test_roofline_ceilings_nominal_and_measured():
+    """The FP32-row ceiling is the shared-load path (8 B per update through
+    128 B/clk/SM = 16 updates/clk/SM) and the 16-bit one ties it with the
+    ALU (32 updates/clk/SM); measured per-SM rates replace the nominal ones
+    and the binding unit follows them; the SM count is a parameter."""
+    rp = bench.roofline_peak(2000.0, "f32", 100)
+    assert rp["measured"] is False and rp["bound"] == "lds"
+    assert rp["c_lds"] == pytest.approx(100 * 16 * 2000e6 / 1e9)
+    assert rp["c_alu"] == pytest.approx(100 * 32 * 2000e6 / 1e9)
+    assert rp["peak"] == rp["peak_nominal"] == rp["c_lds"]
+    r16 = bench.roofline_peak(2000.0, "f16", 100)
+    assert r16["c_lds"] == pytest.approx(r16["c_alu"])
+    onchip = {"lds_bytes_per_clk_per_sm": 120.0, "fma_per_clk_per_sm": 100.0}
+    m = bench.roofline_peak(2000.0, "f16", 100, onchip)
+    assert m["measured"] is True
+    assert m["c_lds"] == pytest.approx(100 * 120 / 4 * 2000e6 / 1e9)      # 30 updates/clk/SM
+    assert m["c_alu"] == pytest.approx(100 * 100 / 4 * 2000e6 / 1e9)      # 25 updates/clk/SM
+    assert m["bound"] == "alu" and m["peak"] == m["c_alu"]
+    assert m["peak_nominal"] == pytest.approx(r16["peak"])
+    e = bench.roofline_entry(0.5 * m["peak"], m, "k")
+    assert e["frac"] == pytest.approx(0.5) and e["bound"] == "alu"
+    assert e["frac_nominal"] == pytest.approx(0.5 * m["peak"] / m["peak_nominal"])
+
+
+def test_sub_records_cover_every_workload_and_survive_a_failure(monkeypatch):
+    """The default run attaches one compact line per other workload (BASELINE
+    configs 1, 2, 4, 5 and the next rows f1-f4); a runner that raises is
+    recorded as an error without losing the others; overrides reach the
+    runner and the ragged batches borrow the headline's CPU baseline."""
+    import argparse
+    keys = [k for k, _, _ in bench.SUB_RECORDS]
+    for want in ("config1", "config2", "config4", "config5", "f1_", "f2_", "f3_", "f4_"):
+        assert sum(k.startswith(want) for k in keys) == 1, want
+    seen = {}
+
+    def fake(a):
+        seen[a.workload] = a
+        if a.workload == "gd_refine_n1024":
+            raise RuntimeError("boom")
+        return {"metric": "m", "value": 1.0, "n_gpus": 1, "config": {"workload": a.workload}}
+
+    monkeypatch.setattr(bench, "RUNNERS", {w: fake for _, w, _ in bench.SUB_RECORDS})
+    monkeypatch.setattr(bench, "run_uniform", fake)
+    args = argparse.Namespace(steps=20, warmup=5, variant=3, fwd_variant=2, dtype="bf16", traffic_bytes=1.0,
+                              slices=None, sub_records=True, e2e_steps=2, all_dtypes=True, texture=True,
+                              cpu_block=1024, no_cpu_baseline=False)
+    head = {"cpu_baseline": {"value": 3.0, "sample": "s"}}
+    out = bench.run_sub_records(args, head)
+    assert list(out) == keys
+    assert out["config5_gd_refine_n1024"]["error"] == "RuntimeError: boom"
+    assert "n_gpus" not in out["config1_fbp_single_n256"]
+    assert out["f4_sap_patching_n8192"]["config"]["slices_per_gpu"] == 4
+    assert out["config4_fbp_ragged_batch"]["cpu_baseline"]["value"] == 3.0
+    assert "cpu_baseline" not in out["config2_fbp_stack_n2048"]
+    a = seen["fbp_single_n256"]
+    assert (a.steps, a.warmup, a.variant, a.dtype, a.texture) == (200, 3, -1, "f32", False)
+    assert args.steps == 20 and args.variant == 3          # the headline's arguments are untouched
