@@ -941,7 +941,7 @@ def run_mixed(args) -> None:
     updates = sum(g.n * g.n * g.n_angles for g in rows_geoms)
     n_off = sum(1 for sc in scans if sc.overlap)
     tdt = getattr(torch, DT[args.dtype])
-    variant = max(0, args.variant)
+    variant = args.variant              # -1: the library's batch default (orbit units where they apply)
     outs = [torch.empty((g.n, g.n), device=dev) for g in rows_geoms]
     wsp = torch.empty(api.batched_scans_workspace_bytes(sinos, outs, scans, tdt), dtype=torch.uint8,
                       device=dev)
@@ -986,7 +986,8 @@ def run_mixed(args) -> None:
                     f"off the axis, folded), N in {w.n_choices}, half-turn K in {w.k_choices}, random "
                     "ellipses, Ram-Lak; one persistent launch per step, CUDA-graph replay, atomic work queue",
         "parallelism": f"scans sharded over {ws} GPU(s), no collective",
-        "bp_variant": variant})
+        "bp_variant": variant if variant >= 0 else "library batch default (7: FP32 orbit units, "
+                                                   "generic 64 x 32 tiles where an item has no symmetry)"})
     line.update({"slices_per_s": len(idx) * len(per_rank) / (ms_step / 1e3),
                  "group_cyclic": {"value": rate_c / 1e9, "unit": UNIT, "ms_per_step": ms_c,
                                   "ratio_to_queue": ms_step / ms_c},

@@ -312,7 +312,8 @@ fbp_status fbp_filter_offset(const float *sino, void *filt, float *row_scale, fb
  * 16384 angles (256 KB, held on every device that runs it until the library
  * is unloaded) and calls no allocating routine; inputs and outputs are as for
  * fbp_backproject, and the result equals fbp_backproject's.
- *   * n_angles > 16384 returns FBP_ERR_UNSUPPORTED.
+ *   * n_angles > 16384 returns FBP_ERR_UNSUPPORTED; filt and slice may not
+ *     overlap (FBP_ERR_INVALID_ARG), as for fbp_backproject.
  *   * The first call on a device looks up the array's device address; make
  *     that first call before any stream capture.
  *   * All calls share the array and overwrite it completely.  Calls whose
@@ -377,7 +378,17 @@ int fbp_bp_variant_supports(int variant, fbp_dtype dtype, const fbp_geometry *g)
  *   workspace  device, >= fbp_batched_workspace_bytes(items, count, dtype)
  *              bytes, 256-byte aligned, owned by the caller.  It holds the
  *              filtered rows of every item and the work-queue counter.
- *   bp_variant tile variant for backprojection, -1 = default.
+ *   bp_variant tile variant for backprojection (fbp_bp_variant_info),
+ *              -1 = default (7 for FP32 rows, 10 for 16-bit rows).  With a
+ *              symmetric variant, items whose geometry has the 90-degree
+ *              symmetry (angle step pi/K with K even, det_center = (D-1)/2,
+ *              n a multiple of twice the variant's tile) run its orbit units
+ *              and every other item runs generic tiles of the same thread
+ *              count (64 x 32 for 128-thread variants, 64 x 64 for 256);
+ *              with a generic variant every item runs that variant's tiles.
+ *              Each item's slice is bit-identical to fbp_backproject_variant
+ *              on the same rows with the shape the item ran.  Packed
+ *              variants (10, 11) with FP32 rows return FBP_ERR_UNSUPPORTED.
  * The call captures into a CUDA graph once each item's geometry has been
  * seen by the library (tables exist).
  */
@@ -437,7 +448,10 @@ fbp_status fbp_batched_scans(const fbp_scan_item *items, int count,
  * interpolation index outside the staged table; 3 reserved; 4 a
  * union-find loop of the patching kernels (sap.h) past its cap; 5 a
  * quadtree leaf entry outside the slice (sap.h); 6 a wait of the streamed
- * filter for its row copy past its cap.  The
+ * filter for its row copy past its cap (the block then stops; after two
+ * expired waits a copy into its shared memory may still be in flight, so
+ * treat code 6 as voiding that launch's output and any kernel enqueued after
+ * it on the stream: synchronise and discard those results).  The
  * first fault recorded stays until read.  This call synchronises `stream`,
  * reads and clears the word, and returns FBP_OK or FBP_ERR_DEVICE_STATUS
  * (code in *code if non-NULL).

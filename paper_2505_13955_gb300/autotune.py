@@ -8,7 +8,8 @@ dtype, the device name and its SM count.  Two cases:
 * ``tune_single(g, dtype)`` -- fbp_backproject on one geometry: every variant
   that ``variant_supports`` accepts is timed on one slice of random rows;
 * ``tune_batched(sinos, geoms, dtype)`` -- fbp_batched on a ragged batch: the
-  variants its persistent kernel supports are timed on the batch itself.
+  variants its persistent kernel supports (symmetric ones included: orbit
+  units where an item has the symmetry) are timed on the batch itself.
 
 Timing: CUDA events on the current stream, one warm-up launch, best of
 ``reps``.  Cache: $FBP_AUTOTUNE_CACHE, else ~/.cache/fbp_gb300/autotune.json.
@@ -85,8 +86,9 @@ def single_key(g: api.Geometry, dtype, device=None) -> str:
 
 
 def batched_key(geoms, dtype, device=None) -> str:
+    # v2: the persistent kernel runs orbit units, so symmetric shapes are candidates
     mix = sorted({(g.n_angles, g.n) for g in geoms})
-    return f"batched|{_device_key(device)}|{_dtype_name(dtype)}|" + ",".join(f"{k}x{n}" for k, n in mix)
+    return f"batched-v2|{_device_key(device)}|{_dtype_name(dtype)}|" + ",".join(f"{k}x{n}" for k, n in mix)
 
 
 def tune_single(g: api.Geometry, dtype=torch.float32, reps: int = 3, force: bool = False,
@@ -130,8 +132,12 @@ def tune_batched(sinos, geoms, dtype=torch.float32, reps: int = 2, force: bool =
     ws = torch.empty(api.batched_workspace_bytes(sinos, outs, geoms, dtype), dtype=torch.uint8,
                      device="cuda")
     shapes = api.bp_variants()
-    cands = variants if variants is not None else [s["variant"] for s in shapes
-                                                   if not s["symmetric"] and not s["texture"]]
+    # symmetric shapes run orbit units for the items with the symmetry and
+    # generic tiles of the same threads for the others; packed shapes only
+    # for 16-bit rows
+    cands = variants if variants is not None else [
+        s["variant"] for s in shapes
+        if not s["texture"] and not (s["packed16"] and dtype == torch.float32)]
     times = {}
     for v in cands:
         try:

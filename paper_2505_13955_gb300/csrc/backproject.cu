@@ -38,6 +38,7 @@ constexpr ShapeDesc kShapes[] = {
     {16, 8, 2, 4, 32, 1, 0, 4},    // 9: orbit of 32 x 32 tiles, 32 pairs
     {16, 16, 4, 4, 8, 1, 1, 2},    // 10: as 8, packed pair arithmetic (16-bit rows only)
     {16, 8, 2, 4, 16, 1, 1, 4},    // 11: as 6, packed pair arithmetic (16-bit rows only)
+    {16, 8, 4, 4, 32, 0, 0, 0},    // 12: 64 x 32, 128 threads (the 128-thread orbits' batch fallback)
 };
 constexpr int kNumShapes = sizeof(kShapes) / sizeof(kShapes[0]);
 
@@ -235,23 +236,31 @@ fbp_status launch_variant(const BpLaunch &L, int v, cudaStream_t s, unsigned *st
         case 9: return launch_shape<9, T>(L, s, status);
         case 10: return launch_shape<10, T>(L, s, status);
         case 11: return launch_shape<11, T>(L, s, status);
+        case 12: return launch_shape<12, T>(L, s, status);
     }
     return fail(FBP_ERR_INVALID_ARG, "backprojection variant %d", v);
 }
 
 // ---------------------------------------------------------------------------
-// Persistent ragged-batch kernel: blocks pull (item, tile) units from a
-// global counter until the queue is empty.  Items arrive sorted by angle
-// count, largest first, so the heaviest tiles are handed out first.  The
-// loop is capped at total+1 iterations per block; past the cap it records
-// FAULT_QUEUE_CAP and exits (it cannot wait on anything).
+// Persistent ragged-batch kernel: blocks pull work units from a global
+// counter (or take every P-th unit, cyclic order) until the queue is empty.
+// A unit is one 90-degree orbit of four tiles (bp_orbit.cuh) for an item
+// whose geometry has the symmetry, else one tile of the generic routine
+// (bp_tile.cuh); the two shapes share the block's threads.  Both routines are
+// the single-slice kernels' own, so every item equals its single-slice run
+// with the same shape bit for bit.  The loop is capped at total+1 iterations
+// per block; past the cap it records FAULT_QUEUE_CAP and exits (it cannot
+// wait on anything).
 // ---------------------------------------------------------------------------
-template <int TXT, int TYT, int PX, int PY, int KT, typename T>
-__global__ void __launch_bounds__(TXT *TYT) bp_persistent_kernel(BpBatchArgs a)
+template <int GTX, int GTY, int GPX, int GPY, int GKT, int OTX, int OTY, int OPX, int OPY, int OKT,
+          bool ORBIT, bool PACKED, int MINB, typename T>
+__global__ void __launch_bounds__(GTX *GTY, MINB) bp_persistent_kernel(BpBatchArgs a)
 {
+    static_assert(!ORBIT || OTX * OTY == GTX * GTY, "orbit and tile shapes share the block");
     extern __shared__ __align__(16) unsigned char bp_smem[];
     __shared__ int s_unit;
-    constexpr int TW = TXT * PX, TH = TYT * PY;
+    constexpr int TW = GTX * GPX, TH = GTY * GPY;
+    constexpr int OTILE = OTX * OPX;
     for (int iter = 0;; ++iter) {
         int u;
         if (a.cyclic) {
@@ -276,6 +285,31 @@ __global__ void __launch_bounds__(TXT *TYT) bp_persistent_kernel(BpBatchArgs a)
         }
         const BpBatchItem &it = a.items[lo];
         const int t = u - it.unit_begin;
+        if constexpr (ORBIT) {
+            if (it.orbit) {
+                BpOrbitJob j;
+                j.filt = it.filt;
+                j.row_scale = it.row_scale;
+                j.out = it.slice;
+                j.out16 = nullptr;
+                j.hu_a = j.hu_b = 0.f;
+                j.cs = it.cs;
+                j.K = it.K;
+                j.D = it.D;
+                j.N = it.N;
+                j.alpha = it.alpha;
+                j.det_center = it.det_center;
+                j.scale = it.scale;
+                j.accumulate = 0;
+                j.H = it.H;
+                j.W = 2 * it.H + 1;
+                j.x0 = (t % it.tiles_x) * OTILE;
+                j.y0 = (t / it.tiles_x) * OTILE;
+                j.status = a.status;
+                bp_orbit<OTILE, OTX, OTY, OPX, OPY, OKT, T, false, PACKED>(j, bp_smem);
+                continue;
+            }
+        }
         BpTileJob j;
         j.filt = it.filt;
         j.row_scale = it.row_scale;
@@ -295,34 +329,49 @@ __global__ void __launch_bounds__(TXT *TYT) bp_persistent_kernel(BpBatchArgs a)
         j.x0 = (t % it.tiles_x) * TW;
         j.y0 = (t / it.tiles_x) * TH;
         j.status = a.status;
-        bp_tile<TXT, TYT, PX, PY, KT, T, false>(j, bp_smem);
+        bp_tile<GTX, GTY, GPX, GPY, GKT, T, false>(j, bp_smem);
     }
 }
+
+// Generic variant an orbit variant falls back to for items without the
+// symmetry, with the same threads: 12 (64 x 32 tiles) for 128-thread orbits,
+// 0 (64 x 64) for 256-thread ones.
+constexpr int fallback_variant(int threads) { return threads == 128 ? 12 : 0; }
 
 template <int V, typename T>
 fbp_status launch_persistent_shape(BpBatchArgs &a, int sms, cudaStream_t s)
 {
     constexpr ShapeDesc sd = kShapes[V];
-    auto kern = bp_persistent_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, T>;
-    const size_t smem = bp_smem_size<sd.kt>(2 * a.max_H + 1);
-    if (smem > 200 * 1024) return fail(FBP_ERR_UNSUPPORTED, "backprojection window too wide");
-    fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
-    if (st != FBP_OK) return st;
-    int per_sm = 0;
-    st = blocks_per_sm(reinterpret_cast<const void *>(kern), sd.txt * sd.tyt, smem, &per_sm);
-    if (st != FBP_OK) return st;
-    if (per_sm < 1) return fail(FBP_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
-    const int grid = std::max(1, std::min(sms * per_sm, a.total_units));
-    kern<<<grid, sd.txt * sd.tyt, smem, s>>>(a);
-    FBP_CUDA_TRY(cudaGetLastError());
-    return FBP_OK;
+    constexpr bool kOrbit = sd.orbit != 0;
+    if constexpr (sd.packed && sizeof(T) != 2) {
+        return fail(FBP_ERR_UNSUPPORTED, "variant %d is for 16-bit rows", V);
+    } else {
+        constexpr ShapeDesc gd = kOrbit ? kShapes[fallback_variant(sd.txt * sd.tyt)] : sd;
+        constexpr bool kPacked = sd.packed && sizeof(T) == 2;
+        auto kern = bp_persistent_kernel<gd.txt, gd.tyt, gd.px, gd.py, gd.kt, sd.txt, sd.tyt, sd.px, sd.py,
+                                         sd.kt, kOrbit, kPacked, (kOrbit ? sd.minb : 1), T>;
+        size_t smem = 0;
+        bool any_tile = false, any_orbit = false;
+        for (int i = 0; i < a.count; ++i) (a.items[i].orbit ? any_orbit : any_tile) = true;
+        if (any_tile) smem = bp_smem_size<gd.kt>(2 * a.max_H + 1);
+        if (any_orbit) smem = std::max(smem, bp_orbit_smem_size<sd.kt, T>(2 * a.max_H_orbit + 1));
+        if (smem > 200 * 1024) return fail(FBP_ERR_UNSUPPORTED, "backprojection window too wide");
+        fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
+        if (st != FBP_OK) return st;
+        int per_sm = 0;
+        st = blocks_per_sm(reinterpret_cast<const void *>(kern), sd.txt * sd.tyt, smem, &per_sm);
+        if (st != FBP_OK) return st;
+        if (per_sm < 1) return fail(FBP_ERR_UNSUPPORTED, "persistent kernel does not fit on an SM");
+        const int grid = std::max(1, std::min(sms * per_sm, a.total_units));
+        kern<<<grid, sd.txt * sd.tyt, smem, s>>>(a);
+        FBP_CUDA_TRY(cudaGetLastError());
+        return FBP_OK;
+    }
 }
 
 template <typename T>
 fbp_status launch_persistent_t(BpBatchArgs &a, int v, int sms, cudaStream_t s)
 {
-    if (v < 0 || v >= kNumShapes || kShapes[v].orbit)
-        return fail(FBP_ERR_UNSUPPORTED, "variant %d is not available for ragged batches", v);
     switch (v) {
         case 0: return launch_persistent_shape<0, T>(a, sms, s);
         case 1: return launch_persistent_shape<1, T>(a, sms, s);
@@ -330,8 +379,15 @@ fbp_status launch_persistent_t(BpBatchArgs &a, int v, int sms, cudaStream_t s)
         case 3: return launch_persistent_shape<3, T>(a, sms, s);
         case 4: return launch_persistent_shape<4, T>(a, sms, s);
         case 5: return launch_persistent_shape<5, T>(a, sms, s);
+        case 6: return launch_persistent_shape<6, T>(a, sms, s);
+        case 7: return launch_persistent_shape<7, T>(a, sms, s);
+        case 8: return launch_persistent_shape<8, T>(a, sms, s);
+        case 9: return launch_persistent_shape<9, T>(a, sms, s);
+        case 10: return launch_persistent_shape<10, T>(a, sms, s);
+        case 11: return launch_persistent_shape<11, T>(a, sms, s);
+        case 12: return launch_persistent_shape<12, T>(a, sms, s);
     }
-    return fail(FBP_ERR_INVALID_ARG, "backprojection variant %d", v);
+    return fail(FBP_ERR_UNSUPPORTED, "variant %d is not available for ragged batches", v);
 }
 
 }  // namespace
@@ -372,13 +428,32 @@ bool bp_variant_shape(int v, fbp_bp_shape *out)
 int bp_tile_w(int v) { return v >= 0 && v < kNumShapes ? kShapes[v].txt * kShapes[v].px : 64; }
 int bp_tile_h(int v) { return v >= 0 && v < kNumShapes ? kShapes[v].tyt * kShapes[v].py : 64; }
 
-bool bp_orbit_eligible(const BpLaunch &L, int tile)
+bool bp_persistent_shape(int v, fbp_dtype dtype, BpPersistentShape *out)
+{
+    if (v < 0 || v >= kNumShapes || !out) return false;
+    const ShapeDesc &d = kShapes[v];
+    if (d.packed && dtype == FBP_F32) return false;
+    if (!d.orbit) {
+        *out = {0, d.txt * d.px, d.tyt * d.py};
+        return true;
+    }
+    const ShapeDesc &f = kShapes[fallback_variant(d.txt * d.tyt)];
+    *out = {d.txt * d.px, f.txt * f.px, f.tyt * f.py};
+    return true;
+}
+
+bool bp_orbit_geometry(int K, double angle_step, int D, double det_center, int N, int tile)
 {
     const double pi = 3.14159265358979323846;
-    if (L.K % 2 != 0 || L.N % (2 * tile) != 0) return false;
-    if (std::fabs(L.angle_step * L.K - pi) > 1e-9 * pi) return false;
-    if (std::fabs(L.det_center - 0.5 * (L.D - 1)) > 1e-9 * (1.0 + L.D)) return false;
+    if (K % 2 != 0 || N % (2 * tile) != 0) return false;
+    if (std::fabs(angle_step * K - pi) > 1e-9 * pi) return false;
+    if (std::fabs(det_center - 0.5 * (D - 1)) > 1e-9 * (1.0 + D)) return false;
     return true;
+}
+
+bool bp_orbit_eligible(const BpLaunch &L, int tile)
+{
+    return bp_orbit_geometry(L.K, L.angle_step, L.D, L.det_center, L.N, tile);
 }
 
 constexpr size_t kSmemBudget = 200 * 1024;
@@ -412,6 +487,7 @@ bool bp_variant_fits(int v, const BpLaunch &L)
         case 9: smem = variant_smem<9>(L); break;
         case 10: smem = variant_smem<10>(L); break;
         case 11: smem = variant_smem<11>(L); break;
+        case 12: smem = variant_smem<12>(L); break;
         default: return false;
     }
     if (smem > kSmemBudget) return false;

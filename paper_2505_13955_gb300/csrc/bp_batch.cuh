@@ -17,14 +17,15 @@ struct BpBatchItem {            // one slice of the batch, 80 bytes
     double alpha, det_center;
     int K, D, N;
     float scale;                // angle_step
-    int tiles_x, H;             // tiles per row, staged half-window
-    int unit_begin;             // first work unit (tile) of this item
-    int pad_;
+    int tiles_x, H;             // tiles (orbits) per row, staged half-window
+    int unit_begin;             // first work unit (tile, or orbit of four tiles) of this item
+    int orbit;                  // 1: units are 90-degree orbits (bp_orbit.cuh), 0: tiles
 };
 
 struct BpBatchArgs {
     BpBatchItem items[kMaxBatch];
-    int count, total_units, max_H;
+    int count, total_units;
+    int max_H, max_H_orbit;     // widest staged half-windows of the tile and the orbit items
     int cyclic;                 // 1: block b takes units b, b + P, b + 2P (P = grid); 0: atomic queue
     int *counter;               // work-queue counter (workspace), zeroed before launch
     unsigned *status;
@@ -55,5 +56,14 @@ fbp_status launch_filter_batched(const FilterBatchArgs &a, int total_groups, fbp
 int filter_pairs_per_block(int L);   // row pairs one filter block transforms for length L
 int bp_tile_w(int variant);
 int bp_tile_h(int variant);
+// The persistent kernel's shapes for `variant`: the orbit tile side (0 if the
+// variant has no orbit form) and the generic tile it falls back to for items
+// whose geometry has no 90-degree symmetry.
+struct BpPersistentShape {
+    int orbit_tile;
+    int tile_w, tile_h;
+};
+bool bp_persistent_shape(int variant, fbp_dtype dtype, BpPersistentShape *out);
+bool bp_orbit_geometry(int K, double angle_step, int D, double det_center, int N, int tile);
 
 }  // namespace fbp

@@ -495,7 +495,12 @@ static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kin
         return fail(FBP_ERR_INVALID_ARG, "variant %d", bp_variant);
     if (order != FBP_ORDER_QUEUE && order != FBP_ORDER_GROUP_CYCLIC)
         return fail(FBP_ERR_INVALID_ARG, "order %d", order);
-    const int variant = bp_variant < 0 ? 0 : bp_variant;
+    // default: the symmetric orbit shape (FP32 rows: 32 x 32 orbits; 16-bit
+    // rows: packed 64 x 64 orbits), generic tiles for items without the symmetry
+    const int variant = bp_variant >= 0 ? bp_variant : (dtype == FBP_F32 ? 7 : 10);
+    BpPersistentShape shape;
+    if (!bp_persistent_shape(variant, dtype, &shape))
+        return fail(FBP_ERR_UNSUPPORTED, "variant %d is not available for ragged batches of this dtype", variant);
     std::vector<size_t> foff, soff;
     const size_t need = workspace_layout(plan, dtype, &foff, &soff);
     if (!workspace) return fail(FBP_ERR_WORKSPACE, "workspace is NULL");
@@ -552,21 +557,43 @@ static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kin
     }
     fa->count = count;
 
-    // backprojection descriptors.  Queue: items by total cost K n^2, largest
-    // first.  Group-cyclic: by cost per unit (K per tile), largest first, so
-    // every run of P consecutive units holds units of similar cost.
+    // backprojection descriptors.  An item whose geometry has the 90-degree
+    // symmetry runs orbit units (four tiles each), any other generic tiles.
+    // Queue: items by total cost K n^2, largest first.  Group-cyclic: by cost
+    // per unit, largest first, so every run of P consecutive units holds
+    // units of similar cost.
+    std::vector<int> orbit(count), tiles_x(count), H(count);
+    std::vector<long long> n_units(count), unit_cost(count);
+    for (int i = 0; i < count; ++i) {
+        const fbp_geometry &g = plan[i].gb;
+        const double alpha = g.pixel_size / g.det_spacing;
+        orbit[i] = shape.orbit_tile > 0 &&
+                   bp_orbit_geometry(g.n_angles, g.angle_step, g.n_det, g.det_center, g.n, shape.orbit_tile);
+        if (orbit[i]) {
+            const int T = shape.orbit_tile;
+            tiles_x[i] = g.n / T / 2;
+            H[i] = bp_window_half(alpha, T, T);
+            n_units[i] = (long long)tiles_x[i] * tiles_x[i];
+            unit_cost[i] = 4LL * T * T * g.n_angles;
+        } else {
+            const int TW = shape.tile_w, TH = shape.tile_h;
+            tiles_x[i] = (g.n + TW - 1) / TW;
+            H[i] = bp_window_half(alpha, TW, TH);
+            n_units[i] = (long long)tiles_x[i] * ((g.n + TH - 1) / TH);
+            unit_cost[i] = (long long)TW * TH * g.n_angles;
+        }
+    }
     std::vector<int> idx(count);
     std::iota(idx.begin(), idx.end(), 0);
     std::stable_sort(idx.begin(), idx.end(), [&](int x, int y) {
         const fbp_geometry &a = plan[x].gb, &b = plan[y].gb;
-        if (order == FBP_ORDER_GROUP_CYCLIC) return a.n_angles > b.n_angles;
+        if (order == FBP_ORDER_GROUP_CYCLIC) return unit_cost[x] > unit_cost[y];
         return (long long)a.n_angles * a.n * a.n > (long long)b.n_angles * b.n * b.n;
     });
     auto *ba = new BpBatchArgs();
     std::unique_ptr<BpBatchArgs> ba_owner(ba);
-    const int TW = bp_tile_w(variant), TH = bp_tile_h(variant);
     long long units = 0;
-    int max_H = 0;
+    int max_H = 0, max_H_orbit = 0;
     for (int r = 0; r < count; ++r) {
         const int i = idx[r];
         const fbp_geometry &g = plan[i].gb;
@@ -581,17 +608,21 @@ static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kin
         b.D = g.n_det;
         b.N = g.n;
         b.scale = (float)g.angle_step;
-        b.tiles_x = (g.n + TW - 1) / TW;
-        b.H = bp_window_half(b.alpha, TW, TH);
+        b.tiles_x = tiles_x[i];
+        b.H = H[i];
         b.unit_begin = (int)units;
-        b.pad_ = 0;
-        max_H = std::max(max_H, b.H);
-        units += (long long)b.tiles_x * ((g.n + TH - 1) / TH);
+        b.orbit = orbit[i];
+        if (orbit[i])
+            max_H_orbit = std::max(max_H_orbit, H[i]);
+        else
+            max_H = std::max(max_H, H[i]);
+        units += n_units[i];
         if (units > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "batch too large");
     }
     ba->count = count;
     ba->total_units = (int)units;
     ba->max_H = max_H;
+    ba->max_H_orbit = max_H_orbit;
     ba->cyclic = order == FBP_ORDER_GROUP_CYCLIC ? 1 : 0;
     ba->counter = reinterpret_cast<int *>(ws);
     ba->status = status;

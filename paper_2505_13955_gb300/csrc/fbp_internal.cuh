@@ -42,6 +42,9 @@ struct AngleKey {
 };
 // cos/sin of theta_k = start + k*step, k in [0, K), in double precision.
 fbp_status angle_table(const fbp_geometry &g, cudaStream_t s, const double2 **out);
+// The kernel behind angle_table, enqueued on s into caller-owned cs[K]
+// (returns the launch's error; allocates nothing).
+cudaError_t enqueue_angle_table(double2 *cs, int K, double start, double step, cudaStream_t s);
 
 // Filter transform shape: L = R * C, C = 32 * VPL threads per row pair
 // (n = C n1 + n2, k = k1 + R k2, k2 = kr + VPL kl; see filter.cu).

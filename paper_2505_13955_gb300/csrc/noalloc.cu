@@ -29,16 +29,6 @@ constexpr int kNoAllocMaxAngles = 16384;   // 16384 x 16 B = 256 KB per device
 
 static __device__ __align__(256) double2 g_noalloc_angles[kNoAllocMaxAngles];
 
-// cos/sin of theta_k = start + k * step in double precision into the array.
-__global__ void noalloc_angle_kernel(double2 *cs, int K, double start, double step)
-{
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= K) return;
-    double s, c;
-    sincos(start + (double)k * step, &s, &c);
-    cs[k] = make_double2(c, s);
-}
-
 // Device address of the static array on the current device.  In host code
 // the name g_noalloc_angles is only a host-side stand-in, so the address is
 // looked up once per device (with that device current) and cached.
@@ -90,13 +80,18 @@ extern "C" fbp_status fbp_backproject_noalloc(const void *filt, const float *row
     if (!filt || !slice) return fail(FBP_ERR_INVALID_ARG, "filt or slice is NULL");
     if (dtype != FBP_F32 && !row_scale)
         return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit input");
+    // the same aliasing rule as fbp_backproject: the rows and the slices may not overlap
+    const size_t nin = (size_t)n_slices * g->n_angles * g->n_det * (dtype == FBP_F32 ? 4 : 2);
+    const size_t nout = (size_t)n_slices * g->n * g->n * 4;
+    const char *pi = static_cast<const char *>(filt), *po = reinterpret_cast<const char *>(slice);
+    if (pi < po + nout && po < pi + nin) return fail(FBP_ERR_INVALID_ARG, "slice overlaps filt");
 
     double2 *cs = nullptr;
     st = noalloc_table(&cs);
     if (st != FBP_OK) return st;
     const int K = g->n_angles;
-    noalloc_angle_kernel<<<(K + 255) / 256, 256, 0, stream>>>(cs, K, g->angle_start, g->angle_step);
-    FBP_CUDA_TRY(cudaGetLastError());
+    // the kernel that fills fbp_backproject's cached tables, so both read the same angles
+    FBP_CUDA_TRY(enqueue_angle_table(cs, K, g->angle_start, g->angle_step, stream));
 
     BpLaunch a;
     a.filt = filt;

@@ -293,6 +293,13 @@ int filter_length(int D)
     return L;
 }
 
+cudaError_t enqueue_angle_table(double2 *cs, int K, double start, double step, cudaStream_t s)
+{
+    if (K <= 0) return cudaSuccess;
+    angle_table_kernel<<<(K + 255) / 256, 256, 0, s>>>(cs, K, start, step);
+    return cudaGetLastError();
+}
+
 fbp_status angle_table(const fbp_geometry &g, cudaStream_t s, const double2 **out)
 {
     int dev = 0;
@@ -310,9 +317,7 @@ fbp_status angle_table(const fbp_geometry &g, cudaStream_t s, const double2 **ou
                     g.n_angles);
     double2 *p = nullptr;
     FBP_CUDA_TRY(cudaMalloc(&p, sizeof(double2) * (size_t)g.n_angles));
-    int K = g.n_angles;
-    angle_table_kernel<<<(K + 255) / 256, 256, 0, s>>>(p, K, g.angle_start, g.angle_step);
-    cudaError_t e = cudaGetLastError();
+    cudaError_t e = enqueue_angle_table(p, g.n_angles, g.angle_start, g.angle_step, s);
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
     if (e != cudaSuccess) {
         cudaFree(p);

@@ -47,10 +47,11 @@ def test_backproject_matches_oracle(G):
     assert_within_dr(to_np(f), ref, TOL, str(G))
 
 
-@pytest.mark.parametrize("variant", range(12))
+@pytest.mark.parametrize("variant", range(13))
 def test_every_table_variant_matches_oracle(variant):
     api = fbp_api()
     shape = api.bp_variants()[variant]
+    assert not shape["texture"]
     if shape["packed16"]:
         pytest.skip("16-bit-only variant: covered by the 16-bit test below")
     if shape["symmetric"]:

@@ -21,20 +21,61 @@ def ragged(api, dims, seed=0):
     return sinos, geoms
 
 
-DIMS = [(30, 64), (90, 100), (45, 128), (17, 33), (120, 257), (1, 5), (64, 64)]
+DIMS = [(30, 64), (90, 100), (45, 128), (17, 33), (120, 257), (1, 5), (64, 64), (60, 128)]
 
 
-@pytest.mark.parametrize("variant", [0, 2, 5])
+def item_shape(api, variant, g, dtype=torch.float32):
+    """The single-slice variant a batch item runs: a symmetric variant's own
+    shape where the item's geometry has the symmetry, else the generic
+    variant with the same threads (12 for 128-thread orbits, 0 for 256)."""
+    shape = api.bp_variants()[variant]
+    if not shape["symmetric"] or api.variant_supports(variant, g, dtype):
+        return variant
+    return 12 if shape["threads"] == 128 else 0
+
+
+@pytest.mark.parametrize("variant", [0, 2, 5, 6, 7, 8, 9, 12])
 @pytest.mark.parametrize("kind", ["ramlak", "shepp_logan"])
 def test_batched_bit_identical_to_single_slices(variant, kind):
     api = fbp_api()
     sinos, geoms = ragged(api, DIMS)
     outs = api.fbp_batched(sinos, geoms, kind=kind, variant=variant)
     torch.cuda.synchronize()
+    orbit_items = 0
     for s, g, o in zip(sinos, geoms, outs):
-        single = api.fbp(s, g, kind=kind, variant=variant)
-        assert torch.equal(o, single)
+        v = item_shape(api, variant, g)
+        orbit_items += api.bp_variants()[v]["symmetric"]
+        single = api.fbp(s, g, kind=kind, variant=v)
+        assert torch.equal(o, single), f"K={g.n_angles} N={g.n} ran variant {v}"
+    if api.bp_variants()[variant]["symmetric"]:
+        assert orbit_items >= 1
     assert api.device_status() == 0
+
+
+@pytest.mark.parametrize("variant", [-1, 8, 10, 11])
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+def test_batched_16bit_orbits_bit_identical_to_single_slices(variant, dtype):
+    """16-bit rows: packed and unpacked orbit units in the persistent kernel
+    equal the single-slice kernels of the same shape (the default is 10)."""
+    api = fbp_api()
+    sinos, geoms = ragged(api, DIMS, seed=50)
+    outs = api.fbp_batched(sinos, geoms, dtype=dtype, variant=variant)
+    torch.cuda.synchronize()
+    for s, g, o in zip(sinos, geoms, outs):
+        v = item_shape(api, 10 if variant < 0 else variant, g, dtype)
+        single = api.fbp(s, g, dtype=dtype, variant=v)
+        assert torch.equal(o, single), f"K={g.n_angles} N={g.n} ran variant {v}"
+    assert api.device_status() == 0
+
+
+def test_batched_default_uses_orbits_and_packed_needs_16bit_rows():
+    api = fbp_api()
+    sinos, geoms = ragged(api, DIMS, seed=70)
+    outs = api.fbp_batched(sinos, geoms)                  # FP32 default: orbit variant 7
+    for s, g, o in zip(sinos, geoms, outs):
+        assert torch.equal(o, api.fbp(s, g, variant=item_shape(api, 7, g)))
+    with pytest.raises(api.FbpError, match="UNSUPPORTED"):
+        api.fbp_batched(sinos, geoms, variant=10)         # packed: 16-bit rows only
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
@@ -105,13 +146,16 @@ def test_ragged_workload_sample_vs_oracle():
     outs = api.fbp_batched(sinos, geoms)
     rng = np.random.default_rng(1)
     for s, g, o in zip(sinos, geoms, outs):
-        assert torch.equal(o, api.fbp(s, g, variant=0))   # the batched default tile shape
+        # every item of this workload has the symmetry: the default orbit shape
+        assert api.variant_supports(7, g)
+        assert torch.equal(o, api.fbp(s, g, variant=7))
         go = oracle.Geometry(g.n_angles, g.n_det, g.n)
         q = oracle.filter(to_np(s))
         rows = rng.integers(0, g.n, 300)
         cols = rng.integers(0, g.n, 300)
         ref = oracle.backproject_pixels(q, go, rows, cols)
         got = to_np(o)[rows, cols]
-        full = to_np(o)
-        dr = full.max() - full.min()
+        # DR of the oracle's values (the sampled range: a lower bound of the
+        # image's, so the check is the stricter one)
+        dr = ref.max() - ref.min()
         assert np.max(np.abs(got - ref)) <= 1e-4 * dr
