@@ -986,8 +986,8 @@ def run_mixed(args) -> None:
                     f"off the axis, folded), N in {w.n_choices}, half-turn K in {w.k_choices}, random "
                     "ellipses, Ram-Lak; one persistent launch per step, CUDA-graph replay, atomic work queue",
         "parallelism": f"scans sharded over {ws} GPU(s), no collective",
-        "bp_variant": variant if variant >= 0 else "library batch default (7: FP32 orbit units, "
-                                                   "generic 64 x 32 tiles where an item has no symmetry)"})
+        "bp_variant": variant if variant >= 0 else "library batch default (8: 64 x 64 FP32 orbit units, "
+                                                   "generic 64 x 64 tiles where an item has no symmetry)"})
     line.update({"slices_per_s": len(idx) * len(per_rank) / (ms_step / 1e3),
                  "group_cyclic": {"value": rate_c / 1e9, "unit": UNIT, "ms_per_step": ms_c,
                                   "ratio_to_queue": ms_step / ms_c},

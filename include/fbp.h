@@ -379,7 +379,7 @@ int fbp_bp_variant_supports(int variant, fbp_dtype dtype, const fbp_geometry *g)
  *              bytes, 256-byte aligned, owned by the caller.  It holds the
  *              filtered rows of every item and the work-queue counter.
  *   bp_variant tile variant for backprojection (fbp_bp_variant_info),
- *              -1 = default (7 for FP32 rows, 10 for 16-bit rows).  With a
+ *              -1 = default (8 for FP32 rows, 10 for 16-bit rows).  With a
  *              symmetric variant, items whose geometry has the 90-degree
  *              symmetry (angle step pi/K with K even, det_center = (D-1)/2,
  *              n a multiple of twice the variant's tile) run its orbit units
@@ -440,6 +440,45 @@ fbp_status fbp_batched_scans(const fbp_scan_item *items, int count,
                              fbp_filter_kind kind, fbp_dtype dtype, int bp_variant,
                              fbp_batch_order order, void *workspace, size_t ws_bytes,
                              fbp_stream_t stream);
+
+/*
+ * fbp_host -- filtered backprojection of a stack held in HOST memory, with
+ * host<->device copies overlapped with the kernels (the paper's overlapped
+ * load / FBP computation / store pipeline, Sec. V-A(c), on one GPU).  The
+ * stack is cut into chunks of `chunk` slices; chunk i runs on internal stream
+ * i mod n_streams: copy in, fbp_filter (fbp_filter_counts when pre != NULL),
+ * fbp_backproject_variant with scale = angle_step (fbp_backproject_u16 when
+ * window != NULL), copy out -- so the copies of one chunk run while another
+ * chunk's kernels do.  The results equal those calls on device buffers.
+ *   sino_host   HOST, float [n_slices][K][D]: line integrals, or detector
+ *               counts when pre != NULL.  Pinned memory (cudaHostAlloc or
+ *               cudaHostRegister) lets the copies overlap; pageable memory
+ *               works but serialises them.
+ *   slice_host  HOST, [n_slices][n][n]: float slices, or uint16 codes when
+ *               window != NULL.
+ *   kind, dtype as fbp_filter; bp_variant as fbp_backproject_variant.
+ *   pre         NULL, or the stage-2 pre-processing (fbp_filter_counts; its
+ *               flat is a device pointer).
+ *   window      NULL, or the stage-4 HU window (fbp_backproject_u16).
+ *   chunk       slices per chunk, >= 1; n_streams in [1, 16].
+ *   workspace   device, >= fbp_host_workspace_bytes(g, dtype, chunk,
+ *               n_streams, window != NULL) bytes, 256-byte aligned, owned
+ *               by the caller: per stream one chunk's input, filtered rows,
+ *               row scales and output.
+ *   stream      the pipeline starts after the work already enqueued on it.
+ * Blocking: returns when every slice is in slice_host (or after an error,
+ * once nothing is in flight).  Creates and destroys its streams; allocates
+ * no device memory beyond the first call's constant tables for g (not for
+ * stream capture).  Errors: those of the calls above, FBP_ERR_WORKSPACE,
+ * FBP_ERR_INVALID_ARG for a device pointer as sino_host or slice_host.
+ * fbp_host_workspace_bytes returns 0 for invalid arguments.
+ */
+size_t fbp_host_workspace_bytes(const fbp_geometry *g, fbp_dtype dtype, int chunk, int n_streams,
+                                int codes);
+fbp_status fbp_host(const float *sino_host, void *slice_host, const fbp_geometry *g, int n_slices,
+                    fbp_filter_kind kind, fbp_dtype dtype, int bp_variant,
+                    const fbp_preprocess *pre, const fbp_hu_window *window, int chunk,
+                    int n_streams, void *workspace, size_t ws_bytes, fbp_stream_t stream);
 
 /*
  * Device status word.  Kernels never trap: a kernel that detects a fault

@@ -318,68 +318,57 @@ def fbp(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
     return backproject(filt, g, row_scale=rs, out=out, variant=variant)
 
 
+def host_workspace_bytes(g: Geometry, dtype=torch.float32, chunk: int = 2, n_streams: int = 3,
+                         codes: bool = False) -> int:
+    """fbp_host_workspace_bytes: device bytes fbp_host needs."""
+    L = lib()
+    gc = g.c()
+    n = L.fbp_host_workspace_bytes(ctypes.byref(gc), _DTYPES[dtype], int(chunk), int(n_streams), int(codes))
+    if n == 0:
+        raise FbpError(_lib.FBP_ERR_INVALID_ARG, "fbp_host_workspace_bytes: invalid arguments")
+    return int(n)
+
+
 def fbp_host(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
              out: torch.Tensor | None = None, variant: int = -1, chunk: int = 2,
              n_streams: int = 3, device=None, pre: "Preprocess | None" = None,
-             window: "HuWindow | None" = None) -> torch.Tensor:
-    """FBP of a stack held in host memory: returns (or fills) a host tensor.
+             window: "HuWindow | None" = None, workspace: torch.Tensor | None = None) -> torch.Tensor:
+    """fbp_host: FBP of a stack held in host memory; returns (or fills) a host tensor.
 
     With `pre` the input is detector counts (fbp_filter_counts); with
     `window` the output is the uint16 HU codes (fbp_backproject_u16), held in
-    an int16 tensor.
-
-    The stack is processed in chunks of `chunk` slices on `n_streams` CUDA
-    streams; each stream copies its chunk in, runs fbp_filter and
-    fbp_backproject, and copies the slices out, so host<->device copies of one
-    chunk overlap the kernels of another.  Use pinned host tensors
-    (``tensor.pin_memory()``) for asynchronous copies.  Blocks until the
-    result is in `out`.
+    an int16 tensor.  The C call cuts the stack into chunks of `chunk` slices
+    on `n_streams` streams (copy in, filter, backproject, copy out), so the
+    copies of one chunk overlap another's kernels; use pinned host tensors
+    (``tensor.pin_memory()``) for that.  Blocks until the result is in `out`.
     """
     if sino.is_cuda:
         raise ValueError("fbp_host takes a host (CPU) tensor; use fbp for device tensors")
     if sino.dtype != torch.float32 or not sino.is_contiguous():
         raise ValueError("sino must be a contiguous float32 tensor")
     S = _slices(sino, (g.n_angles, g.n_det), "sino")
-    squeeze = sino.dim() == 2
-    if squeeze:
-        sino = sino.unsqueeze(0)
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     odt = torch.int16 if window is not None else torch.float32
+    squeeze = sino.dim() == 2
     if out is None:
         out = torch.empty((S, g.n, g.n), dtype=odt, pin_memory=True)
-    o3 = out.view(S, g.n, g.n)
+    if out.is_cuda or out.dtype != odt or not out.is_contiguous() or out.numel() != S * g.n * g.n:
+        raise ValueError(f"out must be a contiguous host {odt} tensor of {S} x {g.n} x {g.n}")
     chunk = max(1, min(chunk, S))
     n_streams = max(1, min(n_streams, -(-S // chunk)))
-    caller = torch.cuda.current_stream(dev)
-    streams = [torch.cuda.Stream(dev) for _ in range(n_streams)]
-    bufs = []
-    for _ in range(n_streams):
-        bufs.append((torch.empty((chunk, g.n_angles, g.n_det), dtype=torch.float32, device=dev),
-                     torch.empty((chunk, g.n_angles, g.n_det), dtype=dtype, device=dev),
-                     torch.empty((chunk, g.n_angles), dtype=torch.float32, device=dev)
-                     if dtype != torch.float32 else None,
-                     torch.empty((chunk, g.n, g.n), dtype=odt, device=dev)))
-    for st in streams:
-        st.wait_stream(caller)
-    for i, i0 in enumerate(range(0, S, chunk)):
-        i1 = min(S, i0 + chunk)
-        n = i1 - i0
-        st = streams[i % n_streams]
-        d_in, d_filt, d_rs, d_out = bufs[i % n_streams]
-        with torch.cuda.stream(st):
-            d_in[:n].copy_(sino[i0:i1], non_blocking=True)
-            rs = None if d_rs is None else d_rs[:n]
-            if pre is None:
-                filter(d_in[:n], g, kind=kind, dtype=dtype, out=d_filt[:n], row_scale=rs)
-            else:
-                filter_counts(d_in[:n], g, pre, kind=kind, dtype=dtype, out=d_filt[:n], row_scale=rs)
-            if window is None:
-                backproject(d_filt[:n], g, row_scale=rs, out=d_out[:n], variant=variant)
-            else:
-                backproject_u16(d_filt[:n], g, window, row_scale=rs, out=d_out[:n], variant=variant)
-            o3[i0:i1].copy_(d_out[:n], non_blocking=True)
-    for st in streams:
-        st.synchronize()
+    if workspace is None:
+        workspace = torch.empty(host_workspace_bytes(g, dtype, chunk, n_streams, window is not None),
+                                dtype=torch.uint8, device=dev)
+    L = lib()
+    gc = g.c()
+    pc = pre.c() if pre is not None else None
+    wc = window.c() if window is not None else None
+    with torch.cuda.device(dev):
+        st = L.fbp_host(_ptr(sino), _ptr(out), ctypes.byref(gc), S, kind_id(kind), _DTYPES[dtype], int(variant),
+                        ctypes.byref(pc) if pc is not None else None,
+                        ctypes.byref(wc) if wc is not None else None, chunk, n_streams, _ptr(workspace),
+                        workspace.numel(), _stream(dev))
+    _lib.check(st, L, "fbp_host")
     return out[0] if squeeze and out.dim() == 3 else out
 
 

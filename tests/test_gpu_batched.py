@@ -71,9 +71,9 @@ def test_batched_16bit_orbits_bit_identical_to_single_slices(variant, dtype):
 def test_batched_default_uses_orbits_and_packed_needs_16bit_rows():
     api = fbp_api()
     sinos, geoms = ragged(api, DIMS, seed=70)
-    outs = api.fbp_batched(sinos, geoms)                  # FP32 default: orbit variant 7
+    outs = api.fbp_batched(sinos, geoms)                  # FP32 default: orbit variant 8
     for s, g, o in zip(sinos, geoms, outs):
-        assert torch.equal(o, api.fbp(s, g, variant=item_shape(api, 7, g)))
+        assert torch.equal(o, api.fbp(s, g, variant=item_shape(api, 8, g)))
     with pytest.raises(api.FbpError, match="UNSUPPORTED"):
         api.fbp_batched(sinos, geoms, variant=10)         # packed: 16-bit rows only
 
@@ -147,8 +147,8 @@ def test_ragged_workload_sample_vs_oracle():
     rng = np.random.default_rng(1)
     for s, g, o in zip(sinos, geoms, outs):
         # every item of this workload has the symmetry: the default orbit shape
-        assert api.variant_supports(7, g)
-        assert torch.equal(o, api.fbp(s, g, variant=7))
+        assert api.variant_supports(8, g)
+        assert torch.equal(o, api.fbp(s, g, variant=8))
         go = oracle.Geometry(g.n_angles, g.n_det, g.n)
         q = oracle.filter(to_np(s))
         rows = rng.integers(0, g.n, 300)
