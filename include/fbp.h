@@ -326,6 +326,44 @@ fbp_status fbp_backproject_noalloc(const void *filt, const float *row_scale,
                                    fbp_stream_t stream);
 
 /*
+ * fbp_backproject_staged -- fbp_backproject for 16-bit rows with the
+ * backprojection tables formed once per slice instead of once per block
+ * (the same step, Sec. V-A(c) stage 2; the same sum, bit-identical to
+ * fbp_backproject_variant with the symmetric orbit variant of the same tile:
+ * 10 for shapes 0-1, 11 for shapes 2-5).  A pass over the filtered rows writes, for every
+ * angle pair (th_k, th_k + pi/2) and detector segment, the 16-byte entry of
+ * the orbit kernel (midpoints and slopes of the two rows and their mirrors,
+ * scaled by s_k / S, S = max_k s_k of the slice) into the workspace; the
+ * backprojection then moves each tile's window of entries into shared memory
+ * with one bulk-tensor copy (zero-filled past the detector) and interpolates
+ * as the orbit kernel does, with no block-wide barrier per stage.
+ *   filt, row_scale, dtype  16-bit rows (FBP_F16 or FBP_BF16) and their
+ *              scales, as fbp_backproject; FBP_F32 returns FBP_ERR_UNSUPPORTED.
+ *   slice, g, n_slices, scale, accumulate  as fbp_backproject.
+ *   shape      -1 default (0 when n is a multiple of 128, else 2), or
+ *              0: 64 x 64 orbit tiles, 8 angle pairs per stage, 3 buffers;
+ *              1: 64 x 64, 16 pairs, 2 buffers; 2: 32 x 32, 16 pairs, 3
+ *              buffers; 3: 32 x 32, 8 pairs, 4 buffers; 4: 32 x 32, 8 pairs,
+ *              3 buffers, five blocks per SM; 5: 32 x 32, 8 pairs, 2 buffers,
+ *              six blocks per SM.
+ *   workspace  device, 256-byte aligned, owned by the caller, at least
+ *              fbp_backproject_staged_workspace_bytes(g, 1) bytes; the call
+ *              works through the stack in as many slices at a time as the
+ *              workspace holds (fbp_backproject_staged_workspace_bytes(g, c)
+ *              for c slices: (K/2) (D+1) 16 bytes per slice plus 256).
+ * Geometry: angle step pi/K with K even, det_center = (D-1)/2, n a multiple
+ * of twice the tile (FBP_ERR_UNSUPPORTED otherwise).  The table write and the
+ * backprojection run on `stream`; the call may be captured once g's angle
+ * table exists.  fbp_backproject_staged_shape_count() is the number of shapes.
+ */
+size_t fbp_backproject_staged_workspace_bytes(const fbp_geometry *g, int chunk);
+int fbp_backproject_staged_shape_count(void);
+fbp_status fbp_backproject_staged(const void *filt, const float *row_scale, fbp_dtype dtype,
+                                  float *slice, const fbp_geometry *g, int n_slices, float scale,
+                                  int accumulate, int shape, void *workspace, size_t ws_bytes,
+                                  fbp_stream_t stream);
+
+/*
  * radon_forward -- the matched forward projector A (the adjoint of
  * fbp_backproject with scale 1; the paper's data generation uses a forward
  * model, Sec. V-B(a)):  (A f)_k[j] = sum_{r,c} f[r][c] max(0, 1 - |u_k(r,c) - j|).
@@ -490,7 +528,9 @@ fbp_status fbp_host(const float *sino_host, void *slice_host, const fbp_geometry
  * filter for its row copy past its cap (the block then stops; after two
  * expired waits a copy into its shared memory may still be in flight, so
  * treat code 6 as voiding that launch's output and any kernel enqueued after
- * it on the stream: synchronise and discard those results).  The
+ * it on the stream: synchronise and discard those results); 7 a wait of
+ * fbp_backproject_staged for a window copy past its cap (the block writes
+ * nothing, after a capped wait for its copies).  The
  * first fault recorded stays until read.  This call synchronises `stream`,
  * reads and clears the word, and returns FBP_OK or FBP_ERR_DEVICE_STATUS
  * (code in *code if non-NULL).

@@ -291,6 +291,43 @@ def backproject(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None 
     return out
 
 
+def backproject_staged_workspace_bytes(g: Geometry, chunk: int = 1) -> int:
+    """fbp_backproject_staged_workspace_bytes: workspace for `chunk` slices at a time."""
+    n = lib().fbp_backproject_staged_workspace_bytes(ctypes.byref(g.c()), int(chunk))
+    if n == 0:
+        raise FbpError(_lib.FBP_ERR_INVALID_ARG, "fbp_backproject_staged_workspace_bytes: invalid arguments")
+    return int(n)
+
+
+def backproject_staged(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor, scale: float | None = None,
+                       out: torch.Tensor | None = None, accumulate: bool = False, shape: int = -1,
+                       workspace: torch.Tensor | None = None, chunk: int = 1):
+    """fbp_backproject_staged: 16-bit rows backprojected from tables written
+    once per slice (a workspace of `chunk` slices is allocated if none is
+    given).  Bit-identical to backproject with the packed orbit variant of
+    the same tile."""
+    _need(filt, "filt")
+    if filt.dtype not in (torch.float16, torch.bfloat16):
+        raise ValueError("fbp_backproject_staged takes float16 or bfloat16 rows")
+    S = _slices(filt, (g.n_angles, g.n_det), "filt")
+    _need(row_scale, "row_scale", torch.float32)
+    shape_out = (g.n, g.n) if filt.dim() == 2 else (S, g.n, g.n)
+    if out is None:
+        out = torch.empty(shape_out, dtype=torch.float32, device=filt.device)
+    _need(out, "out", torch.float32)
+    if workspace is None:
+        workspace = torch.empty(backproject_staged_workspace_bytes(g, min(chunk, S)), dtype=torch.uint8,
+                                device=filt.device)
+    L = lib()
+    gc = g.c()
+    sc = g.angle_step if scale is None else scale
+    st = L.fbp_backproject_staged(_ptr(filt), _ptr(row_scale), _DTYPES[filt.dtype], _ptr(out), ctypes.byref(gc), S,
+                                  float(sc), int(accumulate), int(shape), _ptr(workspace), workspace.numel(),
+                                  _stream(filt.device))
+    _lib.check(st, L, "fbp_backproject_staged")
+    return out
+
+
 def radon_forward(img: torch.Tensor, g: Geometry, out: torch.Tensor | None = None,
                   which: str = "default", variant: int = -1):
     """radon_forward: the matched projector A (transpose of backproject, scale 1).

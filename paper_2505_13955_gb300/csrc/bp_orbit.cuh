@@ -121,6 +121,17 @@ template <> __device__ __forceinline__ void mac16<__nv_bfloat16>(float &acc, uns
         : "+f"(acc) : "h"(fr), "r"(e));
 }
 
+// Midpoint and slope of the segment (v0, v1) of a 16-bit row scaled by sc,
+// each operation rounded once (no contraction), so that the staged entries
+// are the same wherever they are formed (in the block, or by the
+// pre-staging pass of bp_staged.cu).
+__device__ __forceinline__ void orbit_mid_slope(float v0, float v1, float sc, float &mid, float &slp)
+{
+    const float x0 = __fmul_rn(v0, sc), x1 = __fmul_rn(v1, sc);
+    mid = __fmul_rn(0.5f, __fadd_rn(x0, x1));
+    slp = __fsub_rn(x1, x0);
+}
+
 // Packed FP32 pairs (two windows' coordinates at once) and packed 16-bit
 // interpolation (two rows at once), for the PACKED 16-bit variant.
 __device__ __forceinline__ unsigned long long pk2(float lo, float hi)
@@ -196,6 +207,137 @@ template <> __device__ __forceinline__ void add2to32<__nv_bfloat16>(float &lo_ac
         : "+f"(lo_acc), "+f"(hi_acc) : "r"(v));
 }
 
+// One angle pair of an orbit block: accumulate the updates of every pixel
+// the thread owns from the pair's two staged windows (cb1, cb2: their shared
+// addresses biased for the rounded index, see bp_orbit; tab_b: FP32 rows'
+// offset of the mirrored-row array).  The block-staged kernel below and the
+// bulk-copy-fed kernel (bp_staged.cu) both run it.
+template <int TXT, int TYT, int PX, int PY, typename T, bool CHECKED, bool PACKED>
+__device__ __forceinline__ void orbit_pair(float (&acc)[4][PY][PX], const float4 pv, const uint32_t cb1,
+                                           const uint32_t cb2, const uint32_t tab_b, const float dxt,
+                                           const float dyt, const int H, unsigned *status)
+{
+    constexpr bool F32 = sizeof(T) == 4;
+    if constexpr (PACKED) {
+        const unsigned long long Mp = pk2(kRoundMagic, kRoundMagic);
+        const unsigned long long nMp = pk2(-kRoundMagic, -kRoundMagic);
+        {
+            const float c = pv.x, s = pv.y;
+            // (u1, u2) of the thread's first pixel, and per-row / per-column steps
+            const unsigned long long u0 = pk2(fmaf(dxt, c, fmaf(dyt, s, pv.z)),
+                                              fmaf(dxt, -s, fmaf(dyt, c, pv.w)));
+            const unsigned long long sx = pk2((float)TXT * c, -(float)TXT * s);
+            const unsigned long long sy = pk2((float)TYT * s, (float)TYT * c);
+#pragma unroll
+            for (int iy = 0; iy < PY; ++iy) {
+                const unsigned long long r = iy == 0 ? u0 : ffma2(pk2((float)iy, (float)iy), sy, u0);
+#pragma unroll
+                for (int ix = 0; ix < PX; ++ix) {
+                    const unsigned long long u = ix == 0 ? r : ffma2(pk2((float)ix, (float)ix), sx, r);
+                    const unsigned long long t = fadd2(u, Mp);
+                    const unsigned long long fr = fsub2(u, fadd2(t, nMp));
+                    float t1, t2, f1, f2;
+                    upk2(t, t1, t2);
+                    upk2(fr, f1, f2);
+                    uint32_t tb1 = __float_as_uint(t1), tb2 = __float_as_uint(t2);
+                    if (CHECKED) {
+                        const int i1 = (int)(tb1 - kRoundMagicBits), i2 = (int)(tb2 - kRoundMagicBits);
+                        if (i1 < -H || i1 > H || i2 < -H || i2 > H) {
+                            atomicCAS(status, 0u, (unsigned)FAULT_TABLE_INDEX);
+                            tb1 = tb2 = kRoundMagicBits;
+                        }
+                    }
+                    const uint4 e1 = lds_u4(cb1 + (tb1 << 4));
+                    const uint4 e2 = lds_u4(cb2 + (tb2 << 4));
+                    const uint32_t h1 = splat16<T>(f1), h2 = splat16<T>(f2);
+                    // W1: th -> p, th' -> Rp, th~ -> R^2 p, th'~ -> R^3 p
+                    add2to32<T>(acc[0][iy][ix], acc[1][iy][ix], hfma2<T>(h1, e1.y, e1.x));
+                    add2to32<T>(acc[2][iy][ix], acc[3][iy][ix], hfma2<T>(h1, e1.w, e1.z));
+                    // W2: th -> R^3 p, th' -> p, th~ -> Rp, th'~ -> R^2 p
+                    add2to32<T>(acc[3][iy][ix], acc[0][iy][ix], hfma2<T>(h2, e2.y, e2.x));
+                    add2to32<T>(acc[1][iy][ix], acc[2][iy][ix], hfma2<T>(h2, e2.w, e2.z));
+                }
+            }
+        }
+    } else {
+        {
+            const float c = pv.x, s = pv.y;
+            const float u10 = fmaf(dxt, c, fmaf(dyt, s, pv.z));
+            const float u20 = fmaf(dxt, -s, fmaf(dyt, c, pv.w));
+            const float s1x = (float)TXT * c, s1y = (float)TYT * s;
+            const float s2x = -(float)TXT * s, s2y = (float)TYT * c;
+#pragma unroll
+            for (int iy = 0; iy < PY; ++iy) {
+                const float r1 = iy == 0 ? u10 : fmaf((float)iy, s1y, u10);
+                const float r2 = iy == 0 ? u20 : fmaf((float)iy, s2y, u20);
+#pragma unroll
+                for (int ix = 0; ix < PX; ++ix) {
+#pragma unroll
+                    for (int win = 0; win < 2; ++win) {
+                        const float u = win == 0 ? (ix == 0 ? r1 : fmaf((float)ix, s1x, r1))
+                                                 : (ix == 0 ? r2 : fmaf((float)ix, s2x, r2));
+                        const float t = __fadd_rn(u, kRoundMagic);
+                        uint32_t tb = __float_as_uint(t);
+                        if (CHECKED) {
+                            const int i = (int)(tb - kRoundMagicBits);
+                            if (i < -H || i > H) {
+                                atomicCAS(status, 0u, (unsigned)FAULT_TABLE_INDEX);
+                                tb = kRoundMagicBits;
+                            }
+                        }
+                        const uint32_t cb = win == 0 ? cb1 : cb2;
+                        // orbit members fed by rows (th, th', th~, th'~)
+                        const int m0 = win == 0 ? 0 : 3, m1 = win == 0 ? 1 : 0;
+                        const int m2 = win == 0 ? 2 : 1, m3 = win == 0 ? 3 : 2;
+                        if constexpr (F32) {
+                            const uint32_t e = cb + (tb << 4);
+                            const float4 e0 = lds_f4(e), e1 = lds_f4(e + tab_b);
+                            acc[m0][iy][ix] += fmaf(u, e0.y, e0.x);
+                            acc[m1][iy][ix] += fmaf(u, e0.w, e0.z);
+                            acc[m2][iy][ix] += fmaf(u, e1.y, e1.x);
+                            acc[m3][iy][ix] += fmaf(u, e1.w, e1.z);
+                        } else {
+                            const uint4 e = lds_u4(cb + (tb << 4));
+                            const float fr = u - (t - kRoundMagic);
+                            const unsigned short f16 = frac16<T>(fr);
+                            mac16<T>(acc[m0][iy][ix], f16, e.x);
+                            mac16<T>(acc[m1][iy][ix], f16, e.y);
+                            mac16<T>(acc[m2][iy][ix], f16, e.z);
+                            mac16<T>(acc[m3][iy][ix], f16, e.w);
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+// The four orbit members' pixels of the thread (its first pixel at column
+// c0, row r0 of the representative tile): p -> [r][c], Rp -> [c][N-1-r],
+// R^2p -> [N-1-r][N-1-c], R^3p -> [N-1-c][r], each value times `gain`.
+template <int TXT, int TYT, int PX, int PY>
+__device__ __forceinline__ void orbit_store(const float (&acc)[4][PY][PX], float *out, unsigned short *out16,
+                                            float hu_a, float hu_b, int accumulate, int N, int c0, int r0,
+                                            float gain)
+{
+#pragma unroll
+    for (int iy = 0; iy < PY; ++iy) {
+        const int r = r0 + TYT * iy;
+#pragma unroll
+        for (int ix = 0; ix < PX; ++ix) {
+            const int c = c0 + TXT * ix;
+            const size_t o0 = (size_t)r * N + c;
+            const size_t o1 = (size_t)c * N + (N - 1 - r);
+            const size_t o2 = (size_t)(N - 1 - r) * N + (N - 1 - c);
+            const size_t o3 = (size_t)(N - 1 - c) * N + r;
+            const size_t os[4] = {o0, o1, o2, o3};
+#pragma unroll
+            for (int o = 0; o < 4; ++o)
+                store_pixel(out, out16, hu_a, hu_b, accumulate, os[o], acc[o][iy][ix] * gain);
+        }
+    }
+}
+
 // PACKED (16-bit rows only): entries hold (q'_th, q'_th'), (d_th, d_th'),
 // and the same for the mirrored rows, so one packed FMA interpolates two
 // rows (the interpolated value is rounded once to the 16-bit type before the
@@ -246,7 +388,7 @@ __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *sme
         for (int w = 0; w < NT / 32; ++w) mx = fmaxf(mx, s_red[w]);
         S = mx > 0.f ? mx : 1.f;
     }
-    const float invS = 1.f / S;
+    const float invS = __frcp_rn(S);
 
     float acc[4][PY][PX];
 #pragma unroll
@@ -292,8 +434,8 @@ __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *sme
             const T *r1 = q + (size_t)(k + K2) * D;
             float sc0 = 1.f, sc1 = 1.f;
             if constexpr (!F32) {
-                sc0 = valid ? __ldg(j.row_scale + k) * invS : 0.f;
-                sc1 = valid ? __ldg(j.row_scale + k + K2) * invS : 0.f;
+                sc0 = valid ? __fmul_rn(__ldg(j.row_scale + k), invS) : 0.f;
+                sc1 = valid ? __fmul_rn(__ldg(j.row_scale + k + K2), invS) : 0.f;
             }
             unsigned char *dst = tab + (size_t)aw * W * EB;
             for (int i = lane; i < W; i += 32) {
@@ -322,12 +464,8 @@ __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *sme
                     // midpoints and slopes of the four rows (scaled by s_k / S)
                     float mid[4], slp[4];
 #pragma unroll
-                    for (int r = 0; r < 4; ++r) {
-                        const float sc = (r & 1) ? sc1 : sc0;
-                        const float x0 = v[2 * r] * sc, x1 = v[2 * r + 1] * sc;
-                        mid[r] = 0.5f * (x0 + x1);
-                        slp[r] = x1 - x0;
-                    }
+                    for (int r = 0; r < 4; ++r) orbit_mid_slope(v[2 * r], v[2 * r + 1], (r & 1) ? sc1 : sc0,
+                                                                mid[r], slp[r]);
                     uint4 e;
                     if constexpr (PACKED) {
                         e.x = pack16<T>(mid[0], mid[1]);
@@ -345,122 +483,15 @@ __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *sme
             }
         }
         __syncthreads();
-        if constexpr (PACKED) {
-            const unsigned long long Mp = pk2(kRoundMagic, kRoundMagic);
-            const unsigned long long nMp = pk2(-kRoundMagic, -kRoundMagic);
-            for (int a = 0; a < na; ++a) {
-                const float4 pv = prm[a];
-                const uint4 ad = adr[a];
-                const float c = pv.x, s = pv.y;
-                // (u1, u2) of the thread's first pixel, and per-row / per-column steps
-                const unsigned long long u0 = pk2(fmaf(dxt, c, fmaf(dyt, s, pv.z)),
-                                                  fmaf(dxt, -s, fmaf(dyt, c, pv.w)));
-                const unsigned long long sx = pk2((float)TXT * c, -(float)TXT * s);
-                const unsigned long long sy = pk2((float)TYT * s, (float)TYT * c);
-#pragma unroll
-                for (int iy = 0; iy < PY; ++iy) {
-                    const unsigned long long r = iy == 0 ? u0 : ffma2(pk2((float)iy, (float)iy), sy, u0);
-#pragma unroll
-                    for (int ix = 0; ix < PX; ++ix) {
-                        const unsigned long long u = ix == 0 ? r : ffma2(pk2((float)ix, (float)ix), sx, r);
-                        const unsigned long long t = fadd2(u, Mp);
-                        const unsigned long long fr = fsub2(u, fadd2(t, nMp));
-                        float t1, t2, f1, f2;
-                        upk2(t, t1, t2);
-                        upk2(fr, f1, f2);
-                        uint32_t tb1 = __float_as_uint(t1), tb2 = __float_as_uint(t2);
-                        if (CHECKED) {
-                            const int i1 = (int)(tb1 - kRoundMagicBits), i2 = (int)(tb2 - kRoundMagicBits);
-                            if (i1 < -H || i1 > H || i2 < -H || i2 > H) {
-                                atomicCAS(j.status, 0u, (unsigned)FAULT_TABLE_INDEX);
-                                tb1 = tb2 = kRoundMagicBits;
-                            }
-                        }
-                        const uint4 e1 = lds_u4(ad.x + (tb1 << 4));
-                        const uint4 e2 = lds_u4(ad.y + (tb2 << 4));
-                        const uint32_t h1 = splat16<T>(f1), h2 = splat16<T>(f2);
-                        // W1: th -> p, th' -> Rp, th~ -> R^2 p, th'~ -> R^3 p
-                        add2to32<T>(acc[0][iy][ix], acc[1][iy][ix], hfma2<T>(h1, e1.y, e1.x));
-                        add2to32<T>(acc[2][iy][ix], acc[3][iy][ix], hfma2<T>(h1, e1.w, e1.z));
-                        // W2: th -> R^3 p, th' -> p, th~ -> Rp, th'~ -> R^2 p
-                        add2to32<T>(acc[3][iy][ix], acc[0][iy][ix], hfma2<T>(h2, e2.y, e2.x));
-                        add2to32<T>(acc[1][iy][ix], acc[2][iy][ix], hfma2<T>(h2, e2.w, e2.z));
-                    }
-                }
-            }
-        } else {
-            for (int a = 0; a < na; ++a) {
-                const float4 pv = prm[a];
-                const uint4 ad = adr[a];
-                const float c = pv.x, s = pv.y;
-                const float u10 = fmaf(dxt, c, fmaf(dyt, s, pv.z));
-                const float u20 = fmaf(dxt, -s, fmaf(dyt, c, pv.w));
-                const float s1x = (float)TXT * c, s1y = (float)TYT * s;
-                const float s2x = -(float)TXT * s, s2y = (float)TYT * c;
-#pragma unroll
-                for (int iy = 0; iy < PY; ++iy) {
-                    const float r1 = iy == 0 ? u10 : fmaf((float)iy, s1y, u10);
-                    const float r2 = iy == 0 ? u20 : fmaf((float)iy, s2y, u20);
-#pragma unroll
-                    for (int ix = 0; ix < PX; ++ix) {
-#pragma unroll
-                        for (int win = 0; win < 2; ++win) {
-                            const float u = win == 0 ? (ix == 0 ? r1 : fmaf((float)ix, s1x, r1))
-                                                     : (ix == 0 ? r2 : fmaf((float)ix, s2x, r2));
-                            const float t = __fadd_rn(u, kRoundMagic);
-                            uint32_t tb = __float_as_uint(t);
-                            if (CHECKED) {
-                                const int i = (int)(tb - kRoundMagicBits);
-                                if (i < -H || i > H) {
-                                    atomicCAS(j.status, 0u, (unsigned)FAULT_TABLE_INDEX);
-                                    tb = kRoundMagicBits;
-                                }
-                            }
-                            const uint32_t cb = win == 0 ? ad.x : ad.y;
-                            // orbit members fed by rows (th, th', th~, th'~)
-                            const int m0 = win == 0 ? 0 : 3, m1 = win == 0 ? 1 : 0;
-                            const int m2 = win == 0 ? 2 : 1, m3 = win == 0 ? 3 : 2;
-                            if constexpr (F32) {
-                                const uint32_t e = cb + (tb << 4);
-                                const float4 e0 = lds_f4(e), e1 = lds_f4(e + tab_b);
-                                acc[m0][iy][ix] += fmaf(u, e0.y, e0.x);
-                                acc[m1][iy][ix] += fmaf(u, e0.w, e0.z);
-                                acc[m2][iy][ix] += fmaf(u, e1.y, e1.x);
-                                acc[m3][iy][ix] += fmaf(u, e1.w, e1.z);
-                            } else {
-                                const uint4 e = lds_u4(cb + (tb << 4));
-                                const float fr = u - (t - kRoundMagic);
-                                const unsigned short f16 = frac16<T>(fr);
-                                mac16<T>(acc[m0][iy][ix], f16, e.x);
-                                mac16<T>(acc[m1][iy][ix], f16, e.y);
-                                mac16<T>(acc[m2][iy][ix], f16, e.z);
-                                mac16<T>(acc[m3][iy][ix], f16, e.w);
-                            }
-                        }
-                    }
-                }
-            }
+        for (int a = 0; a < na; ++a) {
+            const uint4 ad = adr[a];
+            orbit_pair<TXT, TYT, PX, PY, T, CHECKED, PACKED>(acc, prm[a], ad.x, ad.y, tab_b, dxt, dyt, H,
+                                                               j.status);
         }
     }
 
-    // stores: p -> [r][c], Rp -> [c][N-1-r], R^2p -> [N-1-r][N-1-c], R^3p -> [N-1-c][r]
-    const float gain = j.scale * S;
-#pragma unroll
-    for (int iy = 0; iy < PY; ++iy) {
-        const int r = j.y0 + ty + TYT * iy;
-#pragma unroll
-        for (int ix = 0; ix < PX; ++ix) {
-            const int c = j.x0 + tx + TXT * ix;
-            const size_t o0 = (size_t)r * N + c;
-            const size_t o1 = (size_t)c * N + (N - 1 - r);
-            const size_t o2 = (size_t)(N - 1 - r) * N + (N - 1 - c);
-            const size_t o3 = (size_t)(N - 1 - c) * N + r;
-            const size_t os[4] = {o0, o1, o2, o3};
-#pragma unroll
-            for (int o = 0; o < 4; ++o)
-                store_pixel(j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, os[o], acc[o][iy][ix] * gain);
-        }
-    }
+    orbit_store<TXT, TYT, PX, PY>(acc, j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, N, j.x0 + tx, j.y0 + ty,
+                                  j.scale * S);
 }
 
 }  // namespace fbp

@@ -1,0 +1,491 @@
+// bp_staged.cu -- K2 for 16-bit rows with the window staging taken off the
+// threads: fbp_backproject_staged.
+//
+// The orbit kernel (bp_orbit.cuh) forms, per block, per angle pair and per
+// window, the 16-byte entries (midpoints and slopes of the rows th, th + pi/2
+// and their mirrors, scaled by s_k / S) from the filtered rows, behind two
+// block barriers per stage.  Here a pass over the filtered rows writes those
+// entries once per slice, for every detector segment, into the caller's
+// workspace:
+//     table[s][k][e], k < K/2 the angle pair, e = j + 1 for segment j in
+//     [-1, D-1] (the segment between bins j and j+1, zero outside [0, D)),
+// and the backprojection moves each window of W entries with one tiled
+// bulk-tensor copy into shared memory -- out-of-range entries (windows that
+// reach past the detector) are filled with zeros by the copy engine, which is
+// exactly the staged kernel's zero padding.  Stages cycle through NS buffers;
+// each copy completes on the buffer's mbarrier (capped waits), and the last
+// warp to finish reading a buffer refills it with the stage NS ahead, so the
+// compute loop has no block-wide barrier.  The entries and the per-pair
+// arithmetic (orbit_mid_slope, orbit_pair) are the orbit kernel's own, so the
+// results are bit-identical to fbp_backproject_variant with the same shape.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+#include <mutex>
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include "bp_batch.cuh"
+#include "bp_orbit.cuh"
+
+namespace fbp {
+void clear_error();
+}
+
+namespace fbp {
+namespace {
+
+constexpr long long kStagedWaitCap = 1LL << 22;   // polls of one wait (well under a second)
+
+// S of each slice: the largest row scale (1 if none is positive), as the
+// orbit kernel forms it.
+__global__ void slice_scale_kernel(const float *row_scale, int K, float *smax)
+{
+    __shared__ float red[32];
+    const float *rs = row_scale + (size_t)blockIdx.x * K;
+    float mx = 0.f;
+    for (int k = threadIdx.x; k < K; k += blockDim.x) mx = fmaxf(mx, __ldg(rs + k));
+#pragma unroll
+    for (int o = 16; o; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = mx;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mx = 0.f;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) mx = fmaxf(mx, red[w]);
+        smax[blockIdx.x] = mx > 0.f ? mx : 1.f;
+    }
+}
+
+// One entry per thread: table[pair][e] for the chunk's S x K/2 pairs.
+template <typename T, bool PACKED>
+__global__ void orbit_prestage_kernel(const T *filt, const float *row_scale, const float *smax, uint4 *table,
+                                      int K, int D, long long pairs)
+{
+    const int K2 = K / 2, E = D + 1;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int jj = e - 1;                   // segment between bins jj and jj + 1
+    const int mj = D - 1 - jj;              // mirrored: q~[jj] = q[mj], q~[jj + 1] = q[mj - 1]
+    for (long long p = blockIdx.y; p < pairs; p += gridDim.y) {
+        const long long s = p / K2;
+        const int k = (int)(p - s * K2);
+        const T *r0 = filt + ((size_t)s * K + k) * D;
+        const T *r1 = r0 + (size_t)K2 * D;
+        const float invS = __frcp_rn(__ldg(smax + s));
+        const float sc0 = __fmul_rn(__ldg(row_scale + (size_t)s * K + k), invS);
+        const float sc1 = __fmul_rn(__ldg(row_scale + (size_t)s * K + k + K2), invS);
+        float v[8];
+        v[0] = (unsigned)jj < (unsigned)D ? load_q<T>(r0 + jj) : 0.f;
+        v[1] = (unsigned)(jj + 1) < (unsigned)D ? load_q<T>(r0 + jj + 1) : 0.f;
+        v[2] = (unsigned)jj < (unsigned)D ? load_q<T>(r1 + jj) : 0.f;
+        v[3] = (unsigned)(jj + 1) < (unsigned)D ? load_q<T>(r1 + jj + 1) : 0.f;
+        v[4] = (unsigned)mj < (unsigned)D ? load_q<T>(r0 + mj) : 0.f;
+        v[5] = (unsigned)(mj - 1) < (unsigned)D ? load_q<T>(r0 + mj - 1) : 0.f;
+        v[6] = (unsigned)mj < (unsigned)D ? load_q<T>(r1 + mj) : 0.f;
+        v[7] = (unsigned)(mj - 1) < (unsigned)D ? load_q<T>(r1 + mj - 1) : 0.f;
+        float mid[4], slp[4];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) orbit_mid_slope(v[2 * r], v[2 * r + 1], (r & 1) ? sc1 : sc0, mid[r], slp[r]);
+        uint4 out;
+        if constexpr (PACKED) {
+            out.x = pack16<T>(mid[0], mid[1]);
+            out.y = pack16<T>(slp[0], slp[1]);
+            out.z = pack16<T>(mid[2], mid[3]);
+            out.w = pack16<T>(slp[2], slp[3]);
+        } else {
+            out.x = pack16<T>(mid[0], slp[0]);
+            out.y = pack16<T>(mid[1], slp[1]);
+            out.z = pack16<T>(mid[2], slp[2]);
+            out.w = pack16<T>(mid[3], slp[3]);
+        }
+        table[(size_t)p * E + e] = out;
+    }
+}
+
+struct StagedArgs {
+    const double2 *cs;         // [K] angle table (k < K/2 is read)
+    float *out;                // the chunk's first slice [N][N]
+    const float *smax;         // the chunk's S per slice
+    int K2, N, H, W, Wp, orbits_x;
+    double alpha, det_center;
+    float scale;
+    int accumulate;
+    unsigned *status;
+};
+
+__device__ __forceinline__ bool staged_wait(uint32_t mbar, unsigned parity)
+{
+    for (long long it = 0; it < kStagedWaitCap; ++it) {
+        uint32_t done;
+        asm volatile("{\n\t.reg .pred p;\n\t"
+                     "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+                     "selp.u32 %0, 1, 0, p;\n\t}"
+                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+// Shared memory: [0, 128) NS mbarriers, NS "warps done" and NS "times
+// issued" counters; [128, 128 + P) the per-stage pair parameters (float4 per
+// pair, P rounded to 128 bytes); then NS stage tables of 2 KT windows of Wp
+// entries (16 bytes each; Wp a multiple of 8, so every window starts on a
+// 128-byte boundary).  The dynamic buffer is rounded up to 128 bytes first.
+template <int KT, int NS>
+__host__ __device__ constexpr size_t staged_params_bytes()
+{
+    return ((size_t)NS * KT * 16 + 127) / 128 * 128;
+}
+template <int KT, int NS>
+__host__ __device__ constexpr size_t staged_smem_bytes(int Wp)
+{
+    return 128 + 128 + staged_params_bytes<KT, NS>() + (size_t)NS * 2 * KT * Wp * 16;
+}
+
+template <int TXT, int TYT, int PX, int PY, int KT, int NS, typename T, bool PACKED, int MINB>
+__global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_kernel(const __grid_constant__ CUtensorMap tmap,
+                                                                   StagedArgs a)
+{
+    constexpr int NT = TXT * TYT, NW = NT / 32, TILE = TXT * PX, WX = TXT / 8;
+    static_assert(TXT * PX == TYT * PY, "square tile");
+    static_assert(KT <= 32 && NS >= 2 && NS <= 4, "stage shape");
+    extern __shared__ unsigned char smem_raw[];
+    const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_raw);
+    const uint32_t base_s = (raw_s + 127u) & ~127u;
+    unsigned char *base = smem_raw + (base_s - raw_s);
+    const uint32_t full_s = base_s;                           // NS x 8 bytes
+    int *done = reinterpret_cast<int *>(base + 8 * NS);
+    int *issued = reinterpret_cast<int *>(base + 12 * NS);
+    float4 *prm = reinterpret_cast<float4 *>(base + 128);
+    const uint32_t tab0 = base_s + 128u + (uint32_t)staged_params_bytes<KT, NS>();
+    const int H = a.H, W = a.W, Wp = a.Wp, K2 = a.K2;
+    const uint32_t stage_bytes = (uint32_t)(2 * KT * Wp * 16);
+
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int tx = (warp % WX) * 8 + (lane & 7);
+    const int ty = (warp / WX) * 4 + (lane >> 3);
+    const int sl = blockIdx.y;
+    const int x0 = (int)(blockIdx.x % a.orbits_x) * TILE, y0 = (int)(blockIdx.x / a.orbits_x) * TILE;
+    const double m = 0.5 * (a.N - 1);
+    const double Xc = (double)x0 + 0.5 * (TILE - 1) - m;
+    const double Yc = (double)y0 + 0.5 * (TILE - 1) - m;
+    const float dxt = (float)tx - 0.5f * (TILE - 1);
+    const float dyt = (float)ty - 0.5f * (TILE - 1);
+    const int n_stages = (K2 + KT - 1) / KT;
+    const long long zbase = (long long)sl * K2;
+
+    // one warp fills buffer b with stage t: the pairs' parameters (FP64 base
+    // coordinates, as bp_orbit) and two window copies per pair
+    auto issue = [&](int t, int b) {
+        const int k0 = t * KT, na = min(KT, K2 - k0);
+        int jl1 = 0, jl2 = 0;
+        if (lane < KT) {
+            float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
+            if (lane < na) {
+                const double2 cs = a.cs[k0 + lane];
+                const double c = a.alpha * cs.x, s = a.alpha * cs.y;
+                const double v1 = fma(c, Xc, fma(s, Yc, a.det_center));
+                const double v2 = fma(-s, Xc, fma(c, Yc, a.det_center));
+                const double jc1 = floor(v1), jc2 = floor(v2);
+                pv = make_float4((float)c, (float)s, (float)(v1 - jc1 - 0.5), (float)(v2 - jc2 - 0.5));
+                jl1 = (int)jc1 - H;
+                jl2 = (int)jc2 - H;
+            }
+            prm[b * KT + lane] = pv;
+        }
+        // the block's earlier reads of buffer b (ordered before this warp by
+        // the done counter) come before the copy engine's writes
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        const uint32_t mbar = full_s + 8u * b;
+        if (lane == 0) {
+            asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
+                         ::"r"(mbar), "r"((uint32_t)(na * 2 * W * 16)) : "memory");
+            issued[b] += 1;
+        }
+        __syncwarp();
+        if (lane != 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+        if (lane < na) {
+            const uint32_t dst = tab0 + (uint32_t)b * stage_bytes + (uint32_t)(2 * lane * Wp * 16);
+            const int z = (int)(zbase + k0 + lane);
+            const unsigned long long map = reinterpret_cast<unsigned long long>(&tmap);
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                         " [%0], [%1, {%2, %3, %4}], [%5];"
+                         ::"r"(dst), "l"(map), "r"(0), "r"(jl1 + 1), "r"(z), "r"(mbar) : "memory");
+            asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                         " [%0], [%1, {%2, %3, %4}], [%5];"
+                         ::"r"(dst + (uint32_t)(Wp * 16)), "l"(map), "r"(0), "r"(jl2 + 1), "r"(z), "r"(mbar)
+                         : "memory");
+        }
+    };
+
+    if (tid == 0) {
+        for (int b = 0; b < NS; ++b) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 32;" ::"r"(full_s + 8u * b) : "memory");
+            done[b] = 0;
+            issued[b] = 0;
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    if (warp == 0)
+        for (int t = 0; t < min(NS, n_stages); ++t) issue(t, t);
+
+    float acc[4][PY][PX];
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+        for (int iy = 0; iy < PY; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < PX; ++ix) acc[o][iy][ix] = 0.f;
+
+    bool ok = true;
+    for (int t = 0; t < n_stages; ++t) {
+        const int b = t % NS;
+        if (!staged_wait(full_s + 8u * b, (unsigned)((t / NS) & 1))) {
+            ok = false;
+            break;
+        }
+        const int na = min(KT, K2 - t * KT);
+        const uint32_t tabb = tab0 + (uint32_t)b * stage_bytes;
+        for (int p = 0; p < na; ++p) {
+            const uint32_t cb1 = tabb + 16u * (uint32_t)(2 * p * Wp + H) - 16u * kRoundMagicBits;
+            const uint32_t cb2 = cb1 + 16u * (uint32_t)Wp;
+            orbit_pair<TXT, TYT, PX, PY, T, false, PACKED>(acc, prm[b * KT + p], cb1, cb2, 0u, dxt, dyt, H,
+                                                           a.status);
+        }
+        // release buffer b; the last warp to do so refills it with stage t + NS
+        __syncwarp();
+        int last = 0;
+        if (lane == 0) {
+            __threadfence_block();
+            last = atomicAdd(&done[b], 1) == NW - 1;
+            if (last) {
+                done[b] = 0;
+                __threadfence_block();
+            }
+        }
+        last = __shfl_sync(0xffffffffu, last, 0);
+        if (last && t + NS < n_stages) issue(t + NS, b);
+    }
+    const bool failed = __syncthreads_or(!ok);
+    if (failed) {
+        // a wait ran out: record it, let every copy this block started land
+        // (capped) and write nothing
+        if (tid == 0) {
+            atomicCAS(a.status, 0u, (unsigned)FAULT_BP_STAGE_WAIT);
+            for (int b = 0; b < NS; ++b)
+                if (issued[b] > 0) staged_wait(full_s + 8u * b, (unsigned)((issued[b] - 1) & 1));
+        }
+        return;
+    }
+    float *out = a.out + (size_t)sl * a.N * a.N;
+    orbit_store<TXT, TYT, PX, PY>(acc, out, nullptr, 0.f, 0.f, a.accumulate, a.N, x0 + tx, y0 + ty,
+                                  a.scale * __ldg(a.smax + sl));
+}
+
+// Compiled shapes: the orbit kernel's 64 x 64 (256 threads, 4 x 4 pixels) and
+// 32 x 32 (128 threads, 2 x 4) tiles, packed pair arithmetic.
+struct StagedShape {
+    int txt, tyt, px, py, kt, ns, minb;
+};
+constexpr StagedShape kStagedShapes[] = {
+    {16, 16, 4, 4, 8, 3, 2},    // 0: 64 x 64 orbit, 8 pairs per stage, 3 buffers
+    {16, 16, 4, 4, 16, 2, 2},   // 1: 64 x 64, 16 pairs, 2 buffers
+    {16, 8, 2, 4, 16, 3, 4},    // 2: 32 x 32 orbit, 16 pairs, 3 buffers
+    {16, 8, 2, 4, 8, 4, 4},     // 3: 32 x 32, 8 pairs, 4 buffers
+    {16, 8, 2, 4, 8, 3, 5},     // 4: 32 x 32, 8 pairs, 3 buffers, five blocks per SM
+    {16, 8, 2, 4, 8, 2, 6},     // 5: 32 x 32, 8 pairs, 2 buffers, six blocks per SM
+};
+constexpr int kNumStagedShapes = sizeof(kStagedShapes) / sizeof(kStagedShapes[0]);
+
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
+{
+    static std::once_flag once;
+    static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+    std::call_once(once, [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess && q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+        else
+            cudaGetLastError();
+    });
+    return fn;
+}
+
+struct StagedLaunch {
+    const void *filt;
+    const float *row_scale;
+    float *slice;
+    const double2 *cs;
+    int K, D, N, S;
+    double alpha, det_center;
+    float scale;
+    int accumulate;
+    fbp_dtype dtype;
+    char *ws;
+    int chunk;                 // slices per pass through the workspace
+};
+
+size_t staged_table_bytes(int K, int D) { return (size_t)(K / 2) * (size_t)(D + 1) * 16; }
+size_t staged_scale_bytes(int chunk) { return ((size_t)chunk * 4 + 255) / 256 * 256; }
+
+template <int V, typename T>
+fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *status)
+{
+    constexpr StagedShape sd = kStagedShapes[V];
+    constexpr int TILE = sd.txt * sd.px;
+    if (L.N % (2 * TILE) != 0) return fail(FBP_ERR_UNSUPPORTED, "n must be a multiple of %d", 2 * TILE);
+    auto kern = bp_staged_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, sd.ns, T, true, sd.minb>;
+    StagedArgs a;
+    a.cs = L.cs;
+    a.K2 = L.K / 2;
+    a.N = L.N;
+    a.H = bp_window_half(L.alpha, TILE, TILE);
+    a.W = 2 * a.H + 1;
+    a.Wp = (a.W + 7) / 8 * 8;
+    if (a.H < 0 || a.W > 256) return fail(FBP_ERR_UNSUPPORTED, "backprojection window too wide for a bulk copy");
+    a.orbits_x = L.N / TILE / 2;
+    a.alpha = L.alpha;
+    a.det_center = L.det_center;
+    a.scale = L.scale;
+    a.accumulate = L.accumulate;
+    a.status = status;
+    const size_t smem = staged_smem_bytes<sd.kt, sd.ns>(a.Wp);
+    if (smem > 220 * 1024) return fail(FBP_ERR_UNSUPPORTED, "backprojection window too wide");
+    fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
+    if (st != FBP_OK) return st;
+    auto encode = tensor_map_encoder();
+    if (!encode) return fail(FBP_ERR_CUDA, "cuTensorMapEncodeTiled is not available from the driver");
+    const long long orbits = (long long)a.orbits_x * a.orbits_x;
+    if (orbits > INT_MAX) return fail(FBP_ERR_UNSUPPORTED, "too many tiles");
+    const int E = L.D + 1;
+    float *smax = reinterpret_cast<float *>(L.ws);
+    uint4 *table = reinterpret_cast<uint4 *>(L.ws + staged_scale_bytes(L.chunk));
+    const size_t kd = (size_t)L.K * L.D;
+    for (int s0 = 0; s0 < L.S; s0 += L.chunk) {
+        const int n = std::min(L.chunk, L.S - s0);
+        const T *filt = static_cast<const T *>(L.filt) + (size_t)s0 * kd;
+        const float *rs = L.row_scale + (size_t)s0 * L.K;
+        slice_scale_kernel<<<n, 256, 0, s>>>(rs, L.K, smax);
+        FBP_CUDA_TRY(cudaGetLastError());
+        const long long pairs = (long long)n * (L.K / 2);
+        dim3 pg((unsigned)((E + 255) / 256), (unsigned)std::min<long long>(pairs, 65535));
+        orbit_prestage_kernel<T, true><<<pg, 256, 0, s>>>(filt, rs, smax, table, L.K, L.D, pairs);
+        FBP_CUDA_TRY(cudaGetLastError());
+        // the chunk's table as a 3-D tensor of 32-bit words: {4 words, E entries, pairs}
+        CUtensorMap map;
+        const cuuint64_t dims[3] = {4, (cuuint64_t)E, (cuuint64_t)pairs};
+        const cuuint64_t strides[2] = {16, (cuuint64_t)E * 16};
+        const cuuint32_t box[3] = {4, (cuuint32_t)a.W, 1};
+        const cuuint32_t estr[3] = {1, 1, 1};
+        const CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, table, dims, strides, box, estr,
+                                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return fail(FBP_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
+        a.out = L.slice + (size_t)s0 * L.N * L.N;
+        a.smax = smax;
+        dim3 grid((unsigned)orbits, (unsigned)n);
+        kern<<<grid, sd.txt * sd.tyt, smem, s>>>(map, a);
+        FBP_CUDA_TRY(cudaGetLastError());
+    }
+    return FBP_OK;
+}
+
+template <typename T>
+fbp_status launch_staged_dtype(const StagedLaunch &L, int v, cudaStream_t s, unsigned *status)
+{
+    switch (v) {
+        case 0: return launch_staged_t<0, T>(L, s, status);
+        case 1: return launch_staged_t<1, T>(L, s, status);
+        case 2: return launch_staged_t<2, T>(L, s, status);
+        case 3: return launch_staged_t<3, T>(L, s, status);
+        case 4: return launch_staged_t<4, T>(L, s, status);
+        case 5: return launch_staged_t<5, T>(L, s, status);
+    }
+    return fail(FBP_ERR_INVALID_ARG, "staged shape %d", v);
+}
+
+}  // namespace
+}  // namespace fbp
+
+using namespace fbp;
+
+extern "C" int fbp_backproject_staged_shape_count(void) { return kNumStagedShapes; }
+
+extern "C" size_t fbp_backproject_staged_workspace_bytes(const fbp_geometry *g, int chunk)
+{
+    clear_error();
+    if (!g || chunk < 1 || g->n_angles < 2 || g->n_det < 1) return 0;
+    return staged_scale_bytes(chunk) + (size_t)chunk * staged_table_bytes(g->n_angles, g->n_det);
+}
+
+extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_scale, fbp_dtype dtype,
+                                             float *slice, const fbp_geometry *g, int n_slices, float scale,
+                                             int accumulate, int shape, void *workspace, size_t ws_bytes,
+                                             fbp_stream_t stream)
+{
+    clear_error();
+    fbp_status st = check_geometry(g, false, true);
+    if (st != FBP_OK) return st;
+    if (dtype != FBP_F16 && dtype != FBP_BF16)
+        return fail(dtype == FBP_F32 ? FBP_ERR_UNSUPPORTED : FBP_ERR_INVALID_ARG,
+                    "fbp_backproject_staged takes 16-bit rows (dtype %d)", (int)dtype);
+    if (shape < -1 || shape >= kNumStagedShapes) return fail(FBP_ERR_INVALID_ARG, "shape %d", shape);
+    if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
+    if (!(scale == scale) || scale > 3.4e38f || scale < -3.4e38f)
+        return fail(FBP_ERR_INVALID_ARG, "scale is not finite");
+    if (!bp_orbit_geometry(g->n_angles, g->angle_step, g->n_det, g->det_center, g->n, 16))
+        return fail(FBP_ERR_UNSUPPORTED, "fbp_backproject_staged needs angle step pi/K with K even and "
+                    "det_center = (D-1)/2");
+    if (n_slices == 0) return FBP_OK;
+    if (!filt || !slice || !row_scale) return fail(FBP_ERR_INVALID_ARG, "filt, row_scale or slice is NULL");
+    const size_t nin = (size_t)n_slices * g->n_angles * g->n_det * 2;
+    const size_t nout = (size_t)n_slices * g->n * g->n * 4;
+    const char *pi = static_cast<const char *>(filt), *po = reinterpret_cast<const char *>(slice);
+    if (pi < po + nout && po < pi + nin) return fail(FBP_ERR_INVALID_ARG, "slice overlaps filt");
+    if (!workspace) return fail(FBP_ERR_WORKSPACE, "workspace is NULL");
+    if (reinterpret_cast<uintptr_t>(workspace) & 255)
+        return fail(FBP_ERR_WORKSPACE, "workspace is not 256-byte aligned");
+    const size_t per = staged_table_bytes(g->n_angles, g->n_det);
+    int chunk = 0;
+    for (int c = std::min(n_slices, 1 << 16); c >= 1; c = c > 8 ? c / 2 : c - 1)
+        if (staged_scale_bytes(c) + (size_t)c * per <= ws_bytes) {
+            chunk = c;
+            break;
+        }
+    if (chunk < 1)
+        return fail(FBP_ERR_WORKSPACE, "workspace has %zu bytes, one slice needs %zu", ws_bytes,
+                    staged_scale_bytes(1) + per);
+    if ((long long)chunk * (g->n_angles / 2) > INT_MAX)
+        chunk = (int)std::max(1LL, (long long)INT_MAX / (g->n_angles / 2));
+    const double2 *cs = nullptr;
+    st = angle_table(*g, stream, &cs);
+    if (st != FBP_OK) return st;
+    unsigned *status = nullptr;
+    st = device_status_word(&status);
+    if (st != FBP_OK) return st;
+    StagedLaunch L;
+    L.filt = filt;
+    L.row_scale = row_scale;
+    L.slice = slice;
+    L.cs = cs;
+    L.K = g->n_angles;
+    L.D = g->n_det;
+    L.N = g->n;
+    L.S = n_slices;
+    L.alpha = g->pixel_size / g->det_spacing;
+    L.det_center = g->det_center;
+    L.scale = scale;
+    L.accumulate = accumulate ? 1 : 0;
+    L.dtype = dtype;
+    L.ws = static_cast<char *>(workspace);
+    L.chunk = chunk;
+    // default: the 64 x 64 orbit where n allows it, else 32 x 32
+    if (shape < 0) shape = g->n % 128 == 0 ? 0 : 2;
+    return dtype == FBP_F16 ? launch_staged_dtype<__half>(L, shape, stream, status)
+                            : launch_staged_dtype<__nv_bfloat16>(L, shape, stream, status);
+}

@@ -30,6 +30,7 @@ enum DeviceFault : unsigned {
     FAULT_UNION_CAP = 4,      // patching: a union-find loop ran past its cap
     FAULT_LEAF = 5,           // patching: a quadtree leaf entry outside the slice
     FAULT_STREAM_WAIT = 6,    // streamed filter: a wait for its row copy ran past its cap
+    FAULT_BP_STAGE_WAIT = 7,  // bulk-copy-fed backprojection: a wait for a window copy ran past its cap
 };
 fbp_status device_status_word(unsigned **out);   // current device
 

@@ -110,3 +110,23 @@ def test_precision_n8192_16bit_sampled(n8192, dtype, variant):
         record(f"fbp_precision_n8192/{name}/variant{variant}/slice{s}/vs_f32_gpu", e32)
         assert err <= 2e-3, f"{dtype}: {err:.2e} of DR vs the FP64 oracle"
         assert e32 <= 2e-3, f"{dtype}: {e32:.2e} of DR vs the FP32 GPU image"
+
+
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+def test_precision_n8192_staged_equals_orbit_kernel(n8192, dtype):
+    """The bulk-copy-fed kernel (fbp_backproject_staged, default 64 x 64
+    shape) on the full-size workload: bit-identical to the packed orbit
+    kernel of the same tile over the whole 8192^2 image, and within the
+    16-bit bar of the oracle on the sampled pixels."""
+    api, sinos, refs = n8192
+    g = api.Geometry(4096, 8192, 8192)
+    filt, rs = api.filter(to_gpu(sinos), g, dtype=dtype)
+    staged = api.backproject_staged(filt, g, rs, chunk=2)
+    orbit = api.backproject(filt, g, row_scale=rs, variant=10)
+    assert torch.equal(staged, orbit)
+    for s, (rows, cols, ref) in enumerate(refs):
+        got = to_np(staged[s][torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()])
+        err = np.max(np.abs(got - ref)) / (ref.max() - ref.min())
+        record(f"fbp_precision_n8192/{str(dtype).replace('torch.', '')}/staged/slice{s}/vs_oracle", err)
+        assert err <= 2e-3
+    assert api.device_status() == 0
