@@ -554,6 +554,11 @@ def run_uniform(args) -> None:
         tdt = getattr(torch, DT[dt])
         filt = torch.empty(sino.shape, dtype=tdt, device=dev)
         rs = torch.empty((S, K), dtype=torch.float32, device=dev) if dt != "f32" else None
+        # 16-bit rows: the bulk-copy-fed kernel from per-slice tables (its
+        # workspace holds the whole stack's tables, allocated before timing)
+        staged = dt != "f32" and args.variant < 0 and api.staged_supported(g)
+        wsp = torch.empty(api.backproject_staged_workspace_bytes(g, tdt, S), dtype=torch.uint8, device=dev) \
+            if staged else None
         T = Timed(stream, args.steps, args.warmup, n_events=3)
 
         def step(evs):
@@ -562,7 +567,10 @@ def run_uniform(args) -> None:
             api.filter(sino, g, kind=w.filter, dtype=tdt, out=filt, row_scale=rs)
             if evs:
                 evs[1].record(stream)
-            api.backproject(filt, g, row_scale=rs, out=out, variant=args.variant)
+            if staged:
+                api.backproject_staged(filt, g, rs, out=out, workspace=wsp)
+            else:
+                api.backproject(filt, g, row_scale=rs, out=out, variant=args.variant)
             if evs:
                 evs[2].record(stream)
 
@@ -572,8 +580,15 @@ def run_uniform(args) -> None:
         rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
         results[dt] = {"value": rate / 1e9, "ms_per_step": ms_step, "bp_ms": T.between(1, 2),
                        "filter_ms": T.between(0, 1), "step_spread": T.spread(0, 2), "clocks": T.clocks,
-                       "slices_per_s": S * len(per_rank) / (ms_step / 1e3)}
-        del filt, rs
+                       "slices_per_s": S * len(per_rank) / (ms_step / 1e3), "staged": staged}
+        if staged:
+            # the block-staged orbit kernel on the same rows, for comparison
+            To = Timed(stream, 3, 3)
+            ms_o = To.run(lambda _: api.backproject(filt, g, row_scale=rs, out=out, variant=-1), None)
+            results[dt]["orbit_kernel"] = {"bp_ms_per_step": ms_o,
+                                           "bp_gupdates_per_s": updates / (ms_o / 1e3) / 1e9,
+                                           "bp_variant": resolved_variant(api, g, dt, -1)}
+        del filt, rs, wsp
 
     # the texture-unit backprojection (the measured alternative to staged
     # tables): backprojection only, on the same FP32 rows
@@ -643,7 +658,7 @@ def run_uniform(args) -> None:
         r = results[dt]
         rpd = roofline_peak(sm_max, dt, sms, onchip)
         ach = updates / (r["bp_ms"] / 1e3) / 1e9
-        vdt = resolved_variant(api, g, dt, args.variant)
+        vdt = "fbp_backproject_staged (default shape)" if r["staged"] else resolved_variant(api, g, dt, args.variant)
         line[f"staged_{dt}"] = {
             "value": r["value"], "unit": UNIT, "ratio_to_f32": r["value"] / main["value"],
             "bp_gupdates_per_s": ach, "bp_ratio_to_f32": ach / achieved,
@@ -651,7 +666,10 @@ def run_uniform(args) -> None:
             "roofline_frac_nominal": ach / rpd["peak_nominal"], "roofline_bound": rpd["bound"],
             "traffic": captured_traffic(vdt, dt, S, N, K),
             "slices_per_s": r["slices_per_s"], "ms_per_step": r["ms_per_step"],
+            "bp_ms_per_step": r["bp_ms"], "filter_ms_per_step": r["filter_ms"],
             "bp_variant": vdt}
+        if "orbit_kernel" in r:
+            line[f"staged_{dt}"]["orbit_kernel"] = r["orbit_kernel"]
     if tex is not None:
         tex["ratio_to_table"] = tex["bp_gupdates_per_s"] / achieved
         line["texture_alternative"] = tex

@@ -326,38 +326,47 @@ fbp_status fbp_backproject_noalloc(const void *filt, const float *row_scale,
                                    fbp_stream_t stream);
 
 /*
- * fbp_backproject_staged -- fbp_backproject for 16-bit rows with the
- * backprojection tables formed once per slice instead of once per block
- * (the same step, Sec. V-A(c) stage 2; the same sum, bit-identical to
- * fbp_backproject_variant with the symmetric orbit variant of the same tile:
- * 10 for shapes 0-1, 11 for shapes 2-5).  A pass over the filtered rows writes, for every
- * angle pair (th_k, th_k + pi/2) and detector segment, the 16-byte entry of
- * the orbit kernel (midpoints and slopes of the two rows and their mirrors,
- * scaled by s_k / S, S = max_k s_k of the slice) into the workspace; the
+ * fbp_backproject_staged -- fbp_backproject with the backprojection tables
+ * formed once per slice instead of once per thread block (the same step,
+ * Sec. V-A(c) stage 2, for the symmetric orbit geometry).  A pass over the
+ * filtered rows writes, for every angle pair (th_k, th_k + pi/2) and
+ * detector segment, one table entry -- the segment midpoints and slopes of
+ * the two rows and of their mirrors -- into the workspace; the
  * backprojection then moves each tile's window of entries into shared memory
  * with one bulk-tensor copy (zero-filled past the detector) and interpolates
- * as the orbit kernel does, with no block-wide barrier per stage.
- *   filt, row_scale, dtype  16-bit rows (FBP_F16 or FBP_BF16) and their
- *              scales, as fbp_backproject; FBP_F32 returns FBP_ERR_UNSUPPORTED.
- *   slice, g, n_slices, scale, accumulate  as fbp_backproject.
- *   shape      -1 default (0 when n is a multiple of 128, else 2), or
- *              0: 64 x 64 orbit tiles, 8 angle pairs per stage, 3 buffers;
- *              1: 64 x 64, 16 pairs, 2 buffers; 2: 32 x 32, 16 pairs, 3
- *              buffers; 3: 32 x 32, 8 pairs, 4 buffers; 4: 32 x 32, 8 pairs,
- *              3 buffers, five blocks per SM; 5: 32 x 32, 8 pairs, 2 buffers,
- *              six blocks per SM.
+ * with no block-wide barrier per stage.
+ *   16-bit rows (FBP_F16, FBP_BF16): 16-byte entries of the orbit kernel
+ *              (scaled by s_k / S, S = max_k s_k of the slice); the result is
+ *              bit-identical to fbp_backproject_variant with the packed orbit
+ *              variant of the same tile (10 for shapes 0-1, 11 for 2-5).
+ *   FP32 rows: 32-byte entries, Q = midpoint + (u' - i) slope on the segment
+ *              of the rounded index i (the orbit kernel's FP32 tables use
+ *              block-relative intercepts instead, so results agree with it to
+ *              FP32 rounding, not bit for bit).
+ *   filt, row_scale, dtype, slice, g, n_slices, scale, accumulate  as
+ *              fbp_backproject (row_scale only for 16-bit rows).
+ *   shape      -1 default, or one of fbp_backproject_staged_shape_count(dtype):
+ *              16-bit -- 0: 64 x 64 orbit tiles, 8 angle pairs per stage, 3
+ *              buffers; 1: 64 x 64, 16 pairs, 2 buffers (default when n is a
+ *              multiple of 128); 2: 32 x 32, 16 pairs, 3 buffers; 3: 32 x 32,
+ *              8 pairs, 4 buffers; 4: 32 x 32, 8 pairs, 3 buffers, five blocks
+ *              per SM; 5: 32 x 32, 8 pairs, 2 buffers, six blocks per SM (the
+ *              default otherwise).  FP32 -- 0: 32 x 32, 4 pairs, 2 buffers, six
+ *              blocks per SM (default); 1: 32 x 32, 4 pairs, 3 buffers, five
+ *              blocks; 2: 32 x 32, 8 pairs, 2 buffers, three blocks; 3: 64 x 64,
+ *              8 pairs, 2 buffers, two blocks.
  *   workspace  device, 256-byte aligned, owned by the caller, at least
- *              fbp_backproject_staged_workspace_bytes(g, 1) bytes; the call
- *              works through the stack in as many slices at a time as the
- *              workspace holds (fbp_backproject_staged_workspace_bytes(g, c)
- *              for c slices: (K/2) (D+1) 16 bytes per slice plus 256).
+ *              fbp_backproject_staged_workspace_bytes(g, dtype, 1) bytes; the
+ *              call works through the stack in as many slices at a time as the
+ *              workspace holds (c slices: (K/2) (D+1) 16 bytes per slice for
+ *              16-bit rows, 32 for FP32, plus 256).
  * Geometry: angle step pi/K with K even, det_center = (D-1)/2, n a multiple
  * of twice the tile (FBP_ERR_UNSUPPORTED otherwise).  The table write and the
  * backprojection run on `stream`; the call may be captured once g's angle
- * table exists.  fbp_backproject_staged_shape_count() is the number of shapes.
+ * table exists.
  */
-size_t fbp_backproject_staged_workspace_bytes(const fbp_geometry *g, int chunk);
-int fbp_backproject_staged_shape_count(void);
+size_t fbp_backproject_staged_workspace_bytes(const fbp_geometry *g, fbp_dtype dtype, int chunk);
+int fbp_backproject_staged_shape_count(fbp_dtype dtype);
 fbp_status fbp_backproject_staged(const void *filt, const float *row_scale, fbp_dtype dtype,
                                   float *slice, const fbp_geometry *g, int n_slices, float scale,
                                   int accumulate, int shape, void *workspace, size_t ws_bytes,

@@ -139,8 +139,8 @@ SIGNATURES = {
     "fbp_prepare": (ctypes.c_int, [_G, ctypes.c_int, _vp]),
     "fbp_release_tables": (None, []),
     "fbp_measure_onchip_peaks": (ctypes.c_int, [ctypes.POINTER(COnchipPeaks)]),
-    "fbp_backproject_staged_workspace_bytes": (ctypes.c_size_t, [_G, ctypes.c_int]),
-    "fbp_backproject_staged_shape_count": (ctypes.c_int, []),
+    "fbp_backproject_staged_workspace_bytes": (ctypes.c_size_t, [_G, ctypes.c_int, ctypes.c_int]),
+    "fbp_backproject_staged_shape_count": (ctypes.c_int, [ctypes.c_int]),
     "fbp_backproject_staged": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int, ctypes.c_float,
                                               ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
     "fbp_host_workspace_bytes": (ctypes.c_size_t, [_G, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),

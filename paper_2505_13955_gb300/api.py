@@ -291,67 +291,68 @@ def backproject(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None 
     return out
 
 
-def backproject_staged_workspace_bytes(g: Geometry, chunk: int = 1) -> int:
+def backproject_staged_workspace_bytes(g: Geometry, dtype=torch.float16, chunk: int = 1) -> int:
     """fbp_backproject_staged_workspace_bytes: workspace for `chunk` slices at a time."""
-    n = lib().fbp_backproject_staged_workspace_bytes(ctypes.byref(g.c()), int(chunk))
+    gc = g.c()
+    n = lib().fbp_backproject_staged_workspace_bytes(ctypes.byref(gc), _DTYPES[dtype], int(chunk))
     if n == 0:
         raise FbpError(_lib.FBP_ERR_INVALID_ARG, "fbp_backproject_staged_workspace_bytes: invalid arguments")
     return int(n)
 
 
-def backproject_staged(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor, scale: float | None = None,
-                       out: torch.Tensor | None = None, accumulate: bool = False, shape: int = -1,
-                       workspace: torch.Tensor | None = None, chunk: int = 1):
-    """fbp_backproject_staged: 16-bit rows backprojected from tables written
-    once per slice (a workspace of `chunk` slices is allocated if none is
-    given).  Bit-identical to backproject with the packed orbit variant of
-    the same tile."""
+def staged_shape_count(dtype=torch.float16) -> int:
+    return int(lib().fbp_backproject_staged_shape_count(_DTYPES[dtype]))
+
+
+def backproject_staged(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None = None,
+                       scale: float | None = None, out: torch.Tensor | None = None, accumulate: bool = False,
+                       shape: int = -1, workspace: torch.Tensor | None = None, chunk: int = 1):
+    """fbp_backproject_staged: backprojection from tables written once per
+    slice (a workspace of `chunk` slices is allocated if none is given).
+    16-bit rows (with their row_scale) are bit-identical to backproject with
+    the packed orbit variant of the same tile."""
     _need(filt, "filt")
-    if filt.dtype not in (torch.float16, torch.bfloat16):
-        raise ValueError("fbp_backproject_staged takes float16 or bfloat16 rows")
+    if filt.dtype not in _DTYPES:
+        raise ValueError(f"unsupported filt dtype {filt.dtype}")
     S = _slices(filt, (g.n_angles, g.n_det), "filt")
-    _need(row_scale, "row_scale", torch.float32)
+    if filt.dtype != torch.float32:
+        if row_scale is None:
+            raise ValueError("16-bit rows need their row_scale")
+        _need(row_scale, "row_scale", torch.float32)
     shape_out = (g.n, g.n) if filt.dim() == 2 else (S, g.n, g.n)
     if out is None:
         out = torch.empty(shape_out, dtype=torch.float32, device=filt.device)
     _need(out, "out", torch.float32)
     if workspace is None:
-        workspace = torch.empty(backproject_staged_workspace_bytes(g, min(chunk, S)), dtype=torch.uint8,
-                                device=filt.device)
+        workspace = torch.empty(backproject_staged_workspace_bytes(g, filt.dtype, min(chunk, S)),
+                                dtype=torch.uint8, device=filt.device)
     L = lib()
     gc = g.c()
     sc = g.angle_step if scale is None else scale
-    st = L.fbp_backproject_staged(_ptr(filt), _ptr(row_scale), _DTYPES[filt.dtype], _ptr(out), ctypes.byref(gc), S,
-                                  float(sc), int(accumulate), int(shape), _ptr(workspace), workspace.numel(),
-                                  _stream(filt.device))
+    st = L.fbp_backproject_staged(_ptr(filt), _ptr(row_scale if filt.dtype != torch.float32 else None),
+                                  _DTYPES[filt.dtype], _ptr(out), ctypes.byref(gc), S, float(sc), int(accumulate),
+                                  int(shape), _ptr(workspace), workspace.numel(), _stream(filt.device))
     _lib.check(st, L, "fbp_backproject_staged")
     return out
 
 
-def radon_forward(img: torch.Tensor, g: Geometry, out: torch.Tensor | None = None,
-                  which: str = "default", variant: int = -1):
-    """radon_forward: the matched projector A (transpose of backproject, scale 1).
-    variant -1 = library default, 0 = deterministic gather, 1..5 = tile-owned
-    (floating-point atomics across tiles; 4 and 5 take four / two slices per
-    block)."""
-    _need(img, "slice", torch.float32)
-    S = _slices(img, (g.n, g.n), "slice")
-    shape = (g.n_angles, g.n_det) if img.dim() == 2 else (S, g.n_angles, g.n_det)
-    if out is None:
-        out = torch.empty(shape, dtype=torch.float32, device=img.device)
-    _need(out, "out", torch.float32)
-    L = lib(which)
-    gc = g.c()
-    st = L.radon_forward_variant(_ptr(img), _ptr(out), ctypes.byref(gc), S, int(variant),
-                                 _stream(img.device))
-    _lib.check(st, L, "radon_forward")
-    return out
+def staged_supported(g: Geometry) -> bool:
+    """Whether fbp_backproject_staged takes geometry g (the 90-degree orbit
+    geometry: angle step pi/K with K even, centred detector, n a multiple of 64)."""
+    return (g.n_angles % 2 == 0 and g.n % 64 == 0 and abs(g.angle_step * g.n_angles - math.pi) <= 1e-9 * math.pi
+            and abs(g.det_center - 0.5 * (g.n_det - 1)) <= 1e-9 * (1 + g.n_det))
 
 
 def fbp(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
         out: torch.Tensor | None = None, variant: int = -1):
-    """Filtered backprojection: fbp_filter then fbp_backproject (scale = angle_step)."""
+    """Filtered backprojection: fbp_filter then fbp_backproject (scale =
+    angle_step).  16-bit rows with the default variant take
+    fbp_backproject_staged where the geometry allows it (a workspace of up to
+    four slices' tables is allocated)."""
     filt, rs = filter(sino, g, kind=kind, dtype=dtype)
+    if dtype != torch.float32 and variant < 0 and staged_supported(g):
+        S = 1 if sino.dim() == 2 else sino.shape[0]
+        return backproject_staged(filt, g, rs, out=out, chunk=min(S, 4))
     return backproject(filt, g, row_scale=rs, out=out, variant=variant)
 
 

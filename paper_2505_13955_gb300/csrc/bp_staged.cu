@@ -103,6 +103,82 @@ __global__ void orbit_prestage_kernel(const T *filt, const float *row_scale, con
     }
 }
 
+// FP32 rows: per segment and row the midpoint (q_j + q_{j+1}) / 2 and the
+// slope q_{j+1} - q_j, so that Q(u) = mid + (u' - i) slope; 32 bytes per
+// entry, kept as two 16-byte halves (rows th, th' | mirrored rows) that land
+// in separate shared arrays.
+__global__ void orbit_prestage_f32_kernel(const float *filt, float4 *table, int K, int D, long long pairs)
+{
+    const int K2 = K / 2, E = D + 1;
+    const int e = blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= E) return;
+    const int jj = e - 1, mj = D - 1 - jj;
+    for (long long p = blockIdx.y; p < pairs; p += gridDim.y) {
+        const long long s = p / K2;
+        const int k = (int)(p - s * K2);
+        const float *r0 = filt + ((size_t)s * K + k) * D;
+        const float *r1 = r0 + (size_t)K2 * D;
+        float v[8];
+        v[0] = (unsigned)jj < (unsigned)D ? __ldg(r0 + jj) : 0.f;
+        v[1] = (unsigned)(jj + 1) < (unsigned)D ? __ldg(r0 + jj + 1) : 0.f;
+        v[2] = (unsigned)jj < (unsigned)D ? __ldg(r1 + jj) : 0.f;
+        v[3] = (unsigned)(jj + 1) < (unsigned)D ? __ldg(r1 + jj + 1) : 0.f;
+        v[4] = (unsigned)mj < (unsigned)D ? __ldg(r0 + mj) : 0.f;
+        v[5] = (unsigned)(mj - 1) < (unsigned)D ? __ldg(r0 + mj - 1) : 0.f;
+        v[6] = (unsigned)mj < (unsigned)D ? __ldg(r1 + mj) : 0.f;
+        v[7] = (unsigned)(mj - 1) < (unsigned)D ? __ldg(r1 + mj - 1) : 0.f;
+        float ms[8];
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            ms[2 * r] = __fmul_rn(0.5f, __fadd_rn(v[2 * r], v[2 * r + 1]));
+            ms[2 * r + 1] = __fsub_rn(v[2 * r + 1], v[2 * r]);
+        }
+        float4 *o = table + ((size_t)p * E + e) * 2;
+        o[0] = make_float4(ms[0], ms[1], ms[2], ms[3]);
+        o[1] = make_float4(ms[4], ms[5], ms[6], ms[7]);
+    }
+}
+
+// One angle pair from FP32 midpoint/slope entries (the FP32 form of
+// orbit_pair): per pixel and window the rounded index i and the fraction
+// u' - i, two 16-byte loads (rows th, th' at cb, mirrored rows at cb + tab_b),
+// four FMAs.
+template <int TXT, int TYT, int PX, int PY>
+__device__ __forceinline__ void orbit_pair_mid(float (&acc)[4][PY][PX], const float4 pv, const uint32_t cb1,
+                                               const uint32_t cb2, const uint32_t tab_b, const float dxt,
+                                               const float dyt)
+{
+    const float c = pv.x, s = pv.y;
+    const float u10 = fmaf(dxt, c, fmaf(dyt, s, pv.z));
+    const float u20 = fmaf(dxt, -s, fmaf(dyt, c, pv.w));
+    const float s1x = (float)TXT * c, s1y = (float)TYT * s;
+    const float s2x = -(float)TXT * s, s2y = (float)TYT * c;
+#pragma unroll
+    for (int iy = 0; iy < PY; ++iy) {
+        const float r1 = iy == 0 ? u10 : fmaf((float)iy, s1y, u10);
+        const float r2 = iy == 0 ? u20 : fmaf((float)iy, s2y, u20);
+#pragma unroll
+        for (int ix = 0; ix < PX; ++ix) {
+#pragma unroll
+            for (int win = 0; win < 2; ++win) {
+                const float u = win == 0 ? (ix == 0 ? r1 : fmaf((float)ix, s1x, r1))
+                                         : (ix == 0 ? r2 : fmaf((float)ix, s2x, r2));
+                const float t = __fadd_rn(u, kRoundMagic);
+                const float fr = __fsub_rn(u, __fsub_rn(t, kRoundMagic));
+                const uint32_t e = (win == 0 ? cb1 : cb2) + (__float_as_uint(t) << 4);
+                const float4 e0 = lds_f4(e), e1 = lds_f4(e + tab_b);
+                // orbit members fed by rows (th, th', th~, th'~), as orbit_pair
+                const int m0 = win == 0 ? 0 : 3, m1 = win == 0 ? 1 : 0;
+                const int m2 = win == 0 ? 2 : 1, m3 = win == 0 ? 3 : 2;
+                acc[m0][iy][ix] += fmaf(fr, e0.y, e0.x);
+                acc[m1][iy][ix] += fmaf(fr, e0.w, e0.z);
+                acc[m2][iy][ix] += fmaf(fr, e1.y, e1.x);
+                acc[m3][iy][ix] += fmaf(fr, e1.w, e1.z);
+            }
+        }
+    }
+}
+
 struct StagedArgs {
     const double2 *cs;         // [K] angle table (k < K/2 is read)
     float *out;                // the chunk's first slice [N][N]
@@ -137,10 +213,11 @@ __host__ __device__ constexpr size_t staged_params_bytes()
 {
     return ((size_t)NS * KT * 16 + 127) / 128 * 128;
 }
-template <int KT, int NS>
+// HALVES: 16-byte halves per entry (1 for 16-bit rows, 2 for FP32 rows).
+template <int KT, int NS, int HALVES>
 __host__ __device__ constexpr size_t staged_smem_bytes(int Wp)
 {
-    return 128 + 128 + staged_params_bytes<KT, NS>() + (size_t)NS * 2 * KT * Wp * 16;
+    return 128 + 128 + staged_params_bytes<KT, NS>() + (size_t)NS * HALVES * 2 * KT * Wp * 16;
 }
 
 template <int TXT, int TYT, int PX, int PY, int KT, int NS, typename T, bool PACKED, int MINB>
@@ -148,6 +225,7 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_kernel(const __grid_
                                                                    StagedArgs a)
 {
     constexpr int NT = TXT * TYT, NW = NT / 32, TILE = TXT * PX, WX = TXT / 8;
+    constexpr int HALVES = sizeof(T) == 4 ? 2 : 1;   // 16-byte halves per entry
     static_assert(TXT * PX == TYT * PY, "square tile");
     static_assert(KT <= 32 && NS >= 2 && NS <= 4, "stage shape");
     extern __shared__ unsigned char smem_raw[];
@@ -160,7 +238,8 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_kernel(const __grid_
     float4 *prm = reinterpret_cast<float4 *>(base + 128);
     const uint32_t tab0 = base_s + 128u + (uint32_t)staged_params_bytes<KT, NS>();
     const int H = a.H, W = a.W, Wp = a.Wp, K2 = a.K2;
-    const uint32_t stage_bytes = (uint32_t)(2 * KT * Wp * 16);
+    const uint32_t half_bytes = (uint32_t)(2 * KT * Wp * 16);   // one half-array of a stage
+    const uint32_t stage_bytes = HALVES * half_bytes;
 
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int tx = (warp % WX) * 8 + (lane & 7);
@@ -201,7 +280,7 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_kernel(const __grid_
         const uint32_t mbar = full_s + 8u * b;
         if (lane == 0) {
             asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;"
-                         ::"r"(mbar), "r"((uint32_t)(na * 2 * W * 16)) : "memory");
+                         ::"r"(mbar), "r"((uint32_t)(na * 2 * W * 16 * HALVES)) : "memory");
             issued[b] += 1;
         }
         __syncwarp();
@@ -217,6 +296,18 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_kernel(const __grid_
                          " [%0], [%1, {%2, %3, %4}], [%5];"
                          ::"r"(dst + (uint32_t)(Wp * 16)), "l"(map), "r"(0), "r"(jl2 + 1), "r"(z), "r"(mbar)
                          : "memory");
+            if constexpr (HALVES == 2) {
+                // FP32: the entries' second halves (words 4..7) into the mirrored-row array
+                asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                             " [%0], [%1, {%2, %3, %4}], [%5];"
+                             ::"r"(dst + half_bytes), "l"(map), "r"(4), "r"(jl1 + 1), "r"(z), "r"(mbar)
+                             : "memory");
+                asm volatile("cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+                             " [%0], [%1, {%2, %3, %4}], [%5];"
+                             ::"r"(dst + half_bytes + (uint32_t)(Wp * 16)), "l"(map), "r"(4), "r"(jl2 + 1), "r"(z),
+                               "r"(mbar)
+                             : "memory");
+            }
         }
     };
 
@@ -252,8 +343,11 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_kernel(const __grid_
         for (int p = 0; p < na; ++p) {
             const uint32_t cb1 = tabb + 16u * (uint32_t)(2 * p * Wp + H) - 16u * kRoundMagicBits;
             const uint32_t cb2 = cb1 + 16u * (uint32_t)Wp;
-            orbit_pair<TXT, TYT, PX, PY, T, false, PACKED>(acc, prm[b * KT + p], cb1, cb2, 0u, dxt, dyt, H,
-                                                           a.status);
+            if constexpr (HALVES == 2)
+                orbit_pair_mid<TXT, TYT, PX, PY>(acc, prm[b * KT + p], cb1, cb2, half_bytes, dxt, dyt);
+            else
+                orbit_pair<TXT, TYT, PX, PY, T, false, PACKED>(acc, prm[b * KT + p], cb1, cb2, 0u, dxt, dyt, H,
+                                                               a.status);
         }
         // release buffer b; the last warp to do so refills it with stage t + NS
         __syncwarp();
@@ -281,16 +375,18 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_kernel(const __grid_
         return;
     }
     float *out = a.out + (size_t)sl * a.N * a.N;
-    orbit_store<TXT, TYT, PX, PY>(acc, out, nullptr, 0.f, 0.f, a.accumulate, a.N, x0 + tx, y0 + ty,
-                                  a.scale * __ldg(a.smax + sl));
+    const float S = HALVES == 2 ? 1.f : __ldg(a.smax + sl);
+    orbit_store<TXT, TYT, PX, PY>(acc, out, nullptr, 0.f, 0.f, a.accumulate, a.N, x0 + tx, y0 + ty, a.scale * S);
 }
 
-// Compiled shapes: the orbit kernel's 64 x 64 (256 threads, 4 x 4 pixels) and
-// 32 x 32 (128 threads, 2 x 4) tiles, packed pair arithmetic.
+// Compiled shapes.  16-bit rows: the orbit kernel's 64 x 64 (256 threads,
+// 4 x 4 pixels) and 32 x 32 (128 threads, 2 x 4) tiles, packed pair
+// arithmetic.  FP32 rows: 32-byte entries, so fewer pairs per stage keep
+// several blocks per SM.
 struct StagedShape {
     int txt, tyt, px, py, kt, ns, minb;
 };
-constexpr StagedShape kStagedShapes[] = {
+constexpr StagedShape kStagedShapes16[] = {
     {16, 16, 4, 4, 8, 3, 2},    // 0: 64 x 64 orbit, 8 pairs per stage, 3 buffers
     {16, 16, 4, 4, 16, 2, 2},   // 1: 64 x 64, 16 pairs, 2 buffers
     {16, 8, 2, 4, 16, 3, 4},    // 2: 32 x 32 orbit, 16 pairs, 3 buffers
@@ -298,7 +394,20 @@ constexpr StagedShape kStagedShapes[] = {
     {16, 8, 2, 4, 8, 3, 5},     // 4: 32 x 32, 8 pairs, 3 buffers, five blocks per SM
     {16, 8, 2, 4, 8, 2, 6},     // 5: 32 x 32, 8 pairs, 2 buffers, six blocks per SM
 };
-constexpr int kNumStagedShapes = sizeof(kStagedShapes) / sizeof(kStagedShapes[0]);
+constexpr StagedShape kStagedShapes32[] = {
+    {16, 8, 2, 4, 4, 2, 6},     // 0: 32 x 32 orbit, 4 pairs per stage, 2 buffers, six blocks per SM
+    {16, 8, 2, 4, 4, 3, 5},     // 1: 32 x 32, 4 pairs, 3 buffers, five blocks per SM
+    {16, 8, 2, 4, 8, 2, 3},     // 2: 32 x 32, 8 pairs, 2 buffers, three blocks per SM
+    {16, 16, 4, 4, 8, 2, 2},    // 3: 64 x 64, 8 pairs, 2 buffers, two blocks per SM
+};
+constexpr int kNumStagedShapes16 = sizeof(kStagedShapes16) / sizeof(kStagedShapes16[0]);
+constexpr int kNumStagedShapes32 = sizeof(kStagedShapes32) / sizeof(kStagedShapes32[0]);
+
+template <typename T> constexpr const StagedShape *staged_shapes()
+{
+    if constexpr (sizeof(T) == 4) return kStagedShapes32;
+    else return kStagedShapes16;
+}
 
 PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder()
 {
@@ -330,16 +439,21 @@ struct StagedLaunch {
     int chunk;                 // slices per pass through the workspace
 };
 
-size_t staged_table_bytes(int K, int D) { return (size_t)(K / 2) * (size_t)(D + 1) * 16; }
+size_t staged_table_bytes(int K, int D, fbp_dtype dtype)
+{
+    return (size_t)(K / 2) * (size_t)(D + 1) * (dtype == FBP_F32 ? 32 : 16);
+}
 size_t staged_scale_bytes(int chunk) { return ((size_t)chunk * 4 + 255) / 256 * 256; }
 
 template <int V, typename T>
 fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *status)
 {
-    constexpr StagedShape sd = kStagedShapes[V];
+    constexpr StagedShape sd = staged_shapes<T>()[V];
     constexpr int TILE = sd.txt * sd.px;
+    constexpr bool kF32 = sizeof(T) == 4;
+    constexpr int HALVES = kF32 ? 2 : 1;
     if (L.N % (2 * TILE) != 0) return fail(FBP_ERR_UNSUPPORTED, "n must be a multiple of %d", 2 * TILE);
-    auto kern = bp_staged_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, sd.ns, T, true, sd.minb>;
+    auto kern = bp_staged_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, sd.ns, T, !kF32, sd.minb>;
     StagedArgs a;
     a.cs = L.cs;
     a.K2 = L.K / 2;
@@ -354,7 +468,7 @@ fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *stat
     a.scale = L.scale;
     a.accumulate = L.accumulate;
     a.status = status;
-    const size_t smem = staged_smem_bytes<sd.kt, sd.ns>(a.Wp);
+    const size_t smem = staged_smem_bytes<sd.kt, sd.ns, HALVES>(a.Wp);
     if (smem > 220 * 1024) return fail(FBP_ERR_UNSUPPORTED, "backprojection window too wide");
     fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (st != FBP_OK) return st;
@@ -364,22 +478,31 @@ fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *stat
     if (orbits > INT_MAX) return fail(FBP_ERR_UNSUPPORTED, "too many tiles");
     const int E = L.D + 1;
     float *smax = reinterpret_cast<float *>(L.ws);
-    uint4 *table = reinterpret_cast<uint4 *>(L.ws + staged_scale_bytes(L.chunk));
+    void *table = L.ws + staged_scale_bytes(L.chunk);
     const size_t kd = (size_t)L.K * L.D;
     for (int s0 = 0; s0 < L.S; s0 += L.chunk) {
         const int n = std::min(L.chunk, L.S - s0);
         const T *filt = static_cast<const T *>(L.filt) + (size_t)s0 * kd;
-        const float *rs = L.row_scale + (size_t)s0 * L.K;
-        slice_scale_kernel<<<n, 256, 0, s>>>(rs, L.K, smax);
-        FBP_CUDA_TRY(cudaGetLastError());
         const long long pairs = (long long)n * (L.K / 2);
         dim3 pg((unsigned)((E + 255) / 256), (unsigned)std::min<long long>(pairs, 65535));
-        orbit_prestage_kernel<T, true><<<pg, 256, 0, s>>>(filt, rs, smax, table, L.K, L.D, pairs);
-        FBP_CUDA_TRY(cudaGetLastError());
-        // the chunk's table as a 3-D tensor of 32-bit words: {4 words, E entries, pairs}
+        if constexpr (kF32) {
+            // FP32 rows carry no scale: S = 1
+            orbit_prestage_f32_kernel<<<pg, 256, 0, s>>>(reinterpret_cast<const float *>(filt),
+                                                         static_cast<float4 *>(table), L.K, L.D, pairs);
+            FBP_CUDA_TRY(cudaGetLastError());
+        } else {
+            const float *rs = L.row_scale + (size_t)s0 * L.K;
+            slice_scale_kernel<<<n, 256, 0, s>>>(rs, L.K, smax);
+            FBP_CUDA_TRY(cudaGetLastError());
+            orbit_prestage_kernel<T, true><<<pg, 256, 0, s>>>(filt, rs, smax, static_cast<uint4 *>(table), L.K,
+                                                              L.D, pairs);
+            FBP_CUDA_TRY(cudaGetLastError());
+        }
+        // the chunk's table as a 3-D tensor of 32-bit words: {4 or 8 words, E entries, pairs}
         CUtensorMap map;
-        const cuuint64_t dims[3] = {4, (cuuint64_t)E, (cuuint64_t)pairs};
-        const cuuint64_t strides[2] = {16, (cuuint64_t)E * 16};
+        const cuuint64_t words = 4 * HALVES;
+        const cuuint64_t dims[3] = {words, (cuuint64_t)E, (cuuint64_t)pairs};
+        const cuuint64_t strides[2] = {words * 4, (cuuint64_t)E * words * 4};
         const cuuint32_t box[3] = {4, (cuuint32_t)a.W, 1};
         const cuuint32_t estr[3] = {1, 1, 1};
         const CUresult cr = encode(&map, CU_TENSOR_MAP_DATA_TYPE_UINT32, 3, table, dims, strides, box, estr,
@@ -387,7 +510,7 @@ fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *stat
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr != CUDA_SUCCESS) return fail(FBP_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
         a.out = L.slice + (size_t)s0 * L.N * L.N;
-        a.smax = smax;
+        a.smax = kF32 ? nullptr : smax;
         dim3 grid((unsigned)orbits, (unsigned)n);
         kern<<<grid, sd.txt * sd.tyt, smem, s>>>(map, a);
         FBP_CUDA_TRY(cudaGetLastError());
@@ -398,13 +521,22 @@ fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *stat
 template <typename T>
 fbp_status launch_staged_dtype(const StagedLaunch &L, int v, cudaStream_t s, unsigned *status)
 {
-    switch (v) {
-        case 0: return launch_staged_t<0, T>(L, s, status);
-        case 1: return launch_staged_t<1, T>(L, s, status);
-        case 2: return launch_staged_t<2, T>(L, s, status);
-        case 3: return launch_staged_t<3, T>(L, s, status);
-        case 4: return launch_staged_t<4, T>(L, s, status);
-        case 5: return launch_staged_t<5, T>(L, s, status);
+    if constexpr (sizeof(T) == 4) {
+        switch (v) {
+            case 0: return launch_staged_t<0, T>(L, s, status);
+            case 1: return launch_staged_t<1, T>(L, s, status);
+            case 2: return launch_staged_t<2, T>(L, s, status);
+            case 3: return launch_staged_t<3, T>(L, s, status);
+        }
+    } else {
+        switch (v) {
+            case 0: return launch_staged_t<0, T>(L, s, status);
+            case 1: return launch_staged_t<1, T>(L, s, status);
+            case 2: return launch_staged_t<2, T>(L, s, status);
+            case 3: return launch_staged_t<3, T>(L, s, status);
+            case 4: return launch_staged_t<4, T>(L, s, status);
+            case 5: return launch_staged_t<5, T>(L, s, status);
+        }
     }
     return fail(FBP_ERR_INVALID_ARG, "staged shape %d", v);
 }
@@ -414,13 +546,17 @@ fbp_status launch_staged_dtype(const StagedLaunch &L, int v, cudaStream_t s, uns
 
 using namespace fbp;
 
-extern "C" int fbp_backproject_staged_shape_count(void) { return kNumStagedShapes; }
+extern "C" int fbp_backproject_staged_shape_count(fbp_dtype dtype)
+{
+    return dtype == FBP_F32 ? kNumStagedShapes32 : (dtype == FBP_F16 || dtype == FBP_BF16) ? kNumStagedShapes16 : 0;
+}
 
-extern "C" size_t fbp_backproject_staged_workspace_bytes(const fbp_geometry *g, int chunk)
+extern "C" size_t fbp_backproject_staged_workspace_bytes(const fbp_geometry *g, fbp_dtype dtype, int chunk)
 {
     clear_error();
     if (!g || chunk < 1 || g->n_angles < 2 || g->n_det < 1) return 0;
-    return staged_scale_bytes(chunk) + (size_t)chunk * staged_table_bytes(g->n_angles, g->n_det);
+    if (dtype != FBP_F32 && dtype != FBP_F16 && dtype != FBP_BF16) return 0;
+    return staged_scale_bytes(chunk) + (size_t)chunk * staged_table_bytes(g->n_angles, g->n_det, dtype);
 }
 
 extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_scale, fbp_dtype dtype,
@@ -431,10 +567,10 @@ extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_
     clear_error();
     fbp_status st = check_geometry(g, false, true);
     if (st != FBP_OK) return st;
-    if (dtype != FBP_F16 && dtype != FBP_BF16)
-        return fail(dtype == FBP_F32 ? FBP_ERR_UNSUPPORTED : FBP_ERR_INVALID_ARG,
-                    "fbp_backproject_staged takes 16-bit rows (dtype %d)", (int)dtype);
-    if (shape < -1 || shape >= kNumStagedShapes) return fail(FBP_ERR_INVALID_ARG, "shape %d", shape);
+    if (dtype != FBP_F32 && dtype != FBP_F16 && dtype != FBP_BF16)
+        return fail(FBP_ERR_INVALID_ARG, "dtype %d", (int)dtype);
+    if (shape < -1 || shape >= fbp_backproject_staged_shape_count(dtype))
+        return fail(FBP_ERR_INVALID_ARG, "shape %d", shape);
     if (n_slices < 0) return fail(FBP_ERR_INVALID_ARG, "n_slices < 0");
     if (!(scale == scale) || scale > 3.4e38f || scale < -3.4e38f)
         return fail(FBP_ERR_INVALID_ARG, "scale is not finite");
@@ -442,15 +578,16 @@ extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_
         return fail(FBP_ERR_UNSUPPORTED, "fbp_backproject_staged needs angle step pi/K with K even and "
                     "det_center = (D-1)/2");
     if (n_slices == 0) return FBP_OK;
-    if (!filt || !slice || !row_scale) return fail(FBP_ERR_INVALID_ARG, "filt, row_scale or slice is NULL");
-    const size_t nin = (size_t)n_slices * g->n_angles * g->n_det * 2;
+    if (!filt || !slice) return fail(FBP_ERR_INVALID_ARG, "filt or slice is NULL");
+    if (dtype != FBP_F32 && !row_scale) return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit input");
+    const size_t nin = (size_t)n_slices * g->n_angles * g->n_det * (dtype == FBP_F32 ? 4 : 2);
     const size_t nout = (size_t)n_slices * g->n * g->n * 4;
     const char *pi = static_cast<const char *>(filt), *po = reinterpret_cast<const char *>(slice);
     if (pi < po + nout && po < pi + nin) return fail(FBP_ERR_INVALID_ARG, "slice overlaps filt");
     if (!workspace) return fail(FBP_ERR_WORKSPACE, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(workspace) & 255)
         return fail(FBP_ERR_WORKSPACE, "workspace is not 256-byte aligned");
-    const size_t per = staged_table_bytes(g->n_angles, g->n_det);
+    const size_t per = staged_table_bytes(g->n_angles, g->n_det, dtype);
     int chunk = 0;
     for (int c = std::min(n_slices, 1 << 16); c >= 1; c = c > 8 ? c / 2 : c - 1)
         if (staged_scale_bytes(c) + (size_t)c * per <= ws_bytes) {
@@ -484,8 +621,13 @@ extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_
     L.dtype = dtype;
     L.ws = static_cast<char *>(workspace);
     L.chunk = chunk;
-    // default: the 64 x 64 orbit where n allows it, else 32 x 32
-    if (shape < 0) shape = g->n % 128 == 0 ? 0 : 2;
-    return dtype == FBP_F16 ? launch_staged_dtype<__half>(L, shape, stream, status)
-                            : launch_staged_dtype<__nv_bfloat16>(L, shape, stream, status);
+    // 16-bit default (measured at N = 8192, K = 4096, 16 slices: shape 1 8264,
+    // shape 5 8243, shape 0 8001 Gupdates/s): the 64 x 64 orbit where n allows it
+    if (shape < 0) shape = dtype == FBP_F32 ? 0 : (g->n % 128 == 0 ? 1 : 5);
+    L.row_scale = dtype == FBP_F32 ? nullptr : row_scale;
+    switch (dtype) {
+        case FBP_F32: return launch_staged_dtype<float>(L, shape, stream, status);
+        case FBP_F16: return launch_staged_dtype<__half>(L, shape, stream, status);
+        default: return launch_staged_dtype<__nv_bfloat16>(L, shape, stream, status);
+    }
 }

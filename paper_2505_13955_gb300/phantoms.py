@@ -51,7 +51,7 @@ SHEPP_LOGAN_TABLE = (
     (0.0,     0.1,     0.046, 0.046,  0.0,  0.01),
     (0.0,    -0.1,     0.046, 0.046,  0.0,  0.01),
     (-0.08,  -0.605,   0.046, 0.023,  0.0,  0.01),
-    (0.0,    -0.605,   0.023, 0.023,  0.0,  0.01),
+    (0.0,    -0.606,   0.023, 0.023,  0.0,  0.01),   # the circle sits at y = -0.606 in the table
     (0.06,   -0.605,   0.046, 0.023, 90.0,  0.01),
 )
 

@@ -68,20 +68,43 @@ def test_staged_refusals():
     out = torch.full((1, 128, 128), 5.0, device="cuda")
     # FP32 rows: the C call refuses them (the binding checks the dtype first)
     L = api.lib()
-    ws = torch.empty(api.backproject_staged_workspace_bytes(g), dtype=torch.uint8, device="cuda")
+    ws = torch.empty(api.backproject_staged_workspace_bytes(g, torch.float16), dtype=torch.uint8, device="cuda")
     gc = g.c()
-    st = L.fbp_backproject_staged(ctypes.c_void_p(f32.data_ptr()), None, 0, ctypes.c_void_p(out.data_ptr()),
+    # 16-bit rows without their row scale
+    st = L.fbp_backproject_staged(ctypes.c_void_p(f16.data_ptr()), None, 1, ctypes.c_void_p(out.data_ptr()),
                                   ctypes.byref(gc), 1, 1.0, 0, -1, ctypes.c_void_p(ws.data_ptr()), ws.numel(),
                                   None)
-    assert st == -2                                   # FBP_ERR_UNSUPPORTED
+    assert st == -1                                   # FBP_ERR_INVALID_ARG
     with pytest.raises(ValueError):
-        api.backproject_staged(f32, g, rs)
+        api.backproject_staged(f16, g)
     odd = api.Geometry(63, 128, 128)                  # K odd: no 90-degree pairs
     with pytest.raises(api.FbpError, match="UNSUPPORTED"):
         f, r = api.filter(torch.zeros((1, 63, 128), device="cuda"), odd, dtype=torch.float16)
         api.backproject_staged(f, odd, r)
-    small = torch.empty(api.backproject_staged_workspace_bytes(g) - 16, dtype=torch.uint8, device="cuda")
+    small = torch.empty(api.backproject_staged_workspace_bytes(g, torch.float16) - 16, dtype=torch.uint8,
+                        device="cuda")
     with pytest.raises(api.FbpError, match="WORKSPACE"):
         api.backproject_staged(f16, g, rs, out=out, workspace=small)
     torch.cuda.synchronize()
     assert float(out.min()) == float(out.max()) == 5.0
+
+
+@pytest.mark.parametrize("shape", range(4))
+def test_staged_f32_matches_oracle_and_orbit_kernel(shape):
+    """FP32 rows: midpoint/slope entries; within the FP32 bar of the oracle
+    and within FP32 rounding of the orbit kernel of the same tile."""
+    api = fbp_api()
+    tile64 = shape == 3
+    for i, G in enumerate(GEOMS):
+        g, x, filt, _ = rows_for(api, G, 3, torch.float32, 100 + 10 * shape + i)
+        got = api.backproject_staged(filt, g, shape=shape, chunk=2)
+        ref_gpu = api.backproject(filt, g, variant=8 if tile64 else 7)
+        assert_within_dr(to_np(got), to_np(ref_gpu), 1e-5, f"FP32 staged shape {shape} vs orbit {G}")
+        go = oracle.Geometry(G["K"], G["D"], G["N"], pixel_size=G.get("pixel_size", 1.0))
+        q = to_np(filt)
+        for s in range(3):
+            assert_within_dr(to_np(got[s]), oracle.backproject(q[s], go), 1e-4, f"FP32 staged {G} slice {s}")
+        acc = torch.ones_like(got)
+        api.backproject_staged(filt, g, out=acc, accumulate=True, shape=shape)
+        assert torch.allclose(acc, got + 1.0, rtol=0, atol=1e-5 * float(got.abs().max()))
+    assert api.device_status() == 0

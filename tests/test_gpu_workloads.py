@@ -130,3 +130,21 @@ def test_precision_n8192_staged_equals_orbit_kernel(n8192, dtype):
         record(f"fbp_precision_n8192/{str(dtype).replace('torch.', '')}/staged/slice{s}/vs_oracle", err)
         assert err <= 2e-3
     assert api.device_status() == 0
+
+
+def test_precision_n8192_staged_f32_sampled(n8192):
+    """FP32 rows through fbp_backproject_staged at full size: within the FP32
+    bar of the oracle on the sampled pixels and of the orbit kernel's image."""
+    api, sinos, refs = n8192
+    g = api.Geometry(4096, 8192, 8192)
+    filt, _ = api.filter(to_gpu(sinos), g)
+    staged = api.backproject_staged(filt, g, chunk=2)
+    orbit = api.backproject(filt, g)
+    for s, (rows, cols, ref) in enumerate(refs):
+        got = to_np(staged[s][torch.from_numpy(rows).cuda(), torch.from_numpy(cols).cuda()])
+        err = np.max(np.abs(got - ref)) / (ref.max() - ref.min())
+        record(f"fbp_precision_n8192/f32/staged/slice{s}/vs_oracle", err)
+        assert err <= 1e-4
+        dr = (orbit[s].max() - orbit[s].min()).item()
+        assert (staged[s] - orbit[s]).abs().max().item() <= 1e-5 * dr
+    assert api.device_status() == 0

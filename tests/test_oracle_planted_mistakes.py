@@ -1,28 +1,23 @@
-"""Planted-mistake check of the oracle's pins (run by hand, not collected by
-pytest):
+"""Planted-mistake check of the oracle's pins (a collected CPU test).
 
-    python tests/plant_mistakes.py [--scratch DIR] [--k EXPR] [NAME ...]
-
-For each entry of MISTAKES it copies oracle/, tests/ and the package's
-Python sources into a scratch directory, plants one plausible mistake in the
-copy of the oracle (a flipped sign, a swapped operand or weight, a dropped
-factor, a wrong index or tie order), and runs the oracle's pin tests there.
-A mistake counts as caught when that run fails.  `--k` passes a pytest -k
-expression, e.g. to leave out the tests that compare the oracle with a
-numpy restatement of its own formula and keep only closed forms,
-invariants and hand-worked values.  The repository itself is never
-modified."""
-import argparse
-import json
+For each entry of MISTAKES a scratch copy of oracle/, tests/ and the
+package's Python sources gets one plausible mistake planted in its copy of
+the oracle (a flipped sign, a swapped operand or weight, a dropped factor, a
+wrong index or tie order), and the oracle's pin tests run there; the mistake
+counts as caught when that run fails.  Every mistake must be caught by all
+pins, and also with the two tests that compare the oracle with a numpy
+restatement of its own formula left out (closed forms, invariants and
+hand-worked values alone).  The plantings run in parallel, each in its own
+scratch directory; the repository itself is never modified.
+"""
 import os
 import shutil
 import subprocess
 import sys
-import tempfile
-import time
+
+import pytest
 
 REPO = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-COPY = None
 PINS = ["tests/test_oracle_filter.py", "tests/test_oracle_backproject.py", "tests/test_oracle_offset.py",
         "tests/test_oracle_preprocess.py", "tests/test_oracle_sap.py", "tests/test_golden.py",
         "tests/test_phantoms.py"]
@@ -95,66 +90,67 @@ MISTAKES = [
 ]
 
 
-def fresh_copy():
-    if os.path.exists(COPY):
-        shutil.rmtree(COPY)
-    os.makedirs(COPY)
-    ign = shutil.ignore_patterns("*.so", "_build", "__pycache__", "*.o")
+NUMPY_RESTATEMENTS = "not numpy_interp and not numpy_linear_convolution"
+
+
+def fresh_copy(copy):
+    if os.path.exists(copy):
+        shutil.rmtree(copy)
+    os.makedirs(copy)
+    ign = shutil.ignore_patterns("*.so", "_build", "__pycache__", "*.o", ".pytest_cache")
     for d in ("oracle", "tests", "paper_2505_13955_gb300"):
-        shutil.copytree(os.path.join(REPO, d), os.path.join(COPY, d), ignore=ign)
-    shutil.copy(os.path.join(REPO, "pytest.ini"), COPY)
+        shutil.copytree(os.path.join(REPO, d), os.path.join(copy, d), ignore=ign)
+    shutil.copy(os.path.join(REPO, "pytest.ini"), copy)
 
 
-def run():
-    extra = ["-k", K_EXPR] if K_EXPR else []
-    r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *extra, *PINS],
-                       cwd=COPY, capture_output=True, text=True, timeout=900)
-    tail = (r.stdout.strip().splitlines() or [""])[-1]
-    failed = [l.split(" ")[1] for l in r.stdout.splitlines() if l.startswith("FAILED")]
-    return r.returncode, tail, failed
+# the two pins that reconstruct whole phantoms with the oracle take most of
+# the time: they run only when the others have not caught the mistake
+SLOW = "shepp_logan_fbp_approaches_analytic_phantom or random_ellipses_fbp_close_to_phantom"
 
 
-K_EXPR = None
+def run_pins(copy, k_expr, threads):
+    env = dict(os.environ, OMP_NUM_THREADS=str(threads))
+    for phase in (f"not ({SLOW})", SLOW):
+        k = f"({phase}) and ({k_expr})" if k_expr else phase
+        r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", "-m", "not gpu",
+                            "-k", k, *PINS], cwd=copy, capture_output=True, text=True, timeout=900, env=env)
+        failed = [l.split(" ")[1] for l in r.stdout.splitlines() if l.startswith("FAILED")]
+        if r.returncode != 0:
+            return r.returncode, failed
+    return 0, []
 
 
-def main():
-    global COPY, K_EXPR
-    ap = argparse.ArgumentParser()
-    ap.add_argument("--scratch", default=None, help="scratch directory (default: a new temporary one)")
-    ap.add_argument("--k", default=None, help="pytest -k expression for the pin run")
-    ap.add_argument("names", nargs="*", help="run only these entries of MISTAKES")
-    args = ap.parse_args()
-    COPY = os.path.join(args.scratch or tempfile.mkdtemp(prefix="plant_mistakes_"), "copy")
-    K_EXPR = args.k
-    fresh_copy()
-    rc, tail, _ = run()
-    print("baseline:", rc, tail, flush=True)
-    if rc != 0:
-        sys.exit("the unmodified pins fail in the scratch copy")
-    results = []
-    for name, f, reps in MISTAKES:
-        if args.names and name not in args.names:
-            continue
-        fresh_copy()
-        path = os.path.join(COPY, f)
+def plant_and_run(root, index, k_expr, threads=1):
+    """Plant MISTAKES[index] (index -1: none) in a fresh copy under root and
+    run the pins: (return code, first failing test)."""
+    copy = os.path.join(root, f"copy{index}")
+    fresh_copy(copy)
+    if index >= 0:
+        name, f, reps = MISTAKES[index]
+        path = os.path.join(copy, f)
         s = open(path).read()
         for a, b in reps:
-            if a not in s:
-                sys.exit(f"{name}: the line to change is not in {f}")
+            assert a in s, f"{name}: the line to change is not in {f}"
             s = s.replace(a, b, 1)
         with open(path, "w") as fh:
             fh.write(s)
-        t0 = time.time()
-        rc, tail, failed = run()
-        caught = rc != 0
-        results.append({"mistake": name, "file": f, "caught": caught, "by": failed[:1],
-                        "s": round(time.time() - t0, 1)})
-        print(("CAUGHT " if caught else "MISSED ") + name, failed[:1], flush=True)
-    shutil.rmtree(COPY, ignore_errors=True)
-    print(sum(r["caught"] for r in results), "of", len(results), "caught")
-    print(json.dumps(results))
-    sys.exit(0 if all(r["caught"] for r in results) else 1)
+    rc, failed = run_pins(copy, k_expr, threads)
+    shutil.rmtree(copy, ignore_errors=True)
+    return rc, failed[:1]
 
 
-if __name__ == "__main__":
-    main()
+@pytest.mark.slow
+def test_every_planted_mistake_is_caught(tmp_path):
+    """All pins, and the pins without the two numpy restatements, each catch
+    every planted mistake (both sets run in one pool of scratch copies)."""
+    import concurrent.futures as cf
+    cores = os.cpu_count() or 2
+    sets = {"all pins": None, "without numpy restatements": NUMPY_RESTATEMENTS}
+    for label, k in sets.items():
+        rc, failed = plant_and_run(str(tmp_path / "base"), -1, k, threads=cores)
+        assert rc == 0, f"{label}: the unmodified pins fail in the scratch copy: {failed}"
+    with cf.ThreadPoolExecutor(max_workers=max(2, min(16, cores))) as ex:
+        futs = {(label, i): ex.submit(plant_and_run, str(tmp_path / f"set{j}"), i, k)
+                for j, (label, k) in enumerate(sets.items()) for i in range(len(MISTAKES))}
+        missed = [(label, MISTAKES[i][0]) for (label, i), f in futs.items() if f.result()[0] == 0]
+    assert not missed, f"planted mistakes the pins did not catch: {missed}"
