@@ -61,6 +61,7 @@ ALU_OPS_PER_UPDATE = 4          # coordinate step, fraction, interpolate, accumu
 SHARED_BYTES_PER_CLK = 128      # nominal shared-memory load bandwidth per SM
 SAMPLES_PER_UPDATE = 2          # linear interpolation reads two detector samples
 BP_KERNEL_REGEX = "bp_kernel|bp_orbit_kernel"
+BP_STAGED_REGEX = "bp_staged_kernel"
 
 
 def roofline_peak(sm_mhz: float, dtype: str, sms: int, onchip: dict | None = None) -> dict:
@@ -233,7 +234,7 @@ def peaks() -> dict:
 def bp_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("bp_tile.cuh", "bp_orbit.cuh", "backproject.cu"):
+    for f in ("bp_tile.cuh", "bp_orbit.cuh", "backproject.cu", "bp_staged.cu"):
         with open(os.path.join(ROOT, "paper_2505_13955_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -554,9 +555,9 @@ def run_uniform(args) -> None:
         tdt = getattr(torch, DT[dt])
         filt = torch.empty(sino.shape, dtype=tdt, device=dev)
         rs = torch.empty((S, K), dtype=torch.float32, device=dev) if dt != "f32" else None
-        # 16-bit rows: the bulk-copy-fed kernel from per-slice tables (its
-        # workspace holds the whole stack's tables, allocated before timing)
-        staged = dt != "f32" and args.variant < 0 and api.staged_supported(g)
+        # the bulk-copy-fed kernel from per-slice tables (its workspace holds
+        # the whole stack's tables, allocated before timing)
+        staged = args.variant < 0 and api.staged_supported(g)
         wsp = torch.empty(api.backproject_staged_workspace_bytes(g, tdt, S), dtype=torch.uint8, device=dev) \
             if staged else None
         T = Timed(stream, args.steps, args.warmup, n_events=3)
@@ -628,7 +629,8 @@ def run_uniform(args) -> None:
     sm_max, sms, onchip = device_ceilings(dev)
     rp = roofline_peak(sm_max, args.dtype, sms, onchip)
     achieved = updates / (main["bp_ms"] / 1e3) / 1e9
-    variant = resolved_variant(api, g, args.dtype, args.variant)
+    variant = "fbp_backproject_staged (default shape)" if main["staged"] else \
+        resolved_variant(api, g, args.dtype, args.variant)
     traffic = args.traffic_bytes
     if traffic is None:
         traffic = captured_traffic(variant, args.dtype, S, N, K)
@@ -647,12 +649,13 @@ def run_uniform(args) -> None:
         # filter + backprojection time of each timed step (CUDA events)
         "step_ms_spread": main["step_spread"],
         "bp_gupdates_per_s": achieved,
-        "roofline": roofline_entry(achieved, rp, BP_KERNEL_REGEX, traffic,
+        "roofline": roofline_entry(achieved, rp, BP_STAGED_REGEX if main["staged"] else BP_KERNEL_REGEX, traffic,
                                    traffic_basis="ncu dram bytes per slice x slices, kernel unchanged "
                                                  "since capture (null otherwise)"),
         "onchip_measured": onchip,
         "clocks": main["clocks"],
-        "gpu_launches": 2 * args.steps,
+        # filter, backprojection (+ the table pass of the staged path)
+        "gpu_launches": (3 if main["staged"] else 2) * args.steps,
     })
     for dt in dtypes[1:]:
         r = results[dt]
@@ -670,6 +673,8 @@ def run_uniform(args) -> None:
             "bp_variant": vdt}
         if "orbit_kernel" in r:
             line[f"staged_{dt}"]["orbit_kernel"] = r["orbit_kernel"]
+    if "orbit_kernel" in main:
+        line["orbit_kernel"] = main["orbit_kernel"]
     if tex is not None:
         tex["ratio_to_table"] = tex["bp_gupdates_per_s"] / achieved
         line["texture_alternative"] = tex

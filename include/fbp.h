@@ -494,9 +494,12 @@ fbp_status fbp_batched_scans(const fbp_scan_item *items, int count,
  * load / FBP computation / store pipeline, Sec. V-A(c), on one GPU).  The
  * stack is cut into chunks of `chunk` slices; chunk i runs on internal stream
  * i mod n_streams: copy in, fbp_filter (fbp_filter_counts when pre != NULL),
- * fbp_backproject_variant with scale = angle_step (fbp_backproject_u16 when
- * window != NULL), copy out -- so the copies of one chunk run while another
- * chunk's kernels do.  The results equal those calls on device buffers.
+ * the backprojection with scale = angle_step -- fbp_backproject_staged
+ * where the geometry has the orbit symmetry with n a multiple of 64, the
+ * output is FP32 and bp_variant is -1, else fbp_backproject_variant, or
+ * fbp_backproject_u16 when window != NULL -- copy out, so the copies of one
+ * chunk run while another chunk's kernels do.  The results equal those calls
+ * on device buffers.
  *   sino_host   HOST, float [n_slices][K][D]: line integrals, or detector
  *               counts when pre != NULL.  Pinned memory (cudaHostAlloc or
  *               cudaHostRegister) lets the copies overlap; pageable memory
@@ -511,7 +514,7 @@ fbp_status fbp_batched_scans(const fbp_scan_item *items, int count,
  *   workspace   device, >= fbp_host_workspace_bytes(g, dtype, chunk,
  *               n_streams, window != NULL) bytes, 256-byte aligned, owned
  *               by the caller: per stream one chunk's input, filtered rows,
- *               row scales and output.
+ *               row scales, output and (staged path) tables.
  *   stream      the pipeline starts after the work already enqueued on it.
  * Blocking: returns when every slice is in slice_host (or after an error,
  * once nothing is in flight).  Creates and destroys its streams; allocates

@@ -346,11 +346,11 @@ def staged_supported(g: Geometry) -> bool:
 def fbp(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
         out: torch.Tensor | None = None, variant: int = -1):
     """Filtered backprojection: fbp_filter then fbp_backproject (scale =
-    angle_step).  16-bit rows with the default variant take
-    fbp_backproject_staged where the geometry allows it (a workspace of up to
-    four slices' tables is allocated)."""
+    angle_step).  With the default variant, rows take fbp_backproject_staged
+    where the geometry allows it (a workspace of up to four slices' tables is
+    allocated)."""
     filt, rs = filter(sino, g, kind=kind, dtype=dtype)
-    if dtype != torch.float32 and variant < 0 and staged_supported(g):
+    if variant < 0 and staged_supported(g):
         S = 1 if sino.dim() == 2 else sino.shape[0]
         return backproject_staged(filt, g, rs, out=out, chunk=min(S, 4))
     return backproject(filt, g, row_scale=rs, out=out, variant=variant)

@@ -10,10 +10,13 @@
 // stream i mod n_streams -- copy in, filter, backproject, copy out -- each
 // stream with its own buffers in the caller's workspace, so one stream's
 // copies run while another's kernels do.  Every step is a call of the
-// library's own device entry points on the chunk.
+// library's own device entry points on the chunk (fbp_backproject_staged,
+// with the chunk's tables in the stream's buffers, where the geometry has
+// the orbit symmetry and the output is FP32).
 #include <cstdint>
 #include <vector>
 
+#include "bp_batch.cuh"
 #include "fbp_internal.cuh"
 
 using namespace fbp;
@@ -29,8 +32,17 @@ constexpr int kMaxHostStreams = 16;
 size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 struct HostLayout {
-    size_t in, filt, scale, out, per_stream;
+    size_t in, filt, scale, out, table, per_stream;
 };
+
+// Slices whose geometry has the orbit symmetry (n a multiple of 64) and whose
+// output is FP32 backproject through fbp_backproject_staged: each stream's
+// buffers then include one chunk's tables.
+bool host_staged(const fbp_geometry &g, bool codes)
+{
+    return !codes && g.n % 64 == 0 &&
+           bp_orbit_geometry(g.n_angles, g.angle_step, g.n_det, g.det_center, g.n, 32);
+}
 
 HostLayout host_layout(const fbp_geometry &g, fbp_dtype dtype, int chunk, bool codes)
 {
@@ -40,7 +52,8 @@ HostLayout host_layout(const fbp_geometry &g, fbp_dtype dtype, int chunk, bool c
     l.filt = align256(rows * g.n_det * (dtype == FBP_F32 ? 4 : 2));
     l.scale = dtype == FBP_F32 ? 0 : align256(rows * sizeof(float));
     l.out = align256((size_t)chunk * g.n * g.n * (codes ? 2 : 4));
-    l.per_stream = l.in + l.filt + l.scale + l.out;
+    l.table = host_staged(g, codes) ? align256(fbp_backproject_staged_workspace_bytes(&g, dtype, chunk)) : 0;
+    l.per_stream = l.in + l.filt + l.scale + l.out + l.table;
     return l;
 }
 
@@ -147,10 +160,15 @@ extern "C" fbp_status fbp_host(const float *sino_host, void *slice_host, const f
                  : fbp_filter(d_in, d_filt, d_scale, dtype, kind, g, n, s);
         if (st != FBP_OK) break;
         const float scale = (float)g->angle_step;
-        st = codes ? fbp_backproject_u16(d_filt, d_scale, dtype, static_cast<unsigned short *>(d_out), g, n,
-                                         scale, window, bp_variant, s)
-                   : fbp_backproject_variant(d_filt, d_scale, dtype, static_cast<float *>(d_out), g, n, scale,
-                                             0, bp_variant, s);
+        if (codes)
+            st = fbp_backproject_u16(d_filt, d_scale, dtype, static_cast<unsigned short *>(d_out), g, n, scale,
+                                     window, bp_variant, s);
+        else if (l.table && bp_variant < 0)
+            st = fbp_backproject_staged(d_filt, d_scale, dtype, static_cast<float *>(d_out), g, n, scale, 0, -1,
+                                        base + l.in + l.filt + l.scale + l.out, l.table, s);
+        else
+            st = fbp_backproject_variant(d_filt, d_scale, dtype, static_cast<float *>(d_out), g, n, scale, 0,
+                                         bp_variant, s);
         if (st != FBP_OK) break;
         e = cudaMemcpyAsync(dst + (size_t)i0 * out_slice, d_out, (size_t)n * out_slice, cudaMemcpyDeviceToHost, s);
         if (e != cudaSuccess) st = cuda_fail(e, "fbp_host: copy out");
