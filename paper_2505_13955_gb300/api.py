@@ -336,6 +336,26 @@ def backproject_staged(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor 
     return out
 
 
+def radon_forward(img: torch.Tensor, g: Geometry, out: torch.Tensor | None = None,
+                  which: str = "default", variant: int = -1):
+    """radon_forward: the matched projector A (transpose of backproject, scale 1).
+    variant -1 = library default, 0 = deterministic gather, 1..5 = tile-owned
+    (floating-point atomics across tiles; 4 and 5 take four / two slices per
+    block)."""
+    _need(img, "slice", torch.float32)
+    S = _slices(img, (g.n, g.n), "slice")
+    shape = (g.n_angles, g.n_det) if img.dim() == 2 else (S, g.n_angles, g.n_det)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.float32, device=img.device)
+    _need(out, "out", torch.float32)
+    L = lib(which)
+    gc = g.c()
+    st = L.radon_forward_variant(_ptr(img), _ptr(out), ctypes.byref(gc), S, int(variant),
+                                 _stream(img.device))
+    _lib.check(st, L, "radon_forward")
+    return out
+
+
 def staged_supported(g: Geometry) -> bool:
     """Whether fbp_backproject_staged takes geometry g (the 90-degree orbit
     geometry: angle step pi/K with K even, centred detector, n a multiple of 64)."""

@@ -173,3 +173,14 @@ def test_missing_library_fails_loudly(monkeypatch, tmp_path):
     monkeypatch.setattr(_lib, "_libs", {})
     with pytest.raises(RuntimeError, match="not built"):
         _lib.load()
+
+
+def test_binding_exposes_its_public_calls():
+    """The Python binding keeps one function per C entry point it wraps."""
+    from paper_2505_13955_gb300 import api
+    for name in ("filter", "filter_counts", "filter_offset", "backproject", "backproject_u16", "backproject_staged",
+                 "backproject_staged_workspace_bytes", "radon_forward", "fbp", "fbp_offset", "fbp_counts", "fbp_host",
+                 "host_workspace_bytes", "fbp_batched", "fbp_batched_scans", "sap_edges", "sap_patches",
+                 "sap_depatch_pack", "sap_host", "prepare", "device_status", "release_tables",
+                 "measure_onchip_peaks", "lsq_refine", "radon", "radon_t"):
+        assert callable(getattr(api, name, None)), name
