@@ -557,7 +557,7 @@ def run_uniform(args) -> None:
         rs = torch.empty((S, K), dtype=torch.float32, device=dev) if dt != "f32" else None
         # the bulk-copy-fed kernel from per-slice tables (its workspace holds
         # the whole stack's tables, allocated before timing)
-        staged = args.variant < 0 and api.staged_supported(g)
+        staged = args.variant < 0 and api.staged_preferred(g)
         wsp = torch.empty(api.backproject_staged_workspace_bytes(g, tdt, S), dtype=torch.uint8, device=dev) \
             if staged else None
         T = Timed(stream, args.steps, args.warmup, n_events=3)
@@ -710,6 +710,9 @@ def run_pipeline(args) -> None:
     stream = torch.cuda.current_stream(dev)
     api.prepare(g, kind=w.filter, device=dev)
     updates = S * N * N * K
+    staged = args.variant < 0 and api.staged_preferred(g)
+    wsp = torch.empty(api.backproject_staged_workspace_bytes(g, torch.float32, S), dtype=torch.uint8,
+                      device=dev) if staged else None
     T = Timed(stream, args.steps, args.warmup, n_events=3)
 
     def step(evs):
@@ -718,7 +721,10 @@ def run_pipeline(args) -> None:
         api.filter_counts(counts, g, pre, kind=w.filter, out=filt)
         if evs:
             evs[1].record(stream)
-        api.backproject_u16(filt, g, win, out=codes, variant=args.variant)
+        if staged:
+            api.backproject_staged_u16(filt, g, win, out=codes, workspace=wsp)
+        else:
+            api.backproject_u16(filt, g, win, out=codes, variant=args.variant)
         if evs:
             evs[2].record(stream)
 
@@ -735,7 +741,10 @@ def run_pipeline(args) -> None:
 
     def plain(_):
         api.filter(lines, g, kind=w.filter, out=filt)
-        api.backproject(filt, g, out=out, variant=args.variant)
+        if staged:
+            api.backproject_staged(filt, g, out=out, workspace=wsp)
+        else:
+            api.backproject(filt, g, out=out, variant=args.variant)
 
     plain_ms = T2.run(plain, None)
     del lines, out
@@ -770,7 +779,8 @@ def run_pipeline(args) -> None:
                     f"Ram-Lak + backprojection + HU window [{P['hu_min']}, {P['hu_max']}] to uint16",
         "l2": "inputs larger than L2, no flush",
         "parallelism": f"slices sharded over {ws} GPU(s), no collective",
-        "bp_variant": resolved_variant(api, g, "f32", args.variant)})
+        "bp_variant": "fbp_backproject_staged_u16 (default shape)" if staged else
+                      resolved_variant(api, g, "f32", args.variant)})
     line.update({
         "slices_per_s": S * len(per_rank) / (ms_step / 1e3),
         "filter_counts_ms_per_step": f_ms, "bp_u16_ms_per_step": bp_ms,
@@ -778,7 +788,7 @@ def run_pipeline(args) -> None:
         "filter_counts_hbm_frac": (fbytes / (f_ms / 1e3) / 1e9 / hbm) if hbm else None,
         "plain_fbp_ms_per_step": plain_ms, "ratio_to_plain_fbp": plain_ms / ms_step,
         "roofline": roofline_entry(achieved, rp, BP_KERNEL_REGEX),
-        "clocks": clocks, "gpu_launches": 2 * args.steps,
+        "clocks": clocks, "gpu_launches": (3 if staged else 2) * args.steps,
     })
     if e2e is not None:
         line["e2e"] = e2e
@@ -814,6 +824,10 @@ def run_offset(args) -> None:
         gv, _ = api.offset_geometry(g, delta, fold)
         api.prepare(gv, kind=w.filter, device=dev)
         filt = torch.empty((S, gv.n_angles, gv.n_det), dtype=torch.float32, device=dev)
+        # folded rows are a centred half turn: the staged path applies
+        staged = args.variant < 0 and api.staged_preferred(gv)
+        wsp = torch.empty(api.backproject_staged_workspace_bytes(gv, torch.float32, S), dtype=torch.uint8,
+                          device=dev) if staged else None
         T = Timed(stream, args.steps if fold else max(1, args.steps // 2), args.warmup, n_events=3)
 
         def step(evs):
@@ -822,7 +836,10 @@ def run_offset(args) -> None:
             api.filter_offset(sino, g, delta, fold, kind=w.filter, out=filt)
             if evs:
                 evs[1].record(stream)
-            api.backproject(filt, gv, out=out, variant=args.variant)
+            if staged:
+                api.backproject_staged(filt, gv, out=out, workspace=wsp)
+            else:
+                api.backproject(filt, gv, out=out, variant=args.variant)
             if evs:
                 evs[2].record(stream)
 
@@ -832,7 +849,9 @@ def run_offset(args) -> None:
         rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
         results[fold] = {"value": rate / 1e9, "ms_per_step": ms_step, "filter_ms": T.between(0, 1),
                          "bp_ms": T.between(1, 2), "clocks": T.clocks, "gv": gv,
-                         "variant": resolved_variant(api, gv, "f32", args.variant),
+                         "staged": staged,
+                         "variant": "fbp_backproject_staged (default shape)" if staged else
+                                    resolved_variant(api, gv, "f32", args.variant),
                          "slices_per_s": S * len(per_rank) / (ms_step / 1e3)}
         del filt
     if rank != 0:
@@ -859,7 +878,7 @@ def run_offset(args) -> None:
                      "filter_offset_ms_per_step": unf["filter_ms"], "bp_ms_per_step": unf["bp_ms"],
                      "bp_variant": unf["variant"], "slices_per_s": unf["slices_per_s"]},
         "speedup_fold_vs_unfolded": unf["ms_per_step"] / main["ms_per_step"],
-        "clocks": main["clocks"], "gpu_launches": 2 * args.steps,
+        "clocks": main["clocks"], "gpu_launches": (3 if main["staged"] else 2) * args.steps,
     })
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_sample_offset(w, args.cpu_block)

@@ -372,6 +372,15 @@ fbp_status fbp_backproject_staged(const void *filt, const float *row_scale, fbp_
                                   int accumulate, int shape, void *workspace, size_t ws_bytes,
                                   fbp_stream_t stream);
 
+/* fbp_backproject_staged with the stage-4 mapping in the epilogue (as
+ * fbp_backproject_u16): each pixel's value scale * sum_k Q_k becomes its
+ * uint16 code (fbp_hu_coefficients) in slice [n_slices][n][n] (device).
+ * Arguments and errors as fbp_backproject_staged, plus the window's. */
+fbp_status fbp_backproject_staged_u16(const void *filt, const float *row_scale, fbp_dtype dtype,
+                                      unsigned short *slice, const fbp_geometry *g, int n_slices,
+                                      float scale, const fbp_hu_window *w, int shape, void *workspace,
+                                      size_t ws_bytes, fbp_stream_t stream);
+
 /*
  * radon_forward -- the matched forward projector A (the adjoint of
  * fbp_backproject with scale 1; the paper's data generation uses a forward
@@ -495,7 +504,8 @@ fbp_status fbp_batched_scans(const fbp_scan_item *items, int count,
  * stack is cut into chunks of `chunk` slices; chunk i runs on internal stream
  * i mod n_streams: copy in, fbp_filter (fbp_filter_counts when pre != NULL),
  * the backprojection with scale = angle_step -- fbp_backproject_staged
- * where the geometry has the orbit symmetry with n a multiple of 64, the
+ * where the geometry has the orbit symmetry with n a multiple of 64 and at
+ * least 1024, the
  * output is FP32 and bp_variant is -1, else fbp_backproject_variant, or
  * fbp_backproject_u16 when window != NULL -- copy out, so the copies of one
  * chunk run while another chunk's kernels do.  The results equal those calls

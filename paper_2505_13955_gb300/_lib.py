@@ -143,6 +143,9 @@ SIGNATURES = {
     "fbp_backproject_staged_shape_count": (ctypes.c_int, [ctypes.c_int]),
     "fbp_backproject_staged": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int, ctypes.c_float,
                                               ctypes.c_int, ctypes.c_int, _vp, ctypes.c_size_t, _vp]),
+    "fbp_backproject_staged_u16": (ctypes.c_int, [_vp, _vp, ctypes.c_int, _vp, _G, ctypes.c_int, ctypes.c_float,
+                                                  ctypes.POINTER(CHuWindow), ctypes.c_int, _vp, ctypes.c_size_t,
+                                                  _vp]),
     "fbp_host_workspace_bytes": (ctypes.c_size_t, [_G, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "fbp_host": (ctypes.c_int, [_vp, _vp, _G, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                 ctypes.POINTER(CPreprocess), ctypes.POINTER(CHuWindow), ctypes.c_int,

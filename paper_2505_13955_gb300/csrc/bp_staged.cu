@@ -181,7 +181,9 @@ __device__ __forceinline__ void orbit_pair_mid(float (&acc)[4][PY][PX], const fl
 
 struct StagedArgs {
     const double2 *cs;         // [K] angle table (k < K/2 is read)
-    float *out;                // the chunk's first slice [N][N]
+    float *out;                // the chunk's first slice [N][N], or null when out16 is set
+    unsigned short *out16;     // or the chunk's first slice of uint16 codes (bp_tile.cuh: store_pixel)
+    float hu_a, hu_b;
     const float *smax;         // the chunk's S per slice
     int K2, N, H, W, Wp, orbits_x;
     double alpha, det_center;
@@ -220,7 +222,8 @@ __host__ __device__ constexpr size_t staged_smem_bytes(int Wp)
     return 128 + 128 + staged_params_bytes<KT, NS>() + (size_t)NS * HALVES * 2 * KT * Wp * 16;
 }
 
-template <int TXT, int TYT, int PX, int PY, int KT, int NS, typename T, bool PACKED, int MINB>
+// CODES: the epilogue writes uint16 CT-number codes (out16) instead of FP32.
+template <int TXT, int TYT, int PX, int PY, int KT, int NS, typename T, bool PACKED, int MINB, bool CODES>
 __global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_kernel(const __grid_constant__ CUtensorMap tmap,
                                                                    StagedArgs a)
 {
@@ -374,9 +377,14 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_kernel(const __grid_
         }
         return;
     }
-    float *out = a.out + (size_t)sl * a.N * a.N;
+    const size_t so = (size_t)sl * a.N * a.N;
     const float S = HALVES == 2 ? 1.f : __ldg(a.smax + sl);
-    orbit_store<TXT, TYT, PX, PY>(acc, out, nullptr, 0.f, 0.f, a.accumulate, a.N, x0 + tx, y0 + ty, a.scale * S);
+    if constexpr (CODES)
+        orbit_store<TXT, TYT, PX, PY>(acc, nullptr, a.out16 + so, a.hu_a, a.hu_b, 0, a.N, x0 + tx, y0 + ty,
+                                      a.scale * S);
+    else
+        orbit_store<TXT, TYT, PX, PY>(acc, a.out + so, nullptr, 0.f, 0.f, a.accumulate, a.N, x0 + tx, y0 + ty,
+                                      a.scale * S);
 }
 
 // Compiled shapes.  16-bit rows: the orbit kernel's 64 x 64 (256 threads,
@@ -429,6 +437,8 @@ struct StagedLaunch {
     const void *filt;
     const float *row_scale;
     float *slice;
+    unsigned short *slice16;   // uint16 codes instead of slice, or null
+    float hu_a, hu_b;
     const double2 *cs;
     int K, D, N, S;
     double alpha, det_center;
@@ -445,7 +455,7 @@ size_t staged_table_bytes(int K, int D, fbp_dtype dtype)
 }
 size_t staged_scale_bytes(int chunk) { return ((size_t)chunk * 4 + 255) / 256 * 256; }
 
-template <int V, typename T>
+template <int V, typename T, bool CODES>
 fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *status)
 {
     constexpr StagedShape sd = staged_shapes<T>()[V];
@@ -453,7 +463,7 @@ fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *stat
     constexpr bool kF32 = sizeof(T) == 4;
     constexpr int HALVES = kF32 ? 2 : 1;
     if (L.N % (2 * TILE) != 0) return fail(FBP_ERR_UNSUPPORTED, "n must be a multiple of %d", 2 * TILE);
-    auto kern = bp_staged_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, sd.ns, T, !kF32, sd.minb>;
+    auto kern = bp_staged_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, sd.ns, T, !kF32, sd.minb, CODES>;
     StagedArgs a;
     a.cs = L.cs;
     a.K2 = L.K / 2;
@@ -509,7 +519,10 @@ fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *stat
                                    CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr != CUDA_SUCCESS) return fail(FBP_ERR_CUDA, "cuTensorMapEncodeTiled failed (%d)", (int)cr);
-        a.out = L.slice + (size_t)s0 * L.N * L.N;
+        a.out = L.slice16 ? nullptr : L.slice + (size_t)s0 * L.N * L.N;
+        a.out16 = L.slice16 ? L.slice16 + (size_t)s0 * L.N * L.N : nullptr;
+        a.hu_a = L.hu_a;
+        a.hu_b = L.hu_b;
         a.smax = kF32 ? nullptr : smax;
         dim3 grid((unsigned)orbits, (unsigned)n);
         kern<<<grid, sd.txt * sd.tyt, smem, s>>>(map, a);
@@ -518,27 +531,33 @@ fbp_status launch_staged_t(const StagedLaunch &L, cudaStream_t s, unsigned *stat
     return FBP_OK;
 }
 
-template <typename T>
-fbp_status launch_staged_dtype(const StagedLaunch &L, int v, cudaStream_t s, unsigned *status)
+template <typename T, bool CODES>
+fbp_status launch_staged_shape(const StagedLaunch &L, int v, cudaStream_t s, unsigned *status)
 {
     if constexpr (sizeof(T) == 4) {
         switch (v) {
-            case 0: return launch_staged_t<0, T>(L, s, status);
-            case 1: return launch_staged_t<1, T>(L, s, status);
-            case 2: return launch_staged_t<2, T>(L, s, status);
-            case 3: return launch_staged_t<3, T>(L, s, status);
+            case 0: return launch_staged_t<0, T, CODES>(L, s, status);
+            case 1: return launch_staged_t<1, T, CODES>(L, s, status);
+            case 2: return launch_staged_t<2, T, CODES>(L, s, status);
+            case 3: return launch_staged_t<3, T, CODES>(L, s, status);
         }
     } else {
         switch (v) {
-            case 0: return launch_staged_t<0, T>(L, s, status);
-            case 1: return launch_staged_t<1, T>(L, s, status);
-            case 2: return launch_staged_t<2, T>(L, s, status);
-            case 3: return launch_staged_t<3, T>(L, s, status);
-            case 4: return launch_staged_t<4, T>(L, s, status);
-            case 5: return launch_staged_t<5, T>(L, s, status);
+            case 0: return launch_staged_t<0, T, CODES>(L, s, status);
+            case 1: return launch_staged_t<1, T, CODES>(L, s, status);
+            case 2: return launch_staged_t<2, T, CODES>(L, s, status);
+            case 3: return launch_staged_t<3, T, CODES>(L, s, status);
+            case 4: return launch_staged_t<4, T, CODES>(L, s, status);
+            case 5: return launch_staged_t<5, T, CODES>(L, s, status);
         }
     }
     return fail(FBP_ERR_INVALID_ARG, "staged shape %d", v);
+}
+
+template <typename T>
+fbp_status launch_staged_dtype(const StagedLaunch &L, int v, cudaStream_t s, unsigned *status)
+{
+    return L.slice16 ? launch_staged_shape<T, true>(L, v, s, status) : launch_staged_shape<T, false>(L, v, s, status);
 }
 
 }  // namespace
@@ -559,12 +578,13 @@ extern "C" size_t fbp_backproject_staged_workspace_bytes(const fbp_geometry *g, 
     return staged_scale_bytes(chunk) + (size_t)chunk * staged_table_bytes(g->n_angles, g->n_det, dtype);
 }
 
-extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_scale, fbp_dtype dtype,
-                                             float *slice, const fbp_geometry *g, int n_slices, float scale,
-                                             int accumulate, int shape, void *workspace, size_t ws_bytes,
-                                             fbp_stream_t stream)
+namespace {
+
+fbp_status staged_impl(const void *filt, const float *row_scale, fbp_dtype dtype, float *slice,
+                       unsigned short *slice16, float hu_a, float hu_b, const fbp_geometry *g, int n_slices,
+                       float scale, int accumulate, int shape, void *workspace, size_t ws_bytes,
+                       fbp_stream_t stream)
 {
-    clear_error();
     fbp_status st = check_geometry(g, false, true);
     if (st != FBP_OK) return st;
     if (dtype != FBP_F32 && dtype != FBP_F16 && dtype != FBP_BF16)
@@ -578,11 +598,12 @@ extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_
         return fail(FBP_ERR_UNSUPPORTED, "fbp_backproject_staged needs angle step pi/K with K even and "
                     "det_center = (D-1)/2");
     if (n_slices == 0) return FBP_OK;
-    if (!filt || !slice) return fail(FBP_ERR_INVALID_ARG, "filt or slice is NULL");
+    if (!filt || !(slice || slice16)) return fail(FBP_ERR_INVALID_ARG, "filt or slice is NULL");
     if (dtype != FBP_F32 && !row_scale) return fail(FBP_ERR_INVALID_ARG, "row_scale is required for 16-bit input");
     const size_t nin = (size_t)n_slices * g->n_angles * g->n_det * (dtype == FBP_F32 ? 4 : 2);
-    const size_t nout = (size_t)n_slices * g->n * g->n * 4;
-    const char *pi = static_cast<const char *>(filt), *po = reinterpret_cast<const char *>(slice);
+    const size_t nout = (size_t)n_slices * g->n * g->n * (slice16 ? 2 : 4);
+    const char *pi = static_cast<const char *>(filt);
+    const char *po = slice16 ? reinterpret_cast<const char *>(slice16) : reinterpret_cast<const char *>(slice);
     if (pi < po + nout && po < pi + nin) return fail(FBP_ERR_INVALID_ARG, "slice overlaps filt");
     if (!workspace) return fail(FBP_ERR_WORKSPACE, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(workspace) & 255)
@@ -609,6 +630,9 @@ extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_
     L.filt = filt;
     L.row_scale = row_scale;
     L.slice = slice;
+    L.slice16 = slice16;
+    L.hu_a = hu_a;
+    L.hu_b = hu_b;
     L.cs = cs;
     L.K = g->n_angles;
     L.D = g->n_det;
@@ -630,4 +654,30 @@ extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_
         case FBP_F16: return launch_staged_dtype<__half>(L, shape, stream, status);
         default: return launch_staged_dtype<__nv_bfloat16>(L, shape, stream, status);
     }
+}
+
+}  // namespace
+
+extern "C" fbp_status fbp_backproject_staged(const void *filt, const float *row_scale, fbp_dtype dtype,
+                                             float *slice, const fbp_geometry *g, int n_slices, float scale,
+                                             int accumulate, int shape, void *workspace, size_t ws_bytes,
+                                             fbp_stream_t stream)
+{
+    clear_error();
+    if (n_slices > 0 && !slice) return fail(FBP_ERR_INVALID_ARG, "slice is NULL");
+    return staged_impl(filt, row_scale, dtype, slice, nullptr, 0.f, 0.f, g, n_slices, scale, accumulate, shape,
+                       workspace, ws_bytes, stream);
+}
+
+extern "C" fbp_status fbp_backproject_staged_u16(const void *filt, const float *row_scale, fbp_dtype dtype,
+                                                 unsigned short *slice, const fbp_geometry *g, int n_slices,
+                                                 float scale, const fbp_hu_window *w, int shape, void *workspace,
+                                                 size_t ws_bytes, fbp_stream_t stream)
+{
+    float a = 0.f, b = 0.f;
+    fbp_status st = fbp_hu_coefficients(w, &a, &b);     // validates the window (and clears the error)
+    if (st != FBP_OK) return st;
+    if (n_slices > 0 && !slice) return fail(FBP_ERR_INVALID_ARG, "slice is NULL");
+    return staged_impl(filt, row_scale, dtype, nullptr, slice, a, b, g, n_slices, scale, 0, shape, workspace,
+                       ws_bytes, stream);
 }

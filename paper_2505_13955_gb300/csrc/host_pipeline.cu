@@ -35,12 +35,14 @@ struct HostLayout {
     size_t in, filt, scale, out, table, per_stream;
 };
 
-// Slices whose geometry has the orbit symmetry (n a multiple of 64) and whose
-// output is FP32 backproject through fbp_backproject_staged: each stream's
-// buffers then include one chunk's tables.
+// Slices whose geometry has the orbit symmetry (n a multiple of 64, at least
+// 1024: smaller slices are launch-bound, and the table pass costs more than
+// it saves) and whose output is FP32 backproject through
+// fbp_backproject_staged: each stream's buffers then include one chunk's
+// tables.
 bool host_staged(const fbp_geometry &g, bool codes)
 {
-    return !codes && g.n % 64 == 0 &&
+    return !codes && g.n % 64 == 0 && g.n >= 1024 &&
            bp_orbit_geometry(g.n_angles, g.angle_step, g.n_det, g.det_center, g.n, 32);
 }
 

@@ -179,6 +179,7 @@ def test_binding_exposes_its_public_calls():
     """The Python binding keeps one function per C entry point it wraps."""
     from paper_2505_13955_gb300 import api
     for name in ("filter", "filter_counts", "filter_offset", "backproject", "backproject_u16", "backproject_staged",
+                 "backproject_staged_u16",
                  "backproject_staged_workspace_bytes", "radon_forward", "fbp", "fbp_offset", "fbp_counts", "fbp_host",
                  "host_workspace_bytes", "fbp_batched", "fbp_batched_scans", "sap_edges", "sap_patches",
                  "sap_depatch_pack", "sap_host", "prepare", "device_status", "release_tables",

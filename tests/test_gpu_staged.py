@@ -108,3 +108,42 @@ def test_staged_f32_matches_oracle_and_orbit_kernel(shape):
         api.backproject_staged(filt, g, out=acc, accumulate=True, shape=shape)
         assert torch.allclose(acc, got + 1.0, rtol=0, atol=1e-5 * float(got.abs().max()))
     assert api.device_status() == 0
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_staged_u16_codes_equal_the_fp32_sequence_on_the_staged_image(dtype):
+    """The code epilogue takes the staged image's FP32 value through
+    RN(RN(a mu) + b), rounds to nearest even and clamps: applied in numpy
+    float32 to fbp_backproject_staged's FP32 image it gives the same codes
+    bit for bit."""
+    api = fbp_api()
+    G = GEOMS[1]
+    g, x, filt, rs = rows_for(api, G, 2, dtype, 55)
+    win = api.HuWindow(0.5, 0.0, -1000.0, 3000.0)
+    a, b = api.hu_coefficients(win)
+    mu = api.backproject_staged(filt, g, rs)
+    codes = api.backproject_staged_u16(filt, g, win, row_scale=rs, chunk=1)
+    want = oracle.hu_codes_f32(mu.cpu().numpy(), np.float32(a), np.float32(b))
+    assert np.array_equal(codes.cpu().numpy().view(np.uint16), want)
+    assert api.device_status() == 0
+
+
+def test_staged_offset_scan_matches_the_orbit_path():
+    """A folded full-turn offset scan is a centred half turn: fbp_offset takes
+    the staged path (n >= 1024) and agrees with the orbit kernel's image to
+    FP32 rounding."""
+    import math
+    api = fbp_api()
+    from paper_2505_13955_gb300 import phantoms
+    n, k = 1024, 360
+    d, c, ov = 9 * n // 16, n / 16 - 0.5, n / 32
+    ell = phantoms.random_ellipses(phantoms.rng_for(3), count_range=(5, 10))
+    p = phantoms.sinogram(ell, 2 * k, d, n, angle_step=2 * math.pi / (2 * k), det_center=c)
+    g = api.Geometry(2 * k, d, n, angle_step=2 * math.pi / (2 * k), det_center=c)
+    x = torch.from_numpy(p).cuda()
+    staged = api.fbp_offset(x, g, ov, fold=True)
+    gv, _ = api.offset_geometry(g, ov, True)
+    assert api.staged_preferred(gv)
+    orbit = api.fbp_offset(x, g, ov, fold=True, variant=7)
+    dr = (orbit.max() - orbit.min()).item()
+    assert (staged - orbit).abs().max().item() <= 1e-5 * dr
