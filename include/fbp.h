@@ -306,8 +306,8 @@ fbp_status fbp_filter_offset(const float *sino, void *filt, float *row_scale, fb
  *
  * fbp_backproject caches its FP64 angle table in device memory it allocates
  * with cudaMalloc the first time it sees a geometry.  Callers whose device
- * memory is owned by a framework's pool, fixed up front, or who enqueue work
- * inside CUDA stream capture cannot allow that allocation.  This variant
+ * memory is owned by a framework's pool or fixed up front cannot allow that
+ * allocation.  This variant
  * computes the angle table on `stream` into a static device array of at most
  * 16384 angles (256 KB, held on every device that runs it until the library
  * is unloaded) and calls no allocating routine; inputs and outputs are as for

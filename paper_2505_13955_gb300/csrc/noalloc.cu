@@ -5,9 +5,9 @@
 // the library fills with cudaMalloc on the first call for each geometry.  Some
 // callers cannot allow that: code running under a framework that owns every
 // byte of device memory through its own pool (any cudaMalloc outside it can
-// fail or fragment the pool), code whose device memory is fixed up front
-// (embedded and real-time pipelines), and code that enqueues work inside CUDA
-// stream capture, where a cudaMalloc is not allowed.  This entry point keeps
+// fail or fragment the pool), and code whose device memory is fixed up front
+// (embedded and real-time pipelines, where a failed allocation mid-run is not
+// an option).  This entry point keeps
 // the angle table in a file-scope static device array of fixed size instead,
 // recomputes it on the caller's stream at every call, and calls no allocating
 // routine.  The caller still provides the input rows and the output slices.

@@ -542,3 +542,59 @@ def test_forward_tile_shared_memory_allows_its_blocks_per_sm(NS, threads, blocks
     assert smem <= 227 * 1024
     assert blocks * (smem + 1024) <= 228 * 1024
     assert threads % 32 == 0
+
+
+# Staged backprojection (bp_staged.cu): the shapes of kStagedShapes32 and
+# kStagedShapes16 as (TXT, TYT, PX, PY, KT, NS, blocks per SM), and the
+# shared-memory layout of bp_staged_kernel restated from its offsets.
+STAGED_F32 = [(16, 8, 2, 4, 4, 2, 6), (16, 8, 2, 4, 4, 3, 5), (16, 8, 2, 4, 8, 2, 3), (16, 16, 4, 4, 8, 2, 2)]
+# (shapes 2 and 3 of the 16-bit list are compiled with registers for four
+# blocks per SM, but their stage buffers allow two and three: None, no
+# occupancy is stated for them)
+STAGED_16 = [(16, 16, 4, 4, 8, 3, 2), (16, 16, 4, 4, 16, 2, 2), (16, 8, 2, 4, 16, 3, None),
+             (16, 8, 2, 4, 8, 4, None), (16, 8, 2, 4, 8, 3, 5), (16, 8, 2, 4, 8, 2, 6)]
+
+
+def staged_smem_bytes(KT, NS, halves, Wp):
+    params = (NS * KT * 16 + 127) // 128 * 128
+    return 128 + 128 + params + NS * halves * 2 * KT * Wp * 16
+
+
+@pytest.mark.parametrize("halves,shape", [(2, s) for s in STAGED_F32] + [(1, s) for s in STAGED_16])
+@pytest.mark.parametrize("alpha", [0.125, 0.9, 1.0, 2.5])
+@pytest.mark.parametrize("raw_offset", [0, 16, 48, 112])
+def test_staged_shared_layout_fits_and_aligns(halves, shape, alpha, raw_offset):
+    """Every address the staged kernel forms -- mbarriers, counters, pair
+    parameters, and each bulk-copy destination of every window of every
+    stage buffer -- lies inside the dynamic allocation the host requests
+    (whatever 16-byte-aligned offset the allocation starts at), every copy
+    destination is 128-byte aligned, every box is at most 256 entries, and
+    the shapes with a stated occupancy fit that many blocks in the SM's
+    shared memory when the window is the orbit's at unit pixel/bin ratio."""
+    TXT, TYT, PX, PY, KT, NS, minb = shape
+    tile = TXT * PX
+    H = window_half(alpha, tile, tile)
+    W = 2 * H + 1
+    if W > 256:
+        pytest.skip("refused on the host: window wider than one bulk copy")
+    Wp = (W + 7) // 8 * 8
+    size = staged_smem_bytes(KT, NS, halves, Wp)
+    raw = 1 << 20 | raw_offset                         # shared address of the dynamic buffer
+    base = (raw + 127) & ~127
+    end = raw + size
+    assert base + 8 * NS <= base + 12 * NS <= base + 16 * NS <= base + 128      # mbarriers, done, issued
+    assert base + 128 + NS * KT * 16 <= base + 128 + (NS * KT * 16 + 127) // 128 * 128
+    tab0 = base + 128 + (NS * KT * 16 + 127) // 128 * 128
+    half_bytes = 2 * KT * Wp * 16
+    stage_bytes = halves * half_bytes
+    for b in range(NS):
+        for lane in range(KT):
+            for h in range(halves):
+                for win in range(2):
+                    dst = tab0 + b * stage_bytes + h * half_bytes + 2 * lane * Wp * 16 + win * Wp * 16
+                    assert dst % 128 == 0
+                    assert raw <= dst and dst + W * 16 <= end
+    # the expected transaction bytes of a full stage fit an mbarrier's count
+    assert KT * 2 * W * 16 * halves < (1 << 20)
+    if alpha == 1.0 and minb is not None:
+        assert minb * (size + 1024) <= 228 * 1024, f"{minb} blocks of {size} bytes"
