@@ -885,6 +885,38 @@ def run_offset(args) -> None:
     return line
 
 
+def batch_launches(api, rows_geoms, tdt, variant) -> int:
+    """Kernels one fbp_batched / fbp_batched_scans call launches: the batched
+    filter; under the default (-1), for the items that run staged units, the
+    table pass (and, for 16-bit rows, the per-item scale pass) and the staged
+    persistent kernel; the persistent tile kernel for the other items."""
+    import torch
+    staged = sum(api.batched_item_staged(g, tdt) for g in rows_geoms) if variant < 0 else 0
+    n = 1
+    if staged:
+        n += 2 + (tdt != torch.float32)
+    if staged < len(rows_geoms):
+        n += 1
+    return n
+
+
+def default_backproject(api, f, g, r, o, staged_ws):
+    """One slice's backprojection as the library's single-slice default path
+    (api.fbp) runs it: the staged kernel where api.staged_preferred(g), else
+    fbp_backproject's default variant."""
+    if api.staged_preferred(g):
+        api.backproject_staged(f, g, r, out=o, workspace=staged_ws)
+    else:
+        api.backproject(f, g, row_scale=r, out=o, variant=-1)
+
+
+def staged_workspace(api, geoms, tdt, dev):
+    import torch
+    need = max([api.backproject_staged_workspace_bytes(g, tdt, 1) for g in geoms if api.staged_preferred(g)],
+               default=256)
+    return torch.empty(need, dtype=torch.uint8, device=dev)
+
+
 def run_ragged(args) -> None:
     """Ragged batch: all items in one fbp_batched call (one filter launch + one
     persistent backprojection launch), captured once in a CUDA graph and
@@ -910,6 +942,7 @@ def run_ragged(args) -> None:
     tuned = autotune.tune_batched(sinos, geoms, tdt, kind=w.filter) if args.variant < 0 else \
         {"variant": args.variant}
     variant = tuned["variant"]
+    n_staged = sum(api.batched_item_staged(g, tdt) for g in geoms) if variant < 0 else 0
     wsp = torch.empty(api.batched_workspace_bytes(sinos, outs, geoms, tdt), dtype=torch.uint8, device=dev)
     stream = torch.cuda.Stream(dev)
     torch.cuda.synchronize()
@@ -921,18 +954,32 @@ def run_ragged(args) -> None:
         ms = T.run(lambda _: graph.replay(), dev.index)
         clocks = T.clocks
         # per-slice launches on the same stream: with the library's default
-        # kernel for each slice (the baseline), and with the batch's tile variant
+        # path for each slice (the baseline), and with the shape each item
+        # ran in the batch
         filts = [torch.empty_like(s, dtype=tdt) for s in sinos]
         rss = [torch.empty((g.n_angles,), device=dev) if args.dtype != "f32" else None for g in geoms]
+        sws = staged_workspace(api, geoms, tdt, dev)
 
         def per_slice_with(v):
             def run(_):
                 for s, g, f, r, o in zip(sinos, geoms, filts, rss, outs):
                     api.filter(s, g, kind=w.filter, dtype=tdt, out=f, row_scale=r)
-                    api.backproject(f, g, row_scale=r, out=o, variant=v)
+                    if v == "default":
+                        default_backproject(api, f, g, r, o, sws)
+                    elif v < 0 and api.batched_item_staged(g, tdt):
+                        api.backproject_staged(f, g, r, out=o, workspace=sws_batch,
+                                               shape=0 if tdt == torch.float32 else 5)
+                    else:
+                        vv = v if v >= 0 else (8 if tdt == torch.float32 else 10)
+                        if not api.variant_supports(vv, g, tdt):
+                            vv = 12 if api.bp_variants()[vv]["threads"] == 128 else 0
+                        api.backproject(f, g, row_scale=r, out=o, variant=vv)
             return run
 
-        ms_single = Timed(stream, max(1, args.steps // 2), args.warmup).run(per_slice_with(-1), None)
+        sws_batch = torch.empty(max([api.backproject_staged_workspace_bytes(g, tdt, 1) for g in geoms
+                                     if api.batched_item_staged(g, tdt)], default=256),
+                                dtype=torch.uint8, device=dev)
+        ms_single = Timed(stream, max(1, args.steps // 2), args.warmup).run(per_slice_with("default"), None)
         ms_same = Timed(stream, max(1, args.steps // 2), args.warmup).run(per_slice_with(variant), None)
     assert api.device_status() == 0
     per_rank = allgather_floats([ms, float(updates)])
@@ -943,15 +990,19 @@ def run_ragged(args) -> None:
         "workload": f"{w.name}: {len(idx)} slices per GPU, N in {w.n_choices}, K in {w.k_choices}, "
                     "random ellipses, Ram-Lak; one persistent launch per step, CUDA-graph replay",
         "parallelism": f"slices sharded over {ws} GPU(s), no collective",
-        "bp_variant": variant, "autotune": tuned})
+        "bp_variant": variant if variant >= 0 else
+        f"library batch default: staged 32 x 32 orbit units for {n_staged} of {len(idx)} items, "
+        f"persistent orbit variant {8 if args.dtype == 'f32' else 10} for the rest", "autotune": tuned})
     line.update({"slices_per_s": len(idx) * len(per_rank) / (ms_step / 1e3),
                  "per_slice_launches": {"value": updates / (ms_single / 1e3) / 1e9, "unit": UNIT,
-                                        "ms_per_step": ms_single, "bp_variant": "library default per slice",
-                                        "launches_per_step": 2 * len(idx)},
+                                        "ms_per_step": ms_single,
+                                        "bp_variant": "library default per slice (fbp: staged kernel where "
+                                                      "n >= 1024 and the orbit geometry, else variant 7)"},
                  "speedup_vs_per_slice": ms_single / ms,
                  "per_slice_launches_same_variant": {"value": updates / (ms_same / 1e3) / 1e9, "unit": UNIT,
-                                                     "ms_per_step": ms_same, "bp_variant": variant},
-                 "clocks": clocks, "gpu_launches": 2 * args.steps})
+                                                     "ms_per_step": ms_same,
+                                                     "bp_variant": "each item's batch shape, one slice per launch"},
+                 "clocks": clocks, "gpu_launches": batch_launches(api, geoms, tdt, variant) * args.steps})
     return line
 
 
@@ -983,7 +1034,8 @@ def run_mixed(args) -> None:
     updates = sum(g.n * g.n * g.n_angles for g in rows_geoms)
     n_off = sum(1 for sc in scans if sc.overlap)
     tdt = getattr(torch, DT[args.dtype])
-    variant = args.variant              # -1: the library's batch default (orbit units where they apply)
+    variant = args.variant              # -1: the library's batch default (staged units where they apply)
+    n_staged = sum(api.batched_item_staged(g, tdt) for g in rows_geoms) if variant < 0 else 0
     outs = [torch.empty((g.n, g.n), device=dev) for g in rows_geoms]
     wsp = torch.empty(api.batched_scans_workspace_bytes(sinos, outs, scans, tdt), dtype=torch.uint8,
                       device=dev)
@@ -1003,15 +1055,17 @@ def run_mixed(args) -> None:
         filts = [torch.empty((g.n_angles, g.n_det), dtype=tdt, device=dev) for g in rows_geoms]
         rss = [torch.empty((g.n_angles,), device=dev) if args.dtype != "f32" else None for g in rows_geoms]
 
+        sws = staged_workspace(api, rows_geoms, tdt, dev)
+
         def per_scan(_):
-            # each scan alone with the library's default kernel
+            # each scan alone through the library's default single-scan path
             for s, sc, gv, f, r, o in zip(sinos, scans, rows_geoms, filts, rss, outs):
                 if sc.overlap:
                     api.filter_offset(s, sc.g, sc.overlap, sc.fold, kind=w.filter, dtype=tdt, out=f,
                                       row_scale=r)
                 else:
                     api.filter(s, sc.g, kind=w.filter, dtype=tdt, out=f, row_scale=r)
-                api.backproject(f, gv, row_scale=r, out=o, variant=-1)
+                default_backproject(api, f, gv, r, o, sws)
 
         T2 = Timed(stream, max(1, args.steps // 2), args.warmup)
         ms_single = T2.run(per_scan, None)
@@ -1028,16 +1082,19 @@ def run_mixed(args) -> None:
                     f"off the axis, folded), N in {w.n_choices}, half-turn K in {w.k_choices}, random "
                     "ellipses, Ram-Lak; one persistent launch per step, CUDA-graph replay, atomic work queue",
         "parallelism": f"scans sharded over {ws} GPU(s), no collective",
-        "bp_variant": variant if variant >= 0 else "library batch default (8: 64 x 64 FP32 orbit units, "
-                                                   "generic 64 x 64 tiles where an item has no symmetry)"})
+        "bp_variant": variant if variant >= 0 else
+        f"library batch default: staged 32 x 32 orbit units for {n_staged} of {len(idx)} items, persistent "
+        f"orbit variant {8 if args.dtype == 'f32' else 10} (generic 64 x 64 tiles without the symmetry) "
+        "for the rest"})
     line.update({"slices_per_s": len(idx) * len(per_rank) / (ms_step / 1e3),
                  "group_cyclic": {"value": rate_c / 1e9, "unit": UNIT, "ms_per_step": ms_c,
                                   "ratio_to_queue": ms_step / ms_c},
                  "per_scan_launches": {"value": updates / (ms_single / 1e3) / 1e9, "unit": UNIT,
-                                       "ms_per_step": ms_single, "bp_variant": "library default per scan",
-                                       "launches_per_step": 2 * len(idx)},
+                                       "ms_per_step": ms_single,
+                                       "bp_variant": "library default per scan (staged kernel where n >= 1024 "
+                                                     "and the orbit geometry, else variant 7 / 5)"},
                  "speedup_vs_per_scan": ms_single / ms,
-                 "clocks": clocks, "gpu_launches": 2 * args.steps})
+                 "clocks": clocks, "gpu_launches": batch_launches(api, rows_geoms, tdt, variant) * args.steps})
     return line
 
 

@@ -426,25 +426,35 @@ int fbp_bp_variant_supports(int variant, fbp_dtype dtype, const fbp_geometry *g)
 
 /*
  * Ragged batches (Sec. V-A(b): specimens with various N_p and N_c
- * reconstructed together).  One persistent filter launch and one persistent
- * backprojection launch cover every item; items may differ in K, D, n and
+ * reconstructed together).  One persistent filter launch and persistent
+ * backprojection launches cover every item; items may differ in K, D, n and
  * geometry.
  *   items      HOST array of `count` items (1 <= count <= 256); each item's
  *              sino/slice are device pointers as above.  n_det <= 8192.
  *   workspace  device, >= fbp_batched_workspace_bytes(items, count, dtype)
  *              bytes, 256-byte aligned, owned by the caller.  It holds the
- *              filtered rows of every item and the work-queue counter.
- *   bp_variant tile variant for backprojection (fbp_bp_variant_info),
- *              -1 = default (8 for FP32 rows, 10 for 16-bit rows).  With a
- *              symmetric variant, items whose geometry has the 90-degree
- *              symmetry (angle step pi/K with K even, det_center = (D-1)/2,
- *              n a multiple of twice the variant's tile) run its orbit units
- *              and every other item runs generic tiles of the same thread
- *              count (64 x 32 for 128-thread variants, 64 x 64 for 256);
- *              with a generic variant every item runs that variant's tiles.
- *              Each item's slice is bit-identical to fbp_backproject_variant
- *              on the same rows with the shape the item ran.  Packed
- *              variants (10, 11) with FP32 rows return FBP_ERR_UNSUPPORTED.
+ *              work-queue counters, the filtered rows of every item and, for
+ *              each item that fbp_batched_item_staged accepts, its padded
+ *              angle-pair table (about 4-6x its FP32 rows, 2-3x its 16-bit
+ *              rows; the size does not depend on bp_variant).
+ *   bp_variant -1 = default: the items that fbp_batched_item_staged accepts
+ *              run in one persistent launch of staged units (90-degree orbits
+ *              of four 32 x 32 tiles whose windows are moved by bulk copies
+ *              from their padded tables; each such slice is bit-identical to
+ *              fbp_backproject_staged with shape 0 for FP32 rows, shape 5 for
+ *              16-bit rows), the others in the persistent tile kernel with
+ *              variant 8 (FP32 rows) or 10 (16-bit rows).  A tile variant
+ *              (fbp_bp_variant_info) runs every item in the persistent tile
+ *              kernel: with a symmetric variant, items whose geometry has the
+ *              90-degree symmetry (angle step pi/K with K even, det_center =
+ *              (D-1)/2, n a multiple of twice the variant's tile) run its
+ *              orbit units and every other item runs generic tiles of the
+ *              same thread count (64 x 32 for 128-thread variants, 64 x 64 for
+ *              256); with a generic variant every item runs that variant's
+ *              tiles.  Each item's slice is then bit-identical to
+ *              fbp_backproject_variant on the same rows with the shape the
+ *              item ran.  Packed variants (10, 11) with FP32 rows return
+ *              FBP_ERR_UNSUPPORTED.
  * The call captures into a CUDA graph once each item's geometry has been
  * seen by the library (tables exist).
  */
@@ -453,6 +463,14 @@ size_t fbp_batched_workspace_bytes(const fbp_batch_item *items, int count,
 fbp_status fbp_batched(const fbp_batch_item *items, int count,
                        fbp_filter_kind kind, fbp_dtype dtype, int bp_variant,
                        void *workspace, size_t ws_bytes, fbp_stream_t stream);
+
+/* 1 if a batch item whose filtered rows have geometry g and dtype runs
+ * staged units under fbp_batched's default (the 90-degree symmetry with
+ * n a multiple of 64, and a backprojection window of at most 72 detector
+ * segments: pixel_size / det_spacing up to about 1.5), 0 otherwise; for an
+ * offset item of fbp_batched_scans pass its virtual geometry
+ * (fbp_offset_geometry).  Host-only, no CUDA call. */
+int fbp_batched_item_staged(const fbp_geometry *g, fbp_dtype dtype);
 
 /*
  * Mixed batches of normal and offset scans (Sec. V-A(b): specimens with
@@ -551,8 +569,10 @@ fbp_status fbp_host(const float *sino_host, void *slice_host, const fbp_geometry
  * expired waits a copy into its shared memory may still be in flight, so
  * treat code 6 as voiding that launch's output and any kernel enqueued after
  * it on the stream: synchronise and discard those results); 7 a wait of
- * fbp_backproject_staged for a window copy past its cap (the block writes
- * nothing, after a capped wait for its copies).  The
+ * fbp_backproject_staged or a staged batch unit for a window copy past its
+ * cap (the block writes nothing, after a capped wait for its copies); 8 a
+ * staged batch window outside its item's padded table (the copy is
+ * clamped into the table; that item's slice is wrong).  The
  * first fault recorded stays until read.  This call synchronises `stream`,
  * reads and clears the word, and returns FBP_OK or FBP_ERR_DEVICE_STATUS
  * (code in *code if non-NULL).

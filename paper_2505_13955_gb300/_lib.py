@@ -123,6 +123,7 @@ SIGNATURES = {
     "fbp_bp_variant_count": (ctypes.c_int, []),
     "fbp_bp_variant_info": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(CBpShape)]),
     "fbp_bp_variant_supports": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, _G]),
+    "fbp_batched_item_staged": (ctypes.c_int, [_G, ctypes.c_int]),
     "fbp_batched_workspace_bytes": (ctypes.c_size_t, [ctypes.POINTER(CBatchItem), ctypes.c_int,
                                                       ctypes.c_int]),
     "fbp_batched": (ctypes.c_int, [ctypes.POINTER(CBatchItem), ctypes.c_int, ctypes.c_int, ctypes.c_int,

@@ -505,6 +505,13 @@ def variant_supports(variant: int, g: Geometry, dtype=torch.float32) -> bool:
     return bool(lib().fbp_bp_variant_supports(int(variant), _DTYPES[dtype], ctypes.byref(gc)))
 
 
+def batched_item_staged(g: Geometry, dtype=torch.float32) -> bool:
+    """fbp_batched_item_staged: whether a batch item with rows of geometry g
+    (an offset item's virtual geometry) runs staged units by default."""
+    gc = g.c()
+    return bool(lib().fbp_batched_item_staged(ctypes.byref(gc), _DTYPES[dtype]))
+
+
 def _items(sinos, outs, geoms):
     arr = (_lib.CBatchItem * len(sinos))()
     for i, (s, o, g) in enumerate(zip(sinos, outs, geoms)):

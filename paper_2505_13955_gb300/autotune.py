@@ -86,9 +86,10 @@ def single_key(g: api.Geometry, dtype, device=None) -> str:
 
 
 def batched_key(geoms, dtype, device=None) -> str:
-    # v2: the persistent kernel runs orbit units, so symmetric shapes are candidates
+    # v3: the default (-1, staged batch units) is a candidate beside every
+    # persistent-kernel shape
     mix = sorted({(g.n_angles, g.n) for g in geoms})
-    return f"batched-v2|{_device_key(device)}|{_dtype_name(dtype)}|" + ",".join(f"{k}x{n}" for k, n in mix)
+    return f"batched-v3|{_device_key(device)}|{_dtype_name(dtype)}|" + ",".join(f"{k}x{n}" for k, n in mix)
 
 
 def tune_single(g: api.Geometry, dtype=torch.float32, reps: int = 3, force: bool = False,
@@ -122,7 +123,9 @@ def tune_single(g: api.Geometry, dtype=torch.float32, reps: int = 3, force: bool
 
 def tune_batched(sinos, geoms, dtype=torch.float32, reps: int = 2, force: bool = False,
                  kind="ramlak", variants=None) -> dict:
-    """Fastest persistent-kernel variant for fbp_batched on this batch."""
+    """Fastest backprojection of fbp_batched on this batch: -1 (the default:
+    staged batch units for the items whose geometry allows them, the
+    persistent tile kernel for the rest) or a persistent-kernel variant."""
     key = batched_key(geoms, dtype)
     if not force:
         hit = _load().get(key)
@@ -135,7 +138,7 @@ def tune_batched(sinos, geoms, dtype=torch.float32, reps: int = 2, force: bool =
     # symmetric shapes run orbit units for the items with the symmetry and
     # generic tiles of the same threads for the others; packed shapes only
     # for 16-bit rows
-    cands = variants if variants is not None else [
+    cands = variants if variants is not None else [-1] + [
         s["variant"] for s in shapes
         if not s["texture"] and not (s["packed16"] and dtype == torch.float32)]
     times = {}

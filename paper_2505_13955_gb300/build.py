@@ -27,7 +27,8 @@ BUILD = os.path.join(HERE, "_build")
 FILTER_UNITS = [f"filter_{fam}_{dt}.cu" for fam in ("plain", "stream", "batched")
                 for dt in ("f32", "f16", "bf16")]
 CU_SOURCES = ["runtime.cu", "filter.cu", *FILTER_UNITS, "backproject.cu", "forward.cu", "fbp_api.cu",
-              "noalloc.cu", "sap.cu", "bp_texture.cu", "probe.cu", "host_pipeline.cu", "bp_staged.cu"]
+              "noalloc.cu", "sap.cu", "bp_texture.cu", "probe.cu", "host_pipeline.cu", "bp_staged.cu",
+              "bp_staged_batch.cu"]
 # only these translation units read FBP_CHECKED; the checked twin shares every other object
 CHECKED_SOURCES = ["backproject.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -31,6 +31,8 @@ struct BpBatchArgs {
     unsigned *status;
 };
 
+static_assert(sizeof(BpBatchItem) == 80, "batch item layout");
+
 struct FilterBatchItem {        // 88 bytes
     const float *sino;          // [K][D], or the offset scan's [K_in][Dp] physical rows
     void *filt;                 // [K][D] in the workspace
@@ -49,6 +51,60 @@ struct FilterBatchArgs {
     FilterBatchItem items[kMaxBatch];
     int count;
 };
+
+// Staged ragged batches (bp_staged_batch.cu): orbit units of 32 x 32 tiles
+// fed by plain bulk copies from per-item padded tables.
+struct StagedBatchItem {        // 88 bytes
+    const void *table;          // padded table (16-bit: [K/2][Ep]; FP32: planes a, b of [K/2][Ep])
+    float *slice;               // [N][N] output
+    const double2 *cs;          // [K] angle table
+    const float *smax;          // 16-bit rows: the item's S (written by the table pass); FP32: null
+    double alpha, det_center;
+    int K2, N, H, W, Ep, P_lo;  // angle pairs, image side, half-window, window, padded row, padding
+    int tiles_x, unit_begin;    // orbits per row (N / 64), first unit of this item
+    float scale;                // angle_step
+    int pad_;
+};
+
+static_assert(sizeof(StagedBatchItem) == 88, "staged batch item layout");
+
+struct StagedBatchArgs {
+    StagedBatchItem items[kMaxBatch];
+    int count, total_units;
+    int Wp;                     // window pitch in shared memory (entries, multiple of 8, >= every W)
+    int cyclic;                 // as BpBatchArgs
+    int *counter;
+    unsigned *status;
+};
+
+struct StagedPrepItem {         // 56 bytes
+    const void *filt;           // [K][D] filtered rows
+    const float *row_scale;     // [K] (16-bit rows) or null
+    void *table;                // the item's padded table
+    float *smax;                // 16-bit rows: where S goes; FP32: null
+    int K, D, Ep, P_lo;
+    int pair_begin, pad_;       // first angle pair of this item in the table pass's grid
+};
+
+static_assert(sizeof(StagedPrepItem) == 56, "table pass item layout");
+
+struct StagedPrepArgs {
+    StagedPrepItem items[kMaxBatch];
+    int count, total_pairs;
+};
+
+// The padded table of one item: half-window H, window W and its pitch Wp,
+// leading zero entries P_lo, padded row Ep, bytes of the table.
+struct StagedItemGeom {
+    int H, W, Wp, P_lo, Ep;
+    size_t table_bytes;
+};
+// true if the item can run staged batch units (the orbit symmetry with 32 x
+// 32 tiles, a window of at most 72 entries); fills *out.  Host only.
+bool staged_batch_geometry(int K, double angle_step, int D, double det_center, int N, double alpha,
+                           fbp_dtype dtype, StagedItemGeom *out);
+int staged_batch_tile();
+fbp_status launch_staged_batch(const StagedPrepArgs &p, StagedBatchArgs &a, fbp_dtype dtype, cudaStream_t s);
 
 fbp_status launch_bp_persistent(BpBatchArgs &a, int variant, fbp_dtype dtype, cudaStream_t s);
 fbp_status launch_filter_batched(const FilterBatchArgs &a, int total_groups, fbp_dtype dtype,

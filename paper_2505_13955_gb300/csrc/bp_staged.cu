@@ -27,7 +27,7 @@
 #include <cudaTypedefs.h>
 
 #include "bp_batch.cuh"
-#include "bp_orbit.cuh"
+#include "bp_staged.cuh"
 
 namespace fbp {
 void clear_error();
@@ -35,8 +35,6 @@ void clear_error();
 
 namespace fbp {
 namespace {
-
-constexpr long long kStagedWaitCap = 1LL << 22;   // polls of one wait (well under a second)
 
 // S of each slice: the largest row scale (1 if none is positive), as the
 // orbit kernel forms it.
@@ -66,7 +64,6 @@ __global__ void orbit_prestage_kernel(const T *filt, const float *row_scale, con
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
     const int jj = e - 1;                   // segment between bins jj and jj + 1
-    const int mj = D - 1 - jj;              // mirrored: q~[jj] = q[mj], q~[jj + 1] = q[mj - 1]
     for (long long p = blockIdx.y; p < pairs; p += gridDim.y) {
         const long long s = p / K2;
         const int k = (int)(p - s * K2);
@@ -75,107 +72,27 @@ __global__ void orbit_prestage_kernel(const T *filt, const float *row_scale, con
         const float invS = __frcp_rn(__ldg(smax + s));
         const float sc0 = __fmul_rn(__ldg(row_scale + (size_t)s * K + k), invS);
         const float sc1 = __fmul_rn(__ldg(row_scale + (size_t)s * K + k + K2), invS);
-        float v[8];
-        v[0] = (unsigned)jj < (unsigned)D ? load_q<T>(r0 + jj) : 0.f;
-        v[1] = (unsigned)(jj + 1) < (unsigned)D ? load_q<T>(r0 + jj + 1) : 0.f;
-        v[2] = (unsigned)jj < (unsigned)D ? load_q<T>(r1 + jj) : 0.f;
-        v[3] = (unsigned)(jj + 1) < (unsigned)D ? load_q<T>(r1 + jj + 1) : 0.f;
-        v[4] = (unsigned)mj < (unsigned)D ? load_q<T>(r0 + mj) : 0.f;
-        v[5] = (unsigned)(mj - 1) < (unsigned)D ? load_q<T>(r0 + mj - 1) : 0.f;
-        v[6] = (unsigned)mj < (unsigned)D ? load_q<T>(r1 + mj) : 0.f;
-        v[7] = (unsigned)(mj - 1) < (unsigned)D ? load_q<T>(r1 + mj - 1) : 0.f;
-        float mid[4], slp[4];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) orbit_mid_slope(v[2 * r], v[2 * r + 1], (r & 1) ? sc1 : sc0, mid[r], slp[r]);
-        uint4 out;
-        if constexpr (PACKED) {
-            out.x = pack16<T>(mid[0], mid[1]);
-            out.y = pack16<T>(slp[0], slp[1]);
-            out.z = pack16<T>(mid[2], mid[3]);
-            out.w = pack16<T>(slp[2], slp[3]);
-        } else {
-            out.x = pack16<T>(mid[0], slp[0]);
-            out.y = pack16<T>(mid[1], slp[1]);
-            out.z = pack16<T>(mid[2], slp[2]);
-            out.w = pack16<T>(mid[3], slp[3]);
-        }
+        const uint4 out = orbit_entry16<T, PACKED>(r0, r1, D, jj, sc0, sc1);
         table[(size_t)p * E + e] = out;
     }
 }
 
-// FP32 rows: per segment and row the midpoint (q_j + q_{j+1}) / 2 and the
-// slope q_{j+1} - q_j, so that Q(u) = mid + (u' - i) slope; 32 bytes per
-// entry, kept as two 16-byte halves (rows th, th' | mirrored rows) that land
-// in separate shared arrays.
+// FP32 rows: 32-byte midpoint/slope entries (orbit_entry32), whose two
+// 16-byte halves (rows th, th' | mirrored rows) land in separate shared
+// arrays.
 __global__ void orbit_prestage_f32_kernel(const float *filt, float4 *table, int K, int D, long long pairs)
 {
     const int K2 = K / 2, E = D + 1;
     const int e = blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= E) return;
-    const int jj = e - 1, mj = D - 1 - jj;
+    const int jj = e - 1;
     for (long long p = blockIdx.y; p < pairs; p += gridDim.y) {
         const long long s = p / K2;
         const int k = (int)(p - s * K2);
         const float *r0 = filt + ((size_t)s * K + k) * D;
         const float *r1 = r0 + (size_t)K2 * D;
-        float v[8];
-        v[0] = (unsigned)jj < (unsigned)D ? __ldg(r0 + jj) : 0.f;
-        v[1] = (unsigned)(jj + 1) < (unsigned)D ? __ldg(r0 + jj + 1) : 0.f;
-        v[2] = (unsigned)jj < (unsigned)D ? __ldg(r1 + jj) : 0.f;
-        v[3] = (unsigned)(jj + 1) < (unsigned)D ? __ldg(r1 + jj + 1) : 0.f;
-        v[4] = (unsigned)mj < (unsigned)D ? __ldg(r0 + mj) : 0.f;
-        v[5] = (unsigned)(mj - 1) < (unsigned)D ? __ldg(r0 + mj - 1) : 0.f;
-        v[6] = (unsigned)mj < (unsigned)D ? __ldg(r1 + mj) : 0.f;
-        v[7] = (unsigned)(mj - 1) < (unsigned)D ? __ldg(r1 + mj - 1) : 0.f;
-        float ms[8];
-#pragma unroll
-        for (int r = 0; r < 4; ++r) {
-            ms[2 * r] = __fmul_rn(0.5f, __fadd_rn(v[2 * r], v[2 * r + 1]));
-            ms[2 * r + 1] = __fsub_rn(v[2 * r + 1], v[2 * r]);
-        }
         float4 *o = table + ((size_t)p * E + e) * 2;
-        o[0] = make_float4(ms[0], ms[1], ms[2], ms[3]);
-        o[1] = make_float4(ms[4], ms[5], ms[6], ms[7]);
-    }
-}
-
-// One angle pair from FP32 midpoint/slope entries (the FP32 form of
-// orbit_pair): per pixel and window the rounded index i and the fraction
-// u' - i, two 16-byte loads (rows th, th' at cb, mirrored rows at cb + tab_b),
-// four FMAs.
-template <int TXT, int TYT, int PX, int PY>
-__device__ __forceinline__ void orbit_pair_mid(float (&acc)[4][PY][PX], const float4 pv, const uint32_t cb1,
-                                               const uint32_t cb2, const uint32_t tab_b, const float dxt,
-                                               const float dyt)
-{
-    const float c = pv.x, s = pv.y;
-    const float u10 = fmaf(dxt, c, fmaf(dyt, s, pv.z));
-    const float u20 = fmaf(dxt, -s, fmaf(dyt, c, pv.w));
-    const float s1x = (float)TXT * c, s1y = (float)TYT * s;
-    const float s2x = -(float)TXT * s, s2y = (float)TYT * c;
-#pragma unroll
-    for (int iy = 0; iy < PY; ++iy) {
-        const float r1 = iy == 0 ? u10 : fmaf((float)iy, s1y, u10);
-        const float r2 = iy == 0 ? u20 : fmaf((float)iy, s2y, u20);
-#pragma unroll
-        for (int ix = 0; ix < PX; ++ix) {
-#pragma unroll
-            for (int win = 0; win < 2; ++win) {
-                const float u = win == 0 ? (ix == 0 ? r1 : fmaf((float)ix, s1x, r1))
-                                         : (ix == 0 ? r2 : fmaf((float)ix, s2x, r2));
-                const float t = __fadd_rn(u, kRoundMagic);
-                const float fr = __fsub_rn(u, __fsub_rn(t, kRoundMagic));
-                const uint32_t e = (win == 0 ? cb1 : cb2) + (__float_as_uint(t) << 4);
-                const float4 e0 = lds_f4(e), e1 = lds_f4(e + tab_b);
-                // orbit members fed by rows (th, th', th~, th'~), as orbit_pair
-                const int m0 = win == 0 ? 0 : 3, m1 = win == 0 ? 1 : 0;
-                const int m2 = win == 0 ? 2 : 1, m3 = win == 0 ? 3 : 2;
-                acc[m0][iy][ix] += fmaf(fr, e0.y, e0.x);
-                acc[m1][iy][ix] += fmaf(fr, e0.w, e0.z);
-                acc[m2][iy][ix] += fmaf(fr, e1.y, e1.x);
-                acc[m3][iy][ix] += fmaf(fr, e1.w, e1.z);
-            }
-        }
+        orbit_entry32(r0, r1, D, jj, o[0], o[1]);
     }
 }
 
@@ -191,36 +108,6 @@ struct StagedArgs {
     int accumulate;
     unsigned *status;
 };
-
-__device__ __forceinline__ bool staged_wait(uint32_t mbar, unsigned parity)
-{
-    for (long long it = 0; it < kStagedWaitCap; ++it) {
-        uint32_t done;
-        asm volatile("{\n\t.reg .pred p;\n\t"
-                     "mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-                     "selp.u32 %0, 1, 0, p;\n\t}"
-                     : "=r"(done) : "r"(mbar), "r"(parity) : "memory");
-        if (done) return true;
-    }
-    return false;
-}
-
-// Shared memory: [0, 128) NS mbarriers, NS "warps done" and NS "times
-// issued" counters; [128, 128 + P) the per-stage pair parameters (float4 per
-// pair, P rounded to 128 bytes); then NS stage tables of 2 KT windows of Wp
-// entries (16 bytes each; Wp a multiple of 8, so every window starts on a
-// 128-byte boundary).  The dynamic buffer is rounded up to 128 bytes first.
-template <int KT, int NS>
-__host__ __device__ constexpr size_t staged_params_bytes()
-{
-    return ((size_t)NS * KT * 16 + 127) / 128 * 128;
-}
-// HALVES: 16-byte halves per entry (1 for 16-bit rows, 2 for FP32 rows).
-template <int KT, int NS, int HALVES>
-__host__ __device__ constexpr size_t staged_smem_bytes(int Wp)
-{
-    return 128 + 128 + staged_params_bytes<KT, NS>() + (size_t)NS * HALVES * 2 * KT * Wp * 16;
-}
 
 // CODES: the epilogue writes uint16 CT-number codes (out16) instead of FP32.
 template <int TXT, int TYT, int PX, int PY, int KT, int NS, typename T, bool PACKED, int MINB, bool CODES>

@@ -468,20 +468,48 @@ static fbp_status plan_items(const fbp_scan_item *items, int count, std::vector<
     return FBP_OK;
 }
 
-// Workspace: [256 B: queue counter] then, per item, its filtered rows and
-// (16-bit dtypes) its row scales, each 256-byte aligned.
-static size_t workspace_layout(const std::vector<ScanPlan> &plan, fbp_dtype dtype,
-                               std::vector<size_t> *filt_off, std::vector<size_t> *scale_off)
+// Padded table of an item that runs staged batch units (bp_staged_batch.cu):
+// the 90-degree orbit symmetry with 32 x 32 tiles and a window that fits.
+static bool staged_item(const ScanPlan &p, fbp_dtype dtype, StagedItemGeom *out)
 {
+    const fbp_geometry &g = p.gb;
+    return staged_batch_geometry(g.n_angles, g.angle_step, g.n_det, g.det_center, g.n,
+                                 g.pixel_size / g.det_spacing, dtype, out);
+}
+
+// Workspace: [256 B: two work-queue counters] then, per item, its filtered
+// rows, (16-bit dtypes) its row scales and (items that can run staged batch
+// units) its padded table, each 256-byte aligned; then (16-bit dtypes) one
+// float S per item.
+struct BatchLayout {
+    std::vector<size_t> filt, scale, table;   // table 0: the item has none
+    size_t smax = 0, total = 0;
+};
+
+static BatchLayout workspace_layout(const std::vector<ScanPlan> &plan, fbp_dtype dtype)
+{
+    BatchLayout L;
     size_t off = 256;
     for (const ScanPlan &p : plan) {
         const size_t rows = (size_t)p.gb.n_angles;
-        if (filt_off) filt_off->push_back(off);
+        L.filt.push_back(off);
         off += align256(rows * p.gb.n_det * dtype_size(dtype));
-        if (scale_off) scale_off->push_back(dtype == FBP_F32 ? 0 : off);
+        L.scale.push_back(dtype == FBP_F32 ? 0 : off);
         if (dtype != FBP_F32) off += align256(rows * 4);
+        StagedItemGeom sg;
+        if (staged_item(p, dtype, &sg)) {
+            L.table.push_back(off);
+            off += align256(sg.table_bytes);
+        } else {
+            L.table.push_back(0);
+        }
     }
-    return off;
+    if (dtype != FBP_F32) {
+        L.smax = off;
+        off += align256(plan.size() * 4);
+    }
+    L.total = off;
+    return L;
 }
 
 static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kind kind,
@@ -495,16 +523,19 @@ static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kin
         return fail(FBP_ERR_INVALID_ARG, "variant %d", bp_variant);
     if (order != FBP_ORDER_QUEUE && order != FBP_ORDER_GROUP_CYCLIC)
         return fail(FBP_ERR_INVALID_ARG, "order %d", order);
-    // default: the 64 x 64 orbit shape (FP32 rows: variant 8, 16-bit rows: the
-    // packed variant 10), generic tiles for items without the symmetry.  For
-    // batches of many smaller slices the 64 x 64 orbit beats the 32 x 32 one
-    // that single N = 8192 slices prefer (ragged workload: 512 vs 569 ms).
+    // the persistent tile kernel's shape (items that do not run staged batch
+    // units by default, every item when a variant is given): the 64 x 64
+    // orbit (FP32 rows: variant 8, 16-bit rows: the packed variant 10),
+    // generic tiles for items without the symmetry.  For batches of many
+    // smaller slices the 64 x 64 orbit beats the 32 x 32 one that single
+    // N = 8192 slices prefer (ragged workload: 512 vs 569 ms).
     const int variant = bp_variant >= 0 ? bp_variant : (dtype == FBP_F32 ? 8 : 10);
     BpPersistentShape shape;
     if (!bp_persistent_shape(variant, dtype, &shape))
         return fail(FBP_ERR_UNSUPPORTED, "variant %d is not available for ragged batches of this dtype", variant);
-    std::vector<size_t> foff, soff;
-    const size_t need = workspace_layout(plan, dtype, &foff, &soff);
+    const BatchLayout lay = workspace_layout(plan, dtype);
+    const std::vector<size_t> &foff = lay.filt, &soff = lay.scale;
+    const size_t need = lay.total;
     if (!workspace) return fail(FBP_ERR_WORKSPACE, "workspace is NULL");
     if (reinterpret_cast<uintptr_t>(workspace) & 255)
         return fail(FBP_ERR_WORKSPACE, "workspace is not 256-byte aligned");
@@ -559,16 +590,32 @@ static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kin
     }
     fa->count = count;
 
-    // backprojection descriptors.  An item whose geometry has the 90-degree
-    // symmetry runs orbit units (four tiles each), any other generic tiles.
-    // Queue: items by total cost K n^2, largest first.  Group-cyclic: by cost
-    // per unit, largest first, so every run of P consecutive units holds
-    // units of similar cost.
+    // backprojection.  By default (bp_variant -1) the items with a padded
+    // table run staged batch units (bp_staged_batch.cu: 90-degree orbits of
+    // 32 x 32 tiles, windows moved by bulk copies); the others -- and every
+    // item when a variant is given -- run the persistent tile kernel, where
+    // an item whose geometry has the 90-degree symmetry runs orbit units
+    // (four tiles each) and any other generic tiles.  Queue: items by total
+    // cost K n^2, largest first.  Group-cyclic: by cost per unit, largest
+    // first, so every run of P consecutive units holds units of similar cost.
+    std::vector<char> staged(count, 0);
+    std::vector<StagedItemGeom> sg(count);
+    if (bp_variant < 0)
+        for (int i = 0; i < count; ++i) staged[i] = lay.table[i] != 0 && staged_item(plan[i], dtype, &sg[i]);
     std::vector<int> orbit(count), tiles_x(count), H(count);
     std::vector<long long> n_units(count), unit_cost(count);
     for (int i = 0; i < count; ++i) {
         const fbp_geometry &g = plan[i].gb;
         const double alpha = g.pixel_size / g.det_spacing;
+        if (staged[i]) {
+            const int T = staged_batch_tile();
+            orbit[i] = 1;
+            tiles_x[i] = g.n / T / 2;
+            H[i] = sg[i].H;
+            n_units[i] = (long long)tiles_x[i] * tiles_x[i];
+            unit_cost[i] = 4LL * T * T * g.n_angles;
+            continue;
+        }
         orbit[i] = shape.orbit_tile > 0 &&
                    bp_orbit_geometry(g.n_angles, g.angle_step, g.n_det, g.det_center, g.n, shape.orbit_tile);
         if (orbit[i]) {
@@ -594,12 +641,54 @@ static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kin
     });
     auto *ba = new BpBatchArgs();
     std::unique_ptr<BpBatchArgs> ba_owner(ba);
-    long long units = 0;
-    int max_H = 0, max_H_orbit = 0;
+    auto *sa = new StagedBatchArgs();
+    std::unique_ptr<StagedBatchArgs> sa_owner(sa);
+    auto *sp = new StagedPrepArgs();
+    std::unique_ptr<StagedPrepArgs> sp_owner(sp);
+    long long units = 0, s_units = 0, s_pairs = 0;
+    int nb = 0, ns = 0, max_H = 0, max_H_orbit = 0, Wp = 8;
     for (int r = 0; r < count; ++r) {
         const int i = idx[r];
         const fbp_geometry &g = plan[i].gb;
-        BpBatchItem &b = ba->items[r];
+        if (staged[i]) {
+            StagedBatchItem &b = sa->items[ns];
+            StagedPrepItem &q = sp->items[ns];
+            ++ns;
+            float *smax = dtype == FBP_F32 ? nullptr : reinterpret_cast<float *>(ws + lay.smax) + i;
+            q.filt = ws + foff[i];
+            q.row_scale = dtype == FBP_F32 ? nullptr : reinterpret_cast<const float *>(ws + soff[i]);
+            q.table = ws + lay.table[i];
+            q.smax = smax;
+            q.K = g.n_angles;
+            q.D = g.n_det;
+            q.Ep = sg[i].Ep;
+            q.P_lo = sg[i].P_lo;
+            q.pair_begin = (int)s_pairs;
+            q.pad_ = 0;
+            b.table = q.table;
+            b.slice = plan[i].slice;
+            b.cs = cs[i];
+            b.smax = smax;
+            b.alpha = g.pixel_size / g.det_spacing;
+            b.det_center = g.det_center;
+            b.K2 = g.n_angles / 2;
+            b.N = g.n;
+            b.H = sg[i].H;
+            b.W = sg[i].W;
+            b.Ep = sg[i].Ep;
+            b.P_lo = sg[i].P_lo;
+            b.tiles_x = tiles_x[i];
+            b.unit_begin = (int)s_units;
+            b.scale = (float)g.angle_step;
+            b.pad_ = 0;
+            Wp = std::max(Wp, sg[i].Wp);
+            s_units += n_units[i];
+            s_pairs += g.n_angles / 2;
+            if (s_units > 0x7fffffffLL || s_pairs > 0x7fffffffLL)
+                return fail(FBP_ERR_UNSUPPORTED, "batch too large");
+            continue;
+        }
+        BpBatchItem &b = ba->items[nb++];
         b.filt = ws + foff[i];
         b.row_scale = dtype == FBP_F32 ? nullptr : reinterpret_cast<const float *>(ws + soff[i]);
         b.slice = plan[i].slice;
@@ -621,18 +710,32 @@ static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kin
         units += n_units[i];
         if (units > 0x7fffffffLL) return fail(FBP_ERR_UNSUPPORTED, "batch too large");
     }
-    ba->count = count;
+    const int cyclic = order == FBP_ORDER_GROUP_CYCLIC ? 1 : 0;
+    ba->count = nb;
     ba->total_units = (int)units;
     ba->max_H = max_H;
     ba->max_H_orbit = max_H_orbit;
-    ba->cyclic = order == FBP_ORDER_GROUP_CYCLIC ? 1 : 0;
+    ba->cyclic = cyclic;
     ba->counter = reinterpret_cast<int *>(ws);
     ba->status = status;
+    sa->count = ns;
+    sa->total_units = (int)s_units;
+    sa->Wp = Wp;
+    sa->cyclic = cyclic;
+    sa->counter = reinterpret_cast<int *>(ws) + 1;
+    sa->status = status;
+    sp->count = ns;
+    sp->total_pairs = (int)s_pairs;
 
-    if (!ba->cyclic) FBP_CUDA_TRY(cudaMemsetAsync(ws, 0, sizeof(int), stream));
+    if (!cyclic) FBP_CUDA_TRY(cudaMemsetAsync(ws, 0, 2 * sizeof(int), stream));
     st = launch_filter_batched(*fa, groups, dtype, stream);
     if (st != FBP_OK) return st;
-    return launch_bp_persistent(*ba, variant, dtype, stream);
+    if (ns > 0) {
+        st = launch_staged_batch(*sp, *sa, dtype, stream);
+        if (st != FBP_OK) return st;
+    }
+    if (nb > 0) return launch_bp_persistent(*ba, variant, dtype, stream);
+    return FBP_OK;
 }
 
 static fbp_status plan_plain(const fbp_batch_item *items, int count, std::vector<ScanPlan> *plan)
@@ -656,7 +759,15 @@ size_t fbp_batched_workspace_bytes(const fbp_batch_item *items, int count, fbp_d
     clear_error();
     std::vector<ScanPlan> plan;
     if (!dtype_ok(dtype) || plan_plain(items, count, &plan) != FBP_OK) return 0;
-    return workspace_layout(plan, dtype, nullptr, nullptr);
+    return workspace_layout(plan, dtype).total;
+}
+
+int fbp_batched_item_staged(const fbp_geometry *g, fbp_dtype dtype)
+{
+    clear_error();
+    if (!g || !dtype_ok(dtype) || check_geometry(g, false, true) != FBP_OK) return 0;
+    return staged_batch_geometry(g->n_angles, g->angle_step, g->n_det, g->det_center, g->n,
+                                 g->pixel_size / g->det_spacing, dtype, nullptr) ? 1 : 0;
 }
 
 fbp_status fbp_batched(const fbp_batch_item *items, int count, fbp_filter_kind kind,
@@ -676,7 +787,7 @@ size_t fbp_batched_scans_workspace_bytes(const fbp_scan_item *items, int count, 
     clear_error();
     std::vector<ScanPlan> plan;
     if (!dtype_ok(dtype) || plan_items(items, count, &plan) != FBP_OK) return 0;
-    return workspace_layout(plan, dtype, nullptr, nullptr);
+    return workspace_layout(plan, dtype).total;
 }
 
 fbp_status fbp_batched_scans(const fbp_scan_item *items, int count, fbp_filter_kind kind,

@@ -31,6 +31,7 @@ enum DeviceFault : unsigned {
     FAULT_LEAF = 5,           // patching: a quadtree leaf entry outside the slice
     FAULT_STREAM_WAIT = 6,    // streamed filter: a wait for its row copy ran past its cap
     FAULT_BP_STAGE_WAIT = 7,  // bulk-copy-fed backprojection: a wait for a window copy ran past its cap
+    FAULT_BP_WINDOW = 8,      // staged batch: a window outside its item's padded table (copy clamped)
 };
 fbp_status device_status_word(unsigned **out);   // current device
 

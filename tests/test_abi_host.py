@@ -7,6 +7,7 @@ import re
 
 import pytest
 
+from batch_layout import align256, staged_table_bytes
 from paper_2505_13955_gb300 import _lib
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -150,11 +151,32 @@ def test_batched_workspace_query_and_validation(L):
         items[i].g = L.fbp_geometry_default(K, D, N)
     n32 = L.fbp_batched_workspace_bytes(items, 3, 0)
     n16 = L.fbp_batched_workspace_bytes(items, 3, 1)
-    raw32 = sum(K * D * 4 for K, D, _ in dims)
-    raw16 = sum(K * D * 2 + K * 4 for K, D, _ in dims)
-    assert raw32 + 256 <= n32 <= raw32 + 256 + 3 * 255
-    assert raw16 + 256 <= n16 <= raw16 + 256 + 6 * 255
-    assert n32 % 256 == 0
+    # counters, then per item its rows, (16-bit) row scales and padded table,
+    # then (16-bit) one S per item
+    for i in range(3):
+        assert L.fbp_batched_item_staged(ctypes.byref(items[i].g), 0) == 1
+    t32 = [staged_table_bytes(K, D, N, f32=True) for K, D, N in dims]
+    t16 = [staged_table_bytes(K, D, N, f32=False) for K, D, N in dims]
+    assert n32 == 256 + sum(align256(K * D * 4) + t for (K, D, _), t in zip(dims, t32))
+    assert n16 == 256 + sum(align256(K * D * 2) + align256(K * 4) + t for (K, D, _), t in zip(dims, t16)) + 256
+    # the tables: between the unpadded K/2 x (D + 1) entries and the rows' 6x
+    for (K, D, N), t in zip(dims, t32):
+        assert K // 2 * (D + 1) * 32 <= t <= 6 * K * D * 4
+    # items without staged units keep the rows-only layout
+    for i, (K, D, N) in enumerate(dims):
+        items[i].g = L.fbp_geometry_default(K + 1, D, N)          # odd K: no orbit symmetry
+        assert L.fbp_batched_item_staged(ctypes.byref(items[i].g), 0) == 0
+    raw32 = sum(align256((K + 1) * D * 4) for K, D, _ in dims)
+    assert L.fbp_batched_workspace_bytes(items, 3, 0) == 256 + raw32
+    for i, (K, D, N) in enumerate(dims):
+        items[i].g = L.fbp_geometry_default(K, D, N)
+    # a window wider than 72 entries (pixel / bin ratio 1.6), and no geometry
+    wide = L.fbp_geometry_default(720, 512, 512)
+    wide.pixel_size = 1.6
+    assert L.fbp_batched_item_staged(ctypes.byref(wide), 0) == 0
+    wide.pixel_size = 1.45
+    assert L.fbp_batched_item_staged(ctypes.byref(wide), 1) == 1
+    assert L.fbp_batched_item_staged(None, 0) == 0
     # count limits and NULL pointers
     assert L.fbp_batched_workspace_bytes(items, 0, 0) == 0
     assert L.fbp_batched_workspace_bytes(items, 257, 0) == 0

@@ -1,6 +1,7 @@
-"""GPU parity: fbp_batched (one filter launch + one persistent backprojection
-launch over a ragged batch) -- bit-identical per item to the same slice run
-alone through fbp_filter + fbp_backproject with the same tile shape, within
+"""GPU parity: fbp_batched (one filter launch + persistent backprojection
+launches over a ragged batch) -- bit-identical per item to the same slice run
+alone through fbp_filter + fbp_backproject (or fbp_backproject_staged, for
+the items the default runs as staged units) with the same shape, within
 tolerance of the oracle, and replayable from a captured CUDA graph."""
 import numpy as np
 import pytest
@@ -52,30 +53,98 @@ def test_batched_bit_identical_to_single_slices(variant, kind):
     assert api.device_status() == 0
 
 
-@pytest.mark.parametrize("variant", [-1, 8, 10, 11])
+def staged_shape(dtype):
+    """The fbp_backproject_staged shape of the default's staged batch units."""
+    return 0 if dtype == torch.float32 else 5
+
+
+def single_default(api, s, g, kind="ramlak", dtype=torch.float32):
+    """The single-slice run a batch item under the default equals: the staged
+    kernel's 32 x 32 shape where fbp_batched_item_staged accepts the item,
+    else the persistent tile kernel's variant (8 for FP32 rows, packed 10
+    for 16-bit rows) or its generic fallback."""
+    if api.batched_item_staged(g, dtype):
+        filt, rs = api.filter(s, g, kind=kind, dtype=dtype)
+        return api.backproject_staged(filt, g, rs, shape=staged_shape(dtype)), "staged"
+    v = item_shape(api, 8 if dtype == torch.float32 else 10, g, dtype)
+    return api.fbp(s, g, kind=kind, dtype=dtype, variant=v), v
+
+
+@pytest.mark.parametrize("variant", [8, 10, 11])
 @pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
 def test_batched_16bit_orbits_bit_identical_to_single_slices(variant, dtype):
     """16-bit rows: packed and unpacked orbit units in the persistent kernel
-    equal the single-slice kernels of the same shape (the default is 10)."""
+    equal the single-slice kernels of the same shape."""
     api = fbp_api()
     sinos, geoms = ragged(api, DIMS, seed=50)
     outs = api.fbp_batched(sinos, geoms, dtype=dtype, variant=variant)
     torch.cuda.synchronize()
     for s, g, o in zip(sinos, geoms, outs):
-        v = item_shape(api, 10 if variant < 0 else variant, g, dtype)
+        v = item_shape(api, variant, g, dtype)
         single = api.fbp(s, g, dtype=dtype, variant=v)
         assert torch.equal(o, single), f"K={g.n_angles} N={g.n} ran variant {v}"
     assert api.device_status() == 0
 
 
-def test_batched_default_uses_orbits_and_packed_needs_16bit_rows():
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("kind", ["ramlak", "shepp_logan"])
+def test_batched_default_bit_identical_to_single_slices(dtype, kind):
+    """The default: items with the orbit symmetry (n a multiple of 64) run
+    staged units and equal fbp_backproject_staged with the 32 x 32 shape;
+    the others run the persistent tile kernel (orbit variant 8 / packed 10,
+    or its generic fallback)."""
     api = fbp_api()
     sinos, geoms = ragged(api, DIMS, seed=70)
-    outs = api.fbp_batched(sinos, geoms)                  # FP32 default: orbit variant 8
+    outs = api.fbp_batched(sinos, geoms, kind=kind, dtype=dtype)
+    torch.cuda.synchronize()
+    ran = []
     for s, g, o in zip(sinos, geoms, outs):
-        assert torch.equal(o, api.fbp(s, g, variant=item_shape(api, 8, g)))
+        single, how = single_default(api, s, g, kind, dtype)
+        ran.append(how)
+        assert torch.equal(o, single), f"K={g.n_angles} N={g.n} ran {how}"
+    assert ran.count("staged") == 3 and len(ran) - ran.count("staged") == 5
+    assert api.device_status() == 0
+
+
+# pixel / bin ratios below and above 1 and detectors narrower and wider than
+# the image: windows of the corner orbits reach far past the detector, into
+# the padding of the item's table
+PADDING_GEOMS = [dict(n_angles=100, n_det=80, n=128, pixel_size=1.3),
+                 dict(n_angles=72, n_det=200, n=128, pixel_size=0.7),
+                 dict(n_angles=36, n_det=33, n=64, pixel_size=1.45),
+                 dict(n_angles=180, n_det=256, n=192)]
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+def test_batched_staged_padding_bit_identical(dtype):
+    api = fbp_api()
+    gen = torch.Generator(device="cuda").manual_seed(31)
+    geoms = [api.Geometry(**kw) for kw in PADDING_GEOMS]
+    assert all(api.batched_item_staged(g, dtype) for g in geoms)
+    sinos = [torch.randn((g.n_angles, g.n_det), device="cuda", generator=gen) for g in geoms]
+    for order in ("queue", "group_cyclic"):
+        scans = [api.Scan(g) for g in geoms]
+        outs = api.fbp_batched_scans(sinos, scans, dtype=dtype, order=order)
+        torch.cuda.synchronize()
+        for s, g, o in zip(sinos, geoms, outs):
+            single, how = single_default(api, s, g, dtype=dtype)
+            assert how == "staged"
+            assert torch.equal(o, single), f"{order}: K={g.n_angles} D={g.n_det} N={g.n} alpha={g.pixel_size}"
+    assert api.device_status() == 0
+
+
+def test_batched_packed_needs_16bit_rows_and_wide_windows_fall_back():
+    api = fbp_api()
+    sinos, geoms = ragged(api, DIMS, seed=70)
     with pytest.raises(api.FbpError, match="UNSUPPORTED"):
         api.fbp_batched(sinos, geoms, variant=10)         # packed: 16-bit rows only
+    # a window wider than the staged batch allows (pixel / bin ratio 1.6):
+    # the default runs the item in the persistent tile kernel
+    g = api.Geometry(64, 128, 128, pixel_size=1.6)
+    assert not api.batched_item_staged(g) and api.batched_item_staged(api.Geometry(64, 128, 128))
+    s = torch.randn((64, 128), device="cuda")
+    out = api.fbp_batched([s], [g])[0]
+    assert torch.equal(out, api.fbp(s, g, variant=item_shape(api, 8, g)))
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
@@ -146,9 +215,11 @@ def test_ragged_workload_sample_vs_oracle():
     outs = api.fbp_batched(sinos, geoms)
     rng = np.random.default_rng(1)
     for s, g, o in zip(sinos, geoms, outs):
-        # every item of this workload has the symmetry: the default orbit shape
-        assert api.variant_supports(8, g)
-        assert torch.equal(o, api.fbp(s, g, variant=8))
+        # every item of this workload has the symmetry with n a multiple of
+        # 64: the default runs it as staged 32 x 32 orbit units
+        assert api.batched_item_staged(g)
+        single, how = single_default(api, s, g)
+        assert how == "staged" and torch.equal(o, single)
         go = oracle.Geometry(g.n_angles, g.n_det, g.n)
         q = oracle.filter(to_np(s))
         rows = rng.integers(0, g.n, 300)

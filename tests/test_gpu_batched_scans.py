@@ -50,6 +50,37 @@ def test_mixed_batch_equals_single_scans(order):
         assert torch.equal(outs[i], ref), f"item {i} differs from the single-scan path"
 
 
+@pytest.mark.parametrize("order", ["queue", "group_cyclic"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
+def test_mixed_batch_default_equals_single_scans(order, dtype):
+    """The default: normal and folded offset items with the orbit symmetry
+    (n a multiple of 64) run staged units and equal fbp_backproject_staged
+    (32 x 32 shape) on the item's filtered rows; unfolded offset items and
+    the others run the persistent kernel's orbit variant 8 / packed 10 or its
+    generic fallback."""
+    api = fbp_api()
+    sinos, scans, _ = mixed_items(api, SPECS, 350)
+    outs = api.fbp_batched_scans(sinos, scans, dtype=dtype, order=order)
+    assert api.device_status() == 0
+    staged = 0
+    for i, (s, sc) in enumerate(zip(sinos, scans)):
+        if sc.overlap:
+            filt, rs, gv = api.filter_offset(s, sc.g, sc.overlap, sc.fold, dtype=dtype)
+        else:
+            gv = sc.g
+            filt, rs = api.filter(s, gv, dtype=dtype)
+        if api.batched_item_staged(gv, dtype):
+            staged += 1
+            ref = api.backproject_staged(filt, gv, rs, shape=0 if dtype == torch.float32 else 5)
+        else:
+            v = 8 if dtype == torch.float32 else 10
+            if not api.variant_supports(v, gv, dtype):
+                v = 0
+            ref = api.backproject(filt, gv, row_scale=rs, variant=v)
+        assert torch.equal(outs[i], ref), f"item {i}"
+    assert staged == 3      # items 0, 3, 4: folded offset scans and a normal scan with n % 64 == 0
+
+
 def test_mixed_batch_matches_oracle():
     api = fbp_api()
     sinos, scans, raw = mixed_items(api, SPECS[:5], 400)

@@ -598,3 +598,54 @@ def test_staged_shared_layout_fits_and_aligns(halves, shape, alpha, raw_offset):
     assert KT * 2 * W * 16 * halves < (1 << 20)
     if alpha == 1.0 and minb is not None:
         assert minb * (size + 1024) <= 228 * 1024, f"{minb} blocks of {size} bytes"
+
+
+# Staged ragged batches (bp_staged_batch.cu): every window copy of every
+# orbit unit stays inside its item's padded table, for the ragged workload's
+# sizes and for pixel/bin ratios and detector widths that push the corner
+# windows far past the detector.
+BATCH_GEOMS = [(720, 512, 512, 1.0), (1800, 1024, 1024, 1.0), (3600, 4096, 4096, 1.0),
+               (100, 80, 128, 1.3), (72, 200, 128, 0.7), (36, 33, 64, 1.45), (180, 256, 192, 1.0),
+               (360, 700, 1024, 1.5), (64, 2, 256, 0.05)]
+
+
+@pytest.mark.parametrize("K,D,N,alpha", BATCH_GEOMS)
+def test_staged_batch_windows_inside_padded_tables(K, D, N, alpha):
+    """The first entry e of each window (floor(v) - H + 1 + P_lo, with v the
+    tile centre's detector coordinate formed in FP64 as the kernel forms it)
+    satisfies 0 <= e <= Ep - W for both windows of every angle pair and every
+    orbit base tile; the copies' sources and sizes are 16-byte multiples and
+    the stage buffers hold the window pitch at the occupancy the launch
+    asks for."""
+    from batch_layout import staged_item_geom
+    geom = staged_item_geom(K, D, N, alpha)
+    assert geom is not None
+    H, W, Wp, P_lo, Ep = geom
+    c_d = 0.5 * (D - 1)
+    m = 0.5 * (N - 1)
+    t = np.arange(0, N // 2, 32, dtype=np.float64) + 15.5 - m       # base tile centres (one axis)
+    Xc, Yc = np.meshgrid(t, t)
+    Xc, Yc = Xc.ravel(), Yc.ravel()
+    th = np.arange(K // 2) * (np.pi / K)
+    worst_lo, worst_hi = 1 << 30, -(1 << 30)
+    for k in range(K // 2):
+        c, s = alpha * np.cos(th[k]), alpha * np.sin(th[k])
+        v1 = c * Xc + (s * Yc + c_d)
+        v2 = -s * Xc + (c * Yc + c_d)
+        for v in (v1, v2):
+            e = np.floor(v).astype(np.int64) - H + 1 + P_lo
+            worst_lo = min(worst_lo, int(e.min()))
+            worst_hi = max(worst_hi, int(e.max()))
+    assert worst_lo >= 0 and worst_hi <= Ep - W, (worst_lo, worst_hi, Ep - W)
+    # at least one entry of margin on the side the geometry reaches
+    assert worst_lo >= 1 or worst_hi <= Ep - W - 1
+    # every real segment [-1, D-1] is in the padded row
+    assert P_lo + D + 1 <= Ep
+    # copies: W entries of 16 bytes from 16-byte entries; shared layout
+    assert (W * 16) % 16 == 0 and Wp % 8 == 0 and W <= Wp <= 72
+    for KT, halves in ((4, 2), (8, 1)):
+        size = staged_smem_bytes(KT, 2, halves, Wp)
+        assert KT * 2 * W * 16 * halves < (1 << 20)
+        assert 5 * (size + 1024) <= 228 * 1024
+        if alpha <= 1.0:
+            assert 6 * (size + 1024) <= 228 * 1024

@@ -7,6 +7,7 @@ import math
 import pytest
 
 import oracle
+from batch_layout import align256, staged_table_bytes
 from paper_2505_13955_gb300 import _lib
 
 
@@ -89,10 +90,20 @@ def test_batched_scans_validate_before_any_cuda_call(L):
     items[1].g = L.fbp_geometry_default(90, 64, 64)
     items[1].overlap = 0.0
     n = L.fbp_batched_scans_workspace_bytes(items, 2, 0)
-    # counter block, then 180 folded rows of the virtual detector, then 90 x 64 rows
-    n_v = oracle.offset_virtual(64, 10.0, 6.0)[0]
+    # counter block, then 180 folded rows of the virtual detector and their
+    # padded table (a centred half turn: staged units), then 90 x 64 rows
+    # and theirs
+    n_v, c_v = oracle.offset_virtual(64, 10.0, 6.0)[:2]
     assert n_v == 107
-    assert n == 256 + ((180 * n_v * 4 + 255) // 256) * 256 + 90 * 64 * 4
+    gv = _lib.CGeometry()
+    off = ctypes.c_int(0)
+    o = _lib.COffsetScan(6.0, 1)
+    assert L.fbp_offset_geometry(ctypes.byref(items[0].g), ctypes.byref(o), ctypes.byref(gv), ctypes.byref(off)) == 0
+    assert L.fbp_batched_item_staged(ctypes.byref(gv), 0) == 1
+    t0 = staged_table_bytes(180, n_v, 64, det_center=c_v, angle_step=2 * math.pi / 360)
+    t1 = staged_table_bytes(90, 64, 64)
+    assert t0 > 0 and t1 > 0
+    assert n == 256 + align256(180 * n_v * 4) + t0 + 90 * 64 * 4 + t1
     ws = ctypes.c_void_p(0x100000)
     assert L.fbp_batched_scans(items, 2, 0, 0, -1, 7, ws, n, None) == _lib.FBP_ERR_INVALID_ARG   # order
     assert L.fbp_batched_scans(items, 2, 0, 0, -1, 1, ws, n - 1, None) == _lib.FBP_ERR_WORKSPACE
