@@ -939,8 +939,12 @@ def run_ragged(args) -> None:
         api.prepare(g, kind=w.filter, device=dev)
     tdt = getattr(torch, DT[args.dtype])
     outs = [torch.empty((g.n, g.n), device=dev) for g in geoms]
-    tuned = autotune.tune_batched(sinos, geoms, tdt, kind=w.filter) if args.variant < 0 else \
-        {"variant": args.variant}
+    if args.variant >= 0:
+        tuned = {"variant": args.variant}
+    elif args.autotune:
+        tuned = autotune.tune_batched(sinos, geoms, tdt, kind=w.filter)
+    else:
+        tuned = {"variant": -1}                     # the library's batch default, untuned
     variant = tuned["variant"]
     n_staged = sum(api.batched_item_staged(g, tdt) for g in geoms) if variant < 0 else 0
     wsp = torch.empty(api.batched_workspace_bytes(sinos, outs, geoms, tdt), dtype=torch.uint8, device=dev)
@@ -1362,6 +1366,9 @@ def main(argv=None):
     ap.add_argument("--all-dtypes", action=argparse.BooleanOptionalAction, default=True,
                     help="also time FP16- and BF16-staged rows in the same run")
     ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
+                    help="ragged batch with --variant -1: pick the backprojection by the autotuner "
+                         "(--no-autotune: the library's batch default)")
     ap.add_argument("--fwd-variant", type=int, default=-1,
                     help="radon_forward kernel for the refinement workload (-1 = default)")
     ap.add_argument("--slices", type=int, default=None,

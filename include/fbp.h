@@ -439,9 +439,10 @@ int fbp_bp_variant_supports(int variant, fbp_dtype dtype, const fbp_geometry *g)
  *              rows; the size does not depend on bp_variant).
  *   bp_variant -1 = default: the items that fbp_batched_item_staged accepts
  *              run in one persistent launch of staged units (90-degree orbits
- *              of four 32 x 32 tiles whose windows are moved by bulk copies
- *              from their padded tables; each such slice is bit-identical to
- *              fbp_backproject_staged with shape 0 for FP32 rows, shape 5 for
+ *              of four tiles, 32 x 32 for FP32 rows and 64 x 64 for 16-bit
+ *              rows, whose windows are moved by bulk copies from their padded
+ *              tables; each such slice is bit-identical to
+ *              fbp_backproject_staged with shape 0 for FP32 rows, shape 1 for
  *              16-bit rows), the others in the persistent tile kernel with
  *              variant 8 (FP32 rows) or 10 (16-bit rows).  A tile variant
  *              (fbp_bp_variant_info) runs every item in the persistent tile
@@ -465,11 +466,12 @@ fbp_status fbp_batched(const fbp_batch_item *items, int count,
                        void *workspace, size_t ws_bytes, fbp_stream_t stream);
 
 /* 1 if a batch item whose filtered rows have geometry g and dtype runs
- * staged units under fbp_batched's default (the 90-degree symmetry with
- * n a multiple of 64, and a backprojection window of at most 72 detector
- * segments: pixel_size / det_spacing up to about 1.5), 0 otherwise; for an
- * offset item of fbp_batched_scans pass its virtual geometry
- * (fbp_offset_geometry).  Host-only, no CUDA call. */
+ * staged units under fbp_batched's default, 0 otherwise: the 90-degree
+ * symmetry with n a multiple of twice the dtype's tile (FP32 rows: 64,
+ * 16-bit rows: 128) and a backprojection window of at most 72 (FP32) / 104
+ * (16-bit) detector segments, i.e. pixel_size / det_spacing up to about 1.5
+ * (FP32) / 1.1 (16-bit).  For an offset item of fbp_batched_scans pass its
+ * virtual geometry (fbp_offset_geometry).  Host-only, no CUDA call. */
 int fbp_batched_item_staged(const fbp_geometry *g, fbp_dtype dtype);
 
 /*

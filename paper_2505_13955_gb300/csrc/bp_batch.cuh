@@ -52,8 +52,9 @@ struct FilterBatchArgs {
     int count;
 };
 
-// Staged ragged batches (bp_staged_batch.cu): orbit units of 32 x 32 tiles
-// fed by plain bulk copies from per-item padded tables.
+// Staged ragged batches (bp_staged_batch.cu): orbit units (32 x 32 tiles for
+// FP32 rows, 64 x 64 for 16-bit rows) fed by plain bulk copies from per-item
+// padded tables.
 struct StagedBatchItem {        // 88 bytes
     const void *table;          // padded table (16-bit: [K/2][Ep]; FP32: planes a, b of [K/2][Ep])
     float *slice;               // [N][N] output
@@ -61,7 +62,7 @@ struct StagedBatchItem {        // 88 bytes
     const float *smax;          // 16-bit rows: the item's S (written by the table pass); FP32: null
     double alpha, det_center;
     int K2, N, H, W, Ep, P_lo;  // angle pairs, image side, half-window, window, padded row, padding
-    int tiles_x, unit_begin;    // orbits per row (N / 64), first unit of this item
+    int tiles_x, unit_begin;    // orbits per row (N / (2 tile)), first unit of this item
     float scale;                // angle_step
     int pad_;
 };
@@ -99,11 +100,12 @@ struct StagedItemGeom {
     int H, W, Wp, P_lo, Ep;
     size_t table_bytes;
 };
-// true if the item can run staged batch units (the orbit symmetry with 32 x
-// 32 tiles, a window of at most 72 entries); fills *out.  Host only.
+// true if the item can run staged batch units (the orbit symmetry with the
+// dtype's tile, a window of at most 72 (FP32) / 104 (16-bit) entries); fills
+// *out.  Host only.
 bool staged_batch_geometry(int K, double angle_step, int D, double det_center, int N, double alpha,
                            fbp_dtype dtype, StagedItemGeom *out);
-int staged_batch_tile();
+int staged_batch_tile(fbp_dtype dtype);
 fbp_status launch_staged_batch(const StagedPrepArgs &p, StagedBatchArgs &a, fbp_dtype dtype, cudaStream_t s);
 
 fbp_status launch_bp_persistent(BpBatchArgs &a, int variant, fbp_dtype dtype, cudaStream_t s);

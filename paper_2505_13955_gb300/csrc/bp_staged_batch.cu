@@ -15,13 +15,14 @@
 //     16-bit rows: [K/2][Ep] 16-byte entries
 //     FP32 rows:   plane a [K/2][Ep], then plane b [K/2][Ep] (the two 16-byte
 //                  halves of the 32-byte midpoint/slope entry)
-// One persistent launch runs orbit units (four 32 x 32 tiles) of every such
-// item, taken from an atomic counter or in group-cyclic order.  The stage
-// ring, the entries, the per-pair arithmetic and the epilogue are
-// fbp_backproject_staged's (bp_staged.cuh), so every item's slice is
-// bit-identical to fbp_backproject_staged with the same shape (FP32 rows:
-// shape 0, 16-bit rows: shape 5).  Stages are numbered per block across its
-// units, so each buffer's mbarrier parity follows from that running count.
+// One persistent launch runs orbit units (four tiles: 32 x 32 for FP32
+// rows, 64 x 64 for 16-bit rows) of every such item, taken from an atomic
+// counter or in group-cyclic order.  The stage ring, the entries, the
+// per-pair arithmetic and the epilogue are fbp_backproject_staged's
+// (bp_staged.cuh), so every item's slice is bit-identical to
+// fbp_backproject_staged with the same shape (FP32 rows: shape 0, 16-bit
+// rows: shape 1).  Stages are numbered per block across its units, so each
+// buffer's mbarrier parity follows from that running count.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -33,8 +34,8 @@
 namespace fbp {
 namespace {
 
-constexpr int kSbTile = 32;          // orbit tile side
-constexpr int kSbMaxWp = 72;         // widest padded window (entries) an item may have
+constexpr int sb_tile(fbp_dtype dtype) { return dtype == FBP_F32 ? 32 : 64; }
+constexpr int sb_max_wp(fbp_dtype dtype) { return dtype == FBP_F32 ? 72 : 104; }
 
 // 16-bit rows: S of each item, the largest row scale (1 if none is positive),
 // as fbp_backproject_staged forms it per slice.
@@ -90,18 +91,22 @@ __global__ void __launch_bounds__(256) staged_batch_prep_kernel(const __grid_con
     }
 }
 
-// The persistent kernel: 128 threads, 32 x 32 orbit tiles of 2 x 4 pixels
-// per thread, KT angle pairs per stage, NS stage buffers.
-template <int KT, int NS, typename T, bool PACKED, int MINB>
-__global__ void __launch_bounds__(128, MINB) bp_staged_batch_kernel(const __grid_constant__ StagedBatchArgs a)
+// The persistent kernel: TXT x TYT threads, orbit tiles of PX x PY pixels
+// per thread, KT angle pairs per stage, NS stage buffers.  Thread 0 takes
+// each unit and publishes its item, tile origin and FP64 tile centre in
+// shared memory; the item's fields are read from the kernel parameters where
+// they are used (the issuing warp reads most of them once per stage), so that
+// the pair loop keeps its registers.
+template <int TXT, int TYT, int PX, int PY, int KT, int NS, typename T, bool PACKED, int MINB>
+__global__ void __launch_bounds__(TXT *TYT, MINB) bp_staged_batch_kernel(const __grid_constant__ StagedBatchArgs a)
 {
-    constexpr int TXT = 16, TYT = 8, PX = 2, PY = 4;
-    constexpr int NW = 4, TILE = kSbTile, WX = TXT / 8;
+    constexpr int NW = TXT * TYT / 32, TILE = TXT * PX, WX = TXT / 8;
     constexpr int HALVES = sizeof(T) == 4 ? 2 : 1;
-    static_assert(TXT * PX == TILE && TYT * PY == TILE, "32 x 32 tile");
-    static_assert(KT <= 32 && NS >= 2 && NS <= 4, "stage shape");
+    static_assert(TXT * PX == TYT * PY, "square tile");
+    static_assert(KT <= 32 && (NS == 2 || NS == 4), "stage shape");
     extern __shared__ unsigned char smem_raw[];
     __shared__ int s_unit;
+    __shared__ double s_xy[2];             // the unit's base tile centre (X, Y)
     const uint32_t raw_s = (uint32_t)__cvta_generic_to_shared(smem_raw);
     const uint32_t base_s = (raw_s + 127u) & ~127u;
     unsigned char *base = smem_raw + (base_s - raw_s);
@@ -130,36 +135,47 @@ __global__ void __launch_bounds__(128, MINB) bp_staged_batch_kernel(const __grid
     }
     __syncthreads();
 
-    unsigned long long gs = 0;     // stages this block has consumed, over all its units
+    // stages this block has consumed, over all its units; NS divides 2^32, so
+    // the buffer (g mod NS) and the parity (bit log2 NS of g) survive a wrap
+    unsigned gs = 0;
+    __shared__ int s_item, s_x0, s_y0;
     for (int iter = 0;; ++iter) {
-        int u;
-        if (a.cyclic) {
-            const long long uc = (long long)blockIdx.x + (long long)iter * gridDim.x;
-            u = uc < a.total_units ? (int)uc : a.total_units;
-        } else {
-            // (every thread has read the previous unit's number: the unit
-            // ends with a block barrier)
-            if (tid == 0) s_unit = atomicAdd(a.counter, 1);
-            __syncthreads();
-            u = s_unit;
+        // (every thread has read the previous unit's state: the unit ends
+        // with a block barrier)
+        if (tid == 0) {
+            int u;
+            if (a.cyclic) {
+                const long long uc = (long long)blockIdx.x + (long long)iter * gridDim.x;
+                u = uc < a.total_units ? (int)uc : a.total_units;
+            } else {
+                u = atomicAdd(a.counter, 1);
+            }
+            if (u < a.total_units && iter > a.total_units) {
+                atomicCAS(a.status, 0u, (unsigned)FAULT_QUEUE_CAP);
+                u = a.total_units;
+            }
+            s_unit = u;
+            if (u < a.total_units) {
+                int lo = 0, hi = a.count - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (a.items[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
+                }
+                const StagedBatchItem &it = a.items[lo];
+                const int t = u - it.unit_begin;
+                const int x0 = (t % it.tiles_x) * TILE, y0 = (t / it.tiles_x) * TILE;
+                const double m = 0.5 * (it.N - 1);
+                s_item = lo;
+                s_x0 = x0;
+                s_y0 = y0;
+                s_xy[0] = (double)x0 + 0.5 * (TILE - 1) - m;
+                s_xy[1] = (double)y0 + 0.5 * (TILE - 1) - m;
+            }
         }
-        if (u >= a.total_units) break;
-        if (iter > a.total_units) {
-            if (tid == 0) atomicCAS(a.status, 0u, (unsigned)FAULT_QUEUE_CAP);
-            break;
-        }
-        int lo = 0, hi = a.count - 1;
-        while (lo < hi) {
-            const int mid = (lo + hi + 1) >> 1;
-            if (a.items[mid].unit_begin <= u) lo = mid; else hi = mid - 1;
-        }
-        const StagedBatchItem &it = a.items[lo];
-        const int t = u - it.unit_begin;
-        const int x0 = (t % it.tiles_x) * TILE, y0 = (t / it.tiles_x) * TILE;
+        __syncthreads();
+        if (s_unit >= a.total_units) break;
+        const StagedBatchItem &it = a.items[s_item];
         const int K2 = it.K2, H = it.H, W = it.W, Ep = it.Ep, P_lo = it.P_lo;
-        const double m = 0.5 * (it.N - 1);
-        const double Xc = (double)x0 + 0.5 * (TILE - 1) - m;
-        const double Yc = (double)y0 + 0.5 * (TILE - 1) - m;
         const int n_stages = (K2 + KT - 1) / KT;
         const unsigned char *tab_a = static_cast<const unsigned char *>(it.table);
         const size_t plane = (size_t)K2 * Ep * 16;
@@ -175,8 +191,8 @@ __global__ void __launch_bounds__(128, MINB) bp_staged_batch_kernel(const __grid
                 if (lane < na) {
                     const double2 cs = it.cs[k0 + lane];
                     const double c = it.alpha * cs.x, s = it.alpha * cs.y;
-                    const double v1 = fma(c, Xc, fma(s, Yc, it.det_center));
-                    const double v2 = fma(-s, Xc, fma(c, Yc, it.det_center));
+                    const double v1 = fma(c, s_xy[0], fma(s, s_xy[1], it.det_center));
+                    const double v2 = fma(-s, s_xy[0], fma(c, s_xy[1], it.det_center));
                     const double jc1 = floor(v1), jc2 = floor(v2);
                     pv = make_float4((float)c, (float)s, (float)(v1 - jc1 - 0.5), (float)(v2 - jc2 - 0.5));
                     // first entry of each window: segment jc - H, padded
@@ -240,7 +256,7 @@ __global__ void __launch_bounds__(128, MINB) bp_staged_batch_kernel(const __grid
 
         bool ok = true;
         for (int tl = 0; tl < n_stages; ++tl) {
-            const unsigned long long g = gs + tl;
+            const unsigned g = gs + (unsigned)tl;
             const int b = (int)(g % NS);
             if (!staged_wait(full_s + 8u * b, (unsigned)((g / NS) & 1))) {
                 ok = false;
@@ -271,8 +287,10 @@ __global__ void __launch_bounds__(128, MINB) bp_staged_batch_kernel(const __grid
             last = __shfl_sync(0xffffffffu, last, 0);
             if (last && tl + NS < n_stages) issue(tl + NS, b);
         }
-        gs += (unsigned long long)n_stages;
-        // every warp is done with the buffers (the next unit refills them)
+        gs += (unsigned)n_stages;
+        const int x0 = s_x0, y0 = s_y0;
+        // every warp is done with the buffers and the unit's shared state
+        // (thread 0 rewrites both for the next unit)
         const bool failed = __syncthreads_or(!ok);
         if (failed) {
             // a wait ran out: record it, let every copy this block started land
@@ -289,11 +307,12 @@ __global__ void __launch_bounds__(128, MINB) bp_staged_batch_kernel(const __grid
     }
 }
 
-template <int KT, int NS, typename T, bool PACKED, int MINB>
-fbp_status launch_staged_batch_t(const StagedPrepArgs &p, StagedBatchArgs &a, cudaStream_t s)
+template <int TXT, int TYT, int PX, int PY, int KT, int NS, typename T, bool PACKED, int MINB>
+fbp_status launch_staged_batch_t(const StagedPrepArgs &p, StagedBatchArgs &a, fbp_dtype dtype, cudaStream_t s)
 {
     constexpr int HALVES = sizeof(T) == 4 ? 2 : 1;
-    if (a.Wp <= 0 || a.Wp > kSbMaxWp || a.Wp % 8 != 0)
+    static_assert(TXT * PX == (HALVES == 2 ? 32 : 64), "tile of the dtype");
+    if (a.Wp <= 0 || a.Wp > sb_max_wp(dtype) || a.Wp % 8 != 0)
         return fail(FBP_ERR_UNSUPPORTED, "staged batch window %d", a.Wp);
     if constexpr (sizeof(T) == 2) {
         staged_batch_scale_kernel<<<p.count, 256, 0, s>>>(p);
@@ -301,19 +320,19 @@ fbp_status launch_staged_batch_t(const StagedPrepArgs &p, StagedBatchArgs &a, cu
     }
     staged_batch_prep_kernel<T, PACKED><<<(unsigned)p.total_pairs, 256, 0, s>>>(p);
     FBP_CUDA_TRY(cudaGetLastError());
-    auto kern = bp_staged_batch_kernel<KT, NS, T, PACKED, MINB>;
+    auto kern = bp_staged_batch_kernel<TXT, TYT, PX, PY, KT, NS, T, PACKED, MINB>;
     const size_t smem = staged_smem_bytes<KT, NS, HALVES>(a.Wp);
     fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (st != FBP_OK) return st;
     int per_sm = 0;
-    st = blocks_per_sm(reinterpret_cast<const void *>(kern), 128, smem, &per_sm);
+    st = blocks_per_sm(reinterpret_cast<const void *>(kern), TXT * TYT, smem, &per_sm);
     if (st != FBP_OK) return st;
     if (per_sm < 1) return fail(FBP_ERR_UNSUPPORTED, "staged batch kernel does not fit on an SM");
     int dev = 0, sms = 0;
     FBP_CUDA_TRY(cudaGetDevice(&dev));
     FBP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     const int grid = std::max(1, std::min(sms * per_sm, a.total_units));
-    kern<<<grid, 128, smem, s>>>(a);
+    kern<<<grid, TXT * TYT, smem, s>>>(a);
     FBP_CUDA_TRY(cudaGetLastError());
     return FBP_OK;
 }
@@ -323,14 +342,15 @@ fbp_status launch_staged_batch_t(const StagedPrepArgs &p, StagedBatchArgs &a, cu
 bool staged_batch_geometry(int K, double angle_step, int D, double det_center, int N, double alpha,
                            fbp_dtype dtype, StagedItemGeom *out)
 {
-    if (!bp_orbit_geometry(K, angle_step, D, det_center, N, kSbTile)) return false;
+    const int T = sb_tile(dtype);
+    if (!bp_orbit_geometry(K, angle_step, D, det_center, N, T)) return false;
     if (!(alpha > 0.0) || !std::isfinite(alpha)) return false;
-    const int H = bp_window_half(alpha, kSbTile, kSbTile);
+    const int H = bp_window_half(alpha, T, T);
     const int W = 2 * H + 1, Wp = (W + 7) / 8 * 8;
-    if (H < 0 || Wp > kSbMaxWp) return false;
-    // |v - det_center| <= alpha * |(Xc, Yc)| <= alpha (N - 32) / sqrt 2 over
-    // the orbit base tiles (|Xc|, |Yc| <= (N - 32) / 2); slack for rounding
-    const double R = alpha * (N - kSbTile) / std::sqrt(2.0) * (1.0 + 1e-12) + 1e-6;
+    if (H < 0 || Wp > sb_max_wp(dtype)) return false;
+    // |v - det_center| <= alpha * |(Xc, Yc)| <= alpha (N - T) / sqrt 2 over
+    // the orbit base tiles (|Xc|, |Yc| <= (N - T) / 2); slack for rounding
+    const double R = alpha * (N - T) / std::sqrt(2.0) * (1.0 + 1e-12) + 1e-6;
     const double lo = std::floor(det_center - R), hi = std::floor(det_center + R);
     // first entry of a window: floor(v) - H + 1 + P_lo >= 0; its last:
     // floor(v) + H + 1 + P_lo <= Ep - 1; two entries of margin each side
@@ -349,18 +369,18 @@ bool staged_batch_geometry(int K, double angle_step, int D, double det_center, i
     return true;
 }
 
-int staged_batch_tile() { return kSbTile; }
+int staged_batch_tile(fbp_dtype dtype) { return sb_tile(dtype); }
 
-// FP32 rows: fbp_backproject_staged's shape 0 (4 pairs per stage, 2
-// buffers, six blocks per SM); 16-bit rows: its shape 5 (8 pairs, 2 buffers,
-// six blocks per SM).
+// FP32 rows: fbp_backproject_staged's shape 0 (32 x 32 orbits, 128 threads,
+// 4 pairs per stage, 2 buffers, six blocks per SM); 16-bit rows: its shape 1
+// (64 x 64 orbits, 256 threads, 16 pairs, 2 buffers, two blocks per SM).
 fbp_status launch_staged_batch(const StagedPrepArgs &p, StagedBatchArgs &a, fbp_dtype dtype, cudaStream_t s)
 {
     if (a.total_units <= 0 || p.count <= 0) return FBP_OK;
     switch (dtype) {
-        case FBP_F32: return launch_staged_batch_t<4, 2, float, false, 6>(p, a, s);
-        case FBP_F16: return launch_staged_batch_t<8, 2, __half, true, 6>(p, a, s);
-        case FBP_BF16: return launch_staged_batch_t<8, 2, __nv_bfloat16, true, 6>(p, a, s);
+        case FBP_F32: return launch_staged_batch_t<16, 8, 2, 4, 4, 2, float, false, 6>(p, a, dtype, s);
+        case FBP_F16: return launch_staged_batch_t<16, 16, 4, 4, 16, 2, __half, true, 2>(p, a, dtype, s);
+        case FBP_BF16: return launch_staged_batch_t<16, 16, 4, 4, 16, 2, __nv_bfloat16, true, 2>(p, a, dtype, s);
     }
     return fail(FBP_ERR_INVALID_ARG, "dtype");
 }

@@ -469,7 +469,7 @@ static fbp_status plan_items(const fbp_scan_item *items, int count, std::vector<
 }
 
 // Padded table of an item that runs staged batch units (bp_staged_batch.cu):
-// the 90-degree orbit symmetry with 32 x 32 tiles and a window that fits.
+// the 90-degree orbit symmetry with the dtype's tile and a window that fits.
 static bool staged_item(const ScanPlan &p, fbp_dtype dtype, StagedItemGeom *out)
 {
     const fbp_geometry &g = p.gb;
@@ -592,7 +592,8 @@ static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kin
 
     // backprojection.  By default (bp_variant -1) the items with a padded
     // table run staged batch units (bp_staged_batch.cu: 90-degree orbits of
-    // 32 x 32 tiles, windows moved by bulk copies); the others -- and every
+    // 32 x 32 (FP32) or 64 x 64 (16-bit) tiles, windows moved by bulk
+    // copies); the others -- and every
     // item when a variant is given -- run the persistent tile kernel, where
     // an item whose geometry has the 90-degree symmetry runs orbit units
     // (four tiles each) and any other generic tiles.  Queue: items by total
@@ -608,7 +609,7 @@ static fbp_status batched_impl(const std::vector<ScanPlan> &plan, fbp_filter_kin
         const fbp_geometry &g = plan[i].gb;
         const double alpha = g.pixel_size / g.det_spacing;
         if (staged[i]) {
-            const int T = staged_batch_tile();
+            const int T = staged_batch_tile(dtype);
             orbit[i] = 1;
             tiles_x[i] = g.n / T / 2;
             H[i] = sg[i].H;

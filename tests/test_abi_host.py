@@ -174,8 +174,14 @@ def test_batched_workspace_query_and_validation(L):
     wide = L.fbp_geometry_default(720, 512, 512)
     wide.pixel_size = 1.6
     assert L.fbp_batched_item_staged(ctypes.byref(wide), 0) == 0
-    wide.pixel_size = 1.45
-    assert L.fbp_batched_item_staged(ctypes.byref(wide), 1) == 1
+    wide.pixel_size = 1.45                                     # FP32 rows: 32 x 32 tiles, window 69
+    assert L.fbp_batched_item_staged(ctypes.byref(wide), 0) == 1
+    assert L.fbp_batched_item_staged(ctypes.byref(wide), 1) == 0   # 16-bit: 64 x 64 tiles, window 133
+    wide.pixel_size = 1.05
+    assert L.fbp_batched_item_staged(ctypes.byref(wide), 1) == 1   # window 99
+    odd = L.fbp_geometry_default(720, 512, 576)                # n = 9 x 64: FP32 only
+    assert L.fbp_batched_item_staged(ctypes.byref(odd), 0) == 1
+    assert L.fbp_batched_item_staged(ctypes.byref(odd), 2) == 0
     assert L.fbp_batched_item_staged(None, 0) == 0
     # count limits and NULL pointers
     assert L.fbp_batched_workspace_bytes(items, 0, 0) == 0

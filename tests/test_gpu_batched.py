@@ -54,13 +54,14 @@ def test_batched_bit_identical_to_single_slices(variant, kind):
 
 
 def staged_shape(dtype):
-    """The fbp_backproject_staged shape of the default's staged batch units."""
-    return 0 if dtype == torch.float32 else 5
+    """The fbp_backproject_staged shape of the default's staged batch units:
+    32 x 32 orbits for FP32 rows, 64 x 64 for 16-bit rows."""
+    return 0 if dtype == torch.float32 else 1
 
 
 def single_default(api, s, g, kind="ramlak", dtype=torch.float32):
     """The single-slice run a batch item under the default equals: the staged
-    kernel's 32 x 32 shape where fbp_batched_item_staged accepts the item,
+    kernel's shape where fbp_batched_item_staged accepts the item,
     else the persistent tile kernel's variant (8 for FP32 rows, packed 10
     for 16-bit rows) or its generic fallback."""
     if api.batched_item_staged(g, dtype):
@@ -89,10 +90,11 @@ def test_batched_16bit_orbits_bit_identical_to_single_slices(variant, dtype):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
 @pytest.mark.parametrize("kind", ["ramlak", "shepp_logan"])
 def test_batched_default_bit_identical_to_single_slices(dtype, kind):
-    """The default: items with the orbit symmetry (n a multiple of 64) run
-    staged units and equal fbp_backproject_staged with the 32 x 32 shape;
-    the others run the persistent tile kernel (orbit variant 8 / packed 10,
-    or its generic fallback)."""
+    """The default: items with the orbit symmetry (n a multiple of 64 for
+    FP32 rows, 128 for 16-bit rows) run staged units and equal
+    fbp_backproject_staged with the same shape; the others run the
+    persistent tile kernel (orbit variant 8 / packed 10, or its generic
+    fallback)."""
     api = fbp_api()
     sinos, geoms = ragged(api, DIMS, seed=70)
     outs = api.fbp_batched(sinos, geoms, kind=kind, dtype=dtype)
@@ -102,24 +104,31 @@ def test_batched_default_bit_identical_to_single_slices(dtype, kind):
         single, how = single_default(api, s, g, kind, dtype)
         ran.append(how)
         assert torch.equal(o, single), f"K={g.n_angles} N={g.n} ran {how}"
-    assert ran.count("staged") == 3 and len(ran) - ran.count("staged") == 5
+    n_staged = 3 if dtype == torch.float32 else 1          # n = 64, 64, 128 / n = 128
+    assert ran.count("staged") == n_staged and len(ran) == 8
     assert api.device_status() == 0
 
 
 # pixel / bin ratios below and above 1 and detectors narrower and wider than
 # the image: windows of the corner orbits reach far past the detector, into
 # the padding of the item's table
-PADDING_GEOMS = [dict(n_angles=100, n_det=80, n=128, pixel_size=1.3),
-                 dict(n_angles=72, n_det=200, n=128, pixel_size=0.7),
-                 dict(n_angles=36, n_det=33, n=64, pixel_size=1.45),
-                 dict(n_angles=180, n_det=256, n=192)]
+PADDING_GEOMS = {
+    torch.float32: [dict(n_angles=100, n_det=80, n=128, pixel_size=1.3),
+                    dict(n_angles=72, n_det=200, n=128, pixel_size=0.7),
+                    dict(n_angles=36, n_det=33, n=64, pixel_size=1.45),
+                    dict(n_angles=180, n_det=256, n=192)],
+    torch.float16: [dict(n_angles=100, n_det=80, n=256, pixel_size=1.05),
+                    dict(n_angles=72, n_det=200, n=128, pixel_size=0.7),
+                    dict(n_angles=36, n_det=40, n=128, pixel_size=1.08),
+                    dict(n_angles=180, n_det=300, n=256)],
+}
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
 def test_batched_staged_padding_bit_identical(dtype):
     api = fbp_api()
     gen = torch.Generator(device="cuda").manual_seed(31)
-    geoms = [api.Geometry(**kw) for kw in PADDING_GEOMS]
+    geoms = [api.Geometry(**kw) for kw in PADDING_GEOMS[dtype]]
     assert all(api.batched_item_staged(g, dtype) for g in geoms)
     sinos = [torch.randn((g.n_angles, g.n_det), device="cuda", generator=gen) for g in geoms]
     for order in ("queue", "group_cyclic"):
@@ -216,7 +225,7 @@ def test_ragged_workload_sample_vs_oracle():
     rng = np.random.default_rng(1)
     for s, g, o in zip(sinos, geoms, outs):
         # every item of this workload has the symmetry with n a multiple of
-        # 64: the default runs it as staged 32 x 32 orbit units
+        # 128: the default runs it as staged orbit units
         assert api.batched_item_staged(g)
         single, how = single_default(api, s, g)
         assert how == "staged" and torch.equal(o, single)

@@ -54,10 +54,10 @@ def test_mixed_batch_equals_single_scans(order):
 @pytest.mark.parametrize("dtype", [torch.float32, torch.bfloat16])
 def test_mixed_batch_default_equals_single_scans(order, dtype):
     """The default: normal and folded offset items with the orbit symmetry
-    (n a multiple of 64) run staged units and equal fbp_backproject_staged
-    (32 x 32 shape) on the item's filtered rows; unfolded offset items and
-    the others run the persistent kernel's orbit variant 8 / packed 10 or its
-    generic fallback."""
+    (n a multiple of 64 for FP32 rows, 128 for 16-bit rows) run staged units
+    and equal fbp_backproject_staged (32 x 32 / 64 x 64 shape) on the item's
+    filtered rows; unfolded offset items and the others run the persistent
+    kernel's orbit variant 8 / packed 10 or its generic fallback."""
     api = fbp_api()
     sinos, scans, _ = mixed_items(api, SPECS, 350)
     outs = api.fbp_batched_scans(sinos, scans, dtype=dtype, order=order)
@@ -71,14 +71,14 @@ def test_mixed_batch_default_equals_single_scans(order, dtype):
             filt, rs = api.filter(s, gv, dtype=dtype)
         if api.batched_item_staged(gv, dtype):
             staged += 1
-            ref = api.backproject_staged(filt, gv, rs, shape=0 if dtype == torch.float32 else 5)
+            ref = api.backproject_staged(filt, gv, rs, shape=0 if dtype == torch.float32 else 1)
         else:
             v = 8 if dtype == torch.float32 else 10
             if not api.variant_supports(v, gv, dtype):
                 v = 0
             ref = api.backproject(filt, gv, row_scale=rs, variant=v)
         assert torch.equal(outs[i], ref), f"item {i}"
-    assert staged == 3      # items 0, 3, 4: folded offset scans and a normal scan with n % 64 == 0
+    assert staged == 3      # items 0, 3, 4: folded offset scans and a normal scan, n = 128, 128, 256
 
 
 def test_mixed_batch_matches_oracle():

@@ -603,14 +603,19 @@ def test_staged_shared_layout_fits_and_aligns(halves, shape, alpha, raw_offset):
 # Staged ragged batches (bp_staged_batch.cu): every window copy of every
 # orbit unit stays inside its item's padded table, for the ragged workload's
 # sizes and for pixel/bin ratios and detector widths that push the corner
-# windows far past the detector.
-BATCH_GEOMS = [(720, 512, 512, 1.0), (1800, 1024, 1024, 1.0), (3600, 4096, 4096, 1.0),
-               (100, 80, 128, 1.3), (72, 200, 128, 0.7), (36, 33, 64, 1.45), (180, 256, 192, 1.0),
-               (360, 700, 1024, 1.5), (64, 2, 256, 0.05)]
+# windows far past the detector; FP32 rows run 32 x 32 tiles (4 pairs per
+# stage, two 16-byte halves, six blocks per SM), 16-bit rows 64 x 64 tiles
+# (16 pairs per stage, two blocks per SM).
+BATCH_GEOMS = [(True, 720, 512, 512, 1.0), (True, 1800, 1024, 1024, 1.0), (True, 3600, 4096, 4096, 1.0),
+               (True, 100, 80, 128, 1.3), (True, 72, 200, 128, 0.7), (True, 36, 33, 64, 1.45),
+               (True, 180, 256, 192, 1.0), (True, 360, 700, 1024, 1.5), (True, 64, 2, 256, 0.05),
+               (False, 720, 512, 512, 1.0), (False, 3600, 4096, 4096, 1.0), (False, 100, 80, 256, 1.05),
+               (False, 72, 200, 128, 0.7), (False, 36, 40, 128, 1.08), (False, 180, 300, 256, 1.0),
+               (False, 64, 2, 256, 0.05)]
 
 
-@pytest.mark.parametrize("K,D,N,alpha", BATCH_GEOMS)
-def test_staged_batch_windows_inside_padded_tables(K, D, N, alpha):
+@pytest.mark.parametrize("f32,K,D,N,alpha", BATCH_GEOMS)
+def test_staged_batch_windows_inside_padded_tables(f32, K, D, N, alpha):
     """The first entry e of each window (floor(v) - H + 1 + P_lo, with v the
     tile centre's detector coordinate formed in FP64 as the kernel forms it)
     satisfies 0 <= e <= Ep - W for both windows of every angle pair and every
@@ -618,12 +623,13 @@ def test_staged_batch_windows_inside_padded_tables(K, D, N, alpha):
     the stage buffers hold the window pitch at the occupancy the launch
     asks for."""
     from batch_layout import staged_item_geom
-    geom = staged_item_geom(K, D, N, alpha)
+    geom = staged_item_geom(K, D, N, alpha, f32=f32)
     assert geom is not None
     H, W, Wp, P_lo, Ep = geom
+    T = 32 if f32 else 64
     c_d = 0.5 * (D - 1)
     m = 0.5 * (N - 1)
-    t = np.arange(0, N // 2, 32, dtype=np.float64) + 15.5 - m       # base tile centres (one axis)
+    t = np.arange(0, N // 2, T, dtype=np.float64) + 0.5 * (T - 1) - m     # base tile centres (one axis)
     Xc, Yc = np.meshgrid(t, t)
     Xc, Yc = Xc.ravel(), Yc.ravel()
     th = np.arange(K // 2) * (np.pi / K)
@@ -642,10 +648,10 @@ def test_staged_batch_windows_inside_padded_tables(K, D, N, alpha):
     # every real segment [-1, D-1] is in the padded row
     assert P_lo + D + 1 <= Ep
     # copies: W entries of 16 bytes from 16-byte entries; shared layout
-    assert (W * 16) % 16 == 0 and Wp % 8 == 0 and W <= Wp <= 72
-    for KT, halves in ((4, 2), (8, 1)):
-        size = staged_smem_bytes(KT, 2, halves, Wp)
-        assert KT * 2 * W * 16 * halves < (1 << 20)
-        assert 5 * (size + 1024) <= 228 * 1024
-        if alpha <= 1.0:
-            assert 6 * (size + 1024) <= 228 * 1024
+    assert Wp % 8 == 0 and W <= Wp <= (72 if f32 else 104)
+    KT, halves, blocks = (4, 2, 6) if f32 else (16, 1, 2)
+    size = staged_smem_bytes(KT, 2, halves, Wp)
+    assert KT * 2 * W * 16 * halves < (1 << 20)
+    if f32 and alpha > 1.0:
+        blocks = 5
+    assert blocks * (size + 1024) <= 228 * 1024, (blocks, size)
