@@ -234,7 +234,7 @@ def peaks() -> dict:
 def bp_source_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("bp_tile.cuh", "bp_orbit.cuh", "backproject.cu", "bp_staged.cu"):
+    for f in ("bp_tile.cuh", "bp_orbit.cuh", "backproject.cu", "bp_staged.cuh", "bp_staged.cu"):
         with open(os.path.join(ROOT, "paper_2505_13955_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:16]
@@ -900,6 +900,21 @@ def batch_launches(api, rows_geoms, tdt, variant) -> int:
     return n
 
 
+def batch_roofline(api, dev, args, per_gpu_rate: float, variant: int) -> dict:
+    """Roofline of a batch line: the whole graph-replayed step (batched
+    filter, table pass and backprojection) against the backprojection
+    ceiling of the rows' dtype -- a lower bound of the backprojection
+    kernel's own fraction, which the step cannot time apart inside the
+    graph."""
+    smhz, sms, onchip = device_ceilings(dev)
+    rp = roofline_peak(smhz, args.dtype, sms, onchip)
+    kernel = ("bp_staged_batch_kernel (staged units) and bp_persistent_kernel" if variant < 0
+              else f"bp_persistent_kernel (variant {variant})")
+    return roofline_entry(per_gpu_rate, rp, kernel,
+                          achieved_basis="updates of the batch / graph-replayed step time (filter and table "
+                                         "pass included)")
+
+
 def default_backproject(api, f, g, r, o, staged_ws):
     """One slice's backprojection as the library's single-slice default path
     (api.fbp) runs it: the staged kernel where api.staged_preferred(g), else
@@ -1007,6 +1022,7 @@ def run_ragged(args) -> None:
                                                      "ms_per_step": ms_same,
                                                      "bp_variant": "each item's batch shape, one slice per launch"},
                  "clocks": clocks, "gpu_launches": batch_launches(api, geoms, tdt, variant) * args.steps})
+    line["roofline"] = batch_roofline(api, dev, args, rate / 1e9 / ws, variant)
     return line
 
 
@@ -1099,6 +1115,7 @@ def run_mixed(args) -> None:
                                                      "and the orbit geometry, else variant 7 / 5)"},
                  "speedup_vs_per_scan": ms_single / ms,
                  "clocks": clocks, "gpu_launches": batch_launches(api, rows_geoms, tdt, variant) * args.steps})
+    line["roofline"] = batch_roofline(api, dev, args, rate / 1e9 / ws, variant)
     return line
 
 

@@ -25,7 +25,11 @@ def test_autotune_single_and_batched(tmp_path, monkeypatch):
     sinos = [torch.randn((30, 64), device="cuda"), torch.randn((50, 96), device="cuda")]
     geoms = [api.Geometry(30, 64, 64), api.Geometry(50, 96, 96)]
     rb = autotune.tune_batched(sinos, geoms, reps=1)
-    assert not api.bp_variants()[rb["variant"]]["symmetric"]
+    # the default (-1: staged units where an item allows them) and every
+    # persistent shape but the texture and packed ones were timed
+    cands = [-1] + [v["variant"] for v in api.bp_variants() if not v["texture"] and not v["packed16"]]
+    assert sorted(int(k) for k in rb["times_ms"]) == sorted(cands)
+    assert rb["variant"] in cands
     outs = api.fbp_batched(sinos, geoms, variant=rb["variant"])
     assert all(torch.isfinite(o).all() for o in outs)
     data = json.load(open(tmp_path / "tune.json"))
