@@ -62,6 +62,7 @@ SHARED_BYTES_PER_CLK = 128      # nominal shared-memory load bandwidth per SM
 SAMPLES_PER_UPDATE = 2          # linear interpolation reads two detector samples
 BP_KERNEL_REGEX = "bp_kernel|bp_orbit_kernel"
 BP_STAGED_REGEX = "bp_staged_kernel"
+GRAPH_BELOW_UPDATES = 1e9     # uniform steps smaller than this are replayed from a CUDA graph
 
 
 def roofline_peak(sm_mhz: float, dtype: str, sms: int, onchip: dict | None = None) -> dict:
@@ -549,6 +550,7 @@ def run_uniform(args) -> None:
     stream = torch.cuda.current_stream(dev)
     api.prepare(g, kind=w.filter, device=dev)
     updates = S * N * N * K
+    use_graph = args.graph == "on" or (args.graph == "auto" and updates < GRAPH_BELOW_UPDATES)
     dtypes = [args.dtype] + ([d for d in ("f16", "bf16") if d != args.dtype] if args.all_dtypes else [])
     results = {}
     for dt in dtypes:
@@ -562,26 +564,64 @@ def run_uniform(args) -> None:
             if staged else None
         T = Timed(stream, args.steps, args.warmup, n_events=3)
 
-        def step(evs):
-            if evs:
-                evs[0].record(stream)
+        def filter_only():
             api.filter(sino, g, kind=w.filter, dtype=tdt, out=filt, row_scale=rs)
-            if evs:
-                evs[1].record(stream)
+
+        def bp_only():
             if staged:
                 api.backproject_staged(filt, g, rs, out=out, workspace=wsp)
             else:
                 api.backproject(filt, g, row_scale=rs, out=out, variant=args.variant)
+
+        def step(evs):
+            if evs:
+                evs[0].record(stream)
+            filter_only()
+            if evs:
+                evs[1].record(stream)
+            bp_only()
             if evs:
                 evs[2].record(stream)
 
-        ms = T.run(step, dev.index if dt == args.dtype else None)
+        clocks_at = dev.index if dt == args.dtype else None
+        ms = T.run(step, None if use_graph else clocks_at)
         assert api.device_status() == 0
+        res = {"bp_ms": T.between(1, 2), "filter_ms": T.between(0, 1), "step_spread": T.spread(0, 2),
+               "clocks": T.clocks}
+        if use_graph:
+            # a step this short is bound by the host's launch path: the step,
+            # the filter alone and the backprojection alone are each captured
+            # once in a CUDA graph and replayed (all work stays in every step)
+            eager = {"ms_per_step": ms, "bp_ms_per_step": res["bp_ms"], "filter_ms_per_step": res["filter_ms"]}
+            gs = torch.cuda.Stream(dev)
+            graphs = []
+            for fn in (lambda: step(None), filter_only, bp_only):
+                gr = torch.cuda.CUDAGraph()
+                with torch.cuda.graph(gr, stream=gs):
+                    fn()
+                graphs.append(gr)
+            with torch.cuda.stream(gs):
+                Tg = Timed(gs, args.steps, args.warmup, n_events=2)
+
+                def replay(evs):
+                    if evs:
+                        evs[0].record(gs)
+                    graphs[0].replay()
+                    if evs:
+                        evs[1].record(gs)
+
+                ms = Tg.run(replay, clocks_at)
+                f_ms = Timed(gs, args.steps, 1).run(lambda _: graphs[1].replay(), None)
+                b_ms = Timed(gs, args.steps, 1).run(lambda _: graphs[2].replay(), None)
+            torch.cuda.synchronize()
+            assert api.device_status() == 0
+            res = {"bp_ms": b_ms, "filter_ms": f_ms, "step_spread": Tg.spread(0, 1), "clocks": Tg.clocks,
+                   "eager": eager}
+            del graphs
         per_rank = allgather_floats([ms, float(updates)])
         rate, ms_step = aggregate([r[0] for r in per_rank], [int(r[1]) for r in per_rank])
-        results[dt] = {"value": rate / 1e9, "ms_per_step": ms_step, "bp_ms": T.between(1, 2),
-                       "filter_ms": T.between(0, 1), "step_spread": T.spread(0, 2), "clocks": T.clocks,
-                       "slices_per_s": S * len(per_rank) / (ms_step / 1e3), "staged": staged}
+        results[dt] = dict(res, value=rate / 1e9, ms_per_step=ms_step,
+                           slices_per_s=S * len(per_rank) / (ms_step / 1e3), staged=staged)
         if staged:
             # the block-staged orbit kernel on the same rows, for comparison
             To = Timed(stream, 3, 3)
@@ -642,7 +682,9 @@ def run_uniform(args) -> None:
         "l2": "inputs larger than L2 (sinograms per step exceed 129 MB), no flush"
               if S * K * N * 4 > 129e6 else "inputs smaller than L2 (launch-bound case)",
         "parallelism": f"slices sharded over {ws} GPU(s), no collective",
-        "bp_variant": variant})
+        "bp_variant": variant,
+        "launch": "CUDA-graph replay of the step (filter + backprojection), eager timings in 'eager'"
+                  if use_graph else "eager launches"})
     line.update({
         "slices_per_s": main["slices_per_s"],
         "bp_ms_per_step": main["bp_ms"], "filter_ms_per_step": main["filter_ms"],
@@ -657,6 +699,8 @@ def run_uniform(args) -> None:
         # filter, backprojection (+ the table pass of the staged path)
         "gpu_launches": (3 if main["staged"] else 2) * args.steps,
     })
+    if "eager" in main:
+        line["eager"] = main["eager"]
     for dt in dtypes[1:]:
         r = results[dt]
         rpd = roofline_peak(sm_max, dt, sms, onchip)
@@ -1383,6 +1427,9 @@ def main(argv=None):
     ap.add_argument("--all-dtypes", action=argparse.BooleanOptionalAction, default=True,
                     help="also time FP16- and BF16-staged rows in the same run")
     ap.add_argument("--variant", type=int, default=-1)
+    ap.add_argument("--graph", choices=["auto", "on", "off"], default="auto",
+                    help="uniform stacks: replay each step from a CUDA graph (auto: steps under "
+                         f"{GRAPH_BELOW_UPDATES:.0e} updates, which the host's launch path would bound)")
     ap.add_argument("--autotune", action=argparse.BooleanOptionalAction, default=True,
                     help="ragged batch with --variant -1: pick the backprojection by the autotuner "
                          "(--no-autotune: the library's batch default)")

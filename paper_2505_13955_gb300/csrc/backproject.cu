@@ -56,6 +56,7 @@ struct BpArgs {
     int H, W;
     int tiles_x;
     int slice_base;
+    int parts;                 // orbit kernels: blocks (a cluster) per orbit, each a share of the angle pairs
     unsigned *status;
 };
 
@@ -90,13 +91,17 @@ __global__ void __launch_bounds__(TXT *TYT) bp_kernel(BpArgs a)
     bp_tile<TXT, TYT, PX, PY, KT, T, CHECKED>(j, bp_smem);
 }
 
-template <int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED, bool PACKED, int MINB>
+// SPLIT: a.parts blocks per orbit, launched as clusters of a.parts blocks
+// along x; block part p of the cluster sums angle pairs [p K2 / P, (p+1) K2 / P).
+template <int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED, bool PACKED, int MINB,
+          bool SPLIT = false>
 __global__ void __launch_bounds__(TXT *TYT, MINB) bp_orbit_kernel(BpArgs a)
 {
     extern __shared__ __align__(16) unsigned char bp_smem[];
     constexpr int TILE = TXT * PX;
     const int half = a.tiles_x;                 // orbits per row of the top-left quadrant
-    const int o = blockIdx.x;
+    const int P = SPLIT ? a.parts : 1;
+    const int o = blockIdx.x / P, part = blockIdx.x - o * P;
     const int sl = a.slice_base + blockIdx.y;
     BpOrbitJob j;
     const size_t kd = (size_t)a.K * a.D;
@@ -118,8 +123,40 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_orbit_kernel(BpArgs a)
     j.W = a.W;
     j.x0 = (o % half) * TILE;
     j.y0 = (o / half) * TILE;
+    j.kb = (int)((long long)part * (a.K / 2) / P);
+    j.ke = (int)((long long)(part + 1) * (a.K / 2) / P);
     j.status = a.status;
-    bp_orbit<TILE, TXT, TYT, PX, PY, KT, T, CHECKED, PACKED>(j, bp_smem);
+    bp_orbit<TILE, TXT, TYT, PX, PY, KT, T, CHECKED, PACKED, SPLIT>(j, bp_smem);
+}
+
+// Blocks per orbit for the default path's split launch: when a slice has
+// fewer than half as many orbits as the GPU holds resident blocks, its angle
+// pairs are shared among up to 16 blocks (one cluster), each with at least
+// one stage.  The count depends on the geometry and the device only, so a
+// slice gets the same sums whatever the number of slices in the call.
+int orbit_split_parts(long long orbits, int K2, int KT, long long resident)
+{
+    if (orbits <= 0 || orbits * 2 >= resident) return 1;
+    long long P = std::min(16LL, resident / (2 * orbits));
+    P = std::min(P, (long long)((K2 + KT - 1) / KT));
+    return (int)std::max(P, 1LL);
+}
+
+fbp_status device_sm_count(int *out)
+{
+    static std::mutex mu;
+    static std::map<int, int> counts;
+    int dev = 0;
+    FBP_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = counts.find(dev);
+    if (it == counts.end()) {
+        int sms = 0;
+        FBP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        it = counts.emplace(dev, sms).first;
+    }
+    *out = it->second;
+    return FBP_OK;
 }
 
 template <int V, typename T>
@@ -163,8 +200,63 @@ fbp_status launch_orbit_shape(const BpLaunch &L, cudaStream_t s, unsigned *statu
     fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (st != FBP_OK) return st;
     a.tiles_x = L.N / TILE / 2;
+    a.parts = 1;
     const long long orbits = (long long)a.tiles_x * a.tiles_x;
     if (orbits > INT_MAX) return fail(FBP_ERR_UNSUPPORTED, "too many tiles");
+    if (L.split) {
+        int sms = 0;
+        st = device_sm_count(&sms);
+        if (st != FBP_OK) return st;
+        int parts = orbit_split_parts(orbits, L.K / 2, sd.kt, (long long)sms * sd.minb);
+        if (parts > 1) {
+            // clusters of `parts` blocks per orbit, partial sums reduced in shared memory
+            auto skern = bp_orbit_kernel<sd.txt, sd.tyt, sd.px, sd.py, sd.kt, T, kChecked, kPacked, sd.minb, true>;
+            const size_t ssmem = std::max(smem, bp_orbit_split_bytes<sd.txt, sd.tyt, sd.px, sd.py>());
+            st = ensure_dynamic_smem(reinterpret_cast<const void *>(skern), ssmem);
+            if (st != FBP_OK) return st;
+            if (parts > 8) {
+                // above the portable 8: allowed per kernel, capped by what the
+                // device schedules (asked once per device, kernel and shared
+                // memory size, so that a call being captured only launches)
+                static std::mutex mu;
+                static std::map<std::pair<int, size_t>, int> max_cluster;
+                int dev = 0;
+                FBP_CUDA_TRY(cudaGetDevice(&dev));
+                std::lock_guard<std::mutex> lock(mu);
+                auto it = max_cluster.find(std::make_pair(dev, ssmem));
+                if (it == max_cluster.end()) {
+                    FBP_CUDA_TRY(cudaFuncSetAttribute(reinterpret_cast<const void *>(skern),
+                                                      cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+                    cudaLaunchConfig_t q = {};
+                    q.gridDim = dim3(16, 1);
+                    q.blockDim = dim3(sd.txt * sd.tyt);
+                    q.dynamicSmemBytes = ssmem;
+                    int maxc = 0;
+                    FBP_CUDA_TRY(cudaOccupancyMaxPotentialClusterSize(&maxc, skern, &q));
+                    it = max_cluster.emplace(std::make_pair(dev, ssmem), maxc).first;
+                }
+                if (it->second < parts) parts = std::max(std::min(it->second, 8), 1);
+            }
+            a.parts = parts;
+            for (int base = 0; base < L.S; base += 65535) {
+                a.slice_base = base;
+                cudaLaunchConfig_t cfg = {};
+                cfg.gridDim = dim3((unsigned)(orbits * parts), (unsigned)std::min(65535, L.S - base));
+                cfg.blockDim = dim3(sd.txt * sd.tyt);
+                cfg.dynamicSmemBytes = ssmem;
+                cfg.stream = s;
+                cudaLaunchAttribute attr[1];
+                attr[0].id = cudaLaunchAttributeClusterDimension;
+                attr[0].val.clusterDim.x = (unsigned)parts;
+                attr[0].val.clusterDim.y = 1;
+                attr[0].val.clusterDim.z = 1;
+                cfg.attrs = attr;
+                cfg.numAttrs = 1;
+                FBP_CUDA_TRY(cudaLaunchKernelEx(&cfg, skern, a));
+            }
+            return FBP_OK;
+        }
+    }
     for (int base = 0; base < L.S; base += 65535) {
         a.slice_base = base;
         dim3 grid((unsigned)orbits, (unsigned)std::min(65535, L.S - base));
@@ -305,6 +397,8 @@ __global__ void __launch_bounds__(GTX *GTY, MINB) bp_persistent_kernel(BpBatchAr
                 j.W = 2 * it.H + 1;
                 j.x0 = (t % it.tiles_x) * OTILE;
                 j.y0 = (t / it.tiles_x) * OTILE;
+                j.kb = 0;
+                j.ke = it.K / 2;
                 j.status = a.status;
                 bp_orbit<OTILE, OTX, OTY, OPX, OPY, OKT, T, false, PACKED>(j, bp_smem);
                 continue;
@@ -514,15 +608,20 @@ int bp_default_variant(const BpLaunch &L)
 fbp_status launch_backproject(const BpLaunch &L, int variant, cudaStream_t s)
 {
     if (L.S <= 0) return FBP_OK;
-    if (variant < 0) variant = bp_default_variant(L);
+    // the default path may split small slices' angle pairs across clusters
+    BpLaunch Ld = L;
+    if (variant < 0) {
+        variant = bp_default_variant(L);
+        Ld.split = 1;
+    }
     if (variant == kTextureVariant) return launch_backproject_texture(L, s);
     unsigned *status = nullptr;
     fbp_status st = device_status_word(&status);
     if (st != FBP_OK) return st;
     switch (L.dtype) {
-        case FBP_F32: return launch_variant<float>(L, variant, s, status);
-        case FBP_F16: return launch_variant<__half>(L, variant, s, status);
-        case FBP_BF16: return launch_variant<__nv_bfloat16>(L, variant, s, status);
+        case FBP_F32: return launch_variant<float>(Ld, variant, s, status);
+        case FBP_F16: return launch_variant<__half>(Ld, variant, s, status);
+        case FBP_BF16: return launch_variant<__nv_bfloat16>(Ld, variant, s, status);
     }
     return fail(FBP_ERR_INVALID_ARG, "dtype");
 }

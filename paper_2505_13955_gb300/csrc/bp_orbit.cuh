@@ -48,6 +48,7 @@ struct BpOrbitJob {
     int accumulate;
     int H, W;
     int x0, y0;                // origin of the orbit's representative tile (top-left quadrant)
+    int kb, ke;                // angle pairs [kb, ke) of this block (0, K/2 unless split)
     unsigned *status;
 };
 
@@ -343,8 +344,28 @@ __device__ __forceinline__ void orbit_store(const float (&acc)[4][PY][PX], float
 // rows (the interpolated value is rounded once to the 16-bit type before the
 // FP32 accumulation), and both windows' coordinates are formed with packed
 // FP32 pair instructions.
+//
+// SPLIT: the block is one of the P blocks of a thread-block cluster that
+// share the orbit, each summing the angle pairs [kb, ke) of its part.  The
+// partial sums go to each block's shared memory; after a cluster barrier the
+// block of rank r adds, for the entries e = r, r + P, ... of every thread,
+// the P partial sums in rank order (distributed shared memory reads) and
+// stores the pixel; a second cluster barrier keeps every block's shared
+// memory alive until the others have read it.  The sum is deterministic and
+// does not depend on the number of slices in the launch.
+template <int TXT, int TYT, int PX, int PY>
+__host__ __device__ constexpr size_t bp_orbit_split_bytes()
+{
+    return (size_t)4 * PY * PX * TXT * TYT * sizeof(float);
+}
+
+__device__ __forceinline__ void cluster_sync_all()
+{
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
 template <int TILE, int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED,
-          bool PACKED = false>
+          bool PACKED = false, bool SPLIT = false>
 __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *smem)
 {
     constexpr int NT = TXT * TYT;
@@ -398,8 +419,8 @@ __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *sme
 #pragma unroll
             for (int ix = 0; ix < PX; ++ix) acc[o][iy][ix] = 0.f;
 
-    for (int k0 = 0; k0 < K2; k0 += KT) {
-        const int na = min(KT, K2 - k0);
+    for (int k0 = j.kb; k0 < j.ke; k0 += KT) {
+        const int na = min(KT, j.ke - k0);
         __syncthreads();
         if (tid < KT) {
             float4 pv = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -490,8 +511,46 @@ __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *sme
         }
     }
 
-    orbit_store<TXT, TYT, PX, PY>(acc, j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, N, j.x0 + tx, j.y0 + ty,
-                                  j.scale * S);
+    if constexpr (!SPLIT) {
+        orbit_store<TXT, TYT, PX, PY>(acc, j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, N, j.x0 + tx,
+                                      j.y0 + ty, j.scale * S);
+    } else {
+        constexpr int E = 4 * PY * PX;                 // entries per thread
+        __syncthreads();                               // the staging buffers are free
+        float *mine = reinterpret_cast<float *>(smem); // [E][NT]
+#pragma unroll
+        for (int o = 0; o < 4; ++o)
+#pragma unroll
+            for (int iy = 0; iy < PY; ++iy)
+#pragma unroll
+                for (int ix = 0; ix < PX; ++ix) mine[((o * PY + iy) * PX + ix) * NT + tid] = acc[o][iy][ix];
+        cluster_sync_all();
+        uint32_t rank, parts;
+        asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+        asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(parts));
+        const uint32_t base = (uint32_t)__cvta_generic_to_shared(mine) + 4u * (uint32_t)tid;
+        const float gain = j.scale * S;
+        const int c0 = j.x0 + tx, r0 = j.y0 + ty;
+        for (int e = (int)rank; e < E; e += (int)parts) {
+            float v = 0.f;
+            for (uint32_t p = 0; p < parts; ++p) {
+                uint32_t ra;
+                float x;
+                asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(base + 4u * (uint32_t)(e * NT)), "r"(p));
+                asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(x) : "r"(ra) : "memory");
+                v += x;
+            }
+            // entry e = (o, iy, ix): the member's pixel, as orbit_store places it
+            const int ix = e % PX, iy = (e / PX) % PY, o = e / (PX * PY);
+            const int r = r0 + TYT * iy, c = c0 + TXT * ix;
+            const size_t idx = o == 0 ? (size_t)r * N + c
+                             : o == 1 ? (size_t)c * N + (N - 1 - r)
+                             : o == 2 ? (size_t)(N - 1 - r) * N + (N - 1 - c)
+                                      : (size_t)(N - 1 - c) * N + r;
+            store_pixel(j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, idx, v * gain);
+        }
+        cluster_sync_all();
+    }
 }
 
 }  // namespace fbp

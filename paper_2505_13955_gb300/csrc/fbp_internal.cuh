@@ -137,10 +137,13 @@ struct BpLaunch {
     fbp_dtype dtype;
     unsigned short *slice16 = nullptr;   // uint16 CT-number codes instead of `slice`
     float hu_a = 0.f, hu_b = 0.f;        // code = clamp(rint(RN(RN(hu_a * mu) + hu_b)))
+    int split = 0;                       // orbit kernels may split small slices' angle pairs (default path)
 };
 fbp_status launch_backproject(const BpLaunch &a, int variant, cudaStream_t s);
 bool bp_orbit_eligible(const BpLaunch &a, int tile);
 bool bp_variant_fits(int variant, const BpLaunch &a);   // geometry + shared-memory budget
+int orbit_split_parts(long long orbits, int K2, int KT, long long resident);
+fbp_status device_sm_count(int *out);                    // current device, cached
 int bp_default_variant(const BpLaunch &a);
 int bp_variant_count();
 bool bp_variant_shape(int v, fbp_bp_shape *out);
