@@ -523,13 +523,13 @@ fbp_status fbp_batched_scans(const fbp_scan_item *items, int count,
  * load / FBP computation / store pipeline, Sec. V-A(c), on one GPU).  The
  * stack is cut into chunks of `chunk` slices; chunk i runs on internal stream
  * i mod n_streams: copy in, fbp_filter (fbp_filter_counts when pre != NULL),
- * the backprojection with scale = angle_step -- fbp_backproject_staged
- * where the geometry has the orbit symmetry with n a multiple of 64 and at
- * least 1024, the
- * output is FP32 and bp_variant is -1, else fbp_backproject_variant, or
- * fbp_backproject_u16 when window != NULL -- copy out, so the copies of one
- * chunk run while another chunk's kernels do.  The results equal those calls
- * on device buffers.
+ * the backprojection with scale = angle_step -- where bp_variant is -1 and
+ * the geometry has the orbit symmetry with n a multiple of 64 and at least
+ * 1024, fbp_backproject_staged (FP32 out) or fbp_backproject_staged_u16
+ * (window != NULL), else fbp_backproject_variant or fbp_backproject_u16 --
+ * copy out, so the copies of one chunk run while another chunk's kernels
+ * do.  The results equal those calls on device buffers.  The internal
+ * streams are kept per device between calls (created on first need).
  *   sino_host   HOST, float [n_slices][K][D]: line integrals, or detector
  *               counts when pre != NULL.  Pinned memory (cudaHostAlloc or
  *               cudaHostRegister) lets the copies overlap; pageable memory

@@ -10,10 +10,14 @@
 // stream i mod n_streams -- copy in, filter, backproject, copy out -- each
 // stream with its own buffers in the caller's workspace, so one stream's
 // copies run while another's kernels do.  Every step is a call of the
-// library's own device entry points on the chunk (fbp_backproject_staged,
-// with the chunk's tables in the stream's buffers, where the geometry has
-// the orbit symmetry and the output is FP32).
+// library's own device entry points on the chunk (fbp_backproject_staged or,
+// for uint16 codes, fbp_backproject_staged_u16, with the chunk's tables in the
+// stream's buffers, where the geometry has the orbit symmetry).  The internal
+// streams and the start event come from a per-device pool, so a call on a
+// small stack does not pay for creating and destroying them.
 #include <cstdint>
+#include <map>
+#include <mutex>
 #include <vector>
 
 #include "bp_batch.cuh"
@@ -37,13 +41,65 @@ struct HostLayout {
 
 // Slices whose geometry has the orbit symmetry (n a multiple of 64, at least
 // 1024: smaller slices are launch-bound, and the table pass costs more than
-// it saves) and whose output is FP32 backproject through
-// fbp_backproject_staged: each stream's buffers then include one chunk's
-// tables.
-bool host_staged(const fbp_geometry &g, bool codes)
+// it saves) backproject through fbp_backproject_staged (FP32 out) or
+// fbp_backproject_staged_u16 (codes out): each stream's buffers then include
+// one chunk's tables.
+bool host_staged(const fbp_geometry &g, bool)
 {
-    return !codes && g.n % 64 == 0 && g.n >= 1024 &&
+    return g.n % 64 == 0 && g.n >= 1024 &&
            bp_orbit_geometry(g.n_angles, g.angle_step, g.n_det, g.det_center, g.n, 32);
+}
+
+// Internal streams and start events, kept per device and handed to one call
+// at a time (a call takes what it needs from the free list and returns it).
+struct HostResources {
+    std::vector<cudaStream_t> streams;
+    cudaEvent_t ready = nullptr;
+};
+std::mutex g_pool_mu;
+std::map<int, std::vector<HostResources>> g_pool;
+
+cudaError_t take_resources(int used, HostResources *out)
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    {
+        std::lock_guard<std::mutex> lock(g_pool_mu);
+        std::vector<HostResources> &free = g_pool[dev];
+        for (size_t i = 0; i < free.size(); ++i) {
+            if ((int)free[i].streams.size() >= used) {
+                *out = free[i];
+                free.erase(free.begin() + (long)i);
+                return cudaSuccess;
+            }
+        }
+    }
+    HostResources r;
+    e = cudaEventCreateWithFlags(&r.ready, cudaEventDisableTiming);
+    for (int i = 0; i < used && e == cudaSuccess; ++i) {
+        cudaStream_t s = nullptr;
+        e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+        if (e == cudaSuccess) r.streams.push_back(s);
+    }
+    if (e != cudaSuccess) {
+        for (cudaStream_t s : r.streams) cudaStreamDestroy(s);
+        if (r.ready) cudaEventDestroy(r.ready);
+        return e;
+    }
+    *out = r;
+    return cudaSuccess;
+}
+
+void give_back(const HostResources &r)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return;
+    }
+    std::lock_guard<std::mutex> lock(g_pool_mu);
+    g_pool[dev].push_back(r);
 }
 
 HostLayout host_layout(const fbp_geometry &g, fbp_dtype dtype, int chunk, bool codes)
@@ -122,21 +178,15 @@ extern "C" fbp_status fbp_host(const float *sino_host, void *slice_host, const f
     const size_t K = (size_t)g->n_angles, D = (size_t)g->n_det, N = (size_t)g->n;
     const size_t in_slice = K * D * sizeof(float);
     const size_t out_slice = N * N * (codes ? 2 : 4);
-    std::vector<cudaStream_t> streams(used, nullptr);
-    cudaEvent_t ready = nullptr;
-    auto cleanup = [&]() {
-        for (cudaStream_t s : streams)
-            if (s) cudaStreamDestroy(s);
-        if (ready) cudaEventDestroy(ready);
-    };
-    cudaError_t e = cudaEventCreateWithFlags(&ready, cudaEventDisableTiming);
-    for (int i = 0; i < used && e == cudaSuccess; ++i)
-        e = cudaStreamCreateWithFlags(&streams[i], cudaStreamNonBlocking);
+    HostResources res;
+    cudaError_t e = take_resources(used, &res);
+    if (e != cudaSuccess) return cuda_fail(e, "fbp_host: streams");
+    const std::vector<cudaStream_t> streams(res.streams.begin(), res.streams.begin() + used);
     // the pipeline starts after the work already enqueued on the caller's stream
-    if (e == cudaSuccess) e = cudaEventRecord(ready, stream);
-    for (int i = 0; i < used && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(streams[i], ready, 0);
+    e = cudaEventRecord(res.ready, stream);
+    for (int i = 0; i < used && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(streams[i], res.ready, 0);
     if (e != cudaSuccess) {
-        cleanup();
+        give_back(res);
         return cuda_fail(e, "fbp_host: streams");
     }
 
@@ -162,7 +212,10 @@ extern "C" fbp_status fbp_host(const float *sino_host, void *slice_host, const f
                  : fbp_filter(d_in, d_filt, d_scale, dtype, kind, g, n, s);
         if (st != FBP_OK) break;
         const float scale = (float)g->angle_step;
-        if (codes)
+        if (codes && l.table && bp_variant < 0)
+            st = fbp_backproject_staged_u16(d_filt, d_scale, dtype, static_cast<unsigned short *>(d_out), g, n,
+                                            scale, window, -1, base + l.in + l.filt + l.scale + l.out, l.table, s);
+        else if (codes)
             st = fbp_backproject_u16(d_filt, d_scale, dtype, static_cast<unsigned short *>(d_out), g, n, scale,
                                      window, bp_variant, s);
         else if (l.table && bp_variant < 0)
@@ -180,6 +233,6 @@ extern "C" fbp_status fbp_host(const float *sino_host, void *slice_host, const f
         const cudaError_t se = cudaStreamSynchronize(s);
         if (se != cudaSuccess && st == FBP_OK) st = cuda_fail(se, "fbp_host: synchronise");
     }
-    cleanup();
+    give_back(res);
     return st;
 }

@@ -42,6 +42,24 @@ def test_fbp_host_counts_to_codes_equals_device_calls():
     assert torch.equal(out, ref)
 
 
+def test_fbp_host_staged_codes_equal_the_device_path():
+    """n >= 1024 with the orbit symmetry: fbp_host takes the staged kernel
+    for codes as for FP32 slices, as the device path (fbp_counts) does."""
+    api = fbp_api()
+    rng = np.random.default_rng(13)
+    S, K, N = 3, 90, 1024
+    counts = torch.from_numpy(rng.poisson(5e3, (S, K, N)).astype(np.float32)).pin_memory()
+    g = api.Geometry(K, N, N)
+    pre = api.Preprocess(flat_value=1e4, count_floor=1.0, mu_scale=float(N), blur_sigma=1.0)
+    win = api.HuWindow(0.5, 0.0, -1000.0, 3000.0)
+    assert api.staged_preferred(g)
+    out = api.fbp_host(counts, g, pre=pre, window=win, chunk=2, n_streams=2)
+    ref = api.fbp_counts(counts.cuda(), g, pre, window=win).cpu()
+    assert torch.equal(out, ref)
+    # and again: the pooled internal streams give the same result
+    assert torch.equal(api.fbp_host(counts, g, pre=pre, window=win, chunk=1, n_streams=3), ref)
+
+
 def test_fbp_host_refusals():
     api = fbp_api()
     L = api.lib()
