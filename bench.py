@@ -1348,7 +1348,13 @@ def run_gd(args) -> None:
                  # backprojection's per-update accounting (one pixel-angle pair)
                  "roofline": roofline_entry(a_rate, rp, "fwd_tile_kernel" if fwd_variant else "fwd_strip_kernel"),
                  "refine_50": refine,
-                 "eta": eta, "clocks": T.clocks, "gpu_launches": 2 * args.steps})
+                 "eta": eta, "clocks": T.clocks,
+                 # the forward projector, then A^T: the staged table pass and kernel
+                 # (one pass over the stack) where staged_preferred, else one kernel
+                 "gpu_launches": (3 if api.staged_preferred(g) and api.staged_chunk(g, torch.float32, S) >= S
+                                  else 2) * args.steps,
+                 "adjoint_kernel": "fbp_backproject_staged" if api.staged_preferred(g) else
+                                   f"fbp_backproject variant {resolved_variant(api, g, 'f32', -1)}"})
     if not args.no_cpu_baseline and ws == 1:
         line["cpu_baseline"] = cpu_sample_gd(w)
     return line

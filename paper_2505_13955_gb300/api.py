@@ -217,10 +217,10 @@ def fbp_counts(counts: torch.Tensor, g: Geometry, pre: Preprocess, window: HuWin
     S = 1 if counts.dim() == 2 else counts.shape[0]
     if window is None:
         if staged:
-            return backproject_staged(filt, g, rs, chunk=min(S, 4))
+            return backproject_staged(filt, g, rs, chunk=staged_chunk(g, dtype, S))
         return backproject(filt, g, row_scale=rs, variant=variant)
     if staged:
-        return backproject_staged_u16(filt, g, window, row_scale=rs, chunk=min(S, 4))
+        return backproject_staged_u16(filt, g, window, row_scale=rs, chunk=staged_chunk(g, dtype, S))
     return backproject_u16(filt, g, window, row_scale=rs, variant=variant)
 
 
@@ -269,14 +269,17 @@ def fbp_offset(sino: torch.Tensor, g: Geometry, overlap: float, fold: bool = Tru
     if variant < 0 and staged_preferred(gv):
         # folded rows: a centred half turn, so the staged orbit path applies
         S = 1 if sino.dim() == 2 else sino.shape[0]
-        return backproject_staged(filt, gv, rs, out=out, chunk=min(S, 4))
+        return backproject_staged(filt, gv, rs, out=out, chunk=staged_chunk(gv, dtype, S))
     return backproject(filt, gv, row_scale=rs, out=out, variant=variant)
 
 
 def backproject(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None = None,
                 scale: float | None = None, out: torch.Tensor | None = None,
                 accumulate: bool = False, variant: int = -1, which: str = "default"):
-    """fbp_backproject: f = scale * sum_k Q_k(u_k) (scale defaults to angle_step)."""
+    """fbp_backproject: f = scale * sum_k Q_k(u_k) (scale defaults to angle_step).
+    With the default variant, a geometry for which staged_preferred(g) holds
+    takes fbp_backproject_staged (with tables for as many slices as
+    staged_chunk allows, allocated per call), as fbp does."""
     _need(filt, "filt")
     if filt.dtype not in _DTYPES:
         raise ValueError(f"unsupported filt dtype {filt.dtype}")
@@ -285,6 +288,9 @@ def backproject(filt: torch.Tensor, g: Geometry, row_scale: torch.Tensor | None 
     if out is None:
         out = (torch.zeros if accumulate else torch.empty)(shape, dtype=torch.float32,
                                                            device=filt.device)
+    if variant < 0 and which == "default" and staged_preferred(g):
+        return backproject_staged(filt, g, row_scale, scale=scale, out=out, accumulate=accumulate,
+                                  chunk=staged_chunk(g, filt.dtype, S))
     _need(out, "out", torch.float32)
     if tuple(out.shape) != shape:
         raise ValueError(f"out has shape {tuple(out.shape)}, expected {shape}")
@@ -413,16 +419,27 @@ def staged_preferred(g: Geometry) -> bool:
     return staged_supported(g) and g.n >= 1024
 
 
+STAGED_TABLE_BUDGET = 2 << 30     # bytes of staged tables the default paths allocate at most
+
+
+def staged_chunk(g: Geometry, dtype, S: int) -> int:
+    """Slices per pass of the default paths' staged backprojection: every
+    slice at once (one launch, no tail of a partly filled last wave) while
+    their tables fit in STAGED_TABLE_BUDGET bytes, else as many as fit."""
+    per = backproject_staged_workspace_bytes(g, dtype, 2) - backproject_staged_workspace_bytes(g, dtype, 1)
+    return max(1, min(S, STAGED_TABLE_BUDGET // max(per, 1)))
+
+
 def fbp(sino: torch.Tensor, g: Geometry, kind="ramlak", dtype=torch.float32,
         out: torch.Tensor | None = None, variant: int = -1):
     """Filtered backprojection: fbp_filter then fbp_backproject (scale =
     angle_step).  With the default variant, rows take fbp_backproject_staged
-    where staged_preferred(g) (a workspace of up to four slices' tables is
-    allocated)."""
+    where staged_preferred(g) (with tables for as many slices as staged_chunk
+    allows, allocated per call)."""
     filt, rs = filter(sino, g, kind=kind, dtype=dtype)
     if variant < 0 and staged_preferred(g):
         S = 1 if sino.dim() == 2 else sino.shape[0]
-        return backproject_staged(filt, g, rs, out=out, chunk=min(S, 4))
+        return backproject_staged(filt, g, rs, out=out, chunk=staged_chunk(g, dtype, S))
     return backproject(filt, g, row_scale=rs, out=out, variant=variant)
 
 
