@@ -12,6 +12,37 @@
 #include "bp_batch.cuh"
 
 namespace fbp {
+
+// Blocks per orbit for the default path's split launch: when a slice has
+// fewer than half as many orbits as the GPU holds resident blocks, its angle
+// pairs are shared among up to 16 blocks (one cluster), each with at least
+// one stage.  The count depends on the geometry and the device only, so a
+// slice gets the same sums whatever the number of slices in the call.
+int orbit_split_parts(long long orbits, int K2, int KT, long long resident)
+{
+    if (orbits <= 0 || orbits * 2 >= resident) return 1;
+    long long P = std::min(16LL, resident / (2 * orbits));
+    P = std::min(P, (long long)((K2 + KT - 1) / KT));
+    return (int)std::max(P, 1LL);
+}
+
+fbp_status device_sm_count(int *out)
+{
+    static std::mutex mu;
+    static std::map<int, int> counts;
+    int dev = 0;
+    FBP_CUDA_TRY(cudaGetDevice(&dev));
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = counts.find(dev);
+    if (it == counts.end()) {
+        int sms = 0;
+        FBP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        it = counts.emplace(dev, sms).first;
+    }
+    *out = it->second;
+    return FBP_OK;
+}
+
 namespace {
 
 // Compiled tile shapes: threads TXT x TYT, pixels per thread PX x PY,
@@ -127,36 +158,6 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_orbit_kernel(BpArgs a)
     j.ke = (int)((long long)(part + 1) * (a.K / 2) / P);
     j.status = a.status;
     bp_orbit<TILE, TXT, TYT, PX, PY, KT, T, CHECKED, PACKED, SPLIT>(j, bp_smem);
-}
-
-// Blocks per orbit for the default path's split launch: when a slice has
-// fewer than half as many orbits as the GPU holds resident blocks, its angle
-// pairs are shared among up to 16 blocks (one cluster), each with at least
-// one stage.  The count depends on the geometry and the device only, so a
-// slice gets the same sums whatever the number of slices in the call.
-int orbit_split_parts(long long orbits, int K2, int KT, long long resident)
-{
-    if (orbits <= 0 || orbits * 2 >= resident) return 1;
-    long long P = std::min(16LL, resident / (2 * orbits));
-    P = std::min(P, (long long)((K2 + KT - 1) / KT));
-    return (int)std::max(P, 1LL);
-}
-
-fbp_status device_sm_count(int *out)
-{
-    static std::mutex mu;
-    static std::map<int, int> counts;
-    int dev = 0;
-    FBP_CUDA_TRY(cudaGetDevice(&dev));
-    std::lock_guard<std::mutex> lock(mu);
-    auto it = counts.find(dev);
-    if (it == counts.end()) {
-        int sms = 0;
-        FBP_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-        it = counts.emplace(dev, sms).first;
-    }
-    *out = it->second;
-    return FBP_OK;
 }
 
 template <int V, typename T>

@@ -262,8 +262,9 @@ __global__ void __launch_bounds__(kBins) fwd_strip_kernel(FwdArgs a)
 
 
 // ---------------------------------------------------------------------------
-// Tile-owned form.  One block per 64 x 64 pixel tile (and slice) stages the
-// tile once in shared memory and visits every angle; per angle it walks only
+// Tile-owned form.  One block per 64 x 64 pixel tile (and slice group, and
+// share of the angles: fwd_angle_parts) stages the tile once in shared
+// memory and visits its angles; per angle it walks only
 // the bins the tile's footprint covers, over the tile's own lines, with the
 // same support solve as above, and adds each bin's partial sum to the
 // sinogram with a global floating-point reduction.  The image is therefore
@@ -313,6 +314,7 @@ struct FwdTileArgs {
     double alpha, det_center;
     int tiles_x;
     int slice_base;
+    int k_parts;         // blocks per tile along z, each a contiguous share of the angles
 };
 
 // Walk parameters of tile (r0, c0) for angle k, in FP64.  Bin j's ray meets
@@ -453,12 +455,16 @@ __global__ void __launch_bounds__(tile_threads<NS>(), NS == 4 ? 2 : 4) fwd_tile_
     }
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int bl = lane % BPW, lsub = lane / BPW;
-    for (int k0 = 0; k0 < a.K; k0 += kTChunk) {
+    // this block's angles (the bins of an angle are the same sums whichever
+    // block adds them)
+    const int kb = (int)((long long)blockIdx.z * a.K / a.k_parts);
+    const int ke = (int)((long long)(blockIdx.z + 1) * a.K / a.k_parts);
+    for (int k0 = kb; k0 < ke; k0 += kTChunk) {
         __syncthreads();                     // tile staged / previous chunk consumed
-        if (k0 + (int)threadIdx.x < a.K)
+        if (k0 + (int)threadIdx.x < ke)
             prm[threadIdx.x] = tile_angle_setup(a, k0 + threadIdx.x, r0, c0);
         __syncthreads();
-        const int kc = min(kTChunk, a.K - k0);
+        const int kc = min(kTChunk, ke - k0);
         for (int ki = warp; ki < kc; ki += kTThreads / 32) {
             const TileAngle p = prm[ki];
             float *out = a.sino + ((size_t)sl0 * a.K + (k0 + ki)) * a.D;
@@ -528,6 +534,27 @@ bool fwd_tile_eligible(double alpha)
 
 int fwd_variant_count() { return 6; }
 
+// Angle parts per tile: the block count B = tiles x slice groups fills
+// ceil(B P / R) waves of R resident blocks in time proportional to
+// ceil(B P / R) / P; the P in [1, 8] (at least 64 angles each) with the
+// least time, plus 0.5 % per part for restaging the tile, trims the last,
+// partly filled wave (N = 1024, 16 slices: 1024 blocks on 304 slots).
+int fwd_angle_parts(long long blocks, long long resident, int K)
+{
+    if (blocks <= 0 || resident <= 0) return 1;
+    int best = 1;
+    double best_t = 1e300;
+    for (int P = 1; P <= 8 && (P == 1 || K / P >= 64); ++P) {
+        const long long waves = (blocks * P + resident - 1) / resident;
+        const double t = (double)waves / P * (1.0 + 0.005 * P);
+        if (t < best_t - 1e-12) {
+            best_t = t;
+            best = P;
+        }
+    }
+    return best;
+}
+
 template <int BPW, int NS>
 static fbp_status launch_tile_group(FwdTileArgs a, int first, int count, unsigned tiles, cudaStream_t s)
 {
@@ -536,10 +563,16 @@ static fbp_status launch_tile_group(FwdTileArgs a, int first, int count, unsigne
     constexpr size_t smem = tile_smem<NS>();
     fbp_status st = ensure_dynamic_smem(kern, smem);
     if (st != FBP_OK) return st;
+    int per_sm = 0, sms = 0;
+    st = blocks_per_sm(kern, tile_threads<NS>(), smem, &per_sm);
+    if (st == FBP_OK) st = device_sm_count(&sms);
+    if (st != FBP_OK) return st;
     const int groups = count / NS;
+    a.k_parts = fwd_angle_parts((long long)tiles * std::min(65535, groups), (long long)sms * std::max(per_sm, 1),
+                                a.K);
     for (int g0 = 0; g0 < groups; g0 += 65535) {
         a.slice_base = first + NS * g0;
-        dim3 grid(tiles, (unsigned)std::min(65535, groups - g0));
+        dim3 grid(tiles, (unsigned)std::min(65535, groups - g0), (unsigned)a.k_parts);
         fwd_tile_kernel<BPW, NS><<<grid, tile_threads<NS>(), smem, s>>>(a);
         FBP_CUDA_TRY(cudaGetLastError());
     }

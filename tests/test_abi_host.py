@@ -142,6 +142,15 @@ def test_pipeline_entry_points_validate_on_the_host(L):
     assert L.fbp_backproject_u16(p, None, 0, dummy_ptr(), ctypes.byref(g), 0, 1.0, ctypes.byref(w), -1, None) == 0
 
 
+def test_libraries_resolve_every_symbol_at_load(L):
+    """Both shared libraries load with immediate binding: no function the
+    translation units call on one another is left undefined (a lazy load
+    would only fail at the first call, on the GPU machine)."""
+    from paper_2505_13955_gb300 import build
+    for name in ("libfbp.so", "libfbp_checked.so"):
+        ctypes.CDLL(os.path.join(build.HERE, name), mode=os.RTLD_NOW)
+
+
 def test_batched_workspace_query_and_validation(L):
     items = (_lib.CBatchItem * 3)()
     dims = [(720, 512, 512), (1800, 1024, 1024), (3600, 2048, 2048)]
