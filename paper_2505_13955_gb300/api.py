@@ -727,12 +727,13 @@ def sap_depatch_pack(mask_patches: torch.Tensor, leaves: torch.Tensor, p: SapPar
 
 
 def sap_host(slices: torch.Tensor, p: SapParams, patches: torch.Tensor | None = None,
-             leaves: torch.Tensor | None = None, n_streams: int = 2, device=None):
+             leaves: torch.Tensor | None = None, n_streams: int = 4, device=None):
     """Adaptive patching of a stack of uint16 slices held in host memory
     (int16 tensor [S, n, n], pinned for asynchronous copies): each slice is
     copied in, patched (sap_edges + sap_patches) and its patches and leaves
     copied out, on `n_streams` streams so that one slice's copies overlap
-    another's kernels.  Returns host (patches [S, length, P, P],
+    another's kernels, and one slice's serial tail (the one-block selection,
+    the tree's small top levels) overlaps another's edge detection.  Returns host (patches [S, length, P, P],
     leaves [S, length, 3]); blocks until they are filled."""
     if slices.is_cuda:
         raise ValueError("sap_host takes a host tensor; use sap_edges / sap_patches on device tensors")

@@ -376,6 +376,8 @@ __device__ __forceinline__ unsigned digit_of(ulonglong2 k, int pass)
     return (unsigned)(((pass < 8 ? k.x : k.y) >> sh) & 0xff);
 }
 
+constexpr int kSelectBatch = 8;   // rounds of 1024 keys whose loads are issued together
+
 __global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns, ulonglong2 *bufB,
                                                       ulonglong2 *bufC)
 {
@@ -397,18 +399,24 @@ __global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns, 
     for (int pass = 0; pass < 16; ++pass) {
         for (int i = t; i < 32 * 256; i += 1024) (&hist[0][0])[i] = 0;
         __syncthreads();
-        // every warp runs the same number of rounds, so the warp-wide votes see all lanes
-        for (long long b0 = 0; b0 < cnt; b0 += 1024) {
-            const long long i = b0 + t;
-            bool valid = i < cnt;
-            ulonglong2 k = make_ulonglong2(0, 0);
-            if (valid) {
-                k = src[i];
-                valid = (k.x & mx) == tx && (k.y & my) == ty;
+        // every warp runs the same number of rounds, so the warp-wide votes see
+        // all lanes; the keys of kSelectBatch rounds are loaded before any is
+        // counted, so their global-load latencies overlap
+        for (long long b0 = 0; b0 < cnt; b0 += 1024 * kSelectBatch) {
+            ulonglong2 kk[kSelectBatch];
+#pragma unroll
+            for (int u = 0; u < kSelectBatch; ++u) {
+                const long long i = b0 + (long long)u * 1024 + t;
+                kk[u] = i < cnt ? src[i] : make_ulonglong2(0, 0);
             }
-            const unsigned d = valid ? digit_of(k, pass) : 256u;
-            const unsigned same = __match_any_sync(0xffffffffu, d);
-            if (valid && lane == __ffs(same) - 1) atomicAdd(&hist[warp][d], __popc(same));
+#pragma unroll
+            for (int u = 0; u < kSelectBatch; ++u) {
+                const long long i = b0 + (long long)u * 1024 + t;
+                const bool valid = i < cnt && (kk[u].x & mx) == tx && (kk[u].y & my) == ty;
+                const unsigned d = valid ? digit_of(kk[u], pass) : 256u;
+                const unsigned same = __match_any_sync(0xffffffffu, d);
+                if (valid && lane == __ffs(same) - 1) atomicAdd(&hist[warp][d], __popc(same));
+            }
         }
         __syncthreads();
         if (t < 256) {
@@ -445,19 +453,23 @@ __global__ void __launch_bounds__(1024) select_kernel(TreeArgs a, long long Ns, 
             live = next;
             continue;
         }
-        for (long long b0 = 0; b0 < cnt; b0 += 1024) {
-            const long long i = b0 + t;
-            bool keep = false;
-            ulonglong2 k = make_ulonglong2(0, 0);
-            if (i < cnt) {
-                k = src[i];
-                keep = (k.x & mx) == tx && (k.y & my) == ty;
+        for (long long b0 = 0; b0 < cnt; b0 += 1024 * kSelectBatch) {
+            ulonglong2 kk[kSelectBatch];
+#pragma unroll
+            for (int u = 0; u < kSelectBatch; ++u) {
+                const long long i = b0 + (long long)u * 1024 + t;
+                kk[u] = i < cnt ? src[i] : make_ulonglong2(0, 0);
             }
-            const unsigned vote = __ballot_sync(0xffffffffu, keep);
-            unsigned base = 0;
-            if (lane == 0 && vote) base = atomicAdd(&s_pos, __popc(vote));
-            base = __shfl_sync(0xffffffffu, base, 0);
-            if (keep) dst[base + __popc(vote & ((1u << lane) - 1))] = k;
+#pragma unroll
+            for (int u = 0; u < kSelectBatch; ++u) {
+                const long long i = b0 + (long long)u * 1024 + t;
+                const bool keep = i < cnt && (kk[u].x & mx) == tx && (kk[u].y & my) == ty;
+                const unsigned vote = __ballot_sync(0xffffffffu, keep);
+                unsigned base = 0;
+                if (lane == 0 && vote) base = atomicAdd(&s_pos, __popc(vote));
+                base = __shfl_sync(0xffffffffu, base, 0);
+                if (keep) dst[base + __popc(vote & ((1u << lane) - 1))] = kk[u];
+            }
         }
         __syncthreads();
         cnt = live = next;
