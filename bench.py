@@ -624,11 +624,13 @@ def run_uniform(args) -> None:
                            slices_per_s=S * len(per_rank) / (ms_step / 1e3), staged=staged)
         if staged:
             # the block-staged orbit kernel on the same rows, for comparison
+            # (named explicitly: api.backproject's default takes the staged kernel)
+            vo = resolved_variant(api, g, dt, -1)
             To = Timed(stream, 3, 3)
-            ms_o = To.run(lambda _: api.backproject(filt, g, row_scale=rs, out=out, variant=-1), None)
+            ms_o = To.run(lambda _: api.backproject(filt, g, row_scale=rs, out=out, variant=vo), None)
             results[dt]["orbit_kernel"] = {"bp_ms_per_step": ms_o,
                                            "bp_gupdates_per_s": updates / (ms_o / 1e3) / 1e9,
-                                           "bp_variant": resolved_variant(api, g, dt, -1)}
+                                           "bp_variant": vo}
         del filt, rs, wsp
 
     # the texture-unit backprojection (the measured alternative to staged
@@ -1390,16 +1392,18 @@ RUNNERS = {
 # the workload, and what differs from the headline's arguments.  Slice counts
 # below a workload's own are stated in its config ("slices_per_gpu").
 SUB_RECORDS = (
+    # (steps sized so that every timed region lasts at least ~0.5 s: the clock
+    # sampler reads nvidia-smi every 200 ms)
     ("config1_fbp_single_n256", "fbp_single_n256",
-     dict(steps=200, e2e_steps=20, all_dtypes=False, texture=False, cpu_block=256)),
+     dict(steps=20000, e2e_steps=20, all_dtypes=False, texture=False, cpu_block=256)),
     ("config2_fbp_stack_n2048", "fbp_stack_n2048",
      dict(steps=5, e2e_steps=1, all_dtypes=True, texture=False, cpu_block=256)),
     ("config4_fbp_ragged_batch", "fbp_ragged_batch", dict(steps=5)),
-    ("config5_gd_refine_n1024", "gd_refine_n1024", dict(steps=5)),
+    ("config5_gd_refine_n1024", "gd_refine_n1024", dict(steps=30)),
     ("f1_pipeline_n8192", "fbp_pipeline_n8192", dict(steps=3, slices=4, e2e_steps=1, cpu_block=256)),
     ("f2_offset_n8192", "fbp_offset_n8192", dict(steps=4, slices=4, cpu_block=256)),
     ("f3_mixed_batch", "fbp_mixed_batch", dict(steps=5)),
-    ("f4_sap_patching_n8192", "sap_patching_n8192", dict(steps=3, slices=4, e2e_steps=1, cpu_block=1024)),
+    ("f4_sap_patching_n8192", "sap_patching_n8192", dict(steps=200, slices=4, e2e_steps=1, cpu_block=1024)),
 )
 SUB_DROP = ("n_gpus", "higher_is_better", "scaling", "vs_baseline", "data")
 
