@@ -1,23 +1,29 @@
-// bp_staged.cu -- K2 for 16-bit rows with the window staging taken off the
-// threads: fbp_backproject_staged.
+// bp_staged.cu -- K2 with the window staging taken off the threads:
+// fbp_backproject_staged (FP32 and 16-bit rows) and its uint16-code form.
 //
 // The orbit kernel (bp_orbit.cuh) forms, per block, per angle pair and per
-// window, the 16-byte entries (midpoints and slopes of the rows th, th + pi/2
-// and their mirrors, scaled by s_k / S) from the filtered rows, behind two
-// block barriers per stage.  Here a pass over the filtered rows writes those
-// entries once per slice, for every detector segment, into the caller's
-// workspace:
+// window, the table entries (midpoints and slopes of the rows th, th + pi/2
+// and their mirrors; 16-bit rows scaled by s_k / S) from the filtered rows,
+// behind two block barriers per stage.  Here a pass over the filtered rows
+// writes those entries once per slice, for every detector segment, into the
+// caller's workspace:
 //     table[s][k][e], k < K/2 the angle pair, e = j + 1 for segment j in
 //     [-1, D-1] (the segment between bins j and j+1, zero outside [0, D)),
+//     16 bytes per entry for 16-bit rows, 32 for FP32 rows (two 16-byte
+//     halves: rows th, th' | mirrored rows),
 // and the backprojection moves each window of W entries with one tiled
-// bulk-tensor copy into shared memory -- out-of-range entries (windows that
-// reach past the detector) are filled with zeros by the copy engine, which is
-// exactly the staged kernel's zero padding.  Stages cycle through NS buffers;
-// each copy completes on the buffer's mbarrier (capped waits), and the last
-// warp to finish reading a buffer refills it with the stage NS ahead, so the
-// compute loop has no block-wide barrier.  The entries and the per-pair
-// arithmetic (orbit_mid_slope, orbit_pair) are the orbit kernel's own, so the
-// results are bit-identical to fbp_backproject_variant with the same shape.
+// bulk-tensor copy per half into shared memory -- out-of-range entries
+// (windows that reach past the detector) are filled with zeros by the copy
+// engine, which is exactly the staged kernel's zero padding.  Stages cycle
+// through NS buffers; each copy completes on the buffer's mbarrier (capped
+// waits), and the last warp to finish reading a buffer refills it with the
+// stage NS ahead, so the compute loop has no block-wide barrier.  For 16-bit
+// rows the entries and the per-pair arithmetic (orbit_mid_slope, orbit_pair)
+// are the orbit kernel's own, so the results are bit-identical to
+// fbp_backproject_variant with the same shape; FP32 rows use the midpoint
+// form (orbit_pair_mid), within FP32 rounding of the orbit kernel.  The
+// device code shared with the batched form (bp_staged_batch.cu) is in
+// bp_staged.cuh.
 #include <algorithm>
 #include <climits>
 #include <cstdint>
