@@ -233,11 +233,18 @@ def peaks() -> dict:
 
 
 def bp_source_hash() -> str:
+    """Hash of the backprojection kernels' code: the sources with comments
+    and blank lines removed, so that an edit of the comments keeps a
+    captured traffic figure valid."""
     import hashlib
+    import re
     h = hashlib.sha256()
     for f in ("bp_tile.cuh", "bp_orbit.cuh", "backproject.cu", "bp_staged.cuh", "bp_staged.cu"):
-        with open(os.path.join(ROOT, "paper_2505_13955_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2505_13955_gb300", "csrc", f)) as fh:
+            for line in fh:
+                code = re.sub(r"//.*", "", line).rstrip()
+                if code:
+                    h.update(code.encode() + b"\n")
     return h.hexdigest()[:16]
 
 
