@@ -364,6 +364,53 @@ __device__ __forceinline__ void cluster_sync_all()
     asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// The cluster's reduction of one orbit's partial sums (SPLIT launches of the
+// orbit and staged kernels): every thread's accumulators go to `scratch`
+// (this block's shared memory, bp_orbit_split_bytes, free of every other
+// use), then the block of rank r adds, for entries r, r + P, ... of every
+// thread, the P partial sums in rank order and stores the pixel times `gain`
+// (unless `store` is false: a block that has recorded a fault).  Both
+// cluster barriers are reached by every thread of every block.
+template <int TXT, int TYT, int PX, int PY>
+__device__ __forceinline__ void orbit_split_store(const float (&acc)[4][PY][PX], unsigned char *scratch, bool store,
+                                                  float *out, unsigned short *out16, float hu_a, float hu_b,
+                                                  int accumulate, int N, int c0, int r0, float gain)
+{
+    constexpr int NT = TXT * TYT, E = 4 * PY * PX;
+    const int tid = threadIdx.x;
+    float *mine = reinterpret_cast<float *>(scratch); // [E][NT]
+#pragma unroll
+    for (int o = 0; o < 4; ++o)
+#pragma unroll
+        for (int iy = 0; iy < PY; ++iy)
+#pragma unroll
+            for (int ix = 0; ix < PX; ++ix) mine[((o * PY + iy) * PX + ix) * NT + tid] = acc[o][iy][ix];
+    cluster_sync_all();
+    uint32_t rank, parts;
+    asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+    asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(parts));
+    const uint32_t base = (uint32_t)__cvta_generic_to_shared(mine) + 4u * (uint32_t)tid;
+    for (int e = (int)rank; e < E; e += (int)parts) {
+        float v = 0.f;
+        for (uint32_t p = 0; p < parts; ++p) {
+            uint32_t ra;
+            float x;
+            asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(base + 4u * (uint32_t)(e * NT)), "r"(p));
+            asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(x) : "r"(ra) : "memory");
+            v += x;
+        }
+        // entry e = (o, iy, ix): the member's pixel, as orbit_store places it
+        const int ix = e % PX, iy = (e / PX) % PY, o = e / (PX * PY);
+        const int r = r0 + TYT * iy, c = c0 + TXT * ix;
+        const size_t idx = o == 0 ? (size_t)r * N + c
+                         : o == 1 ? (size_t)c * N + (N - 1 - r)
+                         : o == 2 ? (size_t)(N - 1 - r) * N + (N - 1 - c)
+                                  : (size_t)(N - 1 - c) * N + r;
+        if (store) store_pixel(out, out16, hu_a, hu_b, accumulate, idx, v * gain);
+    }
+    cluster_sync_all();
+}
+
 template <int TILE, int TXT, int TYT, int PX, int PY, int KT, typename T, bool CHECKED,
           bool PACKED = false, bool SPLIT = false>
 __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *smem)
@@ -515,41 +562,9 @@ __device__ __forceinline__ void bp_orbit(const BpOrbitJob &j, unsigned char *sme
         orbit_store<TXT, TYT, PX, PY>(acc, j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, N, j.x0 + tx,
                                       j.y0 + ty, j.scale * S);
     } else {
-        constexpr int E = 4 * PY * PX;                 // entries per thread
         __syncthreads();                               // the staging buffers are free
-        float *mine = reinterpret_cast<float *>(smem); // [E][NT]
-#pragma unroll
-        for (int o = 0; o < 4; ++o)
-#pragma unroll
-            for (int iy = 0; iy < PY; ++iy)
-#pragma unroll
-                for (int ix = 0; ix < PX; ++ix) mine[((o * PY + iy) * PX + ix) * NT + tid] = acc[o][iy][ix];
-        cluster_sync_all();
-        uint32_t rank, parts;
-        asm("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
-        asm("mov.u32 %0, %%cluster_nctarank;" : "=r"(parts));
-        const uint32_t base = (uint32_t)__cvta_generic_to_shared(mine) + 4u * (uint32_t)tid;
-        const float gain = j.scale * S;
-        const int c0 = j.x0 + tx, r0 = j.y0 + ty;
-        for (int e = (int)rank; e < E; e += (int)parts) {
-            float v = 0.f;
-            for (uint32_t p = 0; p < parts; ++p) {
-                uint32_t ra;
-                float x;
-                asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(base + 4u * (uint32_t)(e * NT)), "r"(p));
-                asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(x) : "r"(ra) : "memory");
-                v += x;
-            }
-            // entry e = (o, iy, ix): the member's pixel, as orbit_store places it
-            const int ix = e % PX, iy = (e / PX) % PY, o = e / (PX * PY);
-            const int r = r0 + TYT * iy, c = c0 + TXT * ix;
-            const size_t idx = o == 0 ? (size_t)r * N + c
-                             : o == 1 ? (size_t)c * N + (N - 1 - r)
-                             : o == 2 ? (size_t)(N - 1 - r) * N + (N - 1 - c)
-                                      : (size_t)(N - 1 - c) * N + r;
-            store_pixel(j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, idx, v * gain);
-        }
-        cluster_sync_all();
+        orbit_split_store<TXT, TYT, PX, PY>(acc, smem, true, j.out, j.out16, j.hu_a, j.hu_b, j.accumulate, N,
+                                            j.x0 + tx, j.y0 + ty, j.scale * S);
     }
 }
 
