@@ -63,8 +63,11 @@ __host__ __device__ constexpr int fft_VPL(int L)
 //   L   = transform length (power of two >= max(512, 2D-1), so L >= 2D; <= 16384)
 //   G   = spectrum of the cumulative (difference-form) kernel, times tau / L,
 //         complex, in the order the transform's step 2 reads it:
-//         G[(k1 VPL + kr) 32 + l] = spectrum at k = k1 + R (kr + VPL brev5(l)),
-//         brev5 = the 5-bit reversal of the lane index
+//         G[((w NRD + rd) RB + m) 32 + j] = spectrum at
+//         k = k1 + R (kr + VPL (m + RB brev(s))) for warp w, round rd < NRD,
+//         lane j, RB = min(R, 16), NRD = R / RB: c = rd RB + j mod RB,
+//         s = j / RB, k1 = w (R / VPL) + c / VPL, kr = c mod VPL, and brev
+//         the log2(32 / RB)-bit reversal
 //   tw  = twiddle plan (float2), L + C + 32 entries: W_L^{t k1} at k1 C + t,
 //         then W_C^{l kr} at L + 32 kr + l, then W_32^m at L + C + m,
 //         W_M^x = exp(-2 pi i x / M), each rounded once from double

@@ -21,18 +21,23 @@
 //           memory (coalesced across t), forms the differences, runs the
 //           R-point DFT over n1 in registers, multiplies by W_L^{t k1} and
 //           writes row k1 of an R x C shared buffer.
-//   step 2  each warp takes whole rows k1: lane l holds z[k1][l + 32 r],
-//           r < VPL; the C-point DFT over n2 is a VPL-point DFT in registers,
-//           the twiddle W_C^{l kr}, and a 32-point DFT over lanes (warp
-//           shuffles).  The product with G[k1 + R k2] is taken in registers
-//           and the inverse C-point DFT undoes the forward one in place, so
-//           the spectrum never leaves the warp.
+//   step 2  each warp takes whole rows k1 (R / VPL of them): the C-point
+//           DFT over n2 = l + 32 r is a VPL-point DFT over r in registers
+//           (lane l), the twiddle W_C^{l kr}, and R VPL = R 32-point DFTs
+//           over l, one per (row, kr).  For those the warp exchanges its
+//           rows through the shared buffer (swizzled, so neither side has
+//           a bank conflict): lane j = c + R s takes l = s + (32/R) i,
+//           runs the R-point DFT over i in registers, and finishes with a
+//           (32/R)-point DFT over the lanes j, j ^ R, ... (warp shuffles;
+//           none at L = 16384, where R = 32).  The product with
+//           G[k1 + R k2] is taken in registers and the inverse undoes the
+//           forward steps in place, so the spectrum never leaves the warp.
 //   step 3  thread t reads column t, multiplies by W_L^{-t k1}, runs the
 //           inverse R-point DFT and stores its outputs n = C n1 + t < D
 //           straight to global memory (coalesced across t).
-// The shared buffer is read and written row-contiguously in both layouts
-// (row k1 by thread t, row k1 by lane l + 32 r), so no access has a bank
-// conflict and no padding is needed; it is visited four times per pair.
+// Steps 1 and 3 and the natural-order side of step 2 access the buffer
+// row-contiguously, and the exchange inside step 2 is XOR-swizzled within
+// 32-entry runs, so no access has a bank conflict and no padding is needed.
 //
 // The spectrum G already contains tau and 1/L and is stored in step 2's
 // read order; the twiddles come from a plan laid out in the order each step
@@ -72,43 +77,96 @@ __device__ __forceinline__ float2 shfl_xor2(float2 v, int m)
 {
     return make_float2(__shfl_xor_sync(0xffffffffu, v.x, m), __shfl_xor_sync(0xffffffffu, v.y, m));
 }
-
-
-// Decimation-in-frequency radix-2 DFT over the 32 lanes (forward, natural
-// order in, bit-reversed out), on NV values per lane; w32 = the W_32^m table.
-template <int NV>
-__device__ __forceinline__ void lane_dif(float2 (&v)[NV], int lane, const float2 *__restrict__ w32t)
+// a / b, correctly rounded, from y = RN(1 / b): q = RN(a y) is within an
+// ulp of a / b, the residual a - b q is exact in one FMA, and the
+// correction RN(q + (a - b q) y) rounds the quotient correctly (Markstein,
+// IBM J. Res. Dev. 34(1), 1990).  Holds while the quotient is normal; the
+// 16-bit rows divide values by their row's largest magnitude, so the
+// quotient lies in [-1, 1].
+__device__ __forceinline__ float div_rn(float a, float b, float y)
 {
+    const float q = a * y;
+    return fmaf(fmaf(-q, b, a), y, q);
+}
+
+// The same table pointer, opaque to the compiler: loads through it are
+// issued where they are used, instead of being merged with an earlier load
+// of the same entry or hoisted out of the row-pair loop, either of which
+// keeps whole twiddle sets live in registers across the transform.
+__device__ __forceinline__ const float2 *fresh(const float2 *p)
+{
+    const float2 *q;
+    asm volatile("mov.b64 %0, %1;" : "=l"(q) : "l"(p));
+    return q;
+}
+
+
+// Step 2's 32-point transforms over l run on lanes j = c + R s (c < R,
+// s < SL = 32 / R): lane j holds, for one transform c, the R values
+// l = s + SL i (i < R).  After the R-point transform over i (-> m) and the
+// twiddle W_32^{s m}, an SL-point transform over s across the lanes
+// j, j ^ R, j ^ 2R, ... completes it (none when R = 32).
+//
+// lane_dif_s: that SL-point transform, radix-2 decimation in frequency
+// (natural s in, bit-reversed q out).  Written as v' = sgn v + other, then a
+// per-lane twiddle (1 on the low lane), so each stage costs two shuffles,
+// two FMAs and one complex product per value (none in the last stage).
+template <int NV, int R>
+__device__ __forceinline__ void lane_dif_s(float2 (&v)[NV], int s, const float2 *__restrict__ w32t)
+{
+    constexpr int SL = 32 / R;
 #pragma unroll
-    for (int b = 4; b >= 0; --b) {
-        const int h = 1 << b;
-        const bool hi = (lane & h) != 0;
-        const float2 w = __ldg(&w32t[(lane & (h - 1)) * (16 / h)]);      // W_{2h}^{lane mod h}
+    for (int h = SL / 2; h >= 1; h >>= 1) {
+        const bool hi = (s & h) != 0;
+        const float sg = hi ? -1.f : 1.f;
+        float2 w = make_float2(1.f, 0.f);
+        if (h > 1 && hi) w = __ldg(&w32t[(s & (h - 1)) * (16 / h)]);      // W_{2h}^{s mod h}
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            float2 o = shfl_xor2(v[i], h);
-            v[i] = hi ? cmul(csub(o, v[i]), w) : cadd(v[i], o);
+            const float2 o = shfl_xor2(v[i], R * h);
+            float2 x = make_float2(fmaf(sg, v[i].x, o.x), fmaf(sg, v[i].y, o.y));
+            if (h > 1) x = cmul(x, w);
+            v[i] = x;
         }
     }
 }
 
-// Inverse of lane_dif: decimation-in-time over the 32 lanes with conjugate
-// twiddles (bit-reversed in, natural out), unnormalised.
-template <int NV>
-__device__ __forceinline__ void lane_dit_inv(float2 (&v)[NV], int lane, const float2 *__restrict__ w32t)
+// Inverse of lane_dif_s: decimation in time over s with conjugate twiddles
+// (bit-reversed in, natural out), unnormalised.  The high lane first takes
+// its own value times conj(w), then low: own + other, high: other - own.
+template <int NV, int R>
+__device__ __forceinline__ void lane_dit_inv_s(float2 (&v)[NV], int s, const float2 *__restrict__ w32t)
 {
+    constexpr int SL = 32 / R;
 #pragma unroll
-    for (int b = 0; b < 5; ++b) {
-        const int h = 1 << b;
-        const bool hi = (lane & h) != 0;
-        const float2 w = __ldg(&w32t[(lane & (h - 1)) * (16 / h)]);
+    for (int h = 1; h < SL; h <<= 1) {
+        const bool hi = (s & h) != 0;
+        const float sg = hi ? -1.f : 1.f;
+        float2 w = make_float2(1.f, 0.f);
+        if (h > 1 && hi) {
+            w = __ldg(&w32t[(s & (h - 1)) * (16 / h)]);
+            w.y = -w.y;
+        }
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            float2 o = shfl_xor2(v[i], h);
-            // low lane: mine + other * conj(w); high lane: other - mine * conj(w)
-            v[i] = hi ? csub(o, cmulc(v[i], w)) : cadd(v[i], cmulc(o, w));
+            float2 x = v[i];
+            if (h > 1) x = cmul(x, w);
+            const float2 o = shfl_xor2(x, R * h);
+            v[i] = make_float2(fmaf(sg, x.x, o.x), fmaf(sg, x.y, o.y));
         }
     }
+}
+
+// XOR key of transform c in the swizzled layout of step 2: row k1, value
+// (kr, l) sits at k1 C + 32 kr + (l ^ key(c)), c = (k1 mod RPW) VPL + kr.
+// Both accesses are then free of bank conflicts: the lanes l of one kr
+// write a permutation of one 32-entry run, and the 16 lanes of a half-warp
+// reading (c, l = s + SL i) in one round of pass B hit 16 different 8-byte
+// bank pairs (SL = 32 / min(R, 16) lanes per transform).
+template <int R>
+__host__ __device__ constexpr int swz_key(int c)
+{
+    return R >= 16 ? c : c * (16 / R);
 }
 
 struct RowPairJob {
@@ -185,7 +243,9 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[M])
 #pragma unroll
             for (int m = 0; m < h; ++m) {
                 float2 b = v[blk + m + h];
-                if (m != 0) {                           // W_{2h}^m = W_32^{m * 16 / h}
+                if (m != 0 && m * (16 / h) == 8) {      // W_4^1 = -i (conjugate: +i): a swap
+                    b = INV ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
+                } else if (m != 0) {                    // W_{2h}^m = W_32^{m * 16 / h}
                     float2 w = w32(m * (16 / h));
                     if (INV) w.y = -w.y;
                     b = cmul(b, w);
@@ -456,8 +516,11 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         }
     }
     dft_reg<R, false>(v);
+    {
+        const float2 *twl = fresh(tw);
 #pragma unroll
-    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], __ldg(&tw[k1 * C + t]));  // W_L^{t k1}
+        for (int k1 = 1; k1 < R; ++k1) v[k1] = cmul(v[k1], __ldg(&twl[k1 * C + t]));  // W_L^{t k1}
+    }
 #pragma unroll
     for (int k1 = 0; k1 < R; ++k1) S[k1 * C + t] = v[k1];
     const unsigned za = __ballot_sync(0xffffffffu, nz_a), zb = __ballot_sync(0xffffffffu, nz_b);
@@ -476,31 +539,77 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         zero_b = zero_b && !(red[2 * w + 1] > 0.f);
     }
 
-    // ---- step 2: per row k1, C-point DFT over n2, times G, inverse
+    // ---- step 2: per row k1, C-point DFT over n2, times G, inverse.
+    // Pass A: lane l, per row, the VPL-point DFT over r and W_C^{l kr}; the
+    // values go to the swizzled layout.  Pass B: lane j = c + R s the 32-point
+    // DFTs over l (R-point in registers, W_32^{s m}, SL-point over lanes),
+    // the product with G and the inverse.  Pass C undoes pass A.
     if (active) {
-#pragma unroll
+        constexpr int RB = R < 16 ? R : 16;       // values per lane in pass B
+        constexpr int NRD = R / RB;               // pass B rounds (transforms c of round rd: rd RB + j mod RB)
+        constexpr int SL = 32 / RB;               // lanes per 32-point transform
+#pragma unroll 1
         for (int rr = 0; rr < RPW; ++rr) {
-            const int k1 = gw * RPW + rr;
+            float2 *row = S + (gw * RPW + rr) * C;
             float2 u[VPL];
 #pragma unroll
-            for (int r = 0; r < VPL; ++r) u[r] = S[k1 * C + lane + 32 * r];
+            for (int r = 0; r < VPL; ++r) u[r] = row[lane + 32 * r];
             dft_reg<VPL, false>(u);                                   // r -> kr
             if (lane) {
+                const float2 *twc = fresh(tw + L);
 #pragma unroll
-                for (int kr = 1; kr < VPL; ++kr) u[kr] = cmul(u[kr], __ldg(&tw[L + 32 * kr + lane]));  // W_C^{l kr}
+                for (int kr = 1; kr < VPL; ++kr) u[kr] = cmul(u[kr], __ldg(&twc[32 * kr + lane]));  // W_C^{l kr}
             }
-            lane_dif<VPL>(u, lane, w32t);                             // l -> kl = bit-reversed lane (5 bits)
-            // G is stored in this order: entry (k1 VPL + kr) 32 + lane is k = k1 + R (kr + VPL kl)
+            __syncwarp();                                             // the row is read before it is rewritten
 #pragma unroll
-            for (int kr = 0; kr < VPL; ++kr) u[kr] = cmul(u[kr], __ldg(&Gs[(k1 * VPL + kr) * 32 + lane]));
-            lane_dit_inv<VPL>(u, lane, w32t);                         // kl -> l
+            for (int kr = 0; kr < VPL; ++kr) row[32 * kr + (lane ^ swz_key<R>(rr * VPL + kr))] = u[kr];
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int rd = 0; rd < NRD; ++rd) {
+            const int c = rd * RB + (lane & (RB - 1)), s = lane / RB;
+            float2 *run = S + (gw * RPW + c / VPL) * C + 32 * (c % VPL);
+            const int key = swz_key<R>(c);
+            float2 x[RB];
+#pragma unroll
+            for (int i = 0; i < RB; ++i) x[i] = run[(s + SL * i) ^ key];
+            dft_reg<RB, false>(x);                                    // i -> m
+            if constexpr (SL > 1) {
+#pragma unroll
+                for (int m = 1; m < RB; ++m) x[m] = cmul(x[m], __ldg(&w32t[(s * m) & 31]));   // W_32^{s m}
+            }
+            lane_dif_s<RB, RB>(x, s, w32t);                           // s -> q, kl = m + RB q
+            // G is stored in this order: entry ((gw NRD + rd) RB + m) 32 + j is
+            // k = k1 + R (kr + VPL (m + RB brev(s)))
+#pragma unroll
+            const float2 *g = fresh(Gs + ((gw * NRD + rd) * RB) * 32);
+#pragma unroll
+            for (int m = 0; m < RB; ++m) x[m] = cmul(x[m], __ldg(&g[m * 32 + lane]));
+            lane_dit_inv_s<RB, RB>(x, s, w32t);                       // q -> s
+            if constexpr (SL > 1) {
+#pragma unroll
+                for (int m = 1; m < RB; ++m) x[m] = cmulc(x[m], __ldg(&w32t[(s * m) & 31]));
+            }
+            dft_reg<RB, true>(x);                                     // m -> i
+#pragma unroll
+            for (int i = 0; i < RB; ++i) run[(s + SL * i) ^ key] = x[i];
+        }
+        __syncwarp();
+#pragma unroll 1
+        for (int rr = 0; rr < RPW; ++rr) {
+            float2 *row = S + (gw * RPW + rr) * C;
+            float2 u[VPL];
+#pragma unroll
+            for (int kr = 0; kr < VPL; ++kr) u[kr] = row[32 * kr + (lane ^ swz_key<R>(rr * VPL + kr))];
             if (lane) {
+                const float2 *twc = fresh(tw + L);
 #pragma unroll
-                for (int kr = 1; kr < VPL; ++kr) u[kr] = cmulc(u[kr], __ldg(&tw[L + 32 * kr + lane]));
+                for (int kr = 1; kr < VPL; ++kr) u[kr] = cmulc(u[kr], __ldg(&twc[32 * kr + lane]));
             }
             dft_reg<VPL, true>(u);                                    // kr -> r
+            __syncwarp();
 #pragma unroll
-            for (int r = 0; r < VPL; ++r) S[k1 * C + lane + 32 * r] = u[r];
+            for (int r = 0; r < VPL; ++r) row[lane + 32 * r] = u[r];
         }
     }
     group_sync(bar_id, C);
@@ -508,8 +617,11 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
     // ---- step 3: column t, W_L^{-t k1}, inverse R-point DFT over k1
 #pragma unroll
     for (int k1 = 0; k1 < R; ++k1) v[k1] = S[k1 * C + t];
+    {
+        const float2 *twl = fresh(tw);
 #pragma unroll
-    for (int k1 = 1; k1 < R; ++k1) v[k1] = cmulc(v[k1], __ldg(&tw[k1 * C + t]));
+        for (int k1 = 1; k1 < R; ++k1) v[k1] = cmulc(v[k1], __ldg(&twl[k1 * C + t]));
+    }
     dft_reg<R, true>(v);                                              // k1 -> n1
 
     // ---- store (16-bit: per-row amax scale first)
@@ -548,6 +660,7 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
     }
     if (active) {
         T *qa = static_cast<T *>(job.qa), *qb = static_cast<T *>(job.qb);
+        const float inv_a = __frcp_rn(scale_a), inv_b = __frcp_rn(scale_b);
 #pragma unroll
         for (int n1 = 0; n1 < R; ++n1) {
             const int n = C * n1 + t;
@@ -557,8 +670,8 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
                     qa[n] = xa;
                     if (qb) qb[n] = xb;
                 } else {
-                    qa[n] = cvt_out<T>(__fdiv_rn(xa, scale_a));
-                    if (qb) qb[n] = cvt_out<T>(__fdiv_rn(xb, scale_b));
+                    qa[n] = cvt_out<T>(div_rn(xa, scale_a, inv_a));
+                    if (qb) qb[n] = cvt_out<T>(div_rn(xb, scale_b, inv_b));
                 }
             }
         }
@@ -618,7 +731,7 @@ __device__ __forceinline__ void offset_inputs(RowPairJob &job, const float *sino
 }
 
 template <int L, typename T>
-__global__ void __launch_bounds__(kFilterThreads) filter_kernel(FilterArgs a)
+__global__ void __launch_bounds__(kFilterThreads, L <= 2048 ? 2 : 1) filter_kernel(FilterArgs a)
 {
     constexpr int C = group_threads(L);
     constexpr int GP = kFilterThreads / C;        // row pairs per block

@@ -236,11 +236,19 @@ __global__ void diff_spectrum_kernel(float2 *G, const double *Hr, int D, int L, 
 {
     const int o = blockIdx.x * blockDim.x + threadIdx.x;
     if (o >= L) return;
-    // stored in the transform's step-2 order: o = (k1 VPL + kr) 32 + l
+    // stored in the order step 2 of the transform reads it:
+    // o = ((w NRD + rd) RB + m) 32 + j for warp w, round rd, value m of lane
+    // j; RB = min(R, 16) values per lane, NRD = R / RB rounds.  Lane j works
+    // on transform c = rd RB + j mod RB (row k1 = w (R / VPL) + c / VPL,
+    // kr = c mod VPL) and holds kl = m + RB brev(s), s = j / RB
     const int R = fft_R(L), VPL = fft_VPL(L);
-    const int l = o & 31, kr = (o >> 5) % VPL, k1 = o / (32 * VPL);
-    const int kl = (int)(__brev((unsigned)l) >> 27);
-    const int k = k1 + R * (kr + VPL * kl);
+    const int RB = R < 16 ? R : 16, NRD = R / RB;
+    const int j = o & 31, m = (o >> 5) % RB, rd = (o / (32 * RB)) % NRD, w = o / (32 * R);
+    const int c = rd * RB + j % RB, s = j / RB;
+    const int k1 = w * (R / VPL) + c / VPL, kr = c % VPL;
+    const int sbits = __ffs(32 / RB) - 1;                     // log2 (32 / RB) >= 1
+    const int q = (int)(__brev((unsigned)s) >> (32 - sbits));
+    const int k = k1 + R * (kr + VPL * (m + RB * q));
     const double dc = Hr[0];
     double gr, gi;
     if (k == 0) {

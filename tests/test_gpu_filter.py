@@ -72,6 +72,11 @@ def test_filter_16bit_per_row_scale(dtype, rel, D):
     assert np.all(err <= bound)
     # stored values lie in [-1, 1]
     assert float(q16.float().abs().max()) <= 1.0
+    # and each is the 16-bit rounding of the correctly rounded FP32 quotient
+    # of the FP32 row (same transform arithmetic before the store)
+    quot = (to_np(q32) / expect_scale[:, None].astype(np.float32)).astype(np.float32)
+    want = torch.from_numpy(quot).to(dtype)
+    assert torch.equal(q16.cpu().view(torch.int16), want.view(torch.int16))
     assert np.all(to_np(q16)[3] == 0.0) and to_np(rs)[3] == 1.0
 
 

@@ -126,20 +126,43 @@ def test_filter_shapes_and_indices(L):
     assert (512 // C) * 4 * NWG == 64
 
 
+def brev_bits(x, bits):
+    return int(format(x, f"0{bits}b")[::-1], 2) if bits else 0
+
+
+def step2_shape(L):
+    """Step 2's pass-B shape: RB = min(R, 16) values per lane, NRD = R / RB
+    rounds, SL = 32 / RB lanes per 32-point transform."""
+    R, VPL = FFT_SHAPES[L]
+    RB = min(R, 16)
+    return R, VPL, RB, R // RB, 32 // RB
+
+
+def swz_key(R, c):
+    # restates filter_impl.cuh:swz_key
+    return c if R >= 16 else c * (16 // R)
+
+
+def g_entry_k(L, o):
+    """runtime.cu:diff_spectrum_kernel's order: spectrum index k of entry o."""
+    R, VPL, RB, NRD, SL = step2_shape(L)
+    j, m, rd, w = o & 31, (o >> 5) % RB, (o // (32 * RB)) % NRD, o // (32 * R)
+    c, s = rd * RB + j % RB, j // RB
+    k1, kr = w * (R // VPL) + c // VPL, c % VPL
+    q = brev_bits(s, SL.bit_length() - 1)
+    return k1 + R * (kr + VPL * (m + RB * q))
+
+
 @pytest.mark.parametrize("L", sorted(FFT_SHAPES))
 def test_filter_table_layouts(L):
-    """runtime.cu writes G entry o at k = k1 + R (kr + VPL brev5(l)) with
-    l = o % 32, kr = (o / 32) % VPL, k1 = o / (32 VPL); filter.cu reads entry
-    (k1 VPL + kr) 32 + lane.  The twiddle plan has L + C + 32 entries:
-    W_L^{t k1} at k1 C + t, W_C^{l kr} at L + 32 kr + l, W_32^m at L + C + m."""
+    """runtime.cu writes G entry o = ((w NRD + rd) RB + m) 32 + j at
+    k = k1 + R (kr + VPL (m + RB brev(s))); every spectrum index once.  The
+    twiddle plan has L + C + 32 entries: W_L^{t k1} at k1 C + t, W_C^{l kr}
+    at L + 32 kr + l, W_32^m at L + C + m."""
     R, VPL = FFT_SHAPES[L]
     C = 32 * VPL
-    o = np.arange(L)
-    l, kr, k1 = o & 31, (o >> 5) % VPL, o // (32 * VPL)
-    assert np.array_equal((k1 * VPL + kr) * 32 + l, o)
-    brev = np.array([int(format(x, "05b")[::-1], 2) for x in range(32)])
-    k = k1 + R * (kr + VPL * brev[l])
-    assert sorted(k.tolist()) == list(range(L))
+    k = [g_entry_k(L, o) for o in range(L)]
+    assert sorted(k) == list(range(L))
     # twiddle plan: the kernel's reads stay in their sections
     t, kk = np.meshgrid(np.arange(C), np.arange(R))
     assert (kk * C + t).max() < L
@@ -148,6 +171,34 @@ def test_filter_table_layouts(L):
     for h in (1, 2, 4, 8, 16):
         idx = (np.arange(32) & (h - 1)) * (16 // h)
         assert idx.max() < 32 and np.array_equal(idx * 2 * h // 32, np.arange(32) & (h - 1))
+
+
+@pytest.mark.parametrize("L", sorted(FFT_SHAPES))
+def test_filter_step2_exchange_is_conflict_free(L):
+    """The swizzled exchange inside step 2: each 32-entry run (row, kr) is
+    a permutation (pass A writes), pass B's reads cover every entry of the
+    warp's rows once, and each half-warp's 8-byte accesses fall in 16
+    different bank pairs, for pass A and for every read of pass B."""
+    R, VPL, RB, NRD, SL = step2_shape(L)
+    C, RPW = 32 * VPL, R // VPL
+    lane = np.arange(32)
+    seen = np.zeros(RPW * C, int)
+    for rr in range(RPW):
+        for kr in range(VPL):
+            e = rr * C + 32 * kr + (lane ^ swz_key(R, rr * VPL + kr))
+            assert sorted((e - rr * C - 32 * kr).tolist()) == list(range(32))
+            for half in (lane[:16], lane[16:]):
+                assert len(set((e[half] % 16).tolist())) == 16
+    for rd in range(NRD):
+        c = rd * RB + (lane & (RB - 1))
+        s = lane // RB
+        key = np.array([swz_key(R, int(x)) for x in c])
+        for i in range(RB):
+            e = (c // VPL) * C + 32 * (c % VPL) + ((s + SL * i) ^ key)
+            seen[e] += 1
+            for half in (slice(0, 16), slice(16, 32)):
+                assert len(set((e[half] % 16).tolist())) == 16
+    assert (seen == 1).all()
 
 
 def dft_reg_replay(v, inv):
@@ -180,29 +231,81 @@ def test_filter_register_dft_replay(M):
     np.testing.assert_allclose(dft_reg_replay(x, True), np.fft.ifft(x) * M, atol=1e-12)
 
 
+def lane_dif_replay(x, s, R, w):
+    """filter_impl.cuh:lane_dif_s on all 32 lanes at once: x[lane] holds one
+    value; radix-2 DIF over s = lane / R (natural in, bit-reversed out)."""
+    SL = 32 // R
+    h = SL // 2
+    while h >= 1:
+        o = x[np.arange(32) ^ (R * h)]
+        hi = (s & h) != 0
+        y = np.where(hi, -x, x) + o
+        tw = np.where(hi, w((s & (h - 1)) * (16 // h)), 1.0) if h > 1 else 1.0
+        x = y * tw
+        h //= 2
+    return x
+
+
+def lane_dit_inv_replay(x, s, R, w):
+    SL = 32 // R
+    h = 1
+    while h < SL:
+        hi = (s & h) != 0
+        tw = np.where(hi, np.conj(w((s & (h - 1)) * (16 // h))), 1.0) if h > 1 else 1.0
+        y = x * tw
+        o = y[np.arange(32) ^ (R * h)]
+        x = np.where(hi, -y, y) + o
+        h *= 2
+    return x
+
+
 @pytest.mark.parametrize("L", sorted(FFT_SHAPES))
 def test_filter_three_step_factorisation_replay(L):
-    """Step 1 (R-point DFT over n1, W_L^{t k1}), step 2 per row k1 (VPL-point
-    over r, W_C^{l kr}, 32-point over lanes, times G[k1 + R (kr + VPL kl)],
-    and the inverses), step 3 (W_L^{-t k1}, inverse R-point) equal the
+    """Step 1 (R-point DFT over n1, W_L^{t k1}); step 2 per warp as the
+    kernel runs it: pass A (VPL-point over r, W_C^{l kr}, swizzled writes),
+    pass B per round (swizzled reads l = s + SL i, RB-point over i,
+    W_32^{s m}, the lane transform over s, times G in the table's order, and
+    the inverses), pass C; step 3 (W_L^{-t k1}, inverse R-point): equals the
     circular convolution IFFT(FFT(z) G) * L."""
-    R, VPL = FFT_SHAPES[L]
-    C = 32 * VPL
+    R, VPL, RB, NRD, SL = step2_shape(L)
+    C, RPW = 32 * VPL, R // VPL
     rng = np.random.default_rng(L)
     z = rng.standard_normal(L) + 1j * rng.standard_normal(L)
-    G = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    Gk = rng.standard_normal(L) + 1j * rng.standard_normal(L)
+    Gt = np.array([Gk[g_entry_k(L, o)] for o in range(L)])      # the table as stored
     W = lambda m: np.exp(-2j * np.pi * m / L)
+    w32 = lambda m: np.exp(-2j * np.pi * (np.asarray(m) & 31) / 32)
     tk = np.outer(np.arange(R), np.arange(C))
-    S = np.fft.fft(z.reshape(R, C), axis=0) * W(tk)
-    lk = np.outer(np.arange(VPL), np.arange(32)) * R
-    k2 = np.arange(VPL)[:, None] + VPL * np.arange(32)[None, :]
-    for k1 in range(R):
-        A = np.fft.fft(S[k1].reshape(VPL, 32), axis=0) * W(lk)
-        X = np.fft.fft(A, axis=1) * G[k1 + R * k2]
-        A = np.fft.ifft(X, axis=1) * 32 * np.conj(W(lk))
-        S[k1] = (np.fft.ifft(A, axis=0) * VPL).reshape(-1)
-    out = (np.fft.ifft(S * np.conj(W(tk)), axis=0) * R).reshape(-1)
-    ref = np.fft.ifft(np.fft.fft(z) * G) * L
+    S = (np.fft.fft(z.reshape(R, C), axis=0) * W(tk)).reshape(-1)
+    lane = np.arange(32)
+    for gw in range(VPL):                        # NWG = VPL warps per group
+        for rr in range(RPW):                    # pass A
+            k1 = gw * RPW + rr
+            u = np.fft.fft(S[k1 * C + lane[None, :] + 32 * np.arange(VPL)[:, None]], axis=0)
+            u = u * np.exp(-2j * np.pi * np.outer(np.arange(VPL), lane) / C)
+            for kr in range(VPL):
+                S[k1 * C + 32 * kr + (lane ^ swz_key(R, rr * VPL + kr))] = u[kr]
+        for rd in range(NRD):                    # pass B
+            c = rd * RB + (lane & (RB - 1))
+            s = lane // RB
+            base = (gw * RPW + c // VPL) * C + 32 * (c % VPL)
+            key = np.array([swz_key(R, int(x)) for x in c])
+            idx = base[None, :] + ((s[None, :] + SL * np.arange(RB)[:, None]) ^ key[None, :])
+            x = np.fft.fft(S[idx], axis=0)                        # i -> m
+            x = x * w32(s[None, :] * np.arange(RB)[:, None])
+            x = np.array([lane_dif_replay(x[m], s, RB, w32) for m in range(RB)])
+            g = Gt[((gw * NRD + rd) * RB + np.arange(RB))[:, None] * 32 + lane[None, :]]
+            x = x * g
+            x = np.array([lane_dit_inv_replay(x[m], s, RB, w32) for m in range(RB)])
+            x = x * np.conj(w32(s[None, :] * np.arange(RB)[:, None]))
+            S[idx] = np.fft.ifft(x, axis=0) * RB                  # m -> i
+        for rr in range(RPW):                    # pass C
+            k1 = gw * RPW + rr
+            u = np.array([S[k1 * C + 32 * kr + (lane ^ swz_key(R, rr * VPL + kr))] for kr in range(VPL)])
+            u = u * np.exp(2j * np.pi * np.outer(np.arange(VPL), lane) / C)
+            S[k1 * C + lane[None, :] + 32 * np.arange(VPL)[:, None]] = np.fft.ifft(u, axis=0) * VPL
+    out = (np.fft.ifft(S.reshape(R, C) * np.conj(W(tk)), axis=0) * R).reshape(-1)
+    ref = np.fft.ifft(np.fft.fft(z) * Gk) * L
     np.testing.assert_allclose(out, ref, atol=1e-9 * np.abs(ref).max())
 
 
