@@ -548,6 +548,12 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         constexpr int RB = R < 16 ? R : 16;       // values per lane in pass B
         constexpr int NRD = R / RB;               // pass B rounds (transforms c of round rd: rd RB + j mod RB)
         constexpr int SL = 32 / RB;               // lanes per 32-point transform
+        float2 wc[VPL];                            // W_C^{l kr}, the same for every row of the warp
+        {
+            const float2 *twc = fresh(tw + L);
+#pragma unroll
+            for (int kr = 1; kr < VPL; ++kr) wc[kr] = __ldg(&twc[32 * kr + lane]);
+        }
 #pragma unroll 1
         for (int rr = 0; rr < RPW; ++rr) {
             float2 *row = S + (gw * RPW + rr) * C;
@@ -555,11 +561,8 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
 #pragma unroll
             for (int r = 0; r < VPL; ++r) u[r] = row[lane + 32 * r];
             dft_reg<VPL, false>(u);                                   // r -> kr
-            if (lane) {
-                const float2 *twc = fresh(tw + L);
 #pragma unroll
-                for (int kr = 1; kr < VPL; ++kr) u[kr] = cmul(u[kr], __ldg(&twc[32 * kr + lane]));  // W_C^{l kr}
-            }
+            for (int kr = 1; kr < VPL; ++kr) u[kr] = cmul(u[kr], wc[kr]);
             __syncwarp();                                             // the row is read before it is rewritten
 #pragma unroll
             for (int kr = 0; kr < VPL; ++kr) row[32 * kr + (lane ^ swz_key<R>(rr * VPL + kr))] = u[kr];
@@ -574,7 +577,10 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
 #pragma unroll
             for (int i = 0; i < RB; ++i) x[i] = run[(s + SL * i) ^ key];
             dft_reg<RB, false>(x);                                    // i -> m
-            if constexpr (SL > 1) {
+            if constexpr (SL == 2) {                                  // W_32^{s m}: s = 0 or 1, constants
+#pragma unroll
+                for (int m = 1; m < RB; ++m) if (s) x[m] = cmul(x[m], w32(m));
+            } else if constexpr (SL > 2) {
 #pragma unroll
                 for (int m = 1; m < RB; ++m) x[m] = cmul(x[m], __ldg(&w32t[(s * m) & 31]));   // W_32^{s m}
             }
@@ -586,7 +592,10 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
 #pragma unroll
             for (int m = 0; m < RB; ++m) x[m] = cmul(x[m], __ldg(&g[m * 32 + lane]));
             lane_dit_inv_s<RB, RB>(x, s, w32t);                       // q -> s
-            if constexpr (SL > 1) {
+            if constexpr (SL == 2) {
+#pragma unroll
+                for (int m = 1; m < RB; ++m) if (s) x[m] = cmulc(x[m], w32(m));
+            } else if constexpr (SL > 2) {
 #pragma unroll
                 for (int m = 1; m < RB; ++m) x[m] = cmulc(x[m], __ldg(&w32t[(s * m) & 31]));
             }
@@ -595,17 +604,19 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
             for (int i = 0; i < RB; ++i) run[(s + SL * i) ^ key] = x[i];
         }
         __syncwarp();
+        {
+            const float2 *twc = fresh(tw + L);
+#pragma unroll
+            for (int kr = 1; kr < VPL; ++kr) wc[kr] = __ldg(&twc[32 * kr + lane]);
+        }
 #pragma unroll 1
         for (int rr = 0; rr < RPW; ++rr) {
             float2 *row = S + (gw * RPW + rr) * C;
             float2 u[VPL];
 #pragma unroll
             for (int kr = 0; kr < VPL; ++kr) u[kr] = row[32 * kr + (lane ^ swz_key<R>(rr * VPL + kr))];
-            if (lane) {
-                const float2 *twc = fresh(tw + L);
 #pragma unroll
-                for (int kr = 1; kr < VPL; ++kr) u[kr] = cmulc(u[kr], __ldg(&twc[32 * kr + lane]));
-            }
+            for (int kr = 1; kr < VPL; ++kr) u[kr] = cmulc(u[kr], wc[kr]);
             dft_reg<VPL, true>(u);                                    // kr -> r
             __syncwarp();
 #pragma unroll
