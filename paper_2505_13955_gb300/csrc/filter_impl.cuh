@@ -242,16 +242,36 @@ __device__ __forceinline__ void dft_reg(float2 (&v)[M])
         for (int blk = 0; blk < M; blk += 2 * h) {
 #pragma unroll
             for (int m = 0; m < h; ++m) {
+                const float2 a = v[blk + m];
                 float2 b = v[blk + m + h];
-                if (m != 0 && m * (16 / h) == 8) {      // W_4^1 = -i (conjugate: +i): a swap
-                    b = INV ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
-                } else if (m != 0) {                    // W_{2h}^m = W_32^{m * 16 / h}
-                    float2 w = w32(m * (16 / h));
-                    if (INV) w.y = -w.y;
-                    b = cmul(b, w);
+                const int j = m * (16 / h);             // W_{2h}^m = W_32^j
+                if (m == 0 || j == 8) {
+                    if (j == 8)                         // W_32^8 = -i (conjugate: +i): a swap
+                        b = INV ? make_float2(-b.y, b.x) : make_float2(b.y, -b.x);
+                    v[blk + m + h] = csub(a, b);
+                    v[blk + m] = cadd(a, b);
+                } else {
+                    // a +- b w with w = wc + i ws in six FMAs: factor out the
+                    // larger of |wc|, |ws| (Linzer & Feig, IBM J. Res. Dev.
+                    // 37(5), 1993), b w = wc (b.x - r b.y, b.y + r b.x) with
+                    // r = ws / wc, or ws (r b.x - b.y, r b.y + b.x) with r = wc / ws
+                    const float2 w = w32(j);
+                    const float wc = w.x, ws = INV ? -w.y : w.y;
+                    float f, tx, ty;
+                    if (fabsf(wc) >= fabsf(ws)) {
+                        const float r = ws / wc;
+                        f = wc;
+                        tx = fmaf(-r, b.y, b.x);
+                        ty = fmaf(r, b.x, b.y);
+                    } else {
+                        const float r = wc / ws;
+                        f = ws;
+                        tx = fmaf(r, b.x, -b.y);
+                        ty = fmaf(r, b.y, b.x);
+                    }
+                    v[blk + m + h] = make_float2(fmaf(-f, tx, a.x), fmaf(-f, ty, a.y));
+                    v[blk + m] = make_float2(fmaf(f, tx, a.x), fmaf(f, ty, a.y));
                 }
-                v[blk + m + h] = csub(v[blk + m], b);
-                v[blk + m] = cadd(v[blk + m], b);
             }
         }
     }
@@ -354,9 +374,11 @@ __device__ __forceinline__ float offset_sample(const float *p, const float *p2, 
 // is transformed; completion is signalled on an mbarrier.
 struct StreamNext {
     bool issue;                  // a next pair exists
-    const float *src;            // its first row (16-byte aligned)
-    unsigned bytes;              // 4 D per row, a multiple of 16
-    uint32_t stage, mbar;        // shared addresses of the staging buffer and the mbarrier
+    const float *src;            // its first row (16-byte aligned); the second follows at src + D
+    unsigned row_bytes;          // 4 D, a multiple of 16
+    int nrows;                   // 1 or 2
+    uint32_t stage_a, stage_b;   // shared addresses of the two rows' slots (16-byte aligned)
+    uint32_t mbar;               // the mbarrier the copies complete on
 };
 
 __device__ __forceinline__ void bulk_rows(const StreamNext &nx)
@@ -364,11 +386,16 @@ __device__ __forceinline__ void bulk_rows(const StreamNext &nx)
     // the staging buffer was last read through the generic proxy: order those
     // reads before the asynchronous copy overwrites it
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(nx.mbar), "r"(nx.bytes)
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(nx.mbar),
+                 "r"(nx.row_bytes * (unsigned)nx.nrows)
                  : "memory");
     asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
-                 ::"r"(nx.stage), "l"(nx.src), "r"(nx.bytes), "r"(nx.mbar)
+                 ::"r"(nx.stage_a), "l"(nx.src), "r"(nx.row_bytes), "r"(nx.mbar)
                  : "memory");
+    if (nx.nrows == 2)
+        asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                     ::"r"(nx.stage_b), "l"(nx.src + nx.row_bytes / 4), "r"(nx.row_bytes), "r"(nx.mbar)
+                     : "memory");
 }
 
 // Wait for the mbarrier phase with the given parity; false after `cap` polls.
@@ -457,24 +484,29 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         }
         group_sync(bar_id, C);                    // staged rows read before S is written
     } else if (STAGED) {
-        // rows already in shared memory: each difference reads its two samples
+        // rows already in shared memory with zero borders (index -1 and
+        // [D, D + C) read as 0): each difference reads its two samples with
+        // no bounds test; nonzero samples are found from an OR of their bits
         const float *sa = job.a, *sb = job.b;
+        unsigned bits_a = 0u, bits_b = 0u;
 #pragma unroll
         for (int n1 = 0; n1 < R; ++n1) {
             const int n = C * n1 + t;
             float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
             if (C * n1 <= D) {                    // uniform over the group
-                a = n < D ? sa[n] : 0.f;
-                am = (n >= 1 && n - 1 < D) ? sa[n - 1] : 0.f;
+                a = sa[n];
+                am = sa[n - 1];
                 if (sb) {
-                    b = n < D ? sb[n] : 0.f;
-                    bm = (n >= 1 && n - 1 < D) ? sb[n - 1] : 0.f;
+                    b = sb[n];
+                    bm = sb[n - 1];
                 }
-                nz_a |= (a != 0.f);
-                nz_b |= (b != 0.f);
+                bits_a |= __float_as_uint(a);
+                bits_b |= __float_as_uint(b);
             }
             v[n1] = make_float2(a - am, b - bm);
         }
+        nz_a = (bits_a & 0x7fffffffu) != 0u;      // some sample with a nonzero magnitude (or NaN)
+        nz_b = (bits_b & 0x7fffffffu) != 0u;
     } else if (off.on) {
         // offset scans: weighted (and folded) virtual samples, then differences
 #pragma unroll
@@ -792,20 +824,30 @@ __global__ void __launch_bounds__(kFilterThreads) filter_stream_kernel(FilterArg
     extern __shared__ __align__(128) float2 smem_f2[];
     __shared__ float red[4 * (kFilterThreads / 32)];
     __shared__ __align__(8) unsigned long long mbar_store;
+    constexpr int C = kFilterThreads;
     float2 *S = smem_f2;
-    float *stage = reinterpret_cast<float *>(smem_f2 + L);         // 2 D floats (D <= L / 2)
+    // staging: 4 zero floats, row a, then C + 4 zero floats and row b, and
+    // C + 4 zero floats: each row reads 0 at index -1 and on [D, D + C)
+    float *stage = reinterpret_cast<float *>(smem_f2 + L);
+    const int RS = a.D + C + 4;                                     // row stride, a multiple of 4
+    float *row_a = stage + 4, *row_b = stage + 4 + RS;
     const int t = threadIdx.x;
+    for (int i = t; i < C + 4; i += kFilterThreads) {
+        if (i < 4) stage[i] = 0.f;
+        row_a[a.D + i] = 0.f;
+        row_b[a.D + i] = 0.f;
+    }
     const uint32_t mbar = (uint32_t)__cvta_generic_to_shared(&mbar_store);
-    const uint32_t stage_s = (uint32_t)__cvta_generic_to_shared(stage);
     const long long pairs = (a.rows + 1) / 2;
     auto next_of = [&](long long p) {
         StreamNext nx;
         nx.issue = p < pairs;
         const long long r0 = 2 * p;
-        const int nrows = (r0 + 1 < a.rows) ? 2 : 1;
+        nx.nrows = (r0 + 1 < a.rows) ? 2 : 1;
         nx.src = a.sino + (nx.issue ? r0 : 0) * a.D;
-        nx.bytes = (unsigned)(nrows * a.D * 4);
-        nx.stage = stage_s;
+        nx.row_bytes = (unsigned)(a.D * 4);
+        nx.stage_a = (uint32_t)__cvta_generic_to_shared(row_a);
+        nx.stage_b = (uint32_t)__cvta_generic_to_shared(row_b);
         nx.mbar = mbar;
         return nx;
     };
@@ -829,8 +871,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_stream_kernel(FilterArg
         parity ^= 1u;
         bool active;
         RowPairJob job = make_job(a.sino, a.filt, a.row_scale, a.rows, a.D, pair, sizeof(T), active);
-        job.a = stage;
-        job.b = job.b ? stage + a.D : nullptr;
+        job.a = row_a;
+        job.b = job.b ? row_b : nullptr;
         const StreamNext nx = next_of(pair + gridDim.x);
         pending = nx.issue;
         fft_pair<L, T, true>(job, true, a.D, a.G, a.tw, S, red, t, 1, a.pre, a.off, &nx);   // pre, off: off
@@ -841,7 +883,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_stream_kernel(FilterArg
 template <int L, typename T>
 fbp_status launch_stream_l(const FilterArgs &fa, unsigned *status, int skip_copies, cudaStream_t s)
 {
-    const size_t smem = (size_t)L * sizeof(float2) + (size_t)L * sizeof(float);
+    // transform buffer + staging for two rows of D <= L / 2 with zero borders
+    const size_t smem = (size_t)L * sizeof(float2) + (size_t)(L + 2 * kFilterThreads + 12) * sizeof(float);
     auto kern = filter_stream_kernel<L, T>;
     fbp_status st = ensure_dynamic_smem(reinterpret_cast<const void *>(kern), smem);
     if (st != FBP_OK) return st;

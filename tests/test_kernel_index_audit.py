@@ -203,7 +203,9 @@ def test_filter_step2_exchange_is_conflict_free(L):
 
 def dft_reg_replay(v, inv):
     """The kernel's in-register DFT: compile-time bit reversal, then radix-2
-    DIT with twiddle W_32^(m*16/h) at half-size h."""
+    DIT with twiddle W_32^j, j = m*16/h at half-size h: none for m = 0, a
+    swap for j = 8, else the six-FMA form a +- f (tx + i ty) with the
+    larger of |wc|, |ws| factored out."""
     M = len(v)
     bits = M.bit_length() - 1
     v = v.copy()
@@ -213,12 +215,23 @@ def dft_reg_replay(v, inv):
     while h < M:
         for blk in range(0, M, 2 * h):
             for m in range(h):
-                w = np.exp(-2j * np.pi * (m * (16 // h)) / 32)
+                a, b = v[blk + m], v[blk + m + h]
+                j = m * (16 // h)
+                if m == 0 or j == 8:
+                    if j == 8:
+                        b = complex(-b.imag, b.real) if inv else complex(b.imag, -b.real)
+                    v[blk + m + h], v[blk + m] = a - b, a + b
+                    continue
+                wc, ws = math.cos(2 * math.pi * j / 32), -math.sin(2 * math.pi * j / 32)
                 if inv:
-                    w = np.conj(w)
-                b = v[blk + m + h] * (w if m else 1.0)
-                v[blk + m + h] = v[blk + m] - b
-                v[blk + m] = v[blk + m] + b
+                    ws = -ws
+                if abs(wc) >= abs(ws):
+                    r, f = ws / wc, wc
+                    t = complex(b.real - r * b.imag, b.imag + r * b.real)
+                else:
+                    r, f = wc / ws, ws
+                    t = complex(r * b.real - b.imag, r * b.imag + b.real)
+                v[blk + m + h], v[blk + m] = a - f * t, a + f * t
         h *= 2
     return v
 
