@@ -435,7 +435,10 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
     static_assert(R * C == L && RPW >= 1 && R % NWG == 0, "shape");
     const int lane = t & 31, gw = t >> 5;
 
-    // ---- step 1: differences of z[C n1 + t], R-point DFT over n1
+    // ---- step 1: differences of z[C n1 + t], R-point DFT over n1.
+    // L is even and >= 2D - 1, so D <= L / 2 = C R / 2: the differences are
+    // zero for n1 > R / 2 and step 3 stores only n1 < R / 2; the tests on
+    // n1 let the compiler drop that half of the first and last butterflies.
     float2 v[R];
     bool nz_a = false, nz_b = false;     // any nonzero (or NaN) sample in the row
     if (pre.on) {
@@ -474,7 +477,7 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         for (int n1 = 0; n1 < R; ++n1) {
             const int n = C * n1 + t;
             float da = 0.f, db = 0.f;
-            if (active && C * n1 <= D) {          // uniform over the group
+            if (active && n1 <= R / 2 && C * n1 <= D) {   // uniform over the group
                 da = blur_diff(st, n, D, pre);
                 if (job.b) db = blur_diff(st + RS, n, D, pre);
                 nz_a |= (da != 0.f);
@@ -493,7 +496,7 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         for (int n1 = 0; n1 < R; ++n1) {
             const int n = C * n1 + t;
             float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
-            if (C * n1 <= D) {                    // uniform over the group
+            if (n1 <= R / 2 && C * n1 <= D) {     // uniform over the group
                 a = sa[n];
                 am = sa[n - 1];
                 if (sb) {
@@ -513,7 +516,7 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         for (int n1 = 0; n1 < R; ++n1) {
             const int n = C * n1 + t;
             float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
-            if (active && C * n1 <= D) {          // uniform over the group
+            if (active && n1 <= R / 2 && C * n1 <= D) {   // uniform over the group
                 a = offset_sample(job.a, job.a2, n, D, off);
                 b = offset_sample(job.b, job.b2, n, D, off);
                 am = __shfl_up_sync(0xffffffffu, a, 1);
@@ -532,7 +535,7 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         for (int n1 = 0; n1 < R; ++n1) {
             const int n = C * n1 + t;
             float a = 0.f, b = 0.f, am = 0.f, bm = 0.f;
-            if (active && C * n1 <= D) {          // uniform over the group
+            if (active && n1 <= R / 2 && C * n1 <= D) {   // uniform over the group
                 a = n < D ? __ldg(job.a + n) : 0.f;
                 b = (job.b && n < D) ? __ldg(job.b + n) : 0.f;
                 am = __shfl_up_sync(0xffffffffu, a, 1);
@@ -673,7 +676,7 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
         float ma = 0.f, mb = 0.f;
 #pragma unroll
         for (int n1 = 0; n1 < R; ++n1)
-            if (C * n1 + t < D) {
+            if (n1 < R / 2 && C * n1 + t < D) {
                 ma = fmaxf(ma, fabsf(v[n1].x));
                 mb = fmaxf(mb, fabsf(v[n1].y));
             }
@@ -707,7 +710,7 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
 #pragma unroll
         for (int n1 = 0; n1 < R; ++n1) {
             const int n = C * n1 + t;
-            if (n < D) {
+            if (n1 < R / 2 && n < D) {
                 const float xa = zero_a ? 0.f : v[n1].x, xb = zero_b ? 0.f : v[n1].y;
                 if constexpr (sizeof(T) == 4) {
                     qa[n] = xa;
