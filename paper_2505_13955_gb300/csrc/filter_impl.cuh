@@ -622,7 +622,6 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
             lane_dif_s<RB, RB>(x, s, w32t);                           // s -> q, kl = m + RB q
             // G is stored in this order: entry ((gw NRD + rd) RB + m) 32 + j is
             // k = k1 + R (kr + VPL (m + RB brev(s)))
-#pragma unroll
             const float2 *g = fresh(Gs + ((gw * NRD + rd) * RB) * 32);
 #pragma unroll
             for (int m = 0; m < RB; ++m) x[m] = cmul(x[m], __ldg(&g[m * 32 + lane]));
