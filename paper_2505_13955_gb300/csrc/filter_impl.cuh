@@ -576,9 +576,10 @@ __device__ __forceinline__ void fft_pair(const RowPairJob &job, bool active, int
 
     // ---- step 2: per row k1, C-point DFT over n2, times G, inverse.
     // Pass A: lane l, per row, the VPL-point DFT over r and W_C^{l kr}; the
-    // values go to the swizzled layout.  Pass B: lane j = c + R s the 32-point
-    // DFTs over l (R-point in registers, W_32^{s m}, SL-point over lanes),
-    // the product with G and the inverse.  Pass C undoes pass A.
+    // values go to the swizzled layout.  Pass B: lane j = c + RB s, per round,
+    // the 32-point DFTs over l of transforms c (RB-point in registers,
+    // W_32^{s m}, SL-point over lanes), the product with G and the inverse.
+    // Pass C undoes pass A.
     if (active) {
         constexpr int RB = R < 16 ? R : 16;       // values per lane in pass B
         constexpr int NRD = R / RB;               // pass B rounds (transforms c of round rd: rd RB + j mod RB)
