@@ -733,7 +733,8 @@ def sap_host(slices: torch.Tensor, p: SapParams, patches: torch.Tensor | None = 
     copied in, patched (sap_edges + sap_patches) and its patches and leaves
     copied out, on `n_streams` streams so that one slice's copies overlap
     another's kernels, and one slice's serial tail (the one-block selection,
-    the tree's small top levels) overlaps another's edge detection.  Returns host (patches [S, length, P, P],
+    the tree's small top levels) overlaps another's edge detection.  The
+    slices are copied in one at a time on a stream of their own.  Returns host (patches [S, length, P, P],
     leaves [S, length, 3]); blocks until they are filled."""
     if slices.is_cuda:
         raise ValueError("sap_host takes a host tensor; use sap_edges / sap_patches on device tensors")
@@ -750,25 +751,42 @@ def sap_host(slices: torch.Tensor, p: SapParams, patches: torch.Tensor | None = 
     n_streams = max(1, min(n_streams, S))
     caller = torch.cuda.current_stream(dev)
     streams = [torch.cuda.Stream(dev) for _ in range(n_streams)]
+    # the slices come in one after another on a copy stream, each at the full
+    # host-link bandwidth, so that slice 0's kernels start after one slice's
+    # copy instead of after all of them; a buffer is refilled once the
+    # kernels that read it are done
+    copier = torch.cuda.Stream(dev)
     need = sap_workspace_bytes(p)
     bufs = [(torch.empty((p.n, p.n), dtype=torch.int16, device=dev),
              torch.empty((p.n, p.n), dtype=torch.uint8, device=dev),
              torch.empty(need, dtype=torch.uint8, device=dev),
              torch.empty((p.length, p.patch, p.patch), dtype=torch.float32, device=dev),
              torch.empty((p.length, 3), dtype=torch.int32, device=dev)) for _ in range(n_streams)]
+    copier.wait_stream(caller)
     for st in streams:
         st.wait_stream(caller)
+    read_done = [None] * n_streams
     for i in range(S):
-        st = streams[i % n_streams]
-        d_in, d_e, d_ws, d_p, d_l = bufs[i % n_streams]
-        with torch.cuda.stream(st):
+        k = i % n_streams
+        st = streams[k]
+        d_in, d_e, d_ws, d_p, d_l = bufs[k]
+        if read_done[k] is not None:
+            copier.wait_event(read_done[k])
+        with torch.cuda.stream(copier):
             d_in.copy_(slices[i], non_blocking=True)
+            arrived = torch.cuda.Event()
+            arrived.record(copier)
+        st.wait_event(arrived)
+        with torch.cuda.stream(st):
             sap_edges(d_in, p, out=d_e, workspace=d_ws)
             sap_patches(d_in, d_e, p, patches=d_p, leaves=d_l, workspace=d_ws)
+            read_done[k] = torch.cuda.Event()
+            read_done[k].record(st)
             patches[i].copy_(d_p, non_blocking=True)
             leaves[i].copy_(d_l, non_blocking=True)
     for st in streams:
         st.synchronize()
+    copier.synchronize()
     return patches, leaves
 
 
