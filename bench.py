@@ -1410,7 +1410,7 @@ SUB_RECORDS = (
     ("f1_pipeline_n8192", "fbp_pipeline_n8192", dict(steps=3, slices=4, e2e_steps=1, cpu_block=256)),
     ("f2_offset_n8192", "fbp_offset_n8192", dict(steps=4, slices=4, cpu_block=256)),
     ("f3_mixed_batch", "fbp_mixed_batch", dict(steps=5)),
-    ("f4_sap_patching_n8192", "sap_patching_n8192", dict(steps=200, slices=4, e2e_steps=1, cpu_block=1024)),
+    ("f4_sap_patching_n8192", "sap_patching_n8192", dict(steps=50, slices=16, e2e_steps=2, cpu_block=1024)),
 )
 SUB_DROP = ("n_gpus", "higher_is_better", "scaling", "vs_baseline", "data")
 

@@ -171,7 +171,7 @@ def test_sub_records_cover_every_workload_and_survive_a_failure(monkeypatch):
     assert list(out) == keys
     assert out["config5_gd_refine_n1024"]["error"] == "RuntimeError: boom"
     assert "n_gpus" not in out["config1_fbp_single_n256"]
-    assert out["f4_sap_patching_n8192"]["config"]["slices_per_gpu"] == 4
+    assert out["f4_sap_patching_n8192"]["config"]["slices_per_gpu"] == 16
     assert out["config4_fbp_ragged_batch"]["cpu_baseline"]["value"] == 3.0
     assert "cpu_baseline" not in out["config2_fbp_stack_n2048"]
     a = seen["fbp_single_n256"]
