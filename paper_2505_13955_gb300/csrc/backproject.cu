@@ -160,10 +160,17 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_orbit_kernel(BpArgs a)
     bp_orbit<TILE, TXT, TYT, PX, PY, KT, T, CHECKED, PACKED, SPLIT>(j, bp_smem);
 }
 
-template <int V, typename T>
-fbp_status launch_orbit_shape(const BpLaunch &L, cudaStream_t s, unsigned *status)
+// FP32 rows of small slices on the default path: orbits of 16 x 16 tiles
+// (64 threads, 2 x 2 pixels each), split over clusters like the variants.
+// Four times the orbits of variant 7's 32 x 32 tiles, so more blocks share
+// each slice's angle pairs and more warps hide the staging latency.
+constexpr ShapeDesc kSmallSplitShape = {8, 8, 2, 2, 8, 1, 0, 12};
+
+// The orbit launch of one shape (V: the variant it serves, for messages).
+template <int V, int TXT, int TYT, int PX, int PY, int KT, int PK, int MINB, typename T>
+fbp_status launch_orbit_desc(const BpLaunch &L, cudaStream_t s, unsigned *status)
 {
-    constexpr ShapeDesc sd = kShapes[V];
+    constexpr ShapeDesc sd = {TXT, TYT, PX, PY, KT, 1, PK, MINB};
     constexpr int TILE = sd.txt * sd.px;
 #ifdef FBP_CHECKED
     constexpr bool kChecked = true;
@@ -268,6 +275,30 @@ fbp_status launch_orbit_shape(const BpLaunch &L, cudaStream_t s, unsigned *statu
 }
 
 template <int V, typename T>
+fbp_status launch_orbit_shape(const BpLaunch &L, cudaStream_t s, unsigned *status)
+{
+    constexpr ShapeDesc sd = kShapes[V];
+    return launch_orbit_desc<V, sd.txt, sd.tyt, sd.px, sd.py, sd.kt, sd.packed, sd.minb, T>(L, s, status);
+}
+
+// Whether the default FP32 path takes kSmallSplitShape: the geometry has
+// the orbit symmetry at that tile size and its 16 x 16 orbits are few enough
+// that each is still shared by at least 8 blocks.  Measured with one slice
+// (µs per call, eager): N = 192 16.0 against 18.5 for variant 7's split,
+// N = 256 19.6 against 21.4; at N = 512 (3 blocks per orbit) 101 against 81.
+// Depends on the geometry and the device only.
+bool small_split_applies(const BpLaunch &L)
+{
+    constexpr ShapeDesc sd = kSmallSplitShape;
+    constexpr int TILE = sd.txt * sd.px;
+    if (L.dtype != FBP_F32 || !L.split || !bp_orbit_eligible(L, TILE)) return false;
+    int sms = 0;
+    if (device_sm_count(&sms) != FBP_OK) return false;
+    const long long half = L.N / TILE / 2;
+    return orbit_split_parts(half * half, L.K / 2, sd.kt, (long long)sms * sd.minb) >= 8;
+}
+
+template <int V, typename T>
 fbp_status launch_shape(const BpLaunch &L, cudaStream_t s, unsigned *status)
 {
     if constexpr (kShapes[V].orbit) return launch_orbit_shape<V, T>(L, s, status);
@@ -324,7 +355,15 @@ fbp_status launch_variant(const BpLaunch &L, int v, cudaStream_t s, unsigned *st
         case 4: return launch_shape<4, T>(L, s, status);
         case 5: return launch_shape<5, T>(L, s, status);
         case 6: return launch_shape<6, T>(L, s, status);
-        case 7: return launch_shape<7, T>(L, s, status);
+        case 7:
+            if constexpr (sizeof(T) == 4) {
+                if (small_split_applies(L)) {
+                    constexpr ShapeDesc sd = kSmallSplitShape;
+                    return launch_orbit_desc<7, sd.txt, sd.tyt, sd.px, sd.py, sd.kt, sd.packed, sd.minb, T>(
+                        L, s, status);
+                }
+            }
+            return launch_shape<7, T>(L, s, status);
         case 8: return launch_shape<8, T>(L, s, status);
         case 9: return launch_shape<9, T>(L, s, status);
         case 10: return launch_shape<10, T>(L, s, status);

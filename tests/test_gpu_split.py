@@ -2,9 +2,9 @@
 shared among the blocks of a thread-block cluster (one orbit per cluster,
 partial sums added in rank order through distributed shared memory).
 
-Checked against the FP64 oracle, against the unsplit kernel of the same
-shape (same arithmetic per pair, sums grouped differently: within a few
-float ulps of the image), for run-to-run determinism, for independence from
+Checked against the FP64 oracle, against the unsplit variant 7 (the same
+per-pair arithmetic on 32 x 32 or 16 x 16 tiles, sums grouped differently:
+within a few float ulps of the image), for run-to-run determinism, for independence from
 the number of slices in the call, with accumulate, and for uint16 codes
 (bit-identical to the quantisation of the FP32 default image)."""
 import numpy as np
@@ -33,7 +33,7 @@ def test_split_default_matches_oracle_and_unsplit_kernel(K, N):
     g = api.Geometry(K, N, N)
     gen = torch.Generator(device="cuda").manual_seed(K + N)
     q = torch.randn((2, K, N), device="cuda", generator=gen)
-    got = api.backproject(q, g)                               # default: v7, split
+    got = api.backproject(q, g)                               # default: split (16 x 16 orbits where N is small)
     unsplit = api.backproject(q, g, variant=7)
     torch.cuda.synchronize()
     assert_within_dr(to_np(got), to_np(unsplit), 1e-6, "split vs unsplit v7")

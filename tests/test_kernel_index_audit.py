@@ -333,7 +333,7 @@ def test_forward_candidate_count_bound(alpha):
     assert bound <= 24
 
 
-ORBIT_SHAPES = [(16, 8, 2, 4), (16, 16, 4, 4)]   # (TXT, TYT, PX, PY), square tiles
+ORBIT_SHAPES = [(16, 8, 2, 4), (16, 16, 4, 4), (8, 8, 2, 2)]   # (TXT, TYT, PX, PY), square tiles
 
 
 def orbit_max_index(N, K, D, alpha, shape, tiles=None):
