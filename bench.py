@@ -232,14 +232,21 @@ def peaks() -> dict:
         return {}
 
 
-def bp_source_hash() -> str:
+BP_SOURCES = ("bp_tile.cuh", "bp_orbit.cuh", "backproject.cu", "bp_staged.cuh", "bp_staged.cu")
+# the files that hold the staged kernel's device code (the pair arithmetic,
+# the pipeline, the kernel): its captured traffic stays valid across edits
+# of the other kernels' launch code
+STAGED_SOURCES = ("bp_orbit.cuh", "bp_staged.cuh", "bp_staged.cu")
+
+
+def bp_source_hash(files=BP_SOURCES) -> str:
     """Hash of the backprojection kernels' code: the sources with comments
     and blank lines removed, so that an edit of the comments keeps a
     captured traffic figure valid."""
     import hashlib
     import re
     h = hashlib.sha256()
-    for f in ("bp_tile.cuh", "bp_orbit.cuh", "backproject.cu", "bp_staged.cuh", "bp_staged.cu"):
+    for f in files:
         with open(os.path.join(ROOT, "paper_2505_13955_gb300", "csrc", f)) as fh:
             for line in fh:
                 code = re.sub(r"//.*", "", line).rstrip()
@@ -258,7 +265,7 @@ def captured_traffic(variant: int, dtype: str, n_slices: int, n: int, k: int):
     except (OSError, ValueError):
         return None
     for t in entries if isinstance(entries, list) else [entries]:
-        if t.get("source_hash") != bp_source_hash() or t.get("dtype") != dtype:
+        if t.get("source_hash") != bp_source_hash(tuple(t.get("sources", BP_SOURCES))) or t.get("dtype") != dtype:
             continue
         if variant != t.get("variant") or t.get("n") != n or t.get("k") != k:
             continue
