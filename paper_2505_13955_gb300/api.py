@@ -753,25 +753,28 @@ def sap_host(slices: torch.Tensor, p: SapParams, patches: torch.Tensor | None = 
     streams = [torch.cuda.Stream(dev) for _ in range(n_streams)]
     # the slices come in one after another on a copy stream, each at the full
     # host-link bandwidth, so that slice 0's kernels start after one slice's
-    # copy instead of after all of them; a buffer is refilled once the
-    # kernels that read it are done
+    # copy instead of after all of them; twice as many input buffers as
+    # streams let the copies run ahead of the kernels, and a buffer is
+    # refilled once the kernels that read it are done
     copier = torch.cuda.Stream(dev)
     need = sap_workspace_bytes(p)
-    bufs = [(torch.empty((p.n, p.n), dtype=torch.int16, device=dev),
-             torch.empty((p.n, p.n), dtype=torch.uint8, device=dev),
+    n_in = min(S, 2 * n_streams)
+    ins = [torch.empty((p.n, p.n), dtype=torch.int16, device=dev) for _ in range(n_in)]
+    bufs = [(torch.empty((p.n, p.n), dtype=torch.uint8, device=dev),
              torch.empty(need, dtype=torch.uint8, device=dev),
              torch.empty((p.length, p.patch, p.patch), dtype=torch.float32, device=dev),
              torch.empty((p.length, 3), dtype=torch.int32, device=dev)) for _ in range(n_streams)]
     copier.wait_stream(caller)
     for st in streams:
         st.wait_stream(caller)
-    read_done = [None] * n_streams
+    read_done = [None] * n_in
     for i in range(S):
-        k = i % n_streams
-        st = streams[k]
-        d_in, d_e, d_ws, d_p, d_l = bufs[k]
-        if read_done[k] is not None:
-            copier.wait_event(read_done[k])
+        st = streams[i % n_streams]
+        b = i % n_in
+        d_in = ins[b]
+        d_e, d_ws, d_p, d_l = bufs[i % n_streams]
+        if read_done[b] is not None:
+            copier.wait_event(read_done[b])
         with torch.cuda.stream(copier):
             d_in.copy_(slices[i], non_blocking=True)
             arrived = torch.cuda.Event()
@@ -780,8 +783,8 @@ def sap_host(slices: torch.Tensor, p: SapParams, patches: torch.Tensor | None = 
         with torch.cuda.stream(st):
             sap_edges(d_in, p, out=d_e, workspace=d_ws)
             sap_patches(d_in, d_e, p, patches=d_p, leaves=d_l, workspace=d_ws)
-            read_done[k] = torch.cuda.Event()
-            read_done[k].record(st)
+            read_done[b] = torch.cuda.Event()
+            read_done[b].record(st)
             patches[i].copy_(d_p, non_blocking=True)
             leaves[i].copy_(d_l, non_blocking=True)
     for st in streams:
