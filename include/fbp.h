@@ -162,7 +162,11 @@ fbp_status fbp_filter(const float *sino, void *filt, float *row_scale,
  *              or has it added when `accumulate` is nonzero.
  *   scale      angle_step for FBP; 1 for the transpose of radon_forward.
  * Every pixel of the n x n square is computed.  Accumulation is FP32; the
- * per-(tile, angle) base coordinate is formed in FP64.
+ * per-(tile, angle) base coordinate is formed in FP64.  The kernel and its
+ * tile are chosen from the geometry, dtype and device; a slice with too few
+ * tiles to fill the GPU has its angle pairs shared among the blocks of a
+ * thread-block cluster (partial sums added in a fixed order), so a slice's
+ * result is the same run to run and whatever n_slices is.
  */
 fbp_status fbp_backproject(const void *filt, const float *row_scale,
                            fbp_dtype dtype, float *slice, const fbp_geometry *g,
