@@ -701,9 +701,21 @@ def run_uniform(args) -> None:
         "bp_variant": variant,
         "launch": "CUDA-graph replay of the step (filter + backprojection), eager timings in 'eager'"
                   if use_graph else "eager launches"})
+    hbm = peaks().get("hbm_gbs") or 6800.0
+
+    def filter_hbm(filter_ms, dt):
+        # K1's algorithmic bytes: every FP32 input sample read once and every
+        # filtered sample written once (plus one row scale per 16-bit row)
+        out_b = 4 if dt == "f32" else 2
+        nbytes = S * K * N * (4 + out_b) + (0 if dt == "f32" else S * K * 4)
+        gbs = nbytes / (filter_ms / 1e3) / 1e9 if filter_ms else None
+        return {"gb_per_s": gbs, "hbm_frac": gbs / hbm if gbs else None,
+                "bytes_per_step": nbytes, "peak_gb_per_s": hbm}
+
     line.update({
         "slices_per_s": main["slices_per_s"],
         "bp_ms_per_step": main["bp_ms"], "filter_ms_per_step": main["filter_ms"],
+        "filter_hbm": filter_hbm(main["filter_ms"], args.dtype),
         # filter + backprojection time of each timed step (CUDA events)
         "step_ms_spread": main["step_spread"],
         "bp_gupdates_per_s": achieved,
@@ -730,6 +742,7 @@ def run_uniform(args) -> None:
             "traffic": captured_traffic(vdt, dt, S, N, K),
             "slices_per_s": r["slices_per_s"], "ms_per_step": r["ms_per_step"],
             "bp_ms_per_step": r["bp_ms"], "filter_ms_per_step": r["filter_ms"],
+            "filter_hbm": filter_hbm(r["filter_ms"], dt),
             "bp_variant": vdt}
         if "orbit_kernel" in r:
             line[f"staged_{dt}"]["orbit_kernel"] = r["orbit_kernel"]
