@@ -14,8 +14,11 @@ KINDS = {"ramlak": oracle.RAMLAK, "shepp_logan": oracle.SHEPP_LOGAN}
 @pytest.mark.parametrize("kind", ["ramlak", "shepp_logan"])
 @pytest.mark.parametrize("S,K,D", [
     (1, 1, 1), (1, 3, 2), (1, 5, 7), (2, 3, 64), (1, 7, 255), (3, 5, 256), (1, 9, 257),
-    (1, 4, 300), (2, 33, 1000), (1, 17, 2048), (1, 6, 2049), (1, 5, 4096), (1, 3, 8192)])
+    (1, 4, 300), (1, 5, 512), (2, 33, 1000), (1, 4, 1024), (1, 17, 2048), (1, 6, 2049), (1, 5, 4096),
+    (1, 3, 8192)])
 def test_filter_f32_matches_oracle(kind, S, K, D):
+    """Every transform length, with D = L / 2 at each of them (the one case
+    where the difference at n = D falls in the R / 2-th column of step 1)."""
     api = fbp_api()
     rng = np.random.default_rng(S * 1000 + K * 10 + D)
     p = rng.standard_normal((S, K, D)).astype(np.float32) * 50.0

@@ -18,8 +18,10 @@ pytestmark = [pytest.mark.gpu, needs_gpu]
 TOL = 1e-4
 TOL16 = 2e-3
 # (K, N): the config-1 slice and neighbours; all have the orbit symmetry and
-# few enough orbits per slice for the split (32 x 32 orbits: (N / 64)^2)
-SMALL = [(360, 256), (64, 128), (720, 512), (90, 192)]
+# few enough orbits per slice for the split.  (360, 256), (360, 192) and
+# (180, 128) take the 16 x 16 orbits (at least 8 blocks per orbit); the
+# others the 32 x 32 ones
+SMALL = [(360, 256), (64, 128), (720, 512), (90, 192), (360, 192), (180, 128)]
 
 
 def oracle_bp(q, g):
