@@ -145,7 +145,7 @@ def test_pipeline_entry_points_validate_on_the_host(L):
 def test_libraries_resolve_every_symbol_at_load(L):
     """Both shared libraries load with immediate binding: no function the
     translation units call on one another is left undefined (a lazy load
-    would only fail at the first call, on the GPU machine)."""
+    would only fail at the first call of the missing function, on a GPU)."""
     from paper_2505_13955_gb300 import build
     for name in ("libfbp.so", "libfbp_checked.so"):
         ctypes.CDLL(os.path.join(build.HERE, name), mode=os.RTLD_NOW)
