@@ -164,7 +164,7 @@ __global__ void __launch_bounds__(TXT *TYT, MINB) bp_orbit_kernel(BpArgs a)
 // (64 threads, 2 x 2 pixels each), split over clusters like the variants.
 // Four times the orbits of variant 7's 32 x 32 tiles, so more blocks share
 // each slice's angle pairs and more warps hide the staging latency.
-constexpr ShapeDesc kSmallSplitShape = {8, 8, 2, 2, 8, 1, 0, 12};
+constexpr ShapeDesc kSmallSplitShape = {8, 8, 2, 2, 16, 1, 0, 12};
 
 // The orbit launch of one shape (V: the variant it serves, for messages).
 template <int V, int TXT, int TYT, int PX, int PY, int KT, int PK, int MINB, typename T>
