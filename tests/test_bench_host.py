@@ -175,5 +175,5 @@ def test_sub_records_cover_every_workload_and_survive_a_failure(monkeypatch):
     assert out["config4_fbp_ragged_batch"]["cpu_baseline"]["value"] == 3.0
     assert "cpu_baseline" not in out["config2_fbp_stack_n2048"]
     a = seen["fbp_single_n256"]
-    assert (a.steps, a.warmup, a.variant, a.dtype, a.texture) == (20000, 3, -1, "f32", False)
+    assert (a.steps, a.warmup, a.variant, a.dtype, a.texture) == (40000, 3, -1, "f32", False)
     assert args.steps == 20 and args.variant == 3          # the headline's arguments are untouched
