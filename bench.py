@@ -1197,7 +1197,7 @@ def run_mixed(args) -> None:
     return line
 
 
-SAP_STREAMS = 4          # slices of the patching workload in flight
+SAP_STREAMS = 8          # slices of the patching workload in flight
 SAP_BYTES_PER_PIXEL = 8   # codes read by Canny (2) + edge map written (1) + codes and edges read by
                           # the tree sums (3) + codes read by the patch means (2)
 

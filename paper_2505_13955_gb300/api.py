@@ -727,7 +727,7 @@ def sap_depatch_pack(mask_patches: torch.Tensor, leaves: torch.Tensor, p: SapPar
 
 
 def sap_host(slices: torch.Tensor, p: SapParams, patches: torch.Tensor | None = None,
-             leaves: torch.Tensor | None = None, n_streams: int = 4, device=None):
+             leaves: torch.Tensor | None = None, n_streams: int = 8, device=None):
     """Adaptive patching of a stack of uint16 slices held in host memory
     (int16 tensor [S, n, n], pinned for asynchronous copies): each slice is
     copied in, patched (sap_edges + sap_patches) and its patches and leaves
